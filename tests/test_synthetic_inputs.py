@@ -1,0 +1,37 @@
+"""Checks of the shared synthetic-input generator (not the method)."""
+import numpy as np
+
+from synthetic.phantom import (WORKLOADS, make_workload, pals_dmu, pals_mu,
+                               smooth_heaviside, smooth_heaviside_deriv)
+
+
+def test_smooth_heaviside_is_compact_and_c1():
+    s = np.linspace(-0.5, 0.5, 2001)
+    H = smooth_heaviside(s)
+    assert np.all(H[s <= -0.15] == 0) and np.all(H[s >= 0.15] == 1)
+    fd = np.gradient(H, s)
+    assert np.max(np.abs(fd - smooth_heaviside_deriv(s))) < 1e-3
+
+
+def test_dmu_matches_finite_differences():
+    inp = make_workload("t3d_12")
+    p = inp["params"][1]
+    X = inp["X"]
+    dmu = pals_dmu(p, X, 0.01)
+    for k in range(p.size):
+        d = 1e-7 * max(1, abs(p[k]))
+        e = np.zeros_like(p); e[k] = d
+        fd = (pals_mu(p + e, X, 0.01) - pals_mu(p - e, X, 0.01)) / (2 * d)
+        assert np.max(np.abs(fd - dmu[k])) <= 1e-5 * max(1.0, np.abs(dmu[k]).max())
+
+
+def test_workload_shapes_and_seeding():
+    a = make_workload("t2d_37")
+    b = make_workload("t2d_37")
+    assert np.array_equal(a["mu"], b["mu"])
+    wl = a["wl"]
+    assert a["mu"].shape == (wl.K + 1, wl.n) and a["D"].shape == (wl.n,)
+    assert len(a["src_nodes"]) == wl.nsrc and len(a["det_nodes"]) == wl.ndet
+    assert np.all(a["D"] > 0) and np.all(a["mu"] >= 0.01 - 1e-15)
+    assert WORKLOADS["c2_3d64"].n == 64 ** 3 and WORKLOADS["c3_3d128"].n == 2097152
+    assert WORKLOADS["c5_3d192"].n == 7077888
