@@ -1,0 +1,196 @@
+/*
+ * rcg.h -- C ABI of librcg: inner-outer recycled Krylov solves for the
+ * symmetric diffusion operator of diffuse optical tomography and the
+ * one-sided reduced model built from them (O'Connell, Kilmer, de Sturler,
+ * Gugercin, "Computing Reduced Order Models via Inner-Outer Krylov Recycling
+ * in Diffuse Optical Tomography", arXiv 1602.00138).
+ *
+ * Problem (Sec. 2.1, eqs. ModelPDE1-4; Sec. 3): on the unit square (2D) or
+ * cube (3D) with N unknown nodes per axis, h = 1/(N+1), the zero-frequency
+ * diffusion operator with homogeneous Dirichlet lateral faces and Robin
+ * faces at z = 0 and z = 1 is discretised by centred differences, and the
+ * Robin boundary unknowns are eliminated (Sec. 3, Schur complement
+ * A~ = F - D2 G^-1 D1).  A~(p) = A~_* + diag(h^2 mu(p)) is SPD (eq. sum).
+ * Node index: i + Nx*(j + Ny*k), x fastest; (Nx,Ny,Nz) = (N,1,N) in 2D
+ * (axes x and z) and (N,N,N) in 3D.  Interior rows are scaled by h^2:
+ *   (A~ x)_p = sum_f w_f (x_p - x_q) + h^2 mu_p x_p,
+ *   w_f = (D_p + D_q)/2 between unknowns; w_f = D_p towards a lateral ghost
+ *   (x_q = 0); on a Robin face the eliminated boundary unknown leaves
+ *   D_p / (1 + alpha_p) on the diagonal, alpha_p = 2 A D_p / h.
+ * Effective sources / receivers (Sec. 3.1): a source of weight s at face
+ * point (i,j) of z = 0 is b~ = s D_p / (1 + alpha_p) e_p, a detector of
+ * weight c at face point (i,j) of z = 1 is c~ = c alpha_p / (1 + alpha_p) e_p,
+ * p the unknown next to the face point.  Right-hand sides are ordered
+ * [B~ (sources), C~ (detectors)] (Sec. 3.3 eq. solves).
+ *
+ * Method (Algorithm 2, Sec. 4.3): a seed U_0 (k_u smallest eigenvectors of
+ * A~_0) and X_0 = A~_0^-1 [B~, C~] give V = basis([U_0, X_0]) and per-RHS
+ * recycle spaces U_j = [U_0, X_0(:,j)].  For every sample point and RHS the
+ * Galerkin guess from range(V) is checked; if its relative residual exceeds
+ * tol_j the correction equation A~ g = r (eq. resi) is solved by CG deflated
+ * with U_j and the new direction is appended to V and to U_j.
+ *
+ * Conventions for every call:
+ *   - return value: RCG_OK (0) or a negative RCG_ERR_* code; the context
+ *     keeps the last error message (rcg_last_error).  No C++ exception
+ *     crosses this boundary.
+ *   - host pointers ("host") are read during the call and never retained;
+ *     the caller keeps ownership.  Device pointers ("device") must be
+ *     cudaMalloc'ed memory of the device current at rcg_create.
+ *   - matrices are column-major; an n-vector per column.
+ *   - all device work is issued on the stream given to rcg_create; a call
+ *     returns after that stream has finished the call's work unless stated.
+ *   - one context per host thread; contexts are independent.
+ */
+#ifndef RCG_H
+#define RCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define RCG_OK                 0
+#define RCG_ERR_INVALID       -1   /* bad argument or call order            */
+#define RCG_ERR_CUDA          -2   /* a CUDA runtime call failed            */
+#define RCG_ERR_OOM           -3   /* device allocation failed or over cap  */
+#define RCG_ERR_NOT_SPD       -4   /* a small FP64 Cholesky found d <= 0    */
+#define RCG_ERR_NOT_CONVERGED -5   /* some RHS hit maxit; stats still filled */
+#define RCG_ERR_BREAKDOWN     -6   /* p^T A p <= 0 or non-finite in CG      */
+#define RCG_ERR_TIMEOUT       -7   /* a bounded device wait ran out         */
+#define RCG_ERR_RANK_CAP      -8   /* basis V would exceed r_max            */
+
+/* ---- option values --------------------------------------------------- */
+#define RCG_FP64        0   /* every vector and product in float64             */
+#define RCG_MIXED       1   /* float32 vectors / stencil / basis products, float64
+                               refinement residuals, Galerkin matrices and
+                               rank decisions                                  */
+#define RCG_SEQUENTIAL  0   /* the paper's order: V grows between RHS          */
+#define RCG_WAVE        1   /* all RHS of `wave_samples` samples at once with V
+                               frozen; ordered append afterwards               */
+
+typedef struct rcg_ctx rcg_ctx;
+
+typedef struct {
+    int    dim;        /* 2 or 3                                             */
+    int    N;          /* unknown nodes per axis (>= 2)                      */
+    double robin_A;    /* reflection constant A of eq. ModelPDE2 (> 0)       */
+} rcg_grid;
+
+typedef struct {
+    int    precision;     /* RCG_FP64 | RCG_MIXED                           */
+    int    order;         /* RCG_SEQUENTIAL | RCG_WAVE                      */
+    int    wave_samples;  /* samples per wave in RCG_WAVE (0 = all given)   */
+    double tau_rank;      /* append iff ||new part|| / ||x|| > tau_rank     */
+    int    k_u;           /* seed eigenvectors (Sec. 4.2.2: 10)             */
+    int    k_cap;         /* max columns of a recycle space U_j             */
+    int    r_max;         /* max columns of V (device memory is sized by it)*/
+    int    max_samples;   /* sample slots (0..max_samples-1)                */
+    int    maxit;         /* CG iterations per RHS before NOT_CONVERGED     */
+    double inner_eta;     /* RCG_MIXED: float32 CG cycle stops at
+                             eta * ||r_restart|| before an FP64 refinement  */
+    int    check_refine;  /* extra Galerkin refinement steps of the check   */
+    int    keep_solutions;/* keep every delivered x (for rcg_solution_get)  */
+    int    seed_degree;   /* Chebyshev filter degree of the eigen seed      */
+    long long spin_budget;/* reserved: bound of device-side waits           */
+} rcg_options;
+
+typedef struct {
+    int    sample, rhs;   /* sample slot and RHS index                      */
+    int    iters;         /* CG iterations (0: V sufficed)                  */
+    int    restarts;      /* refinement restarts                            */
+    int    appended;      /* 1 if a column was appended to V                */
+    int    status;        /* RCG_OK / RCG_ERR_NOT_CONVERGED / _BREAKDOWN    */
+    double relres0;       /* relres of the Galerkin guess from V            */
+    double relres;        /* final relres, float64 residual recomputed      */
+    double ratio;         /* ||new part|| / ||x|| at the append decision    */
+} rcg_stat;
+
+/* Fill *o with defaults: FP64, sequential, tau_rank 1e-12, k_u 10,
+ * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-5,
+ * check_refine 0 (FP64) / 2 (mixed, set by rcg_create), keep_solutions 0,
+ * seed_degree 0 (automatic). */
+void rcg_options_default(rcg_options *o);
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Device memory for the grid,
+ * the basis (r_max columns) and the coefficient fields is allocated here;
+ * per-wave workspaces grow on demand.  Returns RCG_ERR_OOM if it fails. */
+int  rcg_create(rcg_ctx **out, const rcg_grid *g, const rcg_options *o, void *cuda_stream);
+void rcg_destroy(rcg_ctx *c);
+const char *rcg_last_error(const rcg_ctx *c);
+const char *rcg_strerror(int code);
+
+/* Diffusion coefficient D at the n unknowns (host, float64, > 0, finite).
+ * Fixed across samples (Sec. 2.1: D known). Must precede rcg_set_sample. */
+int rcg_set_diffusion(rcg_ctx *c, const double *D);
+
+/* Sources on the z = 0 face and detectors on the z = 1 face (Sec. 2.1):
+ * face points as (i, j) pairs, 1-based (j = 1 in 2D), and weights
+ * (NULL = 1).  Defines nrhs = nsrc + ndet effective right-hand sides. */
+int rcg_set_sources_detectors(rcg_ctx *c, int nsrc, const int *src_ij, const double *src_w,
+                              int ndet, const int *det_ij, const double *det_w);
+
+/* Per-RHS tolerance (host, nrhs values in (0, 1)); default 1e-8. */
+int rcg_set_tolerances(rcg_ctx *c, const double *tol);
+
+/* Absorption mu at the n unknowns for sample slot s (host / device float64,
+ * >= 0).  A~_s = A~_* + diag(h^2 mu_s) (eq. sum). */
+int rcg_set_sample(rcg_ctx *c, int s, const double *mu);
+int rcg_set_sample_device(rcg_ctx *c, int s, const double *mu_dev);
+
+/* Apply A~_s to ncols device vectors: y_j = A~_s x_j (n per column, leading
+ * dimension n).  prec RCG_FP64 takes double*, RCG_MIXED float* (the float32
+ * operator of the inner iterations).  Parity / benchmarking entry. */
+int rcg_apply(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols);
+
+/* Seed step of Algorithm 2 at sample s0: U_0 = U0 (host n x k_u, column-
+ * major) or, if U0 == NULL, the k_u smallest eigenvectors of A~_{s0} by a
+ * Chebyshev-filtered subspace iteration on the device; X_0 by deflated CG
+ * with U_0; V = basis([U_0, X_0]); U_j = [U_0, X_0(:,j)].  A~_{s0} becomes
+ * A~_* of the cached Galerkin matrix V^T A~_* V.  stats (host, nrhs) may be
+ * NULL.  Resets any previous basis. */
+int rcg_seed(rcg_ctx *c, int s0, const double *U0, rcg_stat *stats);
+
+/* Return to the state right after rcg_seed (V, U_j, caches) without
+ * recomputing it: O(1). */
+int rcg_reset_to_seed(rcg_ctx *c);
+
+/* Algorithm 2 outer loop over samples s_first .. s_first+s_count-1 (each
+ * set by rcg_set_sample), in the order of options.order.  stats (host,
+ * s_count*nrhs, [sample][rhs]) may be NULL.  Returns RCG_ERR_NOT_CONVERGED
+ * if any RHS hit maxit (stats still filled), RCG_ERR_RANK_CAP if V is full. */
+int rcg_solve_all(rcg_ctx *c, int s_first, int s_count, rcg_stat *stats);
+
+/* Current number of columns of V and a copy of V (host, n x r float64). */
+int rcg_basis_rank(const rcg_ctx *c, int *r);
+int rcg_basis_get(rcg_ctx *c, double *V);
+
+/* Delivered solutions of sample s (host, n x nrhs float64) from the last
+ * rcg_solve_all (or rcg_seed for s0); needs options.keep_solutions. */
+int rcg_solution_get(rcg_ctx *c, int s, double *X);
+
+/* Reduced model at absorption mu (host, n): Psi_r = C~_r^T A~_r^-1 B~_r with
+ * A~_r = V^T A~(mu) V, B~_r = V^T B~, C~_r = V^T C~ (eq. newreduced) into
+ * Psi (host, ndet x nsrc column-major: Psi[d + ndet*s]); if dmu != NULL
+ * (host, n x nparam) also J[d + ndet*(s + nsrc*k)] =
+ * -Z_r^T V^T diag(h^2 dmu_k) V X_r (eq. newjac). */
+int rcg_rom_eval(rcg_ctx *c, const double *mu, int nparam, const double *dmu,
+                 double *Psi, double *J);
+
+/* Device-resident variant of rcg_rom_eval: mu_dev (n), dmu_dev (n x nparam),
+ * Psi_dev, J_dev device float64. */
+int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const double *dmu_dev,
+                        double *Psi_dev, double *J_dev);
+
+/* Elapsed device milliseconds of the named phase in the last call that ran
+ * it ("check", "cg", "append", "seed_eig", "seed_x0", "rom"); -1 if none. */
+double rcg_phase_ms(const rcg_ctx *c, const char *phase);
+
+/* Number of kernel launches issued by this context since creation. */
+long long rcg_launch_count(const rcg_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCG_H */

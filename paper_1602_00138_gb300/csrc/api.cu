@@ -1,0 +1,1259 @@
+// librcg host runtime: the C ABI of include/rcg.h, device memory of a
+// context, and the driver of Algorithm 2 (Sec. 4.3) over the kernels.
+//
+// A "wave" is a set of (sample, RHS) lanes handled together with the basis V
+// frozen: the Galerkin check from range(V), batched deflated CG on the lanes
+// whose check failed (with FP64 refinement restarts), and one ordered
+// rank-revealing append of their solutions.  RCG_SEQUENTIAL runs one lane
+// per wave in the paper's order (V grows between right-hand sides);
+// RCG_WAVE puts all RHS of `wave_samples` samples into one wave.
+#include "common.cuh"
+#include "../../include/rcg.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace rcg;
+
+namespace {
+
+template <typename TS>
+__global__ void k_add_lanes(long long n, double *__restrict__ x, long long ldx, const TS *__restrict__ d,
+                            long long ldd, const int *__restrict__ lanes) {
+    const int l = lanes[blockIdx.y];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        x[(long long)l * ldx + p] += (double)d[(long long)l * ldd + p];
+}
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace
+
+struct EngineBase {
+    virtual ~EngineBase() {}
+    virtual void seed(int s0, const double *U0, rcg_stat *stats) = 0;
+    virtual void reset() = 0;
+    virtual int solve_all(int s_first, int s_count, rcg_stat *stats) = 0;
+    virtual int rank() const = 0;
+    virtual void basis_get(double *V) = 0;
+    virtual void rom_eval(const double *mu, int nparam, const double *dmu, double *Psi, double *J) = 0;
+};
+
+struct rcg_ctx {
+    rcg_grid grid{};
+    rcg_options opt{};
+    cudaStream_t st = nullptr;
+    Grid g{};
+    long long n = 0, ld = 0;
+    double h = 0;
+    std::string err;
+    long long launches = 0;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    // host mirrors
+    bool have_D = false, have_rhs = false;
+    int nsrc = 0, ndet = 0, nrhs = 0;
+    std::vector<int> rhs_node;
+    std::vector<double> rhs_w, tol;
+    std::vector<char> sample_set;
+    // device coefficient fields
+    double *D64 = nullptr, *dstar = nullptr, *mu64 = nullptr, *diag64 = nullptr;
+    float *D32 = nullptr, *diag32 = nullptr;
+    int *d_rhs_node = nullptr;
+    double *d_rhs_w = nullptr;
+    std::unique_ptr<EngineBase> eng;
+    std::map<std::string, double> phase;
+    std::vector<std::vector<double>> solutions;   // per sample, host copies (keep_solutions)
+
+    template <typename T> T *alloc(size_t count) {
+        void *p = nullptr;
+        const size_t b = std::max<size_t>(count, 1) * sizeof(T);
+        if (cudaMalloc(&p, b) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{RCG_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed"};
+        }
+        allocs.push_back(p);
+        bytes += b;
+        return (T *)p;
+    }
+    void release(void *p) {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) { allocs.erase(it); cudaFree(p); }
+    }
+    void sync() { RCG_CUDA_TRY(cudaStreamSynchronize(st)); }
+    template <typename T> void h2d(T *d, const T *h, size_t count) {
+        RCG_CUDA_TRY(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
+    template <typename T> void d2h(T *h, const T *d, size_t count) {
+        RCG_CUDA_TRY(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+    }
+    double *diag64_of(int s) { return diag64 + (long long)s * ld; }
+    float *diag32_of(int s) { return diag32 + (long long)s * ld; }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ engine
+template <typename T>
+struct Engine : EngineBase {
+    rcg_ctx *c;
+    cudaStream_t st;
+    Grid g;
+    long long n, ld;
+    int rmax;
+    const T *D;
+    bool mixed;
+
+    // basis and caches
+    T *V = nullptr;
+    int r = 0, r_seed = 0, s_star = -1, k_u = 0;
+    double *Cstar = nullptr;           // V^T A~_* V, ld rmax
+    T *X0 = nullptr;                   // seed solutions (nrhs columns)
+    double *sX0 = nullptr;             // V^T X0, ld rmax
+    bool seeded = false;
+    std::vector<std::vector<int>> priv, priv_seed;   // per RHS: V indices, -1 = X0 column
+    // sequential Galerkin state (current sample)
+    int gs_sample = -1, gs_r = 0;
+    double *Gs = nullptr, *Ls = nullptr;
+    // per-sample wave Galerkin matrices and Delta weights
+    std::vector<double *> Gw, Lw, dw;
+    std::vector<int> dw_star;
+    // lanes workspace
+    int mcap = 0;
+    double *x64 = nullptr;
+    T *xc = nullptr, *rv = nullptr, *pv = nullptr, *qv = nullptr;
+    LaneState ls{};
+    int *d_mask = nullptr, *d_lnode = nullptr, *d_list = nullptr;
+    double *d_lw = nullptr, *d_rr = nullptr;
+    double **p_x64 = nullptr, **p_diag64 = nullptr;
+    T **p_xc = nullptr, **p_r = nullptr, **p_p = nullptr, **p_q = nullptr, **p_diag = nullptr;
+    int *d_spec = nullptr;
+    double **d_sx = nullptr, **d_gsl = nullptr;
+    double *Yb = nullptr;
+    // deflation A W buffers
+    T *au0 = nullptr;
+    int au0_cap = 0;
+    T *awp = nullptr;
+    long long awp_cap = 0;
+    // pointer scratch for generic applies
+    const void **d_ptrA = nullptr, **d_ptrB = nullptr, **d_ptrC = nullptr;
+    int ptr_cap = 0;
+    // append workspace
+    int acap = 0;
+    T *Wb = nullptr, *Qb = nullptr, *AQb = nullptr;
+    double *Cb = nullptr, *M = nullptr, *S = nullptr, *R = nullptr, *RK = nullptr, *Ri = nullptr, *Rhat = nullptr;
+    double *xn2 = nullptr, *ratio_d = nullptr;
+    int *kept_d = nullptr, *d_K = nullptr, *d_cand = nullptr;
+    int *d_info = nullptr;
+    // rom workspace
+    double *Ar = nullptr, *Br = nullptr, *Crm = nullptr, *Xr = nullptr, *Zr = nullptr, *wtmp = nullptr;
+    double *VX = nullptr, *VZ = nullptr;
+
+    explicit Engine(rcg_ctx *ctx) : c(ctx), st(ctx->st), g(ctx->g), n(ctx->n), ld(ctx->ld), rmax(ctx->opt.r_max) {
+        mixed = sizeof(T) == 4;
+        D = mixed ? (const T *)ctx->D32 : (const T *)ctx->D64;
+        V = c->alloc<T>((size_t)rmax * ld);
+        Cstar = c->alloc<double>((size_t)rmax * rmax);
+        Gs = c->alloc<double>((size_t)rmax * rmax);
+        Ls = c->alloc<double>((size_t)rmax * rmax);
+        d_info = c->alloc<int>(4);
+        Gw.assign(c->opt.max_samples, nullptr);
+        Lw.assign(c->opt.max_samples, nullptr);
+        dw.assign(c->opt.max_samples, nullptr);
+        dw_star.assign(c->opt.max_samples, -1);
+    }
+
+    const T *diagT(int s) const { return mixed ? (const T *)c->diag32_of(s) : (const T *)c->diag64_of(s); }
+
+    // --------------------------------------------------------- workspaces
+    void ensure_lanes(int m) {
+        if (m <= mcap) return;
+        for (void *p : std::vector<void *>{x64, xc, rv, pv, qv, ls.rr, ls.pq, ls.wv, ls.gw, ls.kdef, ls.active, ls.flag,
+                                           ls.iters, ls.thresh, ls.W, ls.AW, d_mask, d_lnode, d_list, d_lw, d_rr,
+                                           p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb})
+            c->release(p);
+        mcap = m;
+        x64 = c->alloc<double>((size_t)m * ld);
+        xc = c->alloc<T>((size_t)m * ld);
+        rv = c->alloc<T>((size_t)m * ld);
+        pv = c->alloc<T>((size_t)m * ld);
+        qv = c->alloc<T>((size_t)m * ld);
+        ls.m = m;
+        ls.rr = c->alloc<double>(3 * (size_t)m);
+        ls.pq = c->alloc<double>(2 * (size_t)m);
+        ls.wv = c->alloc<double>(2 * (size_t)m * KMAX);
+        ls.gw = c->alloc<double>((size_t)m * KMAX * KMAX);
+        ls.kdef = c->alloc<int>(m);
+        ls.active = c->alloc<int>(m);
+        ls.flag = c->alloc<int>(m);
+        ls.iters = c->alloc<int>(m);
+        ls.thresh = c->alloc<double>(m);
+        ls.W = (const void **)c->alloc<void *>((size_t)m * KMAX);
+        ls.AW = (const void **)c->alloc<void *>((size_t)m * KMAX);
+        d_mask = c->alloc<int>(m);
+        d_lnode = c->alloc<int>(m);
+        d_list = c->alloc<int>(m);
+        d_lw = c->alloc<double>(m);
+        d_rr = c->alloc<double>(m);
+        p_x64 = c->alloc<double *>(m);
+        p_diag64 = c->alloc<double *>(m);
+        p_xc = c->alloc<T *>(m);
+        p_r = c->alloc<T *>(m);
+        p_p = c->alloc<T *>(m);
+        p_q = c->alloc<T *>(m);
+        p_diag = c->alloc<T *>(m);
+        d_spec = c->alloc<int>((size_t)m * KMAX);
+        d_sx = c->alloc<double *>(m);
+        d_gsl = c->alloc<double *>(m);
+        Yb = c->alloc<double>((size_t)rmax * m);
+        std::vector<double *> hx(m);
+        std::vector<T *> hc(m), hr(m), hp(m), hq(m);
+        for (int l = 0; l < m; ++l) {
+            hx[l] = x64 + (long long)l * ld;
+            hc[l] = xc + (long long)l * ld;
+            hr[l] = rv + (long long)l * ld;
+            hp[l] = pv + (long long)l * ld;
+            hq[l] = qv + (long long)l * ld;
+        }
+        c->h2d(p_x64, hx.data(), m);
+        c->h2d(p_xc, hc.data(), m);
+        c->h2d(p_r, hr.data(), m);
+        c->h2d(p_p, hp.data(), m);
+        c->h2d(p_q, hq.data(), m);
+        c->sync();
+    }
+
+    void ensure_ptr(int k) {
+        if (k <= ptr_cap) return;
+        c->release(d_ptrA); c->release(d_ptrB); c->release(d_ptrC);
+        ptr_cap = std::max(k, 64);
+        d_ptrA = (const void **)c->alloc<void *>(ptr_cap);
+        d_ptrB = (const void **)c->alloc<void *>(ptr_cap);
+        d_ptrC = (const void **)c->alloc<void *>(ptr_cap);
+    }
+
+    void ensure_append(int a) {
+        if (a <= acap) return;
+        for (void *p : std::vector<void *>{Wb, Qb, AQb, Cb, M, S, R, RK, Ri, Rhat, xn2, ratio_d, kept_d, d_K, d_cand})
+            c->release(p);
+        acap = std::max(a, 16);
+        Wb = c->alloc<T>((size_t)acap * ld);
+        Qb = c->alloc<T>((size_t)acap * ld);
+        AQb = c->alloc<T>((size_t)acap * ld);
+        Cb = c->alloc<double>((size_t)(rmax + acap) * acap);
+        M = c->alloc<double>((size_t)acap * acap);
+        S = c->alloc<double>((size_t)acap * acap);
+        R = c->alloc<double>((size_t)acap * acap);
+        RK = c->alloc<double>((size_t)acap * acap);
+        Ri = c->alloc<double>((size_t)acap * acap);
+        Rhat = c->alloc<double>((size_t)acap * acap);
+        xn2 = c->alloc<double>(acap);
+        ratio_d = c->alloc<double>(acap);
+        kept_d = c->alloc<int>(acap);
+        d_K = c->alloc<int>(acap);
+        d_cand = c->alloc<int>(acap);
+    }
+
+    void check_info(const char *what) {
+        int info = 0;
+        c->d2h(&info, d_info, 1);
+        c->sync();
+        if (info != 0) throw Error{RCG_ERR_NOT_SPD, std::string(what) + ": float64 Cholesky found a non-positive pivot"};
+    }
+
+    // A~_s applied to `cnt` columns (pointer lists on the host).
+    void apply_cols(const std::vector<const T *> &src, const std::vector<T *> &dst, const std::vector<int> &samp) {
+        const int cnt = (int)src.size();
+        if (!cnt) return;
+        ensure_ptr(cnt);
+        std::vector<const void *> hs(cnt), hd(cnt), hg(cnt);
+        for (int i = 0; i < cnt; ++i) { hs[i] = src[i]; hd[i] = dst[i]; hg[i] = diagT(samp[i]); }
+        c->h2d(d_ptrA, hs.data(), cnt);
+        c->h2d(d_ptrB, hd.data(), cnt);
+        c->h2d(d_ptrC, hg.data(), cnt);
+        apply_op<T>(st, g, D, (const T *const *)d_ptrC, (const T *const *)d_ptrA, (T *const *)d_ptrB, cnt, nullptr,
+                    nullptr);
+        c->sync();   // the pointer scratch is reused by the next call
+    }
+
+    // ----------------------------------------------------- Galerkin matrices
+    double *delta_weights(int s) {
+        if (!dw[s]) dw[s] = c->alloc<double>(ld);
+        if (dw_star[s] != s_star) {
+            scaled_diff(st, n, c->mu64 + (long long)s * ld, c->mu64 + (long long)s_star * ld, c->h * c->h, dw[s]);
+            dw_star[s] = s_star;
+        }
+        return dw[s];
+    }
+
+    // G = C_* + V^T diag(h^2 (mu_s - mu_*)) V (r x r) and its Cholesky factor L.
+    void galerkin(int s, double *G, double *L) {
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * rmax, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
+                                       cudaMemcpyDeviceToDevice, st));
+        if (s != s_star) gemm_tn<T, T>(st, n, V, ld, r, V, ld, r, G, rmax, true, delta_weights(s));
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(L, sizeof(double) * rmax, G, sizeof(double) * rmax, sizeof(double) * r, r,
+                                       cudaMemcpyDeviceToDevice, st));
+        RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+        chol_inplace(st, L, rmax, r, d_info);
+    }
+
+    std::pair<double *, double *> galerkin_for(int s, bool seq) {
+        if (seq) {
+            if (gs_sample != s || gs_r != r) {
+                galerkin(s, Gs, Ls);
+                check_info("Galerkin matrix V^T A V");
+                gs_sample = s;
+                gs_r = r;
+            }
+            return {Gs, Ls};
+        }
+        if (!Gw[s]) { Gw[s] = c->alloc<double>((size_t)rmax * rmax); Lw[s] = c->alloc<double>((size_t)rmax * rmax); }
+        galerkin(s, Gw[s], Lw[s]);
+        check_info("Galerkin matrix V^T A V");
+        return {Gw[s], Lw[s]};
+    }
+
+    // ------------------------------------------------------------ append
+    // Ordered rank-revealing append of the solutions in lanes `cand` (order
+    // = priority).  Returns per-candidate kept flags and ratios.
+    void append(const std::vector<int> &cand, double tau, int border_sample, std::vector<int> &kept,
+                std::vector<double> &ratio) {
+        const int a = (int)cand.size();
+        kept.assign(a, 0);
+        ratio.assign(a, 0.0);
+        if (!a) return;
+        ensure_append(a);
+        c->h2d(d_cand, cand.data(), a);
+        convert_lanes<double, T>(st, n, (const double *const *)p_x64, d_cand, a, Wb, ld);
+        norm2_lanes(st, n, (const double *const *)p_x64, d_cand, a, xn2);
+        for (int pass = 0; pass < 2 && r > 0; ++pass) {   // W <- (I - V V^T)^2 X
+            gemm_tn<T, T>(st, n, V, ld, r, Wb, ld, a, Cb, r, false);
+            gemm_nn<T, T>(st, n, V, ld, r, Cb, r, a, Wb, ld, -1.0, 1.0);
+        }
+        gemm_tn<T, T>(st, n, Wb, ld, a, Wb, ld, a, M, a, false);
+        ordered_drop_chol(st, M, a, xn2, S, tau, R, kept_d, ratio_d);
+        c->d2h(kept.data(), kept_d, a);
+        c->d2h(ratio.data(), ratio_d, a);
+        c->sync();
+        std::vector<int> K;
+        for (int i = 0; i < a; ++i)
+            if (kept[i]) K.push_back(i);
+        const int ak = (int)K.size();
+        if (!ak) return;
+        if (r + ak > rmax) throw Error{RCG_ERR_RANK_CAP, "basis V would exceed r_max columns"};
+        c->h2d(d_K, K.data(), ak);
+        // Q = W_K R_K^-1
+        gather_sub(st, R, a, d_K, ak, RK);
+        tri_upper_inverse(st, RK, ak, ak, Ri);
+        scatter_rows(st, Ri, ak, d_K, a, Rhat);
+        gemm_nn<T, T>(st, n, Wb, ld, a, Rhat, a, ak, Qb, ld, 1.0, 0.0);
+        // second pass: Q <- (I - V V^T) Q, then Q R2^-1 with R2^T R2 = Q^T Q
+        if (r > 0) {
+            gemm_tn<T, T>(st, n, V, ld, r, Qb, ld, ak, Cb, r, false);
+            gemm_nn<T, T>(st, n, V, ld, r, Cb, r, ak, Qb, ld, -1.0, 1.0);
+        }
+        gemm_tn<T, T>(st, n, Qb, ld, ak, Qb, ld, ak, M, ak, false);
+        RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+        chol_inplace(st, M, ak, ak, d_info);
+        check_info("append second pass Q^T Q");
+        lower_to_upper(st, M, ak, ak, RK);
+        tri_upper_inverse(st, RK, ak, ak, Ri);
+        gemm_nn<T, T>(st, n, Qb, ld, ak, Ri, ak, ak, V + (long long)r * ld, ld, 1.0, 0.0);
+        // C_* bordered with [V Q]^T A~_* Q
+        std::vector<const T *> src(ak);
+        std::vector<T *> dst(ak);
+        for (int i = 0; i < ak; ++i) { src[i] = V + (long long)(r + i) * ld; dst[i] = AQb + (long long)i * ld; }
+        apply_cols(src, dst, std::vector<int>(ak, s_star));
+        gemm_tn<T, T>(st, n, V, ld, r + ak, AQb, ld, ak, Cb, r + ak, false);
+        border_write(st, Cstar, rmax, r, ak, Cb, r + ak);
+        if (border_sample >= 0 && gs_sample == border_sample && gs_r == r) {
+            if (border_sample != s_star) apply_cols(src, dst, std::vector<int>(ak, border_sample));
+            gemm_tn<T, T>(st, n, V, ld, r + ak, AQb, ld, ak, Cb, r + ak, false);
+            border_write(st, Gs, rmax, r, ak, Cb, r + ak);
+            copy_new_rows(st, Gs, Ls, rmax, r, ak);
+            RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+            chol_border(st, Ls, rmax, r, ak, d_info);
+            check_info("bordered Galerkin factor");
+            gs_r = r + ak;
+        }
+        r += ak;
+    }
+
+    // -------------------------------------------------------------- wave
+    struct Lane { int s, j; };
+
+    void wave(const std::vector<Lane> &lanes, bool seed_mode, bool seq, std::vector<rcg_stat> &out) {
+        const int m = (int)lanes.size();
+        ensure_lanes(m);
+        const double tau = seed_mode ? c->opt.tau_rank : c->opt.tau_rank;
+        std::vector<int> lnode(m), samp(m);
+        std::vector<double> lw(m), ltol(m);
+        std::vector<double *> hdiag64(m);
+        std::vector<T *> hdiag(m);
+        for (int l = 0; l < m; ++l) {
+            lnode[l] = c->rhs_node[lanes[l].j];
+            lw[l] = c->rhs_w[lanes[l].j];
+            ltol[l] = c->tol[lanes[l].j];
+            samp[l] = lanes[l].s;
+            hdiag64[l] = c->diag64_of(lanes[l].s);
+            hdiag[l] = (T *)diagT(lanes[l].s);
+        }
+        c->h2d(d_lnode, lnode.data(), m);
+        c->h2d(d_lw, lw.data(), m);
+        c->h2d(p_diag64, hdiag64.data(), m);
+        c->h2d(p_diag, hdiag.data(), m);
+        out.assign(m, rcg_stat{});
+        for (int l = 0; l < m; ++l) { out[l].sample = lanes[l].s; out[l].rhs = lanes[l].j; }
+
+        // ---- check: Galerkin guess from range(V) and its float64 residual
+        cudaEvent_t e0, e1, e2, e3;
+        RCG_CUDA_TRY(cudaEventCreate(&e0)); RCG_CUDA_TRY(cudaEventCreate(&e1));
+        RCG_CUDA_TRY(cudaEventCreate(&e2)); RCG_CUDA_TRY(cudaEventCreate(&e3));
+        RCG_CUDA_TRY(cudaEventRecord(e0, st));
+        std::vector<int> grp_begin;        // lanes sorted by sample: group starts
+        for (int l = 0; l < m; ++l)
+            if (l == 0 || samp[l] != samp[l - 1]) grp_begin.push_back(l);
+        grp_begin.push_back(m);
+        std::map<int, std::pair<double *, double *>> gal;
+        if (r > 0) {
+            for (size_t gi = 0; gi + 1 < grp_begin.size(); ++gi) {
+                const int s = samp[grp_begin[gi]];
+                if (!gal.count(s)) gal[s] = galerkin_for(s, seq);
+            }
+        }
+        const T *Vc = V;
+        auto project = [&](bool first) {
+            // Yb = V^T b (first) or V^T r; Y = G^-1 Yb; x64 (+)= V Y
+            if (first) gather_rows<T>(st, Vc, ld, r, d_lnode, d_lw, m, Yb, rmax);
+            else gemm_tn<T, T>(st, n, Vc, ld, r, rv, ld, m, Yb, rmax, false);
+            for (size_t gi = 0; gi + 1 < grp_begin.size(); ++gi) {
+                const int l0 = grp_begin[gi], l1 = grp_begin[gi + 1];
+                double *L = gal[samp[l0]].second;
+                trsv_lower_batched(st, L, rmax, r, Yb + (long long)l0 * rmax, rmax, l1 - l0, false);
+                trsv_lower_batched(st, L, rmax, r, Yb + (long long)l0 * rmax, rmax, l1 - l0, true);
+            }
+            gemm_nn<T, double>(st, n, Vc, ld, r, Yb, rmax, m, x64, ld, 1.0, first ? 0.0 : 1.0);
+        };
+        auto residual = [&](std::vector<double> &rr_h, const int *mask) {
+            RCG_CUDA_TRY(cudaMemsetAsync(d_rr, 0, sizeof(double) * m, st));
+            residual64(st, g, c->D64, (const double *const *)p_diag64, (const double *const *)p_x64,
+                       mixed ? nullptr : (double *const *)p_r, mixed ? (float *const *)p_r : nullptr, m, d_lnode, d_lw,
+                       d_rr, mask);
+            rr_h.resize(m);
+            c->d2h(rr_h.data(), d_rr, m);
+            c->sync();
+        };
+        if (r > 0) project(true);
+        else for (int l = 0; l < m; ++l) RCG_CUDA_TRY(cudaMemsetAsync(x64 + (long long)l * ld, 0, sizeof(double) * n, st));
+        std::vector<double> rr_h;
+        residual(rr_h, nullptr);
+        if (r > 0 && !seed_mode) {
+            for (int step = 0; step < c->opt.check_refine; ++step) {
+                project(false);
+                residual(rr_h, nullptr);
+            }
+        }
+        std::vector<double> relres0(m);
+        for (int l = 0; l < m; ++l) relres0[l] = std::sqrt(rr_h[l]) / std::fabs(lw[l]);
+        RCG_CUDA_TRY(cudaEventRecord(e1, st));
+
+        // ---- deflated CG on the lanes the check rejected
+        std::vector<int> act(m, 0), done(m, 0), restarts(m, 0), status(m, RCG_OK);
+        std::vector<double> relres(relres0);
+        int nact = 0;
+        for (int l = 0; l < m; ++l) {
+            out[l].relres0 = relres0[l];
+            if (relres0[l] > ltol[l] || seed_mode) {
+                if (relres0[l] > ltol[l]) { act[l] = 1; ++nact; }
+            }
+        }
+        std::vector<int> iters_h(m, 0);
+        if (nact) {
+            // deflation spaces: U_j = [V(:, 0:k_u), X_0(:, j), V(:, priv_j)] (seed: V(:, 0:k_u))
+            std::vector<int> spec((size_t)m * KMAX, 0), kdef(m, 0);
+            std::vector<const void *> Wp((size_t)m * KMAX, nullptr), AWp((size_t)m * KMAX, nullptr);
+            std::vector<double *> sxp(m, nullptr), gsl(m, nullptr);
+            std::vector<int> samples_in;
+            for (int l = 0; l < m; ++l)
+                if (act[l] && std::find(samples_in.begin(), samples_in.end(), samp[l]) == samples_in.end())
+                    samples_in.push_back(samp[l]);
+            const int ku = std::min(k_u, r);
+            if ((int)samples_in.size() * ku > au0_cap) {
+                c->release(au0);
+                au0_cap = (int)samples_in.size() * ku;
+                au0 = c->alloc<T>((size_t)std::max(au0_cap, 1) * ld);
+            }
+            std::vector<const T *> asrc;
+            std::vector<T *> adst;
+            std::vector<int> asamp;
+            for (size_t si = 0; si < samples_in.size(); ++si)
+                for (int q = 0; q < ku; ++q) {
+                    asrc.push_back(V + (long long)q * ld);
+                    adst.push_back(au0 + ((long long)si * ku + q) * ld);
+                    asamp.push_back(samples_in[si]);
+                }
+            long long npriv = 0;
+            int kmax_used = 0;
+            for (int l = 0; l < m; ++l) {
+                if (!act[l]) continue;
+                std::vector<int> sp;
+                for (int q = 0; q < ku; ++q) sp.push_back(q);
+                if (!seed_mode)
+                    for (int e : priv[lanes[l].j]) sp.push_back(e);
+                if ((int)sp.size() > KMAX) sp.erase(sp.begin() + ku, sp.begin() + ku + ((int)sp.size() - KMAX));
+                kdef[l] = (int)sp.size();
+                kmax_used = std::max(kmax_used, kdef[l]);
+                npriv += (int)sp.size() - ku;
+                for (int q = 0; q < (int)sp.size(); ++q) spec[(size_t)l * KMAX + q] = sp[q];
+            }
+            if (npriv > awp_cap) {
+                c->release(awp);
+                awp_cap = npriv;
+                awp = c->alloc<T>((size_t)npriv * ld);
+            }
+            long long pi = 0;
+            for (int l = 0; l < m; ++l) {
+                if (!act[l]) continue;
+                const int si = (int)(std::find(samples_in.begin(), samples_in.end(), samp[l]) - samples_in.begin());
+                for (int q = 0; q < kdef[l]; ++q) {
+                    const int e = spec[(size_t)l * KMAX + q];
+                    const T *w = e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld;
+                    Wp[(size_t)l * KMAX + q] = w;
+                    if (q < ku) {
+                        AWp[(size_t)l * KMAX + q] = au0 + ((long long)si * ku + q) * ld;
+                    } else {
+                        T *d = awp + pi * ld;
+                        ++pi;
+                        AWp[(size_t)l * KMAX + q] = d;
+                        asrc.push_back(w);
+                        adst.push_back(d);
+                        asamp.push_back(samp[l]);
+                    }
+                }
+                sxp[l] = sX0 ? sX0 + (long long)lanes[l].j * rmax : nullptr;
+                gsl[l] = gal.count(samp[l]) ? gal[samp[l]].first : nullptr;
+            }
+            apply_cols(asrc, adst, asamp);
+            c->h2d(d_spec, spec.data(), (size_t)m * KMAX);
+            c->h2d(ls.kdef, kdef.data(), m);
+            c->h2d(ls.W, Wp.data(), (size_t)m * KMAX);
+            c->h2d(ls.AW, AWp.data(), (size_t)m * KMAX);
+            c->h2d(d_sx, sxp.data(), m);
+            c->h2d(d_gsl, gsl.data(), m);
+            if (kmax_used > 0) {
+                lane_gw(st, (const double *const *)d_gsl, rmax, r, d_spec, (const double *const *)d_sx, ls.kdef, ls.gw, m);
+                RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+                lane_inverse(st, ls.gw, ls.kdef, m, d_info);
+                check_info("deflation matrix U_j^T A U_j");
+            }
+            // thresholds and the first (re)start
+            std::vector<double> thr(m, 0.0);
+            auto set_thresh = [&](int l, double rnorm) {
+                const double target = ltol[l] * std::fabs(lw[l]);
+                thr[l] = mixed ? std::max(0.5 * target, c->opt.inner_eta * rnorm) : target;
+            };
+            for (int l = 0; l < m; ++l)
+                if (act[l]) set_thresh(l, std::sqrt(rr_h[l]));
+            c->h2d(ls.thresh, thr.data(), m);
+            c->h2d(d_mask, act.data(), m);
+            RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * m, st));
+            RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * m, st));
+            int t = 0;
+            cg_restart<T>(st, g, p_xc, p_r, p_p, ls, t, d_mask, kmax_used);
+            const int chunk = m > 1 ? 8 : 12;
+            std::vector<int> flag_h(m), active_h(m);
+            while (true) {
+                for (int i = 0; i < chunk; ++i) {
+                    ++t;
+                    cg_iteration<T>(st, g, D, (const T *const *)p_diag, p_xc, p_r, p_p, p_q, ls, t, kmax_used);
+                }
+                c->d2h(flag_h.data(), ls.flag, m);
+                c->d2h(active_h.data(), ls.active, m);
+                c->d2h(iters_h.data(), ls.iters, m);
+                c->sync();
+                std::vector<int> F;
+                bool force = false;
+                for (int l = 0; l < m; ++l) {
+                    if (!act[l] || done[l]) continue;
+                    if (flag_h[l] != 0 || !active_h[l]) F.push_back(l);
+                    else if (iters_h[l] >= c->opt.maxit) { F.push_back(l); force = true; }
+                }
+                if (force) {   // stop lanes over maxit
+                    std::vector<int> zero_act(active_h);
+                    for (int l : F) zero_act[l] = 0;
+                    c->h2d(ls.active, zero_act.data(), m);
+                }
+                if (!F.empty()) {
+                    std::vector<int> fmask(m, 0);
+                    for (int l : F) fmask[l] = 1;
+                    c->h2d(d_list, F.data(), F.size());
+                    c->h2d(d_mask, fmask.data(), m);
+                    dim3 gr((unsigned)std::min<long long>((n + 255) / 256, 512), (unsigned)F.size());
+                    k_add_lanes<T><<<gr, 256, 0, st>>>(n, x64, ld, xc, ld, d_list);
+                    ++c->launches;
+                    RCG_CHECK_LAUNCH();
+                    residual(rr_h, d_mask);
+                    std::vector<int> Rl;
+                    for (int l : F) {
+                        relres[l] = std::sqrt(rr_h[l]) / std::fabs(lw[l]);
+                        if (relres[l] <= ltol[l]) { done[l] = 1; }
+                        else if (iters_h[l] >= c->opt.maxit) { done[l] = 1; status[l] = RCG_ERR_NOT_CONVERGED; }
+                        else if (restarts[l] > 200) { done[l] = 1; status[l] = RCG_ERR_BREAKDOWN; }
+                        else { Rl.push_back(l); ++restarts[l]; set_thresh(l, std::sqrt(rr_h[l])); }
+                    }
+                    if (!Rl.empty()) {
+                        std::vector<int> rmask(m, 0);
+                        for (int l : Rl) rmask[l] = 1;
+                        c->h2d(ls.thresh, thr.data(), m);
+                        c->h2d(d_mask, rmask.data(), m);
+                        cg_restart<T>(st, g, p_xc, p_r, p_p, ls, t, d_mask, kmax_used);
+                    }
+                }
+                bool any = false;
+                for (int l = 0; l < m; ++l)
+                    if (act[l] && !done[l]) any = true;
+                if (!any) break;
+            }
+            c->d2h(iters_h.data(), ls.iters, m);
+            c->sync();
+        }
+        RCG_CUDA_TRY(cudaEventRecord(e2, st));
+
+        // ---- ordered append of the new solutions
+        std::vector<int> cand;
+        for (int l = 0; l < m; ++l)
+            if (seed_mode || (act[l] && status[l] == RCG_OK)) cand.push_back(l);
+        std::vector<int> kept;
+        std::vector<double> ratio;
+        const int r_before = r;
+        append(cand, tau, (seq && !seed_mode) ? lanes[0].s : -1, kept, ratio);
+        int qi = 0;
+        for (size_t ci = 0; ci < cand.size(); ++ci) {
+            const int l = cand[ci];
+            out[l].ratio = ratio[ci];
+            out[l].appended = kept[ci];
+            if (kept[ci] && !seed_mode) {
+                auto &pl = priv[lanes[l].j];
+                pl.push_back(r_before + qi);
+                while (k_u + (int)pl.size() > std::min(c->opt.k_cap, KMAX) && !pl.empty()) pl.erase(pl.begin());
+            }
+            if (kept[ci]) ++qi;
+        }
+        RCG_CUDA_TRY(cudaEventRecord(e3, st));
+        c->sync();
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1); c->phase["check"] += ms;
+        cudaEventElapsedTime(&ms, e1, e2); c->phase["cg"] += ms;
+        cudaEventElapsedTime(&ms, e2, e3); c->phase["append"] += ms;
+        cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+        for (int l = 0; l < m; ++l) {
+            out[l].iters = act[l] ? iters_h[l] : 0;
+            out[l].restarts = restarts[l];
+            out[l].relres = relres[l];
+            out[l].status = status[l];
+        }
+        if (c->opt.keep_solutions) {
+            std::vector<double> hx(n);
+            for (int l = 0; l < m; ++l) {
+                auto &sol = c->solutions[lanes[l].s];
+                if (sol.empty()) sol.assign((size_t)n * c->nrhs, 0.0);
+                c->d2h(sol.data() + (size_t)lanes[l].j * n, x64 + (long long)l * ld, n);
+            }
+            c->sync();
+        }
+    }
+
+    // -------------------------------------------------------------- seed
+    // CholQR of the b columns of X (twice), using Y as scratch.
+    void cholqr(T *X, T *Y, int b) {
+        for (int pass = 0; pass < 2; ++pass) {
+            gemm_tn<T, T>(st, n, X, ld, b, X, ld, b, M, b, false);
+            RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+            chol_inplace(st, M, b, b, d_info);
+            check_info("eigen seed CholQR");
+            lower_to_upper(st, M, b, b, RK);
+            tri_upper_inverse(st, RK, b, b, Ri);
+            gemm_nn<T, T>(st, n, X, ld, b, Ri, b, b, Y, ld, 1.0, 0.0);
+            RCG_CUDA_TRY(cudaMemcpyAsync(X, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+
+    // Rayleigh-Ritz on range(X): X <- Ritz vectors (ascending), AX = A~ X, theta.
+    void rayleigh_ritz(int s0, T *X, T *AX, T *Y, int b, std::vector<double> &theta) {
+        std::vector<const T *> src(b);
+        std::vector<T *> dst(b);
+        for (int i = 0; i < b; ++i) { src[i] = X + (long long)i * ld; dst[i] = AX + (long long)i * ld; }
+        apply_cols(src, dst, std::vector<int>(b, s0));
+        gemm_tn<T, T>(st, n, X, ld, b, AX, ld, b, M, b, false);
+        jacobi_eig(st, M, b, b, Rhat, xn2);          // Rhat: eigenvectors, xn2: eigenvalues
+        gemm_nn<T, T>(st, n, X, ld, b, Rhat, b, b, Y, ld, 1.0, 0.0);
+        RCG_CUDA_TRY(cudaMemcpyAsync(X, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
+        gemm_nn<T, T>(st, n, AX, ld, b, Rhat, b, b, Y, ld, 1.0, 0.0);
+        RCG_CUDA_TRY(cudaMemcpyAsync(AX, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
+        theta.resize(b);
+        c->d2h(theta.data(), xn2, b);
+        c->sync();
+    }
+
+    // k_u smallest eigenvectors of A~_{s0} by Chebyshev-filtered subspace
+    // iteration (Zhou & Saad 2007) with block size k_u + 6: each pass filters
+    // the block with a Chebyshev polynomial damping [a, lambda_max] (a = the
+    // largest Ritz value of the block, lambda_max a Gershgorin bound), then
+    // orthonormalises and does a Rayleigh-Ritz step.  Result: x64 lanes 0..k_u-1.
+    void seed_eig(int s0) {
+        const int b = std::min(k_u + 6, 32);
+        ensure_lanes(std::max(c->nrhs, b));
+        ensure_append(b);
+        T *X = xc, *AX = rv, *Y1 = pv, *Y2 = qv;
+        unsigned long long *gb = (unsigned long long *)d_rr;
+        gershgorin(st, g, c->D64, c->diag64_of(s0), gb);
+        unsigned long long bits = 0;
+        c->d2h(&bits, gb, 1);
+        c->sync();
+        double lmax;
+        std::memcpy(&lmax, &bits, sizeof(double));
+        rand_fill<T>(st, X, n, ld, b, 0x5EED5EEDULL);
+        cholqr(X, Y1, b);
+        std::vector<double> theta, res(b);
+        rayleigh_ritz(s0, X, AX, Y1, b, theta);
+        const int degree = c->opt.seed_degree > 0 ? c->opt.seed_degree : 24;
+        const double tol = mixed ? 3e-6 : 1e-10;
+        double *res_d = d_rr;
+        for (int pass = 0; pass < 400; ++pass) {
+            const double a = theta[b - 1];
+            const double e = 0.5 * (lmax - a), cc = 0.5 * (lmax + a);
+            // Y1 = (A X - c X) / e ; Y_{k+1} = 2 (A Y_k - c Y_k)/e - Y_{k-1}
+            std::vector<const T *> src(b);
+            std::vector<T *> dst(b);
+            T *buf[3] = {X, Y1, Y2};      // Y_k lives in buf[k mod 3]
+            for (int k = 0; k < degree; ++k) {
+                T *Yk = buf[k % 3], *Ykm1 = buf[(k + 2) % 3], *Ynew = buf[(k + 1) % 3];
+                for (int i = 0; i < b; ++i) { src[i] = Yk + (long long)i * ld; dst[i] = AX + (long long)i * ld; }
+                apply_cols(src, dst, std::vector<int>(b, s0));
+                if (k == 0) cheb_step<T>(st, Ynew, AX, Yk, nullptr, n, ld, b, 1.0 / e, -cc / e, 0.0);
+                else cheb_step<T>(st, Ynew, AX, Yk, Ykm1, n, ld, b, 2.0 / e, -2.0 * cc / e, -1.0);
+            }
+            if (degree % 3 != 0)
+                RCG_CUDA_TRY(cudaMemcpyAsync(X, buf[degree % 3], sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
+            cholqr(X, Y1, b);
+            rayleigh_ritz(s0, X, AX, Y1, b, theta);
+            ritz_res<T>(st, AX, X, xn2, n, ld, b, res_d);
+            c->d2h(res.data(), res_d, b);
+            c->sync();
+            double worst = 0;
+            for (int i = 0; i < k_u; ++i) worst = std::max(worst, std::sqrt(res[i]));
+            if (worst <= tol * lmax) break;
+        }
+        for (int i = 0; i < k_u; ++i)
+            convert_cols<T, double>(st, n, X + (long long)i * ld, ld, x64 + (long long)i * ld, ld, 1);
+        c->sync();
+    }
+
+    void seed(int s0, const double *U0, rcg_stat *stats) override {
+        s_star = s0;
+        r = 0;
+        gs_sample = -1;
+        k_u = c->opt.k_u;
+        const int nrhs = c->nrhs;
+        ensure_lanes(std::max(nrhs, k_u));
+        // U_0 -> V through the append (orthonormalises in order)
+        if (k_u > 0) {
+            cudaEvent_t e0, e1;
+            RCG_CUDA_TRY(cudaEventCreate(&e0)); RCG_CUDA_TRY(cudaEventCreate(&e1));
+            RCG_CUDA_TRY(cudaEventRecord(e0, st));
+            if (U0) {
+                for (int q = 0; q < k_u; ++q) c->h2d(x64 + (long long)q * ld, U0 + (size_t)q * n, n);
+            } else {
+                seed_eig(s0);
+            }
+            RCG_CUDA_TRY(cudaEventRecord(e1, st));
+            c->sync();
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0); cudaEventDestroy(e1);
+            c->phase.clear();
+            c->phase["seed_eig"] = ms;
+            std::vector<int> cand(k_u);
+            for (int q = 0; q < k_u; ++q) cand[q] = q;
+            std::vector<int> kept;
+            std::vector<double> ratio;
+            append(cand, 1e-12, -1, kept, ratio);
+            k_u = r;
+        }
+        // X_0 = A~_0^-1 [B~, C~] by deflated CG with U_0, appended in RHS order
+        std::vector<Lane> lanes(nrhs);
+        for (int j = 0; j < nrhs; ++j) lanes[j] = Lane{s0, j};
+        if (!X0) { X0 = c->alloc<T>((size_t)nrhs * ld); sX0 = c->alloc<double>((size_t)rmax * nrhs); }
+        priv.assign(nrhs, {});
+        std::vector<rcg_stat> out;
+        const double eig_ms = c->phase.count("seed_eig") ? c->phase["seed_eig"] : 0.0;
+        c->phase.clear();
+        c->phase["seed_eig"] = eig_ms;
+        wave(lanes, true, false, out);
+        c->phase["seed_x0"] = c->phase["check"] + c->phase["cg"] + c->phase["append"];
+        std::vector<int> all(nrhs);
+        for (int j = 0; j < nrhs; ++j) all[j] = j;
+        c->h2d(d_list, all.data(), nrhs);
+        convert_lanes<double, T>(st, n, (const double *const *)p_x64, d_list, nrhs, X0, ld);
+        RCG_CUDA_TRY(cudaMemsetAsync(sX0, 0, sizeof(double) * rmax * nrhs, st));
+        gemm_tn<T, T>(st, n, V, ld, r, X0, ld, nrhs, sX0, rmax, false);
+        c->sync();
+        priv.assign(nrhs, std::vector<int>{-1});
+        priv_seed = priv;
+        r_seed = r;
+        seeded = true;
+        if (stats) for (int j = 0; j < nrhs; ++j) stats[j] = out[j];
+    }
+
+    void reset() override {
+        if (!seeded) throw Error{RCG_ERR_INVALID, "rcg_reset_to_seed before rcg_seed"};
+        r = r_seed;
+        priv = priv_seed;
+        gs_sample = -1;
+    }
+
+    int solve_all(int s_first, int s_count, rcg_stat *stats) override {
+        if (!seeded) throw Error{RCG_ERR_INVALID, "rcg_solve_all before rcg_seed"};
+        const int nrhs = c->nrhs;
+        int rc = RCG_OK;
+        c->phase.erase("check"); c->phase.erase("cg"); c->phase.erase("append");
+        c->phase["check"] = c->phase["cg"] = c->phase["append"] = 0.0;
+        auto record = [&](const std::vector<rcg_stat> &out) {
+            for (const auto &o : out) {
+                if (o.status == RCG_ERR_NOT_CONVERGED && rc == RCG_OK) rc = RCG_ERR_NOT_CONVERGED;
+                if (o.status == RCG_ERR_BREAKDOWN && rc == RCG_OK) rc = RCG_ERR_BREAKDOWN;
+                if (stats) stats[(size_t)(o.sample - s_first) * nrhs + o.rhs] = o;
+            }
+        };
+        std::vector<rcg_stat> out;
+        if (c->opt.order == RCG_SEQUENTIAL) {
+            for (int s = s_first; s < s_first + s_count; ++s)
+                for (int j = 0; j < nrhs; ++j) {
+                    wave({Lane{s, j}}, false, true, out);
+                    record(out);
+                }
+        } else {
+            const int ws = c->opt.wave_samples > 0 ? c->opt.wave_samples : s_count;
+            for (int s0 = s_first; s0 < s_first + s_count; s0 += ws) {
+                std::vector<Lane> lanes;
+                for (int s = s0; s < std::min(s0 + ws, s_first + s_count); ++s)
+                    for (int j = 0; j < nrhs; ++j) lanes.push_back(Lane{s, j});
+                wave(lanes, false, false, out);
+                record(out);
+            }
+        }
+        return rc;
+    }
+
+    int rank() const override { return r; }
+
+    void basis_get(double *Vh) override {
+        if (r == 0) return;
+        double *tmp = c->alloc<double>((size_t)r * ld);
+        convert_cols<T, double>(st, n, V, ld, tmp, ld, r);
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(Vh, sizeof(double) * n, tmp, sizeof(double) * ld, sizeof(double) * n, r,
+                                       cudaMemcpyDeviceToHost, st));
+        c->sync();
+        c->release(tmp);
+    }
+
+    // ----------------------------------------------------------- reduced model
+    void rom_eval(const double *mu, int nparam, const double *dmu, double *Psi, double *J) override {
+        if (r == 0) throw Error{RCG_ERR_INVALID, "rcg_rom_eval with an empty basis"};
+        const int ns = c->nsrc, nd = c->ndet;
+        cudaEvent_t e0, e1;
+        RCG_CUDA_TRY(cudaEventCreate(&e0)); RCG_CUDA_TRY(cudaEventCreate(&e1));
+        RCG_CUDA_TRY(cudaEventRecord(e0, st));
+        if (!Ar) {
+            Ar = c->alloc<double>((size_t)rmax * rmax);
+            Br = c->alloc<double>((size_t)rmax * ns);
+            Crm = c->alloc<double>((size_t)rmax * nd);
+            Xr = c->alloc<double>((size_t)rmax * ns);
+            Zr = c->alloc<double>((size_t)rmax * nd);
+            wtmp = c->alloc<double>(ld);
+        }
+        // A~_r = C_* + V^T diag(h^2 (mu - mu_*)) V
+        scaled_diff(st, n, mu, c->mu64 + (long long)s_star * ld, c->h * c->h, wtmp);
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(Ar, sizeof(double) * r, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
+                                       cudaMemcpyDeviceToDevice, st));
+        gemm_tn<T, T>(st, n, V, ld, r, V, ld, r, Ar, r, true, wtmp);
+        RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+        chol_inplace(st, Ar, r, r, d_info);
+        check_info("reduced matrix V^T A(p) V");
+        // B~_r, C~_r: row gathers of V (point sources / receivers)
+        gather_rows<T>(st, V, ld, r, c->d_rhs_node, c->d_rhs_w, ns, Br, r);
+        gather_rows<T>(st, V, ld, r, c->d_rhs_node + ns, c->d_rhs_w + ns, nd, Crm, r);
+        RCG_CUDA_TRY(cudaMemcpyAsync(Xr, Br, sizeof(double) * r * ns, cudaMemcpyDeviceToDevice, st));
+        RCG_CUDA_TRY(cudaMemcpyAsync(Zr, Crm, sizeof(double) * r * nd, cudaMemcpyDeviceToDevice, st));
+        trsv_lower_batched(st, Ar, r, r, Xr, r, ns, false);
+        trsv_lower_batched(st, Ar, r, r, Xr, r, ns, true);
+        trsv_lower_batched(st, Ar, r, r, Zr, r, nd, false);
+        trsv_lower_batched(st, Ar, r, r, Zr, r, nd, true);
+        // Psi_r = C~_r^T X_r  (ndet x nsrc)
+        gemm_tn<double, double>(st, r, Crm, r, nd, Xr, r, ns, Psi, nd, false);
+        if (J && dmu) {
+            if (!VX) { VX = c->alloc<double>((size_t)ns * ld); VZ = c->alloc<double>((size_t)nd * ld); }
+            gemm_nn<T, double>(st, n, V, ld, r, Xr, r, ns, VX, ld, 1.0, 0.0);
+            gemm_nn<T, double>(st, n, V, ld, r, Zr, r, nd, VZ, ld, 1.0, 0.0);
+            for (int k = 0; k < nparam; ++k) {
+                scaled_diff(st, n, dmu + (long long)k * n, nullptr, -c->h * c->h, wtmp);
+                gemm_tn<double, double>(st, n, VZ, ld, nd, VX, ld, ns, J + (long long)k * nd * ns, nd, false, wtmp);
+            }
+        }
+        RCG_CUDA_TRY(cudaEventRecord(e1, st));
+        c->sync();
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->phase["rom"] = ms;
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+    }
+};
+
+int fail(rcg_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <typename F> int guarded(rcg_ctx *c, F f) {
+    if (!c) return RCG_ERR_INVALID;
+    long long *prev = g_launch_counter;
+    g_launch_counter = &c->launches;
+    int rc;
+    try {
+        rc = f();
+    } catch (const Error &e) {
+        rc = fail(c, e.code, e.msg);
+    } catch (const std::bad_alloc &) {
+        rc = fail(c, RCG_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        rc = fail(c, RCG_ERR_INVALID, "unexpected exception");
+    }
+    g_launch_counter = prev;
+    return rc;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+void rcg_options_default(rcg_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = RCG_FP64;
+    o->order = RCG_SEQUENTIAL;
+    o->wave_samples = 0;
+    o->tau_rank = 1e-12;
+    o->k_u = 10;
+    o->k_cap = 256;
+    o->r_max = 2048;
+    o->max_samples = 32;
+    o->maxit = 20000;
+    o->inner_eta = 1e-4;
+    o->check_refine = -1;
+    o->keep_solutions = 0;
+    o->seed_degree = 0;
+    o->spin_budget = 0;
+}
+
+const char *rcg_strerror(int code) {
+    switch (code) {
+        case RCG_OK: return "ok";
+        case RCG_ERR_INVALID: return "invalid argument or call order";
+        case RCG_ERR_CUDA: return "CUDA runtime error";
+        case RCG_ERR_OOM: return "out of device memory";
+        case RCG_ERR_NOT_SPD: return "matrix not positive definite";
+        case RCG_ERR_NOT_CONVERGED: return "maximum iterations reached";
+        case RCG_ERR_BREAKDOWN: return "Krylov breakdown";
+        case RCG_ERR_TIMEOUT: return "device wait timed out";
+        case RCG_ERR_RANK_CAP: return "basis rank cap reached";
+        default: return "unknown error";
+    }
+}
+
+const char *rcg_last_error(const rcg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *stream) {
+    if (!out || !gr) return RCG_ERR_INVALID;
+    *out = nullptr;
+    if (gr->dim != 2 && gr->dim != 3) return RCG_ERR_INVALID;
+    if (gr->N < 2 || !(gr->robin_A > 0) || !std::isfinite(gr->robin_A)) return RCG_ERR_INVALID;
+    rcg_ctx *c = new (std::nothrow) rcg_ctx();
+    if (!c) return RCG_ERR_OOM;
+    c->grid = *gr;
+    if (o) c->opt = *o; else rcg_options_default(&c->opt);
+    if (c->opt.precision != RCG_FP64 && c->opt.precision != RCG_MIXED) { delete c; return RCG_ERR_INVALID; }
+    if (c->opt.order != RCG_SEQUENTIAL && c->opt.order != RCG_WAVE) { delete c; return RCG_ERR_INVALID; }
+    if (c->opt.r_max < 1 || c->opt.max_samples < 1 || c->opt.k_u < 0 || c->opt.k_u > 32 || c->opt.maxit < 1) {
+        delete c;
+        return RCG_ERR_INVALID;
+    }
+    if (c->opt.check_refine < 0) c->opt.check_refine = c->opt.precision == RCG_MIXED ? 2 : 0;
+    if (!(c->opt.inner_eta > 0)) c->opt.inner_eta = 1e-4;
+    c->st = (cudaStream_t)stream;
+    const int N = gr->N;
+    c->g.Nx = N;
+    c->g.Ny = gr->dim == 3 ? N : 1;
+    c->g.Nz = N;
+    c->n = (long long)c->g.Nx * c->g.Ny * c->g.Nz;
+    c->g.n = c->n;
+    c->ld = (c->n + 63) / 64 * 64;
+    c->g.ld = c->ld;
+    c->h = 1.0 / (N + 1);
+    c->sample_set.assign(c->opt.max_samples, 0);
+    c->solutions.assign(c->opt.max_samples, {});
+    int rc = guarded(c, [&]() {
+        c->D64 = c->alloc<double>(c->ld);
+        c->D32 = c->alloc<float>(c->ld);
+        c->dstar = c->alloc<double>(c->ld);
+        c->mu64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
+        c->diag64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
+        c->diag32 = c->alloc<float>((size_t)c->opt.max_samples * c->ld);
+        if (c->opt.precision == RCG_MIXED) c->eng.reset(new Engine<float>(c));
+        else c->eng.reset(new Engine<double>(c));
+        return RCG_OK;
+    });
+    if (rc != RCG_OK) { rcg_destroy(c); return rc; }
+    *out = c;
+    return RCG_OK;
+}
+
+void rcg_destroy(rcg_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    c->eng.reset();
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    delete c;
+}
+
+int rcg_set_diffusion(rcg_ctx *c, const double *D) {
+    return guarded(c, [&]() {
+        if (!D) return fail(c, RCG_ERR_INVALID, "D == NULL");
+        for (long long p = 0; p < c->n; ++p)
+            if (!(D[p] > 0) || !std::isfinite(D[p])) return fail(c, RCG_ERR_INVALID, "D must be positive and finite");
+        c->h2d(c->D64, D, c->n);
+        convert_cols<double, float>(c->st, c->n, c->D64, c->ld, c->D32, c->ld, 1);
+        diag_star(c->st, c->g, c->D64, c->h, c->grid.robin_A, c->dstar);
+        c->sync();
+        c->have_D = true;
+        c->have_rhs = false;          // effective source weights depend on D: set them again
+        for (auto &s : c->sample_set) s = 0;
+        return RCG_OK;
+    });
+}
+
+int rcg_set_sources_detectors(rcg_ctx *c, int nsrc, const int *src_ij, const double *src_w, int ndet,
+                              const int *det_ij, const double *det_w) {
+    return guarded(c, [&]() {
+        if (!c->have_D) return fail(c, RCG_ERR_INVALID, "rcg_set_diffusion must come first");
+        if (nsrc < 0 || ndet < 0 || nsrc + ndet < 1 || (nsrc && !src_ij) || (ndet && !det_ij))
+            return fail(c, RCG_ERR_INVALID, "bad source / detector lists");
+        const int Nx = c->g.Nx, Ny = c->g.Ny, Nz = c->g.Nz;
+        std::vector<double> Dh(c->n);
+        c->d2h(Dh.data(), c->D64, c->n);
+        c->sync();
+        c->nsrc = nsrc;
+        c->ndet = ndet;
+        c->nrhs = nsrc + ndet;
+        c->rhs_node.assign(c->nrhs, 0);
+        c->rhs_w.assign(c->nrhs, 0.0);
+        for (int q = 0; q < c->nrhs; ++q) {
+            const bool is_src = q < nsrc;
+            const int *ij = is_src ? src_ij + 2 * q : det_ij + 2 * (q - nsrc);
+            const int i = ij[0], j = ij[1];
+            if (i < 1 || i > Nx || j < 1 || j > Ny) return fail(c, RCG_ERR_INVALID, "face point out of range");
+            const int k = is_src ? 1 : Nz;
+            const long long p = (long long)(i - 1) + (long long)Nx * ((j - 1) + (long long)Ny * (k - 1));
+            const double Dp = Dh[p];
+            const double alpha = 2.0 * c->grid.robin_A * Dp / c->h;
+            const double wt = is_src ? (src_w ? src_w[q] : 1.0) : (det_w ? det_w[q - nsrc] : 1.0);
+            // b~ = s D_p / (1 + alpha_p) e_p,  c~ = c alpha_p / (1 + alpha_p) e_p  (Sec. 3.1)
+            c->rhs_node[q] = (int)p;
+            c->rhs_w[q] = wt * (is_src ? Dp / (1.0 + alpha) : alpha / (1.0 + alpha));
+            if (!(c->rhs_w[q] != 0.0) || !std::isfinite(c->rhs_w[q])) return fail(c, RCG_ERR_INVALID, "zero weight");
+        }
+        c->release(c->d_rhs_node);
+        c->release(c->d_rhs_w);
+        c->d_rhs_node = c->alloc<int>(c->nrhs);
+        c->d_rhs_w = c->alloc<double>(c->nrhs);
+        c->h2d(c->d_rhs_node, c->rhs_node.data(), c->nrhs);
+        c->h2d(c->d_rhs_w, c->rhs_w.data(), c->nrhs);
+        c->tol.assign(c->nrhs, 1e-8);
+        c->sync();
+        c->have_rhs = true;
+        return RCG_OK;
+    });
+}
+
+int rcg_set_tolerances(rcg_ctx *c, const double *tol) {
+    return guarded(c, [&]() {
+        if (!c->have_rhs || !tol) return fail(c, RCG_ERR_INVALID, "set sources/detectors first");
+        for (int j = 0; j < c->nrhs; ++j)
+            if (!(tol[j] > 0 && tol[j] < 1)) return fail(c, RCG_ERR_INVALID, "tolerance out of (0, 1)");
+        c->tol.assign(tol, tol + c->nrhs);
+        return RCG_OK;
+    });
+}
+
+static int set_sample_impl(rcg_ctx *c, int s, const double *mu, bool device) {
+    return guarded(c, [&]() {
+        if (!c->have_D) return fail(c, RCG_ERR_INVALID, "rcg_set_diffusion must come first");
+        if (s < 0 || s >= c->opt.max_samples || !mu) return fail(c, RCG_ERR_INVALID, "bad sample slot or mu");
+        double *dst = c->mu64 + (long long)s * c->ld;
+        if (device) {
+            RCG_CUDA_TRY(cudaMemcpyAsync(dst, mu, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            for (long long p = 0; p < c->n; ++p)
+                if (!(mu[p] >= 0) || !std::isfinite(mu[p])) return fail(c, RCG_ERR_INVALID, "mu must be >= 0 and finite");
+            c->h2d(dst, mu, c->n);
+        }
+        diag_sample(c->st, c->n, c->dstar, dst, c->h * c->h, c->diag64_of(s), c->diag32_of(s));
+        c->sync();
+        c->sample_set[s] = 1;
+        return RCG_OK;
+    });
+}
+
+int rcg_set_sample(rcg_ctx *c, int s, const double *mu) { return set_sample_impl(c, s, mu, false); }
+int rcg_set_sample_device(rcg_ctx *c, int s, const double *mu_dev) { return set_sample_impl(c, s, mu_dev, true); }
+
+int rcg_apply(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols) {
+    return guarded(c, [&]() {
+        if (s < 0 || s >= c->opt.max_samples || !c->sample_set[s] || ncols < 0 || !x_dev || !y_dev)
+            return fail(c, RCG_ERR_INVALID, "bad rcg_apply arguments");
+        if (prec == RCG_FP64) {
+            std::vector<const double *> hs(ncols), hg(ncols);
+            std::vector<double *> hd(ncols);
+            for (int j = 0; j < ncols; ++j) {
+                hs[j] = (const double *)x_dev + (long long)j * c->n;
+                hd[j] = (double *)y_dev + (long long)j * c->n;
+                hg[j] = c->diag64_of(s);
+            }
+            const double **a = c->alloc<const double *>(ncols);
+            double **b = c->alloc<double *>(ncols);
+            const double **g = c->alloc<const double *>(ncols);
+            c->h2d(a, hs.data(), ncols); c->h2d(b, hd.data(), ncols); c->h2d(g, hg.data(), ncols);
+            apply_op<double>(c->st, c->g, c->D64, g, a, b, ncols, nullptr, nullptr);
+            c->sync();
+            c->release((void *)a); c->release(b); c->release((void *)g);
+        } else if (prec == RCG_MIXED) {
+            std::vector<const float *> hs(ncols), hg(ncols);
+            std::vector<float *> hd(ncols);
+            for (int j = 0; j < ncols; ++j) {
+                hs[j] = (const float *)x_dev + (long long)j * c->n;
+                hd[j] = (float *)y_dev + (long long)j * c->n;
+                hg[j] = c->diag32_of(s);
+            }
+            const float **a = c->alloc<const float *>(ncols);
+            float **b = c->alloc<float *>(ncols);
+            const float **g = c->alloc<const float *>(ncols);
+            c->h2d(a, hs.data(), ncols); c->h2d(b, hd.data(), ncols); c->h2d(g, hg.data(), ncols);
+            apply_op<float>(c->st, c->g, c->D32, g, a, b, ncols, nullptr, nullptr);
+            c->sync();
+            c->release((void *)a); c->release(b); c->release((void *)g);
+        } else {
+            return fail(c, RCG_ERR_INVALID, "prec must be RCG_FP64 or RCG_MIXED");
+        }
+        return RCG_OK;
+    });
+}
+
+int rcg_seed(rcg_ctx *c, int s0, const double *U0, rcg_stat *stats) {
+    return guarded(c, [&]() {
+        if (!c->have_rhs || s0 < 0 || s0 >= c->opt.max_samples || !c->sample_set[s0])
+            return fail(c, RCG_ERR_INVALID, "rcg_seed needs D, sources/detectors and sample s0");
+        c->eng->seed(s0, U0, stats);
+        return RCG_OK;
+    });
+}
+
+int rcg_reset_to_seed(rcg_ctx *c) {
+    return guarded(c, [&]() { c->eng->reset(); return RCG_OK; });
+}
+
+int rcg_solve_all(rcg_ctx *c, int s_first, int s_count, rcg_stat *stats) {
+    return guarded(c, [&]() {
+        if (s_first < 0 || s_count < 1 || s_first + s_count > c->opt.max_samples)
+            return fail(c, RCG_ERR_INVALID, "bad sample range");
+        for (int s = s_first; s < s_first + s_count; ++s)
+            if (!c->sample_set[s]) return fail(c, RCG_ERR_INVALID, "sample not set");
+        const int rc = c->eng->solve_all(s_first, s_count, stats);
+        if (rc != RCG_OK) c->err = rcg_strerror(rc);
+        return rc;
+    });
+}
+
+int rcg_basis_rank(const rcg_ctx *c, int *r) {
+    if (!c || !r) return RCG_ERR_INVALID;
+    *r = c->eng->rank();
+    return RCG_OK;
+}
+
+int rcg_basis_get(rcg_ctx *c, double *V) {
+    return guarded(c, [&]() {
+        if (!V) return fail(c, RCG_ERR_INVALID, "V == NULL");
+        c->eng->basis_get(V);
+        return RCG_OK;
+    });
+}
+
+int rcg_solution_get(rcg_ctx *c, int s, double *X) {
+    return guarded(c, [&]() {
+        if (!c->opt.keep_solutions || s < 0 || s >= c->opt.max_samples || !X || c->solutions[s].empty())
+            return fail(c, RCG_ERR_INVALID, "no kept solutions for this sample");
+        std::memcpy(X, c->solutions[s].data(), sizeof(double) * c->solutions[s].size());
+        return RCG_OK;
+    });
+}
+
+int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const double *dmu_dev, double *Psi_dev,
+                        double *J_dev) {
+    return guarded(c, [&]() {
+        if (!mu_dev || !Psi_dev || nparam < 0) return fail(c, RCG_ERR_INVALID, "bad rom arguments");
+        c->eng->rom_eval(mu_dev, nparam, dmu_dev, Psi_dev, J_dev);
+        return RCG_OK;
+    });
+}
+
+int rcg_rom_eval(rcg_ctx *c, const double *mu, int nparam, const double *dmu, double *Psi, double *J) {
+    return guarded(c, [&]() {
+        if (!mu || !Psi || nparam < 0 || (J && !dmu)) return fail(c, RCG_ERR_INVALID, "bad rom arguments");
+        const long long n = c->n;
+        double *dmu_d = nullptr, *mu_d = c->alloc<double>(n);
+        double *P = c->alloc<double>((size_t)c->nsrc * c->ndet);
+        double *Jd = nullptr;
+        c->h2d(mu_d, mu, n);
+        if (J) {
+            dmu_d = c->alloc<double>((size_t)n * std::max(nparam, 1));
+            Jd = c->alloc<double>((size_t)c->nsrc * c->ndet * std::max(nparam, 1));
+            c->h2d(dmu_d, dmu, (size_t)n * nparam);
+        }
+        c->eng->rom_eval(mu_d, nparam, dmu_d, P, Jd);
+        c->d2h(Psi, P, (size_t)c->nsrc * c->ndet);
+        if (J) c->d2h(J, Jd, (size_t)c->nsrc * c->ndet * nparam);
+        c->sync();
+        c->release(mu_d); c->release(P); c->release(dmu_d); c->release(Jd);
+        return RCG_OK;
+    });
+}
+
+double rcg_phase_ms(const rcg_ctx *c, const char *phase) {
+    if (!c || !phase) return -1.0;
+    auto it = c->phase.find(phase);
+    return it == c->phase.end() ? -1.0 : it->second;
+}
+
+long long rcg_launch_count(const rcg_ctx *c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// Internal declarations of librcg: device buffers, launch helpers and the
+// kernels' host-side launchers.  See include/rcg.h for the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+namespace rcg {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define RCG_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            throw ::rcg::Error{-2, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define RCG_CHECK_LAUNCH()                                                          \
+    do {                                                                            \
+        cudaError_t e_ = cudaGetLastError();                                        \
+        if (e_ != cudaSuccess)                                                      \
+            throw ::rcg::Error{-2, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// Launch counter shared by all launchers of a context (set by the caller).
+extern thread_local long long *g_launch_counter;
+inline void count_launch() { if (g_launch_counter) ++*g_launch_counter; }
+
+// ------------------------------------------------------------ grid / operator
+// Matrix-free description of A~_s (see include/rcg.h): x fastest, the z axis
+// (last) carries the Robin faces, y is absent in 2D (Ny == 1).
+struct Grid {
+    int Nx, Ny, Nz;
+    long long n;       // Nx*Ny*Nz
+    long long ld;      // padded column stride of every n-vector (elements)
+};
+
+// Columns addressed as base + j*ld.
+template <typename T> struct Cols {
+    T *p;
+    long long ld;
+    __host__ __device__ T *col(int j) const { return p + (long long)j * ld; }
+};
+
+constexpr int KMAX = 48;        // max deflation columns per lane (U_j)
+constexpr int KCHUNK = 8;       // deflation dot columns fused per pass
+
+// Per-lane CG state on the device (structure of arrays, m lanes).
+struct LaneState {
+    int m;                  // lanes
+    double *rr;             // [3][m]  r^T r ring (slot = iteration mod 3)
+    double *pq;             // [2][m]  p^T A p ring
+    double *wv;             // [2][m][KMAX] (A W)^T r ring
+    double *gw;             // [m][KMAX][KMAX] Cholesky factor of W^T A W (lower)
+    int *kdef;              // [m] deflation columns of the lane
+    int *active;            // [m] 1 while the lane iterates
+    int *flag;              // [m] set to 1 when the recursive residual met thresh
+    int *iters;             // [m]
+    double *thresh;         // [m] stop threshold on ||r|| of the current cycle
+    const void **W;         // [m][KMAX] deflation column pointers (T*)
+    const void **AW;        // [m][KMAX] A~_s W column pointers (T*)
+};
+
+// ------------------------------------------------------------ launchers
+// stencil.cu
+template <typename T>
+void apply_op(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
+              const T *const *src, T *const *dst, int ncols, const int *active,
+              double *dots, int unused = 0);
+void residual64(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
+                const double *const *x, double *const *r, float *const *r32, int ncols,
+                const int *node, const double *bw, double *rr, const int *active);
+
+// dense.cu
+template <typename TA, typename TB>
+void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
+             const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
+             const double *wt = nullptr, const int *rows = nullptr, long long nrows = 0);
+template <typename TA, typename TO>
+void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k,
+             const double *Y, int ldy, int m, TO *Out, long long ldo, double alpha, double beta);
+template <typename TV>
+void gather_rows(cudaStream_t st, const TV *V, long long ldv, int r, const int *node,
+                 const double *w, int m, double *out, int ldo);
+template <typename TS, typename TD>
+void convert_cols(cudaStream_t st, long long n, const TS *src, long long lds, TD *dst,
+                  long long ldd, int ncols);
+template <typename T>
+void col_dots(cudaStream_t st, long long n, const T *A, long long lda, const T *B,
+              long long ldb, int ncols, double *out);
+void add_cols_f32_to_f64(cudaStream_t st, long long n, double *x, long long ldx, const float *d,
+                         long long ldd, const int *lanes, int nl);
+
+// small.cu (float64, small dense matrices)
+void chol_inplace(cudaStream_t st, double *A, int lda, int r, int *info);
+void chol_border(cudaStream_t st, double *L, int ldl, int r_old, int a, int *info);
+void trsv_lower_batched(cudaStream_t st, const double *L, int ldl, int r, double *B, int ldb,
+                        int m, bool transpose);
+void ordered_drop_chol(cudaStream_t st, const double *M, int a, const double *xnorm2, double *S,
+                       double tau, double *R, int *kept, double *ratio);
+void tri_upper_inverse(cudaStream_t st, const double *R, int ldr, int a, double *Ri);
+void lane_inverse(cudaStream_t st, double *gw, const int *kdef, int m, int *info);
+void jacobi_eig(cudaStream_t st, double *A, int lda, int k, double *Q, double *w);
+
+// misc.cu
+void diag_star(cudaStream_t st, const Grid &g, const double *D, double h, double A, double *out);
+void diag_sample(cudaStream_t st, long long n, const double *dstar, const double *mu, double h2,
+                 double *d64, float *d32);
+void scaled_diff(cudaStream_t st, long long n, const double *a, const double *b, double scale, double *w);
+template <typename TS, typename TD>
+void convert_lanes(cudaStream_t st, long long n, const TS *const *src, const int *lanes, int nl,
+                   TD *dst, long long ldd);
+void norm2_lanes(cudaStream_t st, long long n, const double *const *src, const int *lanes, int nl,
+                 double *out);
+void border_write(cudaStream_t st, double *C, int ldc, int r0, int a, const double *B, int ldb);
+void copy_new_rows(cudaStream_t st, const double *G, double *L, int ld, int r0, int a);
+void gather_sub(cudaStream_t st, const double *R, int a, const int *K, int ak, double *RK);
+void scatter_rows(cudaStream_t st, const double *Rinv, int ak, const int *K, int a, double *Rhat);
+void lower_to_upper(cudaStream_t st, const double *L, int lda, int a, double *R);
+void lane_gw(cudaStream_t st, const double *const *Gs, int ldg, int r, const int *spec,
+             const double *const *sx, const int *kdef, double *gw, int m);
+
+template <typename T>
+void rand_fill(cudaStream_t st, T *X, long long n, long long ld, int b, unsigned long long seed);
+template <typename T>
+void cheb_step(cudaStream_t st, T *out, const T *AY, const T *Y, const T *Yp, long long n, long long ld,
+               int b, double alpha, double beta, double gamma);
+void gershgorin(cudaStream_t st, const Grid &g, const double *D, const double *diag, unsigned long long *out);
+template <typename T>
+void ritz_res(cudaStream_t st, const T *AX, const T *X, const double *theta, long long n, long long ld,
+              int b, double *res2);
+
+// cg.cu
+template <typename T>
+void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
+                  T *const *x, T *const *r, T *const *p, T *const *q, LaneState ls, int t,
+                  int kmax_used);
+template <typename T>
+void cg_restart(cudaStream_t st, const Grid &g, T *const *x, T *const *r, T *const *p,
+                LaneState ls, int t, const int *mask, int kmax_used);
+
+}  // namespace rcg

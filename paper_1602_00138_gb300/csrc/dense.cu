@@ -1,0 +1,298 @@
+// Tall-skinny dense products on CUDA cores: C = A^T diag(w) B (split over
+// the long dimension n, float64 accumulation across splits), Out = A Y,
+// row gathers V^T b~ for point right-hand sides, conversions and dots.
+// These serve the Galerkin check (Algorithm 2, "check if V is a good enough
+// space"), the ordered append (Sec. 5.3 incremental QR of the basis) and
+// the reduced model (eq. newreduced).
+#include "common.cuh"
+
+#include <type_traits>
+
+namespace rcg {
+namespace {
+
+constexpr int TN_T = 32;      // output tile (A columns x B columns)
+constexpr int TN_BK = 32;     // rows per shared-memory stage
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+// C[i + j*ldc] += sum_p w[p] A_i[p] B_j[p] over this CTA's row range.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256)
+k_gemm_tn(long long n, const TA *__restrict__ A, long long lda, int ka, const TB *__restrict__ B,
+          long long ldb, int kb, double *__restrict__ C, int ldc, const double *__restrict__ wt,
+          const int *__restrict__ rows, long long nrows, long long chunk) {
+    using AT = typename std::conditional<(sizeof(TA) == 8 || sizeof(TB) == 8), double, float>::type;
+    __shared__ AT As[TN_BK][TN_T + 1];
+    __shared__ AT Bs[TN_BK][TN_T + 1];
+    const int i0 = blockIdx.x * TN_T, j0 = blockIdx.y * TN_T;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long long len = rows ? nrows : n;
+    const long long r0 = (long long)blockIdx.z * chunk;
+    const long long r1 = (r0 + chunk < len) ? r0 + chunk : len;
+    double accd[2][2] = {{0, 0}, {0, 0}};
+    AT acc[2][2] = {{0, 0}, {0, 0}};
+    int since_flush = 0;
+    for (long long base = r0; base < r1; base += TN_BK) {
+        if (wt) {   // skip row chunks where the weight vanishes (finite support of Delta)
+            int nz = 0;
+            if (threadIdx.x < TN_BK) {
+                const long long q = base + threadIdx.x;
+                if (q < r1) nz = wt[rows ? (long long)rows[q] : q] != 0.0;
+            }
+            if (!__syncthreads_or(nz)) continue;
+        }
+        for (int e = threadIdx.x; e < TN_BK * TN_T; e += 256) {
+            const int rr = e % TN_BK, cc = e / TN_BK;
+            const long long q = base + rr;
+            AT av = 0, bv = 0;
+            if (q < r1) {
+                const long long p = rows ? (long long)rows[q] : q;
+                if (i0 + cc < ka) {
+                    av = (AT)A[(long long)(i0 + cc) * lda + p];
+                    if (wt) av = av * (AT)wt[p];
+                }
+                if (j0 + cc < kb) bv = (AT)B[(long long)(j0 + cc) * ldb + p];
+            }
+            As[rr][cc] = av;
+            Bs[rr][cc] = bv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < TN_BK; ++kk) {
+            const AT a0 = As[kk][ty], a1 = As[kk][ty + 16];
+            const AT b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+            acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+        }
+        __syncthreads();
+        if (!std::is_same<AT, double>::value && ++since_flush == 8) {
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) { accd[a][b] += (double)acc[a][b]; acc[a][b] = 0; }
+            since_flush = 0;
+        }
+    }
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+            const double v = accd[a][b] + (double)acc[a][b];
+            if (i < ka && j < kb && v != 0.0) atomicAdd(C + i + (long long)j * ldc, v);
+        }
+}
+
+constexpr int NN_MN = 16;     // output columns per CTA
+constexpr int NN_KC = 32;     // basis columns per shared-memory stage
+
+// Out_j[p] = beta Out_j[p] + alpha sum_c A_c[p] Y[c + j*ldy]
+template <typename TA, typename TO>
+__global__ void __launch_bounds__(256)
+k_gemm_nn(long long n, const TA *__restrict__ A, long long lda, int k, const double *__restrict__ Y,
+          int ldy, int m, TO *__restrict__ Out, long long ldo, double alpha, double beta) {
+    using AT = typename Acc<TA>::type;
+    __shared__ AT Ys[NN_KC][NN_MN];
+    const int j0 = blockIdx.y * NN_MN;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double accd[NN_MN];
+#pragma unroll
+    for (int j = 0; j < NN_MN; ++j) accd[j] = 0.0;
+    for (int c0 = 0; c0 < k; c0 += NN_KC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < NN_KC * NN_MN; e += blockDim.x) {
+            const int cc = e % NN_KC, jj = e / NN_KC;
+            double v = 0.0;
+            if (c0 + cc < k && j0 + jj < m) v = Y[(c0 + cc) + (long long)(j0 + jj) * ldy];
+            Ys[cc][jj] = (AT)v;
+        }
+        __syncthreads();
+        if (p < n) {
+            AT acc[NN_MN];
+#pragma unroll
+            for (int j = 0; j < NN_MN; ++j) acc[j] = 0;
+            const int cend = (k - c0) < NN_KC ? (k - c0) : NN_KC;
+            for (int cc = 0; cc < cend; ++cc) {
+                const AT a = (AT)A[(long long)(c0 + cc) * lda + p];
+#pragma unroll
+                for (int j = 0; j < NN_MN; ++j) acc[j] += a * Ys[cc][j];
+            }
+#pragma unroll
+            for (int j = 0; j < NN_MN; ++j) accd[j] += (double)acc[j];
+        }
+    }
+    if (p < n) {
+#pragma unroll
+        for (int j = 0; j < NN_MN; ++j) {
+            if (j0 + j >= m) break;
+            TO *o = Out + (long long)(j0 + j) * ldo + p;
+            const double old = (beta != 0.0) ? (double)*o : 0.0;
+            *o = (TO)(beta * old + alpha * accd[j]);
+        }
+    }
+}
+
+template <typename TV>
+__global__ void k_gather_rows(const TV *__restrict__ V, long long ldv, int r, const int *__restrict__ node,
+                              const double *__restrict__ w, int m, double *__restrict__ out, int ldo) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)r * m) return;
+    const int c = (int)(e % r), j = (int)(e / r);
+    out[c + (long long)j * ldo] = w[j] * (double)V[(long long)c * ldv + node[j]];
+}
+
+template <typename TS, typename TD>
+__global__ void k_convert(long long n, const TS *__restrict__ s, long long lds, TD *__restrict__ d,
+                          long long ldd, int ncols) {
+    const int j = blockIdx.y;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        d[(long long)j * ldd + p] = (TD)s[(long long)j * lds + p];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_col_dots(long long n, const T *__restrict__ A, long long lda, const T *__restrict__ B, long long ldb,
+           double *__restrict__ out) {
+    const int j = blockIdx.y;
+    double acc = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        acc += (double)A[(long long)j * lda + p] * (double)B[(long long)j * ldb + p];
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(out + j, s);
+    }
+}
+
+__global__ void k_add_f32_f64(long long n, double *__restrict__ x, long long ldx, const float *__restrict__ d,
+                              long long ldd, const int *__restrict__ lanes) {
+    const int l = lanes[blockIdx.y];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        x[(long long)l * ldx + p] += (double)d[(long long)l * ldd + p];
+}
+
+int blocks_for(long long n, int per_col_cols) {
+    long long b = (n + 255) / 256;
+    long long cap = (long long)(4 * 152) / (per_col_cols > 0 ? per_col_cols : 1);
+    if (cap < 8) cap = 8;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+template <typename TA, typename TB>
+void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka, const TB *B, long long ldb,
+             int kb, double *C, int ldc, bool accumulate, const double *wt, const int *rows, long long nrows) {
+    if (ka <= 0 || kb <= 0) return;
+    if (!accumulate) {
+        for (int j = 0; j < kb; ++j)
+            RCG_CUDA_TRY(cudaMemsetAsync(C + (long long)j * ldc, 0, sizeof(double) * ka, st));
+    }
+    const long long len = rows ? nrows : n;
+    if (len <= 0) return;
+    const int gx = (ka + TN_T - 1) / TN_T, gy = (kb + TN_T - 1) / TN_T;
+    // split the long dimension so that the grid covers the GPU about 4 times
+    long long tiles = (long long)gx * gy;
+    long long want = (4LL * 152 + tiles - 1) / tiles;
+    long long maxz = (len + 1023) / 1024;
+    long long z = want < maxz ? want : maxz;
+    if (z < 1) z = 1;
+    if (z > 65535) z = 65535;
+    long long chunk = (len + z - 1) / z;
+    chunk = (chunk + TN_BK - 1) / TN_BK * TN_BK;
+    z = (len + chunk - 1) / chunk;
+    dim3 grid(gx, gy, (unsigned)z);
+    k_gemm_tn<TA, TB><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, kb, C, ldc, wt, rows, nrows, chunk);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+template void gemm_tn<double, double>(cudaStream_t, long long, const double *, long long, int, const double *,
+                                      long long, int, double *, int, bool, const double *, const int *, long long);
+template void gemm_tn<float, float>(cudaStream_t, long long, const float *, long long, int, const float *,
+                                    long long, int, double *, int, bool, const double *, const int *, long long);
+template void gemm_tn<float, double>(cudaStream_t, long long, const float *, long long, int, const double *,
+                                     long long, int, double *, int, bool, const double *, const int *, long long);
+
+template <typename TA, typename TO>
+void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k, const double *Y, int ldy, int m,
+             TO *Out, long long ldo, double alpha, double beta) {
+    if (m <= 0 || n <= 0) return;
+    if (k <= 0) {
+        if (beta == 0.0) {
+            for (int j = 0; j < m; ++j)
+                RCG_CUDA_TRY(cudaMemsetAsync(Out + (long long)j * ldo, 0, sizeof(TO) * n, st));
+        }
+        return;
+    }
+    dim3 grid((unsigned)((n + 255) / 256), (m + NN_MN - 1) / NN_MN);
+    k_gemm_nn<TA, TO><<<grid, 256, 0, st>>>(n, A, lda, k, Y, ldy, m, Out, ldo, alpha, beta);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+template void gemm_nn<double, double>(cudaStream_t, long long, const double *, long long, int, const double *,
+                                      int, int, double *, long long, double, double);
+template void gemm_nn<float, float>(cudaStream_t, long long, const float *, long long, int, const double *,
+                                    int, int, float *, long long, double, double);
+template void gemm_nn<float, double>(cudaStream_t, long long, const float *, long long, int, const double *,
+                                     int, int, double *, long long, double, double);
+
+template <typename TV>
+void gather_rows(cudaStream_t st, const TV *V, long long ldv, int r, const int *node, const double *w, int m,
+                 double *out, int ldo) {
+    if (r <= 0 || m <= 0) return;
+    const long long tot = (long long)r * m;
+    k_gather_rows<TV><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(V, ldv, r, node, w, m, out, ldo);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+template void gather_rows<double>(cudaStream_t, const double *, long long, int, const int *, const double *, int,
+                                  double *, int);
+template void gather_rows<float>(cudaStream_t, const float *, long long, int, const int *, const double *, int,
+                                 double *, int);
+
+template <typename TS, typename TD>
+void convert_cols(cudaStream_t st, long long n, const TS *src, long long lds, TD *dst, long long ldd, int ncols) {
+    if (ncols <= 0) return;
+    dim3 grid(blocks_for(n, ncols), ncols);
+    k_convert<TS, TD><<<grid, 256, 0, st>>>(n, src, lds, dst, ldd, ncols);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+template void convert_cols<double, float>(cudaStream_t, long long, const double *, long long, float *, long long, int);
+template void convert_cols<float, double>(cudaStream_t, long long, const float *, long long, double *, long long, int);
+template void convert_cols<double, double>(cudaStream_t, long long, const double *, long long, double *, long long, int);
+template void convert_cols<float, float>(cudaStream_t, long long, const float *, long long, float *, long long, int);
+
+template <typename T>
+void col_dots(cudaStream_t st, long long n, const T *A, long long lda, const T *B, long long ldb, int ncols,
+              double *out) {
+    if (ncols <= 0) return;
+    RCG_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * ncols, st));
+    dim3 grid(blocks_for(n, ncols), ncols);
+    k_col_dots<T><<<grid, 256, 0, st>>>(n, A, lda, B, ldb, out);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+template void col_dots<double>(cudaStream_t, long long, const double *, long long, const double *, long long, int,
+                               double *);
+template void col_dots<float>(cudaStream_t, long long, const float *, long long, const float *, long long, int,
+                              double *);
+
+void add_cols_f32_to_f64(cudaStream_t st, long long n, double *x, long long ldx, const float *d, long long ldd,
+                         const int *lanes, int nl) {
+    if (nl <= 0) return;
+    dim3 grid(blocks_for(n, nl), nl);
+    k_add_f32_f64<<<grid, 256, 0, st>>>(n, x, ldx, d, ldd, lanes);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+}  // namespace rcg

@@ -1,0 +1,320 @@
+// Small dense float64 kernels: Cholesky of the Galerkin matrices V^T A~ V
+// and of the per-RHS deflation matrices U_j^T A~ U_j, bordered Cholesky
+// updates after a one-column append, batched triangular solves, the ordered
+// rank-revealing Cholesky of the append (pivot-free, in candidate order,
+// with a drop test) and a cyclic Jacobi eigensolver for Rayleigh-Ritz.
+//
+// All matrices are column-major; a Cholesky factor L is lower triangular.
+// These run on one CTA (or one CTA per independent system): the matrices
+// are at most a few thousand wide and live in global memory / L2.
+#include "common.cuh"
+
+#include <cmath>
+
+namespace rcg {
+namespace {
+
+__device__ __forceinline__ bool bad(double d) { return !(d > 0.0) || !isfinite(d); }
+
+// Right-looking Cholesky of the lower triangle of A (r x r), steps k0..r-1.
+// Columns < k0 must already be factored and applied to the trailing part.
+__global__ void __launch_bounds__(1024) k_chol(double *A, int lda, int k0, int r, int *info) {
+    __shared__ double piv;
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int k = k0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = A[k + (long long)k * lda];
+            if (bad(d)) { fail = k + 1; }
+            else { piv = sqrt(d); A[k + (long long)k * lda] = piv; }
+        }
+        __syncthreads();
+        if (fail) break;
+        const double inv = 1.0 / piv;
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i + (long long)k * lda] *= inv;
+        __syncthreads();
+        const int m = r - k - 1;
+        const long long tot = (long long)m * m;
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int ii = (int)(e % m), jj = (int)(e / m);
+            if (ii < jj) continue;
+            const int i = k + 1 + ii, j = k + 1 + jj;
+            A[i + (long long)j * lda] -= A[i + (long long)k * lda] * A[j + (long long)k * lda];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && info) *info = fail;
+}
+
+// New rows r_old..r_old+a-1 of A hold the Gram entries (lower part).  Apply
+// the factored columns 0..r_old-1 to them (forward substitution), then the
+// caller continues with k_chol(k0 = r_old).
+__global__ void __launch_bounds__(1024) k_chol_border(double *A, int lda, int r_old, int a) {
+    const int rn = r_old + a;
+    for (int j = 0; j < r_old; ++j) {
+        const double ljj = A[j + (long long)j * lda];
+        for (int i = r_old + threadIdx.x; i < rn; i += blockDim.x) A[i + (long long)j * lda] /= ljj;
+        __syncthreads();
+        // rows i (new) : A[i][k] -= L[k][j] * L[i][j] for j < k < r_old,
+        // and the new block A[i][k] for r_old <= k <= i
+        const int m = rn - (j + 1);
+        const long long tot = (long long)a * m;
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int i = r_old + (int)(e % a);
+            const int k = j + 1 + (int)(e / a);
+            if (k > i) continue;
+            A[i + (long long)k * lda] -= A[k + (long long)j * lda] * A[i + (long long)j * lda];
+        }
+        __syncthreads();
+    }
+}
+
+// Solve L y = b (or L^T y = b) for column blockIdx.x of B, in place.
+__global__ void __launch_bounds__(256) k_trsv(const double *L, int ldl, int r, double *B, int ldb, int trans) {
+    extern __shared__ double y[];
+    double *b = B + (long long)blockIdx.x * ldb;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) y[i] = b[i];
+    __syncthreads();
+    if (!trans) {
+        for (int j = 0; j < r; ++j) {
+            const double yj = y[j] / L[j + (long long)j * ldl];
+            __syncthreads();
+            if (threadIdx.x == 0) y[j] = yj;
+            for (int k = j + 1 + threadIdx.x; k < r; k += blockDim.x) y[k] -= L[k + (long long)j * ldl] * yj;
+            __syncthreads();
+        }
+    } else {
+        for (int j = r - 1; j >= 0; --j) {
+            const double yj = y[j] / L[j + (long long)j * ldl];
+            __syncthreads();
+            if (threadIdx.x == 0) y[j] = yj;
+            for (int k = threadIdx.x; k < j; k += blockDim.x) y[k] -= L[j + (long long)k * ldl] * yj;
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < r; i += blockDim.x) b[i] = y[i];
+}
+
+// Ordered pivot-free Cholesky of the candidate Gram M (a x a) with drop test:
+// candidate c is kept iff its component orthogonal to the kept candidates
+// before it, ||.||, divided by ||x_c||, exceeds tau.  R is upper triangular
+// (row c = kept candidate c), S is scratch (a x a).
+__global__ void __launch_bounds__(1024)
+k_ordered_drop(const double *M, int a, const double *xnorm2, double tau, double *S, double *R, int *kept,
+               double *ratio) {
+    __shared__ double piv;
+    __shared__ int keep;
+    const long long tot = (long long)a * a;
+    for (long long e = threadIdx.x; e < tot; e += blockDim.x) { S[e] = M[e]; R[e] = 0.0; }
+    __syncthreads();
+    for (int c = 0; c < a; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = S[c + (long long)c * a];
+            const double rt = (d > 0.0 && isfinite(d)) ? sqrt(d / xnorm2[c]) : 0.0;
+            ratio[c] = rt;
+            keep = (rt > tau) ? 1 : 0;
+            kept[c] = keep;
+            piv = keep ? sqrt(d) : 0.0;
+            if (keep) R[c + (long long)c * a] = piv;
+        }
+        __syncthreads();
+        if (keep) {
+            for (int j = c + 1 + threadIdx.x; j < a; j += blockDim.x)
+                R[c + (long long)j * a] = S[c + (long long)j * a] / piv;
+            __syncthreads();
+            const int m = a - c - 1;
+            const long long t2 = (long long)m * m;
+            for (long long e = threadIdx.x; e < t2; e += blockDim.x) {
+                const int i = c + 1 + (int)(e % m), j = c + 1 + (int)(e / m);
+                S[i + (long long)j * a] -= R[c + (long long)i * a] * R[c + (long long)j * a];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse of an upper triangular a x a matrix R (ld ldr) into Ri (ld a):
+// thread j solves R x = e_j by back substitution.
+__global__ void k_tri_upper_inv(const double *R, int ldr, int a, double *Ri) {
+    for (int j = threadIdx.x + blockIdx.x * blockDim.x; j < a; j += blockDim.x * gridDim.x) {
+        for (int i = a - 1; i >= 0; --i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= j; ++k) s -= R[i + (long long)k * ldr] * Ri[k + (long long)j * a];
+            Ri[i + (long long)j * a] = (i <= j) ? s / R[i + (long long)i * ldr] : 0.0;
+        }
+    }
+}
+
+// Per lane: G (k x k, stored in gw) -> G^-1 (in place) via Cholesky.
+__global__ void __launch_bounds__(128) k_lane_inv(double *gw, const int *kdef, int *info) {
+    const int l = blockIdx.x;
+    const int k = kdef[l];
+    double *G = gw + (long long)l * KMAX * KMAX;
+    __shared__ double L[KMAX * KMAX];
+    __shared__ double Li[KMAX * KMAX];
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e % k, j = e / k;
+        // symmetrise: use the mean of the two triangles
+        L[i + j * KMAX] = 0.5 * (G[i + j * KMAX] + G[j + i * KMAX]);
+    }
+    __syncthreads();
+    for (int c = 0; c < k; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = L[c + c * KMAX];
+            if (bad(d)) fail = c + 1;
+            else L[c + c * KMAX] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) break;
+        for (int i = c + 1 + threadIdx.x; i < k; i += blockDim.x) L[i + c * KMAX] /= L[c + c * KMAX];
+        __syncthreads();
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            const int i = e % k, j = e / k;
+            if (i > c && j > c && i >= j) L[i + j * KMAX] -= L[i + c * KMAX] * L[j + c * KMAX];
+        }
+        __syncthreads();
+    }
+    if (fail) {
+        if (threadIdx.x == 0 && info) atomicMax(info, 1);
+        return;
+    }
+    // Li = L^-1 (column j by forward substitution)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        for (int i = 0; i < k; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int q = j; q < i; ++q) s -= L[i + q * KMAX] * Li[q + j * KMAX];
+            Li[i + j * KMAX] = (i >= j) ? s / L[i + i * KMAX] : 0.0;
+        }
+    }
+    __syncthreads();
+    // G^-1 = Li^T Li
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e % k, j = e / k;
+        const int q0 = i > j ? i : j;
+        double s = 0.0;
+        for (int q = q0; q < k; ++q) s += Li[q + i * KMAX] * Li[q + j * KMAX];
+        G[i + j * KMAX] = s;
+    }
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric k x k matrix (one thread;
+// k is small).  A is overwritten; eigenvalues ascending with vectors.
+__global__ void k_jacobi(double *A, int lda, int k, double *Q, double *w) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) Q[i + (long long)j * k] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                const double v = A[i + (long long)j * lda];
+                tot += v * v;
+                if (i != j) off += v * v;
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < k - 1; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                const double apq = A[p + (long long)q * lda];
+                if (apq == 0.0) continue;
+                const double app = A[p + (long long)p * lda], aqq = A[q + (long long)q * lda];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < k; ++r) {
+                    const double arp = A[r + (long long)p * lda], arq = A[r + (long long)q * lda];
+                    A[r + (long long)p * lda] = c * arp - s * arq;
+                    A[r + (long long)q * lda] = s * arp + c * arq;
+                }
+                for (int r = 0; r < k; ++r) {
+                    const double apr = A[p + (long long)r * lda], aqr = A[q + (long long)r * lda];
+                    A[p + (long long)r * lda] = c * apr - s * aqr;
+                    A[q + (long long)r * lda] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < k; ++r) {
+                    const double qrp = Q[r + (long long)p * k], qrq = Q[r + (long long)q * k];
+                    Q[r + (long long)p * k] = c * qrp - s * qrq;
+                    Q[r + (long long)q * k] = s * qrp + c * qrq;
+                }
+            }
+    }
+    // sort ascending (selection sort, swapping vectors)
+    for (int i = 0; i < k; ++i) w[i] = A[i + (long long)i * lda];
+    for (int i = 0; i < k; ++i) {
+        int mi = i;
+        for (int j = i + 1; j < k; ++j)
+            if (w[j] < w[mi]) mi = j;
+        if (mi != i) {
+            const double t = w[i]; w[i] = w[mi]; w[mi] = t;
+            for (int r = 0; r < k; ++r) {
+                const double a = Q[r + (long long)i * k];
+                Q[r + (long long)i * k] = Q[r + (long long)mi * k];
+                Q[r + (long long)mi * k] = a;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void chol_inplace(cudaStream_t st, double *A, int lda, int r, int *info) {
+    if (r <= 0) return;
+    k_chol<<<1, 1024, 0, st>>>(A, lda, 0, r, info);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void chol_border(cudaStream_t st, double *L, int ldl, int r_old, int a, int *info) {
+    if (a <= 0) return;
+    if (r_old > 0) {
+        k_chol_border<<<1, 1024, 0, st>>>(L, ldl, r_old, a);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+    }
+    k_chol<<<1, 1024, 0, st>>>(L, ldl, r_old, r_old + a, info);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void trsv_lower_batched(cudaStream_t st, const double *L, int ldl, int r, double *B, int ldb, int m,
+                        bool transpose) {
+    if (r <= 0 || m <= 0) return;
+    const size_t sh = sizeof(double) * (size_t)r;
+    if (sh > 48 * 1024)
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_trsv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_trsv<<<m, 256, sh, st>>>(L, ldl, r, B, ldb, transpose ? 1 : 0);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void ordered_drop_chol(cudaStream_t st, const double *M, int a, const double *xnorm2, double *S, double tau,
+                       double *R, int *kept, double *ratio) {
+    if (a <= 0) return;
+    k_ordered_drop<<<1, 1024, 0, st>>>(M, a, xnorm2, tau, S, R, kept, ratio);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void tri_upper_inverse(cudaStream_t st, const double *R, int ldr, int a, double *Ri) {
+    if (a <= 0) return;
+    k_tri_upper_inv<<<(a + 127) / 128, 128, 0, st>>>(R, ldr, a, Ri);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void lane_inverse(cudaStream_t st, double *gw, const int *kdef, int m, int *info) {
+    if (m <= 0) return;
+    k_lane_inv<<<m, 128, 0, st>>>(gw, kdef, info);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void jacobi_eig(cudaStream_t st, double *A, int lda, int k, double *Q, double *w) {
+    k_jacobi<<<1, 32, 0, st>>>(A, lda, k, Q, w);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+}  // namespace rcg

@@ -1,0 +1,220 @@
+// Matrix-free application of the Schur-complement diffusion operator
+// A~_s = A~_* + diag(h^2 mu_s) (Sec. 3, eq. sum) on batches of columns.
+//
+//   (A~ x)_p = diag_s[p] x_p - sum_{interior neighbours q} w_pq x_q,
+//   w_pq = (D_p + D_q) / 2,
+//   diag_s[p] = sum_faces w_f^eff + h^2 mu_s[p]   (precomputed, see api.cu)
+//
+// The lateral Dirichlet ghosts and the eliminated Robin unknowns only touch
+// the diagonal, so the off-diagonal part is a plain 5/7-point stencil on the
+// unknown grid.  Face weights are formed on the fly from D (one coefficient
+// stream, the neighbours come from L1/L2), amortised over the NB columns a
+// thread handles.
+#include "common.cuh"
+
+namespace rcg {
+
+thread_local long long *g_launch_counter = nullptr;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T half_sum(T a, T b) { return T(0.5) * (a + b); }
+
+template <int NB>
+__device__ __forceinline__ void block_reduce_add(double (&acc)[NB], double *out, const bool (&act)[NB]) {
+    __shared__ double red[kThreads / 32][NB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        double v = acc[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NB) {
+        const int t = threadIdx.x;
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w][t];
+        if (act[t]) atomicAdd(out + t, s);
+    }
+}
+
+// y_c = A~_{s(c)} x_c for columns c of group blockIdx.y; optional dots x_c^T y_c.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads)
+k_apply(Grid g, const T *__restrict__ D, const T *const *__restrict__ diag_of_col,
+        const T *const *__restrict__ src, T *const *__restrict__ dst, int ncols,
+        const int *__restrict__ active, double *__restrict__ dots) {
+    const int c0 = blockIdx.y * NB;
+    bool act[NB];
+    bool any = false;
+    const T *xs[NB];
+    T *ys[NB];
+    const T *dg[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const int c = c0 + t;
+        act[t] = (c < ncols) && (active == nullptr || active[c] != 0);
+        any |= act[t];
+        xs[t] = act[t] ? src[c] : nullptr;
+        ys[t] = act[t] ? dst[c] : nullptr;
+        dg[t] = act[t] ? diag_of_col[c] : nullptr;
+    }
+    if (!any) return;
+    T acc[NB];      // per-thread partial sums in T; float64 only across threads
+#pragma unroll
+    for (int t = 0; t < NB; ++t) acc[t] = T(0);
+    const long long sxy = (long long)g.Nx * g.Ny;
+    const bool has_y = g.Ny > 1;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.Nx);
+        const long long rest = p / g.Nx;
+        const int j = (int)(rest % g.Ny);
+        const int k = (int)(rest / g.Ny);
+        const T Dp = D[p];
+        const T wxm = i > 0 ? half_sum(Dp, D[p - 1]) : T(0);
+        const T wxp = i < g.Nx - 1 ? half_sum(Dp, D[p + 1]) : T(0);
+        const T wym = (has_y && j > 0) ? half_sum(Dp, D[p - g.Nx]) : T(0);
+        const T wyp = (has_y && j < g.Ny - 1) ? half_sum(Dp, D[p + g.Nx]) : T(0);
+        const T wzm = k > 0 ? half_sum(Dp, D[p - sxy]) : T(0);
+        const T wzp = k < g.Nz - 1 ? half_sum(Dp, D[p + sxy]) : T(0);
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            if (!act[t]) continue;
+            const T *x = xs[t];
+            const T xc = x[p];
+            T v = dg[t][p] * xc;
+            if (i > 0) v -= wxm * x[p - 1];
+            if (i < g.Nx - 1) v -= wxp * x[p + 1];
+            if (has_y && j > 0) v -= wym * x[p - g.Nx];
+            if (has_y && j < g.Ny - 1) v -= wyp * x[p + g.Nx];
+            if (k > 0) v -= wzm * x[p - sxy];
+            if (k < g.Nz - 1) v -= wzp * x[p + sxy];
+            ys[t][p] = v;
+            if (dots) acc[t] += xc * v;
+        }
+    }
+    if (dots) {
+        double accd[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) accd[t] = (double)acc[t];
+        block_reduce_add<NB>(accd, dots + c0, act);
+    }
+}
+
+// r_c = b_c - A~_{s(c)} x_c in float64, b_c = bw_c e_{node_c}; optional float32 copy; rr_c += r^T r.
+template <int NB>
+__global__ void __launch_bounds__(kThreads)
+k_residual64(Grid g, const double *__restrict__ D, const double *const *__restrict__ diag_of_col,
+             const double *const *__restrict__ xsrc, double *const *__restrict__ rdst,
+             float *const *__restrict__ r32dst, int ncols, const int *__restrict__ node,
+             const double *__restrict__ bw, double *__restrict__ rr, const int *__restrict__ active) {
+    const int c0 = blockIdx.y * NB;
+    bool act[NB];
+    bool any = false;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const int c = c0 + t;
+        act[t] = (c < ncols) && (active == nullptr || active[c] != 0);
+        any |= act[t];
+    }
+    if (!any) return;
+    double acc[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) acc[t] = 0.0;
+    const long long sxy = (long long)g.Nx * g.Ny;
+    const bool has_y = g.Ny > 1;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.Nx);
+        const long long rest = p / g.Nx;
+        const int j = (int)(rest % g.Ny);
+        const int k = (int)(rest / g.Ny);
+        const double Dp = D[p];
+        const double wxm = i > 0 ? 0.5 * (Dp + D[p - 1]) : 0.0;
+        const double wxp = i < g.Nx - 1 ? 0.5 * (Dp + D[p + 1]) : 0.0;
+        const double wym = (has_y && j > 0) ? 0.5 * (Dp + D[p - g.Nx]) : 0.0;
+        const double wyp = (has_y && j < g.Ny - 1) ? 0.5 * (Dp + D[p + g.Nx]) : 0.0;
+        const double wzm = k > 0 ? 0.5 * (Dp + D[p - sxy]) : 0.0;
+        const double wzp = k < g.Nz - 1 ? 0.5 * (Dp + D[p + sxy]) : 0.0;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            if (!act[t]) continue;
+            const int c = c0 + t;
+            const double *x = xsrc[c];
+            double v = diag_of_col[c][p] * x[p];
+            if (i > 0) v -= wxm * x[p - 1];
+            if (i < g.Nx - 1) v -= wxp * x[p + 1];
+            if (has_y && j > 0) v -= wym * x[p - g.Nx];
+            if (has_y && j < g.Ny - 1) v -= wyp * x[p + g.Nx];
+            if (k > 0) v -= wzm * x[p - sxy];
+            if (k < g.Nz - 1) v -= wzp * x[p + sxy];
+            const double b = (p == (long long)node[c]) ? bw[c] : 0.0;
+            const double res = b - v;
+            if (rdst) rdst[c][p] = res;
+            if (r32dst) r32dst[c][p] = (float)res;
+            acc[t] += res * res;
+        }
+    }
+    if (rr) block_reduce_add<NB>(acc, rr + c0, act);
+}
+
+int grid_x_for(long long n, int groups) {
+    // about 4 resident CTAs per SM over all groups, at least one node per thread
+    int sms = 152;
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            int v = 0;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+                cached = v;
+        }
+        if (!cached) cached = 152;
+    }
+    sms = cached;
+    long long want = (4LL * sms + groups - 1) / groups;
+    long long maxb = (n + kThreads - 1) / kThreads;
+    long long gx = want < maxb ? want : maxb;
+    if (gx < 1) gx = 1;
+    return (int)gx;
+}
+
+}  // namespace
+
+template <typename T>
+void apply_op(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
+              const T *const *src, T *const *dst, int ncols, const int *active,
+              double *dots, int) {
+    if (ncols <= 0) return;
+    constexpr int NB = sizeof(T) == 8 ? 4 : 8;
+    const int groups = (ncols + NB - 1) / NB;
+    dim3 grid(grid_x_for(g.n, groups), groups);
+    k_apply<T, NB><<<grid, kThreads, 0, st>>>(g, D, diag_of_col, src, dst, ncols, active, dots);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+template void apply_op<double>(cudaStream_t, const Grid &, const double *, const double *const *,
+                               const double *const *, double *const *, int, const int *, double *, int);
+template void apply_op<float>(cudaStream_t, const Grid &, const float *, const float *const *,
+                              const float *const *, float *const *, int, const int *, double *, int);
+
+void residual64(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
+                const double *const *x, double *const *r, float *const *r32, int ncols,
+                const int *node, const double *bw, double *rr, const int *active) {
+    if (ncols <= 0) return;
+    constexpr int NB = 4;
+    const int groups = (ncols + NB - 1) / NB;
+    dim3 grid(grid_x_for(g.n, groups), groups);
+    k_residual64<NB><<<grid, kThreads, 0, st>>>(g, D, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+}  // namespace rcg

@@ -1,0 +1,251 @@
+"""ctypes binding of librcg (include/rcg.h): argument marshalling only.
+
+Every computation happens inside the CUDA library; this module converts
+numpy arrays / torch device tensors to pointers and raises on error codes.
+Importing it fails loudly when the compiled library is missing: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librcg.so")
+
+RCG_OK = 0
+RCG_ERR_INVALID = -1
+RCG_ERR_CUDA = -2
+RCG_ERR_OOM = -3
+RCG_ERR_NOT_SPD = -4
+RCG_ERR_NOT_CONVERGED = -5
+RCG_ERR_BREAKDOWN = -6
+RCG_ERR_TIMEOUT = -7
+RCG_ERR_RANK_CAP = -8
+RCG_FP64, RCG_MIXED = 0, 1
+RCG_SEQUENTIAL, RCG_WAVE = 0, 1
+
+EXPORTED = [
+    "rcg_options_default", "rcg_create", "rcg_destroy", "rcg_last_error", "rcg_strerror",
+    "rcg_set_diffusion", "rcg_set_sources_detectors", "rcg_set_tolerances", "rcg_set_sample",
+    "rcg_set_sample_device", "rcg_apply", "rcg_seed", "rcg_reset_to_seed", "rcg_solve_all",
+    "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device",
+    "rcg_phase_ms", "rcg_launch_count",
+]
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("robin_A", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("order", C.c_int), ("wave_samples", C.c_int),
+                ("tau_rank", C.c_double), ("k_u", C.c_int), ("k_cap", C.c_int), ("r_max", C.c_int),
+                ("max_samples", C.c_int), ("maxit", C.c_int), ("inner_eta", C.c_double),
+                ("check_refine", C.c_int), ("keep_solutions", C.c_int), ("seed_degree", C.c_int),
+                ("spin_budget", C.c_longlong)]
+
+
+class Stat(C.Structure):
+    _fields_ = [("sample", C.c_int), ("rhs", C.c_int), ("iters", C.c_int), ("restarts", C.c_int),
+                ("appended", C.c_int), ("status", C.c_int), ("relres0", C.c_double),
+                ("relres", C.c_double), ("ratio", C.c_double)]
+
+
+class RcgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"librcg error {code}: {msg}")
+        self.code = code
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"librcg not built ({path} missing): run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    sig = {
+        "rcg_options_default": (None, [C.POINTER(Options)]),
+        "rcg_create": (I, [C.POINTER(P), C.POINTER(Grid), C.POINTER(Options), P]),
+        "rcg_destroy": (None, [P]),
+        "rcg_last_error": (C.c_char_p, [P]),
+        "rcg_strerror": (C.c_char_p, [I]),
+        "rcg_set_diffusion": (I, [P, P]),
+        "rcg_set_sources_detectors": (I, [P, I, P, P, I, P, P]),
+        "rcg_set_tolerances": (I, [P, P]),
+        "rcg_set_sample": (I, [P, I, P]),
+        "rcg_set_sample_device": (I, [P, I, P]),
+        "rcg_apply": (I, [P, I, I, P, P, I]),
+        "rcg_seed": (I, [P, I, P, P]),
+        "rcg_reset_to_seed": (I, [P]),
+        "rcg_solve_all": (I, [P, I, I, P]),
+        "rcg_basis_rank": (I, [P, C.POINTER(I)]),
+        "rcg_basis_get": (I, [P, P]),
+        "rcg_solution_get": (I, [P, I, P]),
+        "rcg_rom_eval": (I, [P, P, I, P, P, P]),
+        "rcg_rom_eval_device": (I, [P, P, I, P, P, P]),
+        "rcg_phase_ms": (D, [P, C.c_char_p]),
+        "rcg_launch_count": (LL, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _ptr(a):
+    """Pointer of a C-contiguous numpy array or a CUDA torch tensor (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def default_options(**kw):
+    o = Options()
+    lib().rcg_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def stats_to_dicts(arr):
+    return [dict(sample=s.sample, rhs=s.rhs, iters=s.iters, restarts=s.restarts, appended=s.appended,
+                 status=s.status, relres0=s.relres0, relres=s.relres, ratio=s.ratio) for s in arr]
+
+
+class Context:
+    """One librcg context (rcg_ctx) with the same entry points as the C ABI."""
+
+    def __init__(self, dim, N, robin_A=1.0, stream=None, **opts):
+        self.L = lib()
+        self.opts = default_options(**opts)
+        g = Grid(dim, N, robin_A)
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(stream))
+        self._check(self.L.rcg_create(C.byref(h), C.byref(g), C.byref(self.opts), s), None)
+        self.h = h
+        self.dim, self.N = dim, N
+        self.n = N ** dim
+        self.nsrc = self.ndet = self.nrhs = 0
+
+    def _check(self, rc, h="self"):
+        if rc != RCG_OK and rc != RCG_ERR_NOT_CONVERGED:
+            msg = self.L.rcg_strerror(rc).decode()
+            if h is not None:
+                msg += ": " + self.L.rcg_last_error(self.h).decode()
+            raise RcgError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rcg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- inputs
+    def set_diffusion(self, D):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        return self._check(self.L.rcg_set_diffusion(self.h, _ptr(D)))
+
+    def set_sources_detectors(self, src_ij, det_ij, src_w=None, det_w=None):
+        s = np.ascontiguousarray(src_ij, dtype=np.int32).reshape(-1, 2)
+        d = np.ascontiguousarray(det_ij, dtype=np.int32).reshape(-1, 2)
+        sw = None if src_w is None else np.ascontiguousarray(src_w, dtype=np.float64)
+        dw = None if det_w is None else np.ascontiguousarray(det_w, dtype=np.float64)
+        self.nsrc, self.ndet = len(s), len(d)
+        self.nrhs = self.nsrc + self.ndet
+        return self._check(self.L.rcg_set_sources_detectors(self.h, len(s), _ptr(s), _ptr(sw),
+                                                            len(d), _ptr(d), _ptr(dw)))
+
+    def set_tolerances(self, tol):
+        t = np.ascontiguousarray(tol, dtype=np.float64)
+        return self._check(self.L.rcg_set_tolerances(self.h, _ptr(t)))
+
+    def set_sample(self, s, mu):
+        if hasattr(mu, "data_ptr"):
+            return self._check(self.L.rcg_set_sample_device(self.h, s, _ptr(mu)))
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        return self._check(self.L.rcg_set_sample(self.h, s, _ptr(mu)))
+
+    def apply(self, s, x_dev, y_dev, ncols, prec=RCG_FP64):
+        return self._check(self.L.rcg_apply(self.h, s, prec, _ptr(x_dev), _ptr(y_dev), ncols))
+
+    # ---- method
+    def seed(self, s0, U0=None):
+        st = (Stat * self.nrhs)()
+        U = None if U0 is None else np.asfortranarray(U0, dtype=np.float64)
+        self._check(self.L.rcg_seed(self.h, s0, _ptr(U), st))
+        return stats_to_dicts(st)
+
+    def reset_to_seed(self):
+        return self._check(self.L.rcg_reset_to_seed(self.h))
+
+    def solve_all(self, s_first, s_count, want_stats=True):
+        st = (Stat * (self.nrhs * s_count))() if want_stats else None
+        rc = self._check(self.L.rcg_solve_all(self.h, s_first, s_count, st))
+        return (stats_to_dicts(st) if want_stats else None), rc
+
+    def rank(self):
+        r = C.c_int()
+        self._check(self.L.rcg_basis_rank(self.h, C.byref(r)))
+        return r.value
+
+    def basis(self):
+        r = self.rank()
+        V = np.zeros((self.n, r), dtype=np.float64, order="F")
+        self._check(self.L.rcg_basis_get(self.h, _ptr(V)))
+        return V
+
+    def solutions(self, s):
+        X = np.zeros((self.n, self.nrhs), dtype=np.float64, order="F")
+        self._check(self.L.rcg_solution_get(self.h, s, _ptr(X)))
+        return X
+
+    def rom_eval(self, mu, dmu=None):
+        """Psi_r (ndet, nsrc) and J_r (nparam, ndet, nsrc) or None."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        Psi = np.zeros((self.ndet, self.nsrc), dtype=np.float64, order="F")
+        if dmu is None:
+            self._check(self.L.rcg_rom_eval(self.h, _ptr(mu), 0, None, _ptr(Psi), None))
+            return Psi, None
+        dmu = np.ascontiguousarray(dmu, dtype=np.float64)     # (nparam, n) C order = n x nparam col-major
+        k = dmu.shape[0]
+        J = np.zeros((k, self.nsrc, self.ndet), dtype=np.float64)   # C order = J[d + ndet*(s + nsrc*k)]
+        self._check(self.L.rcg_rom_eval(self.h, _ptr(mu), k, _ptr(dmu), _ptr(Psi), _ptr(J)))
+        return Psi, np.transpose(J, (0, 2, 1))
+
+    def rom_eval_device(self, mu_dev, dmu_dev, Psi_dev, J_dev, nparam):
+        return self._check(self.L.rcg_rom_eval_device(self.h, _ptr(mu_dev), nparam, _ptr(dmu_dev),
+                                                      _ptr(Psi_dev), _ptr(J_dev)))
+
+    def phase_ms(self, name):
+        return self.L.rcg_phase_ms(self.h, name.encode())
+
+    def launch_count(self):
+        return self.L.rcg_launch_count(self.h)
