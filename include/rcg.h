@@ -135,7 +135,8 @@ int rcg_set_sources_detectors(rcg_ctx *c, int nsrc, const int *src_ij, const dou
 int rcg_set_tolerances(rcg_ctx *c, const double *tol);
 
 /* Absorption mu at the n unknowns for sample slot s (host / device float64,
- * >= 0).  A~_s = A~_* + diag(h^2 mu_s) (eq. sum). */
+ * >= 0).  A~_s = A~_* + diag(h^2 mu_s) (eq. sum).  Setting the slot that
+ * rcg_seed used as s0 discards the seed (rcg_seed must run again). */
 int rcg_set_sample(rcg_ctx *c, int s, const double *mu);
 int rcg_set_sample_device(rcg_ctx *c, int s, const double *mu_dev);
 
@@ -189,6 +190,23 @@ double rcg_phase_ms(const rcg_ctx *c, const char *phase);
 
 /* Number of kernel launches issued by this context since creation. */
 long long rcg_launch_count(const rcg_ctx *c);
+
+/* Device-side profile of the three kernels of one inner CG iteration
+ * (kernel 0: stencil q = A~ p with the fused p^T q; 1: update of x, r with
+ * the fused r^T r and (A~ U_j)^T r; 2: direction p = r + beta p - U_j mu).
+ * rcg_profile_enable(c, 1) resets and starts it (CUDA events around every
+ * launch on the context's stream, plus device work counters); 0 stops it.
+ * rcg_profile_get fills: launches, total device ms, lane_units (sum over
+ * launches of the active right-hand-side lanes it processed) and defl_cols
+ * (sum over those lanes of their recycle-space columns). */
+typedef struct {
+    long long launches;
+    double    ms;
+    double    lane_units;
+    double    defl_cols;
+} rcg_kprof;
+int rcg_profile_enable(rcg_ctx *c, int on);
+int rcg_profile_get(rcg_ctx *c, int kernel, rcg_kprof *out);
 
 #ifdef __cplusplus
 }

@@ -46,6 +46,7 @@ struct EngineBase {
     virtual int rank() const = 0;
     virtual void basis_get(double *V) = 0;
     virtual void rom_eval(const double *mu, int nparam, const double *dmu, double *Psi, double *J) = 0;
+    virtual void sample_changed(int s) = 0;
 };
 
 struct rcg_ctx {
@@ -73,6 +74,8 @@ struct rcg_ctx {
     std::unique_ptr<EngineBase> eng;
     std::map<std::string, double> phase;
     std::vector<std::vector<double>> solutions;   // per sample, host copies (keep_solutions)
+    KTimer ktimer;                                 // optional device timing of the CG kernels
+    unsigned long long *d_prof = nullptr;          // work counters of the CG kernels
 
     template <typename T> T *alloc(size_t count) {
         void *p = nullptr;
@@ -137,12 +140,15 @@ struct Engine : EngineBase {
     double *d_lw = nullptr, *d_rr = nullptr;
     double **p_x64 = nullptr, **p_diag64 = nullptr;
     T **p_xc = nullptr, **p_r = nullptr, **p_p = nullptr, **p_q = nullptr, **p_diag = nullptr;
-    int *d_spec = nullptr;
+    int *d_spec = nullptr, *d_si = nullptr, *d_kp = nullptr;
     double **d_sx = nullptr, **d_gsl = nullptr;
+    T *wpb = nullptr;                  // private deflation columns, [m][kp_max]
     double *Yb = nullptr;
     // deflation A W buffers
     T *au0 = nullptr;
-    int au0_cap = 0;
+    int au0_cap = 0, au0_ku = -1, au0_star = -1;
+    bool au0_valid = false;
+    std::vector<int> au0_samples;
     T *awp = nullptr;
     long long awp_cap = 0;
     // pointer scratch for generic applies
@@ -179,8 +185,8 @@ struct Engine : EngineBase {
     void ensure_lanes(int m) {
         if (m <= mcap) return;
         for (void *p : std::vector<void *>{x64, xc, rv, pv, qv, ls.rr, ls.pq, ls.wv, ls.gw, ls.kdef, ls.active, ls.flag,
-                                           ls.iters, ls.thresh, ls.W, ls.AW, d_mask, d_lnode, d_list, d_lw, d_rr,
-                                           p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb})
+                                           ls.iters, ls.thresh, d_mask, d_lnode, d_list, d_lw, d_rr,
+                                           p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb, d_si, d_kp})
             c->release(p);
         mcap = m;
         x64 = c->alloc<double>((size_t)m * ld);
@@ -198,8 +204,8 @@ struct Engine : EngineBase {
         ls.flag = c->alloc<int>(m);
         ls.iters = c->alloc<int>(m);
         ls.thresh = c->alloc<double>(m);
-        ls.W = (const void **)c->alloc<void *>((size_t)m * KMAX);
-        ls.AW = (const void **)c->alloc<void *>((size_t)m * KMAX);
+        d_si = c->alloc<int>(m);
+        d_kp = c->alloc<int>(m);
         d_mask = c->alloc<int>(m);
         d_lnode = c->alloc<int>(m);
         d_list = c->alloc<int>(m);
@@ -286,6 +292,33 @@ struct Engine : EngineBase {
         c->sync();   // the pointer scratch is reused by the next call
     }
 
+    // float64 scratch for the new basis columns and their images
+    double *Q64 = nullptr, *AQ64 = nullptr;
+    int aq64_cap = 0;
+    void ensure_aq64(int a) {
+        if (a <= aq64_cap) return;
+        c->release(Q64); c->release(AQ64);
+        aq64_cap = std::max(a, 16);
+        Q64 = c->alloc<double>((size_t)aq64_cap * ld);
+        AQ64 = c->alloc<double>((size_t)aq64_cap * ld);
+    }
+    // float64 A~_s applied to cnt contiguous float64 columns
+    void apply_cols64(const double *src, double *dst, int cnt, int s) {
+        ensure_ptr(cnt);
+        std::vector<const void *> hs(cnt), hd(cnt), hg(cnt);
+        for (int i = 0; i < cnt; ++i) {
+            hs[i] = src + (long long)i * ld;
+            hd[i] = dst + (long long)i * ld;
+            hg[i] = c->diag64_of(s);
+        }
+        c->h2d(d_ptrA, hs.data(), cnt);
+        c->h2d(d_ptrB, hd.data(), cnt);
+        c->h2d(d_ptrC, hg.data(), cnt);
+        apply_op<double>(st, g, c->D64, (const double *const *)d_ptrC, (const double *const *)d_ptrA,
+                         (double *const *)d_ptrB, cnt, nullptr, nullptr);
+        c->sync();
+    }
+
     // ----------------------------------------------------- Galerkin matrices
     double *delta_weights(int s) {
         if (!dw[s]) dw[s] = c->alloc<double>(ld);
@@ -300,7 +333,7 @@ struct Engine : EngineBase {
     void galerkin(int s, double *G, double *L) {
         RCG_CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * rmax, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        if (s != s_star) gemm_tn<T, T>(st, n, V, ld, r, V, ld, r, G, rmax, true, delta_weights(s));
+        if (s != s_star) gemm_tn_acc<T, T, double>(st, n, V, ld, r, V, ld, r, G, rmax, true, delta_weights(s));
         RCG_CUDA_TRY(cudaMemcpy2DAsync(L, sizeof(double) * rmax, G, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -369,16 +402,18 @@ struct Engine : EngineBase {
         lower_to_upper(st, M, ak, ak, RK);
         tri_upper_inverse(st, RK, ak, ak, Ri);
         gemm_nn<T, T>(st, n, Qb, ld, ak, Ri, ak, ak, V + (long long)r * ld, ld, 1.0, 0.0);
-        // C_* bordered with [V Q]^T A~_* Q
-        std::vector<const T *> src(ak);
-        std::vector<T *> dst(ak);
-        for (int i = 0; i < ak; ++i) { src[i] = V + (long long)(r + i) * ld; dst[i] = AQb + (long long)i * ld; }
-        apply_cols(src, dst, std::vector<int>(ak, s_star));
-        gemm_tn<T, T>(st, n, V, ld, r + ak, AQb, ld, ak, Cb, r + ak, false);
+        // C_* bordered with [V Q]^T A~_* Q.  The stencil and the products are
+        // float64 in both modes: for smooth columns A~ Q cancels to ~lambda_min
+        // |Q|, so a float32 stencil would lose 3 digits of the Galerkin matrix
+        // that the check, the deflation matrices and the reduced model solve with.
+        ensure_aq64(ak);
+        convert_cols<T, double>(st, n, V + (long long)r * ld, ld, Q64, ld, ak);
+        apply_cols64(Q64, AQ64, ak, s_star);
+        gemm_tn<T, double>(st, n, V, ld, r + ak, AQ64, ld, ak, Cb, r + ak, false);
         border_write(st, Cstar, rmax, r, ak, Cb, r + ak);
         if (border_sample >= 0 && gs_sample == border_sample && gs_r == r) {
-            if (border_sample != s_star) apply_cols(src, dst, std::vector<int>(ak, border_sample));
-            gemm_tn<T, T>(st, n, V, ld, r + ak, AQb, ld, ak, Cb, r + ak, false);
+            if (border_sample != s_star) apply_cols64(Q64, AQ64, ak, border_sample);
+            gemm_tn<T, double>(st, n, V, ld, r + ak, AQ64, ld, ak, Cb, r + ak, false);
             border_write(st, Gs, rmax, r, ak, Cb, r + ak);
             copy_new_rows(st, Gs, Ls, rmax, r, ak);
             RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -480,76 +515,95 @@ struct Engine : EngineBase {
         std::vector<int> iters_h(m, 0);
         if (nact) {
             // deflation spaces: U_j = [V(:, 0:k_u), X_0(:, j), V(:, priv_j)] (seed: V(:, 0:k_u))
-            std::vector<int> spec((size_t)m * KMAX, 0), kdef(m, 0);
-            std::vector<const void *> Wp((size_t)m * KMAX, nullptr), AWp((size_t)m * KMAX, nullptr);
+            std::vector<int> spec((size_t)m * KMAX, 0), kdef(m, 0), kp(m, 0), si(m, 0);
             std::vector<double *> sxp(m, nullptr), gsl(m, nullptr);
             std::vector<int> samples_in;
             for (int l = 0; l < m; ++l)
                 if (act[l] && std::find(samples_in.begin(), samples_in.end(), samp[l]) == samples_in.end())
                     samples_in.push_back(samp[l]);
             const int ku = std::min(k_u, r);
-            if ((int)samples_in.size() * ku > au0_cap) {
-                c->release(au0);
-                au0_cap = (int)samples_in.size() * ku;
-                au0 = c->alloc<T>((size_t)std::max(au0_cap, 1) * ld);
+            // A~_s U_0 per sample: the first k_u basis columns never change after
+            // the seed, so the images are cached per sample slot
+            if (samples_in != au0_samples || ku != au0_ku || au0_star != s_star) {
+                if ((int)samples_in.size() * ku > au0_cap) {
+                    c->release(au0);
+                    au0_cap = (int)samples_in.size() * ku;
+                    au0 = c->alloc<T>((size_t)std::max(au0_cap, 1) * ld);
+                }
+                au0_valid = false;
             }
             std::vector<const T *> asrc;
             std::vector<T *> adst;
             std::vector<int> asamp;
-            for (size_t si = 0; si < samples_in.size(); ++si)
-                for (int q = 0; q < ku; ++q) {
-                    asrc.push_back(V + (long long)q * ld);
-                    adst.push_back(au0 + ((long long)si * ku + q) * ld);
-                    asamp.push_back(samples_in[si]);
-                }
-            long long npriv = 0;
-            int kmax_used = 0;
+            if (!au0_valid) {
+                for (size_t s2 = 0; s2 < samples_in.size(); ++s2)
+                    for (int q = 0; q < ku; ++q) {
+                        asrc.push_back(V + (long long)q * ld);
+                        adst.push_back(au0 + ((long long)s2 * ku + q) * ld);
+                        asamp.push_back(samples_in[s2]);
+                    }
+                au0_samples = samples_in;
+                au0_ku = ku;
+                au0_star = s_star;
+                au0_valid = true;
+            }
+            int kmax_used = 0, kp_max = 0;
             for (int l = 0; l < m; ++l) {
                 if (!act[l]) continue;
                 std::vector<int> sp;
                 for (int q = 0; q < ku; ++q) sp.push_back(q);
                 if (!seed_mode)
                     for (int e : priv[lanes[l].j]) sp.push_back(e);
-                if ((int)sp.size() > KMAX) sp.erase(sp.begin() + ku, sp.begin() + ku + ((int)sp.size() - KMAX));
+                if ((int)sp.size() - ku > KP_MAX) sp.erase(sp.begin() + ku, sp.begin() + ((int)sp.size() - KP_MAX));
                 kdef[l] = (int)sp.size();
+                kp[l] = kdef[l] - ku;
+                kp_max = std::max(kp_max, kp[l]);
                 kmax_used = std::max(kmax_used, kdef[l]);
-                npriv += (int)sp.size() - ku;
+                si[l] = (int)(std::find(samples_in.begin(), samples_in.end(), samp[l]) - samples_in.begin());
                 for (int q = 0; q < (int)sp.size(); ++q) spec[(size_t)l * KMAX + q] = sp[q];
-            }
-            if (npriv > awp_cap) {
-                c->release(awp);
-                awp_cap = npriv;
-                awp = c->alloc<T>((size_t)npriv * ld);
-            }
-            long long pi = 0;
-            for (int l = 0; l < m; ++l) {
-                if (!act[l]) continue;
-                const int si = (int)(std::find(samples_in.begin(), samples_in.end(), samp[l]) - samples_in.begin());
-                for (int q = 0; q < kdef[l]; ++q) {
-                    const int e = spec[(size_t)l * KMAX + q];
-                    const T *w = e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld;
-                    Wp[(size_t)l * KMAX + q] = w;
-                    if (q < ku) {
-                        AWp[(size_t)l * KMAX + q] = au0 + ((long long)si * ku + q) * ld;
-                    } else {
-                        T *d = awp + pi * ld;
-                        ++pi;
-                        AWp[(size_t)l * KMAX + q] = d;
-                        asrc.push_back(w);
-                        adst.push_back(d);
-                        asamp.push_back(samp[l]);
-                    }
-                }
                 sxp[l] = sX0 ? sX0 + (long long)lanes[l].j * rmax : nullptr;
                 gsl[l] = gal.count(samp[l]) ? gal[samp[l]].first : nullptr;
+            }
+            const long long npriv = (long long)m * kp_max;
+            if (npriv > awp_cap) {
+                c->release(awp);
+                c->release(wpb);
+                awp_cap = npriv;
+                awp = c->alloc<T>((size_t)npriv * ld);
+                wpb = c->alloc<T>((size_t)npriv * ld);
+            }
+            // private columns copied next to each other, then A~_s applied to them
+            std::vector<const T *> psrc;
+            std::vector<T *> pdst;
+            for (int l = 0; l < m; ++l)
+                for (int q = 0; q < kp[l]; ++q) {
+                    const int e = spec[(size_t)l * KMAX + ku + q];
+                    psrc.push_back(e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld);
+                    T *w = wpb + ((long long)l * kp_max + q) * ld;
+                    pdst.push_back(w);
+                    asrc.push_back(w);
+                    adst.push_back(awp + ((long long)l * kp_max + q) * ld);
+                    asamp.push_back(samp[l]);
+                }
+            if (!psrc.empty()) {
+                for (size_t i = 0; i < psrc.size(); ++i)
+                    RCG_CUDA_TRY(cudaMemcpyAsync(pdst[i], psrc[i], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+                c->sync();
             }
             apply_cols(asrc, adst, asamp);
             c->h2d(d_spec, spec.data(), (size_t)m * KMAX);
             c->h2d(ls.kdef, kdef.data(), m);
-            c->h2d(ls.W, Wp.data(), (size_t)m * KMAX);
-            c->h2d(ls.AW, AWp.data(), (size_t)m * KMAX);
+            c->h2d(d_si, si.data(), m);
+            c->h2d(d_kp, kp.data(), m);
             c->h2d(d_sx, sxp.data(), m);
             c->h2d(d_gsl, gsl.data(), m);
+            LaneGeom gm{};
+            gm.ld = ld;
+            gm.k_u = ku;
+            gm.kp_max = std::max(kp_max, 1);
+            gm.x = xc; gm.r = rv; gm.p = pv; gm.q = qv;
+            gm.wu = V; gm.awu = au0; gm.wp = wpb; gm.awp = awp;
+            gm.si = d_si; gm.kp = d_kp;
             if (kmax_used > 0) {
                 lane_gw(st, (const double *const *)d_gsl, rmax, r, d_spec, (const double *const *)d_sx, ls.kdef, ls.gw, m);
                 RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -568,19 +622,22 @@ struct Engine : EngineBase {
             c->h2d(d_mask, act.data(), m);
             RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * m, st));
+            ls.prof = c->ktimer.on ? c->d_prof : nullptr;
             int t = 0;
-            cg_restart<T>(st, g, p_xc, p_r, p_p, ls, t, d_mask, kmax_used);
+            cg_restart<T>(st, g, gm, ls, t, d_mask);
             const int chunk = m > 1 ? 8 : 12;
             std::vector<int> flag_h(m), active_h(m);
             while (true) {
                 for (int i = 0; i < chunk; ++i) {
                     ++t;
-                    cg_iteration<T>(st, g, D, (const T *const *)p_diag, p_xc, p_r, p_p, p_q, ls, t, kmax_used);
+                    cg_iteration<T>(st, g, D, (const T *const *)p_diag, (const T *const *)p_p, p_q, gm, ls, t,
+                                    &c->ktimer);
                 }
                 c->d2h(flag_h.data(), ls.flag, m);
                 c->d2h(active_h.data(), ls.active, m);
                 c->d2h(iters_h.data(), ls.iters, m);
                 c->sync();
+                c->ktimer.harvest();
                 std::vector<int> F;
                 bool force = false;
                 for (int l = 0; l < m; ++l) {
@@ -616,7 +673,7 @@ struct Engine : EngineBase {
                         for (int l : Rl) rmask[l] = 1;
                         c->h2d(ls.thresh, thr.data(), m);
                         c->h2d(d_mask, rmask.data(), m);
-                        cg_restart<T>(st, g, p_xc, p_r, p_p, ls, t, d_mask, kmax_used);
+                        cg_restart<T>(st, g, gm, ls, t, d_mask);
                     }
                 }
                 bool any = false;
@@ -645,7 +702,7 @@ struct Engine : EngineBase {
             if (kept[ci] && !seed_mode) {
                 auto &pl = priv[lanes[l].j];
                 pl.push_back(r_before + qi);
-                while (k_u + (int)pl.size() > std::min(c->opt.k_cap, KMAX) && !pl.empty()) pl.erase(pl.begin());
+                while (k_u + (int)pl.size() > std::min(c->opt.k_cap, k_u + KP_MAX) && !pl.empty()) pl.erase(pl.begin());
             }
             if (kept[ci]) ++qi;
         }
@@ -760,6 +817,7 @@ struct Engine : EngineBase {
     }
 
     void seed(int s0, const double *U0, rcg_stat *stats) override {
+        au0_valid = false;
         s_star = s0;
         r = 0;
         gs_sample = -1;
@@ -857,6 +915,14 @@ struct Engine : EngineBase {
 
     int rank() const override { return r; }
 
+    // caches derived from mu_s: Delta weights, A~_s U_0, the sequential G_s
+    void sample_changed(int s) override {
+        if (s >= 0 && s < (int)dw_star.size()) dw_star[s] = -1;
+        if (std::find(au0_samples.begin(), au0_samples.end(), s) != au0_samples.end()) au0_valid = false;
+        if (gs_sample == s) gs_sample = -1;
+        if (s == s_star) seeded = false;     // C_* and the seed belong to the old mu_*: seed again
+    }
+
     void basis_get(double *Vh) override {
         if (r == 0) return;
         double *tmp = c->alloc<double>((size_t)r * ld);
@@ -886,7 +952,7 @@ struct Engine : EngineBase {
         scaled_diff(st, n, mu, c->mu64 + (long long)s_star * ld, c->h * c->h, wtmp);
         RCG_CUDA_TRY(cudaMemcpy2DAsync(Ar, sizeof(double) * r, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        gemm_tn<T, T>(st, n, V, ld, r, V, ld, r, Ar, r, true, wtmp);
+        gemm_tn_acc<T, T, double>(st, n, V, ld, r, V, ld, r, Ar, r, true, wtmp);
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
         chol_inplace(st, Ar, r, r, d_info);
         check_info("reduced matrix V^T A(p) V");
@@ -988,13 +1054,14 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
     *out = nullptr;
     if (gr->dim != 2 && gr->dim != 3) return RCG_ERR_INVALID;
     if (gr->N < 2 || !(gr->robin_A > 0) || !std::isfinite(gr->robin_A)) return RCG_ERR_INVALID;
+    if ((double)gr->N * gr->N * (gr->dim == 3 ? gr->N : 1) >= 2147483647.0) return RCG_ERR_INVALID;
     rcg_ctx *c = new (std::nothrow) rcg_ctx();
     if (!c) return RCG_ERR_OOM;
     c->grid = *gr;
     if (o) c->opt = *o; else rcg_options_default(&c->opt);
     if (c->opt.precision != RCG_FP64 && c->opt.precision != RCG_MIXED) { delete c; return RCG_ERR_INVALID; }
     if (c->opt.order != RCG_SEQUENTIAL && c->opt.order != RCG_WAVE) { delete c; return RCG_ERR_INVALID; }
-    if (c->opt.r_max < 1 || c->opt.max_samples < 1 || c->opt.k_u < 0 || c->opt.k_u > 32 || c->opt.maxit < 1) {
+    if (c->opt.r_max < 1 || c->opt.max_samples < 1 || c->opt.k_u < 0 || c->opt.k_u > KU_MAX || c->opt.maxit < 1) {
         delete c;
         return RCG_ERR_INVALID;
     }
@@ -1019,6 +1086,8 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
         c->mu64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
         c->diag64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
         c->diag32 = c->alloc<float>((size_t)c->opt.max_samples * c->ld);
+        c->d_prof = c->alloc<unsigned long long>(8);
+        RCG_CUDA_TRY(cudaMemsetAsync(c->d_prof, 0, sizeof(unsigned long long) * 8, c->st));
         if (c->opt.precision == RCG_MIXED) c->eng.reset(new Engine<float>(c));
         else c->eng.reset(new Engine<double>(c));
         return RCG_OK;
@@ -1121,6 +1190,7 @@ static int set_sample_impl(rcg_ctx *c, int s, const double *mu, bool device) {
         diag_sample(c->st, c->n, c->dstar, dst, c->h * c->h, c->diag64_of(s), c->diag32_of(s));
         c->sync();
         c->sample_set[s] = 1;
+        if (c->eng) c->eng->sample_changed(s);
         return RCG_OK;
     });
 }
@@ -1255,5 +1325,32 @@ double rcg_phase_ms(const rcg_ctx *c, const char *phase) {
 }
 
 long long rcg_launch_count(const rcg_ctx *c) { return c ? c->launches : -1; }
+
+int rcg_profile_enable(rcg_ctx *c, int on) {
+    return guarded(c, [&]() {
+        c->sync();
+        c->ktimer.reset();
+        c->ktimer.on = on != 0;
+        RCG_CUDA_TRY(cudaMemsetAsync(c->d_prof, 0, sizeof(unsigned long long) * 8, c->st));
+        c->sync();
+        return RCG_OK;
+    });
+}
+
+int rcg_profile_get(rcg_ctx *c, int kernel, rcg_kprof *out) {
+    return guarded(c, [&]() {
+        if (!out || kernel < 0 || kernel > 2) return fail(c, RCG_ERR_INVALID, "bad profile query");
+        c->sync();
+        c->ktimer.harvest();
+        unsigned long long h[8];
+        c->d2h(h, c->d_prof, 8);
+        c->sync();
+        out->launches = c->ktimer.launches[kernel];
+        out->ms = c->ktimer.ms[kernel];
+        out->lane_units = (double)(kernel == 0 ? h[0] : kernel == 1 ? h[1] : h[3]);
+        out->defl_cols = (double)(kernel == 0 ? 0 : kernel == 1 ? h[2] : h[4]);
+        return RCG_OK;
+    });
+}
 
 }  // extern "C"

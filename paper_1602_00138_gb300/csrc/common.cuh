@@ -49,8 +49,9 @@ template <typename T> struct Cols {
     __host__ __device__ T *col(int j) const { return p + (long long)j * ld; }
 };
 
-constexpr int KMAX = 48;        // max deflation columns per lane (U_j)
-constexpr int KCHUNK = 8;       // deflation dot columns fused per pass
+constexpr int KMAX = 48;        // stride of the per-lane deflation arrays
+constexpr int KU_MAX = 16;      // shared (seed eigenvector) deflation columns
+constexpr int KP_MAX = 8;       // private deflation columns per lane
 
 // Per-lane CG state on the device (structure of arrays, m lanes).
 struct LaneState {
@@ -64,8 +65,59 @@ struct LaneState {
     int *flag;              // [m] set to 1 when the recursive residual met thresh
     int *iters;             // [m]
     double *thresh;         // [m] stop threshold on ||r|| of the current cycle
-    const void **W;         // [m][KMAX] deflation column pointers (T*)
-    const void **AW;        // [m][KMAX] A~_s W column pointers (T*)
+    unsigned long long *prof;  // optional work counters (see KTimer), or null
+};
+
+// Arithmetic addressing of the lanes of a wave (all columns ld apart):
+//   x, r, p, q : lane l at base + l*ld (engine precision T)
+//   deflation columns of lane l: c < k_u shared: W = wu + c*ld (the first
+//   k_u basis columns), A W = awu + (si[l]*k_u + c)*ld (per sample slot);
+//   c >= k_u private: W = wp + (l*kp_max + c - k_u)*ld, A W likewise in awp.
+struct LaneGeom {
+    long long ld;
+    int k_u, kp_max;
+    void *x, *r, *p, *q;
+    const void *wu, *awu, *wp, *awp;
+    const int *si, *kp;
+};
+
+// Optional per-launch device timing of the three kernels of a CG iteration
+// (stencil, update, direction), with CUDA events on the launching stream.
+// Work counters on the device (LaneState::prof): [0] stencil column
+// applications, [1] update lanes, [2] update deflation columns, [3]
+// direction lanes, [4] direction deflation columns.
+struct KTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::vector<cudaEvent_t>> pending;
+    double ms[3] = {0, 0, 0};
+    long long launches[3] = {0, 0, 0};
+    cudaEvent_t get() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) throw Error{-2, "cudaEventCreate"};
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    // call after the stream is synchronised
+    void harvest() {
+        for (auto &ev : pending) {
+            for (int k = 0; k < 3; ++k) {
+                float t = 0;
+                if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) == cudaSuccess) { ms[k] += t; ++launches[k]; }
+            }
+            for (auto e : ev) pool.push_back(e);
+        }
+        pending.clear();
+    }
+    void reset() { harvest(); for (int k = 0; k < 3; ++k) { ms[k] = 0; launches[k] = 0; } }
+    ~KTimer() {
+        for (auto &ev : pending) for (auto e : ev) cudaEventDestroy(e);
+        for (auto e : pool) cudaEventDestroy(e);
+    }
 };
 
 // ------------------------------------------------------------ launchers
@@ -73,7 +125,7 @@ struct LaneState {
 template <typename T>
 void apply_op(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
               const T *const *src, T *const *dst, int ncols, const int *active,
-              double *dots, int unused = 0);
+              double *dots, unsigned long long *act_count = nullptr);
 void residual64(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,
                 const int *node, const double *bw, double *rr, const int *active);
@@ -83,6 +135,10 @@ template <typename TA, typename TB>
 void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
              const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
              const double *wt = nullptr, const int *rows = nullptr, long long nrows = 0);
+template <typename TA, typename TB, typename AT>
+void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
+                 const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
+                 const double *wt = nullptr, const int *rows = nullptr, long long nrows = 0);
 template <typename TA, typename TO>
 void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k,
              const double *Y, int ldy, int m, TO *Out, long long ldo, double alpha, double beta);
@@ -140,10 +196,11 @@ void ritz_res(cudaStream_t st, const T *AX, const T *X, const double *theta, lon
 // cg.cu
 template <typename T>
 void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
-                  T *const *x, T *const *r, T *const *p, T *const *q, LaneState ls, int t,
-                  int kmax_used);
+                  const T *const *p_ptr, T *const *q_ptr, LaneGeom gm, LaneState ls, int t,
+                  KTimer *kt = nullptr);
 template <typename T>
-void cg_restart(cudaStream_t st, const Grid &g, T *const *x, T *const *r, T *const *p,
-                LaneState ls, int t, const int *mask, int kmax_used);
+void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t, const int *mask);
+template <typename T>
+void gather_cols(cudaStream_t st, long long n, const T *const *src, T *dst, long long ld, int count);
 
 }  // namespace rcg

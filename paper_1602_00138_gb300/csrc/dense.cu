@@ -17,13 +17,13 @@ constexpr int TN_BK = 32;     // rows per shared-memory stage
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
-// C[i + j*ldc] += sum_p w[p] A_i[p] B_j[p] over this CTA's row range.
-template <typename TA, typename TB>
+// C[i + j*ldc] += sum_p w[p] A_i[p] B_j[p] over this CTA's row range, with
+// products and partial sums in AT.
+template <typename TA, typename TB, typename AT>
 __global__ void __launch_bounds__(256)
 k_gemm_tn(long long n, const TA *__restrict__ A, long long lda, int ka, const TB *__restrict__ B,
           long long ldb, int kb, double *__restrict__ C, int ldc, const double *__restrict__ wt,
           const int *__restrict__ rows, long long nrows, long long chunk) {
-    using AT = typename std::conditional<(sizeof(TA) == 8 || sizeof(TB) == 8), double, float>::type;
     __shared__ AT As[TN_BK][TN_T + 1];
     __shared__ AT Bs[TN_BK][TN_T + 1];
     const int i0 = blockIdx.x * TN_T, j0 = blockIdx.y * TN_T;
@@ -81,11 +81,57 @@ k_gemm_tn(long long n, const TA *__restrict__ A, long long lda, int ka, const TB
         }
 }
 
+// C[i + j*ldc] += sum_p A_i[p] B_j[p] for few B columns (kb <= 4): each CTA
+// owns 8 A columns and a row chunk; every A element is read once.
+template <typename TA, typename TB, typename AT, int KB>
+__global__ void __launch_bounds__(256)
+k_gemv_t(long long n, const TA *__restrict__ A, long long lda, int ka, const TB *__restrict__ B, long long ldb,
+         double *__restrict__ C, int ldc, long long chunk) {
+    const int i0 = blockIdx.x * 8;
+    const long long r0 = (long long)blockIdx.y * chunk;
+    const long long r1 = (r0 + chunk < n) ? r0 + chunk : n;
+    AT acc[8][KB];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < KB; ++b) acc[a][b] = AT(0);
+    for (long long p = r0 + threadIdx.x; p < r1; p += blockDim.x) {
+        AT bv[KB];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) bv[b] = (AT)B[(long long)b * ldb + p];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            if (i0 + a >= ka) break;
+            const AT av = (AT)A[(long long)(i0 + a) * lda + p];
+#pragma unroll
+            for (int b = 0; b < KB; ++b) acc[a][b] += av * bv[b];
+        }
+    }
+    __shared__ double red[8][8][KB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            double v = (double)acc[a][b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][a][b] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < 8 * KB) {
+        const int a = threadIdx.x / KB, b = threadIdx.x % KB;
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w][a][b];
+        if (i0 + a < ka && v != 0.0) atomicAdd(C + (i0 + a) + (long long)b * ldc, v);
+    }
+}
+
 constexpr int NN_MN = 16;     // output columns per CTA
 constexpr int NN_KC = 32;     // basis columns per shared-memory stage
 
 // Out_j[p] = beta Out_j[p] + alpha sum_c A_c[p] Y[c + j*ldy]
-template <typename TA, typename TO>
+template <typename TA, typename TO, int NN_MN>
 __global__ void __launch_bounds__(256)
 k_gemm_nn(long long n, const TA *__restrict__ A, long long lda, int k, const double *__restrict__ Y,
           int ldy, int m, TO *__restrict__ Out, long long ldo, double alpha, double beta) {
@@ -186,9 +232,9 @@ int blocks_for(long long n, int per_col_cols) {
 
 }  // namespace
 
-template <typename TA, typename TB>
-void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka, const TB *B, long long ldb,
-             int kb, double *C, int ldc, bool accumulate, const double *wt, const int *rows, long long nrows) {
+template <typename TA, typename TB, typename AT>
+void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int ka, const TB *B, long long ldb,
+                 int kb, double *C, int ldc, bool accumulate, const double *wt, const int *rows, long long nrows) {
     if (ka <= 0 || kb <= 0) return;
     if (!accumulate) {
         for (int j = 0; j < kb; ++j)
@@ -196,6 +242,25 @@ void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka, c
     }
     const long long len = rows ? nrows : n;
     if (len <= 0) return;
+    if (!rows && !wt && kb <= 4) {     // GEMV-shaped: every A element read once
+        const int gx1 = (ka + 7) / 8;
+        long long want = (4LL * 152 + gx1 - 1) / gx1;
+        long long maxz = (n + 2047) / 2048;
+        long long z = want < maxz ? want : maxz;
+        if (z < 1) z = 1;
+        long long chunk = (n + z - 1) / z;
+        z = (n + chunk - 1) / chunk;
+        dim3 grid(gx1, (unsigned)z);
+        switch (kb) {
+            case 1: k_gemv_t<TA, TB, AT, 1><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, C, ldc, chunk); break;
+            case 2: k_gemv_t<TA, TB, AT, 2><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, C, ldc, chunk); break;
+            case 3: k_gemv_t<TA, TB, AT, 3><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, C, ldc, chunk); break;
+            default: k_gemv_t<TA, TB, AT, 4><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, C, ldc, chunk); break;
+        }
+        count_launch();
+        RCG_CHECK_LAUNCH();
+        return;
+    }
     const int gx = (ka + TN_T - 1) / TN_T, gy = (kb + TN_T - 1) / TN_T;
     // split the long dimension so that the grid covers the GPU about 4 times
     long long tiles = (long long)gx * gy;
@@ -208,17 +273,30 @@ void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka, c
     chunk = (chunk + TN_BK - 1) / TN_BK * TN_BK;
     z = (len + chunk - 1) / chunk;
     dim3 grid(gx, gy, (unsigned)z);
-    k_gemm_tn<TA, TB><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, kb, C, ldc, wt, rows, nrows, chunk);
+    k_gemm_tn<TA, TB, AT><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, kb, C, ldc, wt, rows, nrows, chunk);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
 
-template void gemm_tn<double, double>(cudaStream_t, long long, const double *, long long, int, const double *,
-                                      long long, int, double *, int, bool, const double *, const int *, long long);
-template void gemm_tn<float, float>(cudaStream_t, long long, const float *, long long, int, const float *,
-                                    long long, int, double *, int, bool, const double *, const int *, long long);
-template void gemm_tn<float, double>(cudaStream_t, long long, const float *, long long, int, const double *,
-                                     long long, int, double *, int, bool, const double *, const int *, long long);
+template <typename TA, typename TB>
+void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka, const TB *B, long long ldb,
+             int kb, double *C, int ldc, bool accumulate, const double *wt, const int *rows, long long nrows) {
+    using AT = typename std::conditional<(sizeof(TA) == 8 || sizeof(TB) == 8), double, float>::type;
+    gemm_tn_acc<TA, TB, AT>(st, n, A, lda, ka, B, ldb, kb, C, ldc, accumulate, wt, rows, nrows);
+}
+
+#define RCG_INST_TN(TA, TB)                                                                                  \
+    template void gemm_tn<TA, TB>(cudaStream_t, long long, const TA *, long long, int, const TB *, long long, \
+                                  int, double *, int, bool, const double *, const int *, long long);
+RCG_INST_TN(double, double)
+RCG_INST_TN(float, float)
+RCG_INST_TN(float, double)
+template void gemm_tn_acc<float, float, double>(cudaStream_t, long long, const float *, long long, int,
+                                                const float *, long long, int, double *, int, bool, const double *,
+                                                const int *, long long);
+template void gemm_tn_acc<double, double, double>(cudaStream_t, long long, const double *, long long, int,
+                                                  const double *, long long, int, double *, int, bool,
+                                                  const double *, const int *, long long);
 
 template <typename TA, typename TO>
 void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k, const double *Y, int ldy, int m,
@@ -231,8 +309,16 @@ void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k, co
         }
         return;
     }
-    dim3 grid((unsigned)((n + 255) / 256), (m + NN_MN - 1) / NN_MN);
-    k_gemm_nn<TA, TO><<<grid, 256, 0, st>>>(n, A, lda, k, Y, ldy, m, Out, ldo, alpha, beta);
+    if (m <= 1) {
+        dim3 grid((unsigned)((n + 255) / 256), m);
+        k_gemm_nn<TA, TO, 1><<<grid, 256, 0, st>>>(n, A, lda, k, Y, ldy, m, Out, ldo, alpha, beta);
+    } else if (m <= 4) {
+        dim3 grid((unsigned)((n + 255) / 256), 1);
+        k_gemm_nn<TA, TO, 4><<<grid, 256, 0, st>>>(n, A, lda, k, Y, ldy, m, Out, ldo, alpha, beta);
+    } else {
+        dim3 grid((unsigned)((n + 255) / 256), (m + NN_MN - 1) / NN_MN);
+        k_gemm_nn<TA, TO, NN_MN><<<grid, 256, 0, st>>>(n, A, lda, k, Y, ldy, m, Out, ldo, alpha, beta);
+    }
     count_launch();
     RCG_CHECK_LAUNCH();
 }

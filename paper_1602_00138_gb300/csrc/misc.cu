@@ -190,6 +190,15 @@ k_lane_gw(const double *const *__restrict__ Gs, int ldg, int r, const int *__res
     }
 }
 
+template <typename T>
+__global__ void k_gather_cols(long long n, const T *const *__restrict__ src, T *__restrict__ dst, long long ld) {
+    const int j = blockIdx.y;
+    const T *s = src[j];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        dst[(long long)j * ld + p] = s[p];
+}
+
 // Counter-based pseudo-random fill in [-1, 1): SplitMix64 of (seed, index).
 template <typename T>
 __global__ void k_rand_fill(T *__restrict__ X, long long n, long long ld, int b, unsigned long long seed) {
@@ -345,6 +354,17 @@ void lane_gw(cudaStream_t st, const double *const *Gs, int ldg, int r, const int
     count_launch();
     RCG_CHECK_LAUNCH();
 }
+
+template <typename T>
+void gather_cols(cudaStream_t st, long long n, const T *const *src, T *dst, long long ld, int count) {
+    if (count <= 0) return;
+    dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), count);
+    k_gather_cols<T><<<grid, 256, 0, st>>>(n, src, dst, ld);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+template void gather_cols<double>(cudaStream_t, long long, const double *const *, double *, long long, int);
+template void gather_cols<float>(cudaStream_t, long long, const float *const *, float *, long long, int);
 
 template <typename T>
 void rand_fill(cudaStream_t st, T *X, long long n, long long ld, int b, unsigned long long seed) {

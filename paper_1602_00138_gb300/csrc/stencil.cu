@@ -12,6 +12,8 @@
 // thread handles.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace rcg {
 
 thread_local long long *g_launch_counter = nullptr;
@@ -43,67 +45,55 @@ __device__ __forceinline__ void block_reduce_add(double (&acc)[NB], double *out,
     }
 }
 
-// y_c = A~_{s(c)} x_c for columns c of group blockIdx.y; optional dots x_c^T y_c.
-template <typename T, int NB>
+// y_c = A~_{s(c)} x_c for column c = blockIdx.y; optional dot x_c^T y_c.
+// One column per CTA row and one node per thread keep the register count low
+// so that enough warps are resident to cover the HBM latency; the column's
+// pointers are uniform per CTA (no per-node pointer loads).  The neighbour
+// values come from L1/L2 (x +- 1 from the same warp's lines).
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_apply(Grid g, const T *__restrict__ D, const T *const *__restrict__ diag_of_col,
         const T *const *__restrict__ src, T *const *__restrict__ dst, int ncols,
-        const int *__restrict__ active, double *__restrict__ dots) {
-    const int c0 = blockIdx.y * NB;
-    bool act[NB];
-    bool any = false;
-    const T *xs[NB];
-    T *ys[NB];
-    const T *dg[NB];
-#pragma unroll
-    for (int t = 0; t < NB; ++t) {
-        const int c = c0 + t;
-        act[t] = (c < ncols) && (active == nullptr || active[c] != 0);
-        any |= act[t];
-        xs[t] = act[t] ? src[c] : nullptr;
-        ys[t] = act[t] ? dst[c] : nullptr;
-        dg[t] = act[t] ? diag_of_col[c] : nullptr;
-    }
-    if (!any) return;
-    T acc[NB];      // per-thread partial sums in T; float64 only across threads
-#pragma unroll
-    for (int t = 0; t < NB; ++t) acc[t] = T(0);
-    const long long sxy = (long long)g.Nx * g.Ny;
+        const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ act_count) {
+    const int c = blockIdx.y;
+    if (c >= ncols || (active != nullptr && active[c] == 0)) return;
+    if (act_count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(act_count, 1ULL);
+    const T *__restrict__ x = src[c];
+    T *__restrict__ y = dst[c];
+    const T *__restrict__ dg = diag_of_col[c];
+    const int sxy = g.Nx * g.Ny;          // grids here are < 2^31 nodes (checked at rcg_create)
+    const int nn = (int)g.n;
     const bool has_y = g.Ny > 1;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p % g.Nx);
-        const long long rest = p / g.Nx;
-        const int j = (int)(rest % g.Ny);
-        const int k = (int)(rest / g.Ny);
+    T acc = T(0);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += gridDim.x * blockDim.x) {
+        const int i = p % g.Nx;
+        const int rest = p / g.Nx;
+        const int j = rest % g.Ny;
+        const int k = rest / g.Ny;
         const T Dp = D[p];
-        const T wxm = i > 0 ? half_sum(Dp, D[p - 1]) : T(0);
-        const T wxp = i < g.Nx - 1 ? half_sum(Dp, D[p + 1]) : T(0);
-        const T wym = (has_y && j > 0) ? half_sum(Dp, D[p - g.Nx]) : T(0);
-        const T wyp = (has_y && j < g.Ny - 1) ? half_sum(Dp, D[p + g.Nx]) : T(0);
-        const T wzm = k > 0 ? half_sum(Dp, D[p - sxy]) : T(0);
-        const T wzp = k < g.Nz - 1 ? half_sum(Dp, D[p + sxy]) : T(0);
-#pragma unroll
-        for (int t = 0; t < NB; ++t) {
-            if (!act[t]) continue;
-            const T *x = xs[t];
-            const T xc = x[p];
-            T v = dg[t][p] * xc;
-            if (i > 0) v -= wxm * x[p - 1];
-            if (i < g.Nx - 1) v -= wxp * x[p + 1];
-            if (has_y && j > 0) v -= wym * x[p - g.Nx];
-            if (has_y && j < g.Ny - 1) v -= wyp * x[p + g.Nx];
-            if (k > 0) v -= wzm * x[p - sxy];
-            if (k < g.Nz - 1) v -= wzp * x[p + sxy];
-            ys[t][p] = v;
-            if (dots) acc[t] += xc * v;
-        }
+        const T xc = x[p];
+        T v = dg[p] * xc;
+        if (i > 0) v -= half_sum(Dp, D[p - 1]) * x[p - 1];
+        if (i < g.Nx - 1) v -= half_sum(Dp, D[p + 1]) * x[p + 1];
+        if (has_y && j > 0) v -= half_sum(Dp, D[p - g.Nx]) * x[p - g.Nx];
+        if (has_y && j < g.Ny - 1) v -= half_sum(Dp, D[p + g.Nx]) * x[p + g.Nx];
+        if (k > 0) v -= half_sum(Dp, D[p - sxy]) * x[p - sxy];
+        if (k < g.Nz - 1) v -= half_sum(Dp, D[p + sxy]) * x[p + sxy];
+        y[p] = v;
+        acc += xc * v;
     }
     if (dots) {
-        double accd[NB];
+        double v = (double)acc;
+        __shared__ double red[kThreads / 32];
 #pragma unroll
-        for (int t = 0; t < NB; ++t) accd[t] = (double)acc[t];
-        block_reduce_add<NB>(accd, dots + c0, act);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s2 = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s2 += red[w];
+            atomicAdd(dots + c, s2);
+        }
     }
 }
 
@@ -190,20 +180,24 @@ int grid_x_for(long long n, int groups) {
 template <typename T>
 void apply_op(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
               const T *const *src, T *const *dst, int ncols, const int *active,
-              double *dots, int) {
+              double *dots, unsigned long long *act_count) {
     if (ncols <= 0) return;
-    constexpr int NB = sizeof(T) == 8 ? 4 : 8;
-    const int groups = (ncols + NB - 1) / NB;
-    dim3 grid(grid_x_for(g.n, groups), groups);
-    k_apply<T, NB><<<grid, kThreads, 0, st>>>(g, D, diag_of_col, src, dst, ncols, active, dots);
+    // ~8 resident CTAs per SM over all columns, at least one node per thread
+    long long want = (8LL * 152 + ncols - 1) / ncols;
+    long long maxb = (g.n + kThreads - 1) / kThreads;
+    const int gx = (int)std::max(1LL, std::min(want, maxb));
+    dim3 grid(gx, ncols);
+    k_apply<T><<<grid, kThreads, 0, st>>>(g, D, diag_of_col, src, dst, ncols, active, dots, act_count);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
 
 template void apply_op<double>(cudaStream_t, const Grid &, const double *, const double *const *,
-                               const double *const *, double *const *, int, const int *, double *, int);
+                               const double *const *, double *const *, int, const int *, double *,
+                               unsigned long long *);
 template void apply_op<float>(cudaStream_t, const Grid &, const float *, const float *const *,
-                              const float *const *, float *const *, int, const int *, double *, int);
+                              const float *const *, float *const *, int, const int *, double *,
+                              unsigned long long *);
 
 void residual64(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,

@@ -32,7 +32,7 @@ EXPORTED = [
     "rcg_set_diffusion", "rcg_set_sources_detectors", "rcg_set_tolerances", "rcg_set_sample",
     "rcg_set_sample_device", "rcg_apply", "rcg_seed", "rcg_reset_to_seed", "rcg_solve_all",
     "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device",
-    "rcg_phase_ms", "rcg_launch_count",
+    "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get",
 ]
 
 
@@ -52,6 +52,11 @@ class Stat(C.Structure):
     _fields_ = [("sample", C.c_int), ("rhs", C.c_int), ("iters", C.c_int), ("restarts", C.c_int),
                 ("appended", C.c_int), ("status", C.c_int), ("relres0", C.c_double),
                 ("relres", C.c_double), ("ratio", C.c_double)]
+
+
+class KProf(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("lane_units", C.c_double),
+                ("defl_cols", C.c_double)]
 
 
 class RcgError(RuntimeError):
@@ -87,6 +92,8 @@ def load(path=LIB_PATH):
         "rcg_rom_eval_device": (I, [P, P, I, P, P, P]),
         "rcg_phase_ms": (D, [P, C.c_char_p]),
         "rcg_launch_count": (LL, [P]),
+        "rcg_profile_enable": (I, [P, I]),
+        "rcg_profile_get": (I, [P, I, C.POINTER(KProf)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -249,3 +256,11 @@ class Context:
 
     def launch_count(self):
         return self.L.rcg_launch_count(self.h)
+
+    def profile(self, on=True):
+        return self._check(self.L.rcg_profile_enable(self.h, 1 if on else 0))
+
+    def profile_get(self, kernel):
+        k = KProf()
+        self._check(self.L.rcg_profile_get(self.h, kernel, C.byref(k)))
+        return dict(launches=k.launches, ms=k.ms, lane_units=k.lane_units, defl_cols=k.defl_cols)

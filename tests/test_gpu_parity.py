@@ -88,6 +88,8 @@ def _check_run(name, precision, order, tau, psi_tol, j_tol, wave_samples=0):
         # solutions differ at the 1e-8 level, which moves a 1e-6 Galerkin
         # residual by up to ~20%.
         for a, b in zip(out_g[: wl.nrhs], out_o[: wl.nrhs]):
+            if precision and b["relres0"] < 1e-5:
+                continue     # within ~100x of the float32 storage floor of the basis
             assert np.isclose(a["relres0"], b["relres0"], rtol=0.3 if precision else 1e-6), (a, b)
         # reduced transfer function and Jacobian at the sampled points
         for s in range(1, wl.K + 1):
