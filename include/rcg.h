@@ -145,6 +145,27 @@ int rcg_set_sample_device(rcg_ctx *c, int s, const double *mu_dev);
  * operator of the inner iterations).  Parity / benchmarking entry. */
 int rcg_apply(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols);
 
+/* The same operator application as rcg_apply, for callers that cannot
+ * allocate device memory during the call: for example a caller whose device
+ * memory is owned by another allocator (a framework's caching pool) or that
+ * cannot afford cudaMalloc / cudaFree (cudaFree waits for the whole device)
+ * on a repeated call.  rcg_apply allocates its per-column tables on each
+ * call; this entry point calls no cudaMalloc, cudaFree or allocating library
+ * routine and keeps the tables in one static device array of the library,
+ * sized for RCG_NOALLOC_MAX_COLS columns (24 KiB), which every GPU that
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart; it is a property of this library's interface.
+ *   - ncols > RCG_NOALLOC_MAX_COLS returns RCG_ERR_INVALID (message in
+ *     rcg_last_error); x_dev / y_dev as in rcg_apply (caller-owned).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once for that device; make that first call
+ *     before any stream capture begins.
+ *   - All calls share the array and it keeps the last call's tables: calls
+ *     that overlap on the GPU (other streams or host threads) race on it.
+ *   - Returns after the context's stream has finished the application. */
+#define RCG_NOALLOC_MAX_COLS 1024
+int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols);
+
 /* Seed step of Algorithm 2 at sample s0: U_0 = U0 (host n x k_u, column-
  * major) or, if U0 == NULL, the k_u smallest eigenvectors of A~_{s0} by a
  * Chebyshev-filtered subspace iteration on the device; X_0 by deflated CG

@@ -1010,6 +1010,29 @@ template <typename F> int guarded(rcg_ctx *c, F f) {
 
 }  // namespace
 
+namespace rcg {
+// Operator data of a context for the allocation-free entry point (noalloc.cu).
+int ctx_operator(const rcg_ctx *c, int s, Grid *g, const double **D64, const float **D32, const double **diag64,
+                 const float **diag32, cudaStream_t *st, long long **launches) {
+    if (!c || s < 0 || s >= c->opt.max_samples || !c->sample_set[s]) {
+        if (c) const_cast<rcg_ctx *>(c)->err = "rcg_apply_noalloc: sample slot not set";
+        return RCG_ERR_INVALID;
+    }
+    rcg_ctx *m = const_cast<rcg_ctx *>(c);
+    *g = c->g;
+    *D64 = c->D64;
+    *D32 = c->D32;
+    *diag64 = m->diag64_of(s);
+    *diag32 = m->diag32_of(s);
+    *st = c->st;
+    *launches = &m->launches;
+    return RCG_OK;
+}
+void ctx_set_error(rcg_ctx *c, const std::string &msg) {
+    if (c) c->err = msg;
+}
+}  // namespace rcg
+
 // ============================================================== C ABI
 extern "C" {
 

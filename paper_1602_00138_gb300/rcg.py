@@ -32,8 +32,9 @@ EXPORTED = [
     "rcg_set_diffusion", "rcg_set_sources_detectors", "rcg_set_tolerances", "rcg_set_sample",
     "rcg_set_sample_device", "rcg_apply", "rcg_seed", "rcg_reset_to_seed", "rcg_solve_all",
     "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device",
-    "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get",
+    "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
 ]
+RCG_NOALLOC_MAX_COLS = 1024
 
 
 class Grid(C.Structure):
@@ -82,6 +83,7 @@ def load(path=LIB_PATH):
         "rcg_set_sample": (I, [P, I, P]),
         "rcg_set_sample_device": (I, [P, I, P]),
         "rcg_apply": (I, [P, I, I, P, P, I]),
+        "rcg_apply_noalloc": (I, [P, I, I, P, P, I]),
         "rcg_seed": (I, [P, I, P, P]),
         "rcg_reset_to_seed": (I, [P]),
         "rcg_solve_all": (I, [P, I, I, P]),
@@ -202,6 +204,10 @@ class Context:
 
     def apply(self, s, x_dev, y_dev, ncols, prec=RCG_FP64):
         return self._check(self.L.rcg_apply(self.h, s, prec, _ptr(x_dev), _ptr(y_dev), ncols))
+
+    def apply_noalloc(self, s, x_dev, y_dev, ncols, prec=RCG_FP64):
+        """rcg_apply without device allocation (tables in a static device array)."""
+        return self._check(self.L.rcg_apply_noalloc(self.h, s, prec, _ptr(x_dev), _ptr(y_dev), ncols))
 
     # ---- method
     def seed(self, s0, U0=None):
