@@ -187,7 +187,7 @@ def run_ours(args, rank, world, torch):
         launches = ctx.launch_count() - l0
         prof = None
         if profile:
-            prof = [ctx.profile_get(k) for k in range(3)]
+            prof = [ctx.profile_get(k) for k in range(5)]
             ctx.profile(False)
         for s in all_stats:
             check(s)
@@ -210,22 +210,25 @@ def run_ours(args, rank, world, torch):
     mean_iters = float(np.mean([s["iters"] for s in all_stats[-1]]))
 
     # ---- roofline of the dominant inner-CG kernel (device events over the timed region)
-    names = ["k_apply<float> (stencil)", "k_update<float>", "k_direction<float>"]
+    names = ["k_stencil4 (q = A p)", "k_update4 (x, r)", "k_u0dots (shared deflation dots)", "k_mu (lane scalars)",
+             "k_direction4 (p)"]
     s_bytes = 4
     # Algorithmic bytes (unique DRAM bytes a launch must move), per node per active lane:
-    #   stencil   read p, write q; D and the sample diagonal once per sample: 2 + 2/nrhs
-    #   update    read x, p, r, q, write x, r, read the lane's private A~W columns,
-    #             the k_u shared A~_s U_0 columns once per sample: 6 + k_priv + k_u/nrhs
-    #   direction read r, p, write p, private W columns, shared U_0 once: 3 + k_priv + k_u/nrhs
-    kdom = max(range(3), key=lambda k: prof[k]["ms"])
+    #   stencil    read p, write q; D and the sample diagonal once per sample: 2 + 2/nrhs
+    #   update     read x, p, r, q, write x, r, the lane's private A~W columns: 6 + k_priv
+    #   u0dots     read r; the k_u shared A~_s U_0 columns once per tile of 32 lanes: 1 + k_u/32
+    #   direction  read r, p, write p, private W columns, U_0 once per tile: 3 + k_priv + k_u/32
+    kdom = max((0, 1, 2, 4), key=lambda k: prof[k]["ms"])
     P = prof[kdom]
     A = P["lane_units"]
     if kdom == 0:
         alg = A * n * (2 + 2 / wl.nrhs) * s_bytes
+    elif kdom == 2:
+        alg = A * n * (1 + wl.k_u / 32) * s_bytes
     else:
         base = 6 if kdom == 1 else 3
         kpriv = P["defl_cols"] - wl.k_u * A
-        alg = ((base + wl.k_u / wl.nrhs) * A + kpriv) * n * s_bytes
+        alg = ((base + (0 if kdom == 1 else wl.k_u / 32)) * A + kpriv) * n * s_bytes
     per_launch_bytes = alg / max(P["launches"], 1)
     per_launch_s = P["ms"] / 1e3 / max(P["launches"], 1)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -237,8 +240,8 @@ def run_ours(args, rank, world, torch):
     if os.path.exists(tr_path):
         tr = json.load(open(tr_path))
         src = open(os.path.join(ROOT, "paper_1602_00138_gb300", "csrc",
-                                "stencil.cu" if kdom == 0 else "cg.cu"), "rb").read()
-        ent = tr.get(["stencil", "update", "direction"][kdom])
+                                "cg4.cu"), "rb").read()
+        ent = tr.get(["stencil", "update", "u0dots", "mu", "direction"][kdom])
         if ent and ent.get("source_sha256") == hashlib.sha256(src).hexdigest():
             traffic = ent["dram_bytes_per_lane_node"] * n * P["lane_units"] / max(P["launches"], 1)
     roofline = {"bound": "hbm", "kernel": names[kdom], "achieved": round(achieved, 1), "peak": peak,
@@ -246,7 +249,7 @@ def run_ours(args, rank, world, torch):
                 "peak_source": "measured" if peaks else "fallback",
                 "launches": P["launches"], "avg_launch_us": round(per_launch_s * 1e6, 2),
                 "alg_bytes_per_launch": round(per_launch_bytes),
-                "kernels_ms": {names[k]: round(prof[k]["ms"], 3) for k in range(3)}}
+                "kernels_ms": {names[k]: round(prof[k]["ms"], 3) for k in range(5)}}
 
     if args.ncu_region:
         ctx.close()

@@ -212,14 +212,17 @@ double rcg_phase_ms(const rcg_ctx *c, const char *phase);
 /* Number of kernel launches issued by this context since creation. */
 long long rcg_launch_count(const rcg_ctx *c);
 
-/* Device-side profile of the three kernels of one inner CG iteration
- * (kernel 0: stencil q = A~ p with the fused p^T q; 1: update of x, r with
- * the fused r^T r and (A~ U_j)^T r; 2: direction p = r + beta p - U_j mu).
+/* Device-side profile of the kernels of one inner CG iteration (kernel
+ * 0: stencil q = A~ p with the fused p^T q; 1: update of x, r with the fused
+ * r^T r and private (A~ U_j)^T r; 2: the shared (A~ U_0)^T r dots; 3: the
+ * per-lane scalars (decision, beta, mu); 4: direction p = r + beta p - U_j mu;
+ * the float64 path has no separate kernels 2 and 3).
  * rcg_profile_enable(c, 1) resets and starts it (CUDA events around every
  * launch on the context's stream, plus device work counters); 0 stops it.
  * rcg_profile_get fills: launches, total device ms, lane_units (sum over
- * launches of the active right-hand-side lanes it processed) and defl_cols
- * (sum over those lanes of their recycle-space columns). */
+ * launches of the active right-hand-side lanes: stencil columns for 0,
+ * update lanes for 1, direction lanes for 2-4) and defl_cols (sum over those
+ * lanes of their recycle-space columns). */
 typedef struct {
     long long launches;
     double    ms;

@@ -143,6 +143,8 @@ struct Engine : EngineBase {
     int *d_spec = nullptr, *d_si = nullptr, *d_kp = nullptr;
     double **d_sx = nullptr, **d_gsl = nullptr;
     T *wpb = nullptr;                  // private deflation columns, [m][kp_max]
+    float *mu_f = nullptr, *beta_f = nullptr;      // per-lane mu, beta of the float32 iteration
+    int *d_alist = nullptr, *d_tlane = nullptr, *d_tsi = nullptr, *d_tcnt = nullptr;
     double *Yb = nullptr;
     // deflation A W buffers
     T *au0 = nullptr;
@@ -186,7 +188,8 @@ struct Engine : EngineBase {
         if (m <= mcap) return;
         for (void *p : std::vector<void *>{x64, xc, rv, pv, qv, ls.rr, ls.pq, ls.wv, ls.gw, ls.kdef, ls.active, ls.flag,
                                            ls.iters, ls.thresh, d_mask, d_lnode, d_list, d_lw, d_rr,
-                                           p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb, d_si, d_kp})
+                                           p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb, d_si, d_kp,
+                                           mu_f, beta_f, d_alist, d_tlane, d_tsi, d_tcnt})
             c->release(p);
         mcap = m;
         x64 = c->alloc<double>((size_t)m * ld);
@@ -206,6 +209,12 @@ struct Engine : EngineBase {
         ls.thresh = c->alloc<double>(m);
         d_si = c->alloc<int>(m);
         d_kp = c->alloc<int>(m);
+        mu_f = c->alloc<float>((size_t)m * KMAX);
+        beta_f = c->alloc<float>(m);
+        d_alist = c->alloc<int>(m);
+        d_tlane = c->alloc<int>((size_t)m * 32);
+        d_tsi = c->alloc<int>(m);
+        d_tcnt = c->alloc<int>(m);
         d_mask = c->alloc<int>(m);
         d_lnode = c->alloc<int>(m);
         d_list = c->alloc<int>(m);
@@ -627,11 +636,41 @@ struct Engine : EngineBase {
             cg_restart<T>(st, g, gm, ls, t, d_mask);
             const int chunk = m > 1 ? 8 : 12;
             std::vector<int> flag_h(m), active_h(m);
+            // active lanes (not yet done) and tiles of <= 32 of them per sample slot
+            const bool vec = mixed && cg4_supported(g);
+            LaneList ll{d_alist, 0, d_tlane, d_tsi, d_tcnt, 0};
+            auto build_list = [&]() {
+                std::vector<int> al, tl, tsi, tcnt;
+                for (int l = 0; l < m; ++l)
+                    if (act[l] && !done[l]) al.push_back(l);
+                for (size_t q = 0; q < al.size();) {
+                    const int s0 = si[al[q]];
+                    int cnt = 0;
+                    const size_t base = tl.size();
+                    tl.resize(base + 32, -1);
+                    while (q < al.size() && cnt < 32 && si[al[q]] == s0) tl[base + cnt++] = al[q++];
+                    tsi.push_back(s0);
+                    tcnt.push_back(cnt);
+                }
+                ll.na = (int)al.size();
+                ll.ntiles = (int)tcnt.size();
+                if (ll.na) {
+                    c->h2d(d_alist, al.data(), al.size());
+                    c->h2d(d_tlane, tl.data(), tl.size());
+                    c->h2d(d_tsi, tsi.data(), tsi.size());
+                    c->h2d(d_tcnt, tcnt.data(), tcnt.size());
+                }
+            };
+            if (vec) build_list();
             while (true) {
                 for (int i = 0; i < chunk; ++i) {
                     ++t;
-                    cg_iteration<T>(st, g, D, (const T *const *)p_diag, (const T *const *)p_p, p_q, gm, ls, t,
-                                    &c->ktimer);
+                    if (vec)
+                        cg_iteration4(st, g, (const float *)D, (const float *const *)p_diag, (const float *const *)p_p,
+                                      (float *const *)p_q, gm, ls, ll, t, mu_f, beta_f, &c->ktimer);
+                    else
+                        cg_iteration<T>(st, g, D, (const T *const *)p_diag, (const T *const *)p_p, p_q, gm, ls, t,
+                                        &c->ktimer);
                 }
                 c->d2h(flag_h.data(), ls.flag, m);
                 c->d2h(active_h.data(), ls.active, m);
@@ -680,6 +719,7 @@ struct Engine : EngineBase {
                 for (int l = 0; l < m; ++l)
                     if (act[l] && !done[l]) any = true;
                 if (!any) break;
+                if (vec) build_list();
             }
             c->d2h(iters_h.data(), ls.iters, m);
             c->sync();
@@ -1362,7 +1402,7 @@ int rcg_profile_enable(rcg_ctx *c, int on) {
 
 int rcg_profile_get(rcg_ctx *c, int kernel, rcg_kprof *out) {
     return guarded(c, [&]() {
-        if (!out || kernel < 0 || kernel > 2) return fail(c, RCG_ERR_INVALID, "bad profile query");
+        if (!out || kernel < 0 || kernel >= KTimer::NK) return fail(c, RCG_ERR_INVALID, "bad profile query");
         c->sync();
         c->ktimer.harvest();
         unsigned long long h[8];
@@ -1370,6 +1410,7 @@ int rcg_profile_get(rcg_ctx *c, int kernel, rcg_kprof *out) {
         c->sync();
         out->launches = c->ktimer.launches[kernel];
         out->ms = c->ktimer.ms[kernel];
+        // stencil: column applications; update: lanes; the other three: direction lanes
         out->lane_units = (double)(kernel == 0 ? h[0] : kernel == 1 ? h[1] : h[3]);
         out->defl_cols = (double)(kernel == 0 ? 0 : kernel == 1 ? h[2] : h[4]);
         return RCG_OK;

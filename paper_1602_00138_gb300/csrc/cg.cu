@@ -296,25 +296,19 @@ template <typename T>
 void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col, const T *const *p_ptr,
                   T *const *q_ptr, LaneGeom gm, LaneState ls, int t, KTimer *kt) {
     const int sprev = (t - 1) % 3, scur = t % 3, snext = (t + 1) % 3, spq = t % 2, sw = t % 2;
-    std::vector<cudaEvent_t> ev;
-    if (kt && kt->on) {
-        for (int k = 0; k < 4; ++k) ev.push_back(kt->get());
-        RCG_CUDA_TRY(cudaEventRecord(ev[0], st));
-    }
+    const bool tm = kt && kt->on;
+    cudaEvent_t e = tm ? kt->start(st) : nullptr;
     apply_op<T>(st, g, D, diag_of_col, p_ptr, q_ptr, ls.m, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
-    if (!ev.empty()) RCG_CUDA_TRY(cudaEventRecord(ev[1], st));
+    if (tm) { kt->stop(0, e, st); e = kt->start(st); }
     dim3 grid(grid_x(g.n, ls.m), ls.m);
     k_update<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, sprev, scur, spq, sw);
     count_launch();
     RCG_CHECK_LAUNCH();
-    if (!ev.empty()) RCG_CUDA_TRY(cudaEventRecord(ev[2], st));
+    if (tm) { kt->stop(1, e, st); e = kt->start(st); }
     k_direction<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ls.active, sprev, scur, snext, sw, 0);
     count_launch();
     RCG_CHECK_LAUNCH();
-    if (!ev.empty()) {
-        RCG_CUDA_TRY(cudaEventRecord(ev[3], st));
-        kt->pending.push_back(ev);
-    }
+    if (tm) kt->stop(4, e, st);
 }
 
 // (Re)start the masked lanes at iteration number t: given r (the residual of

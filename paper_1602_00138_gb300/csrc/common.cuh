@@ -81,17 +81,20 @@ struct LaneGeom {
     const int *si, *kp;
 };
 
-// Optional per-launch device timing of the three kernels of a CG iteration
-// (stencil, update, direction), with CUDA events on the launching stream.
-// Work counters on the device (LaneState::prof): [0] stencil column
-// applications, [1] update lanes, [2] update deflation columns, [3]
-// direction lanes, [4] direction deflation columns.
+// Optional per-launch device timing of the kernels of a CG iteration, with
+// CUDA events on the launching stream.  Slots: 0 stencil, 1 update, 2 shared
+// deflation dots, 3 per-lane scalars, 4 direction.  Work counters on the
+// device (LaneState::prof): [0] stencil column applications, [1] update
+// lanes, [2] update deflation columns, [3] direction lanes, [4] direction
+// deflation columns.
 struct KTimer {
+    static constexpr int NK = 5;
+    struct Rec { int slot; cudaEvent_t a, b; };
     bool on = false;
     std::vector<cudaEvent_t> pool;
-    std::vector<std::vector<cudaEvent_t>> pending;
-    double ms[3] = {0, 0, 0};
-    long long launches[3] = {0, 0, 0};
+    std::vector<Rec> pending;
+    double ms[NK] = {0, 0, 0, 0, 0};
+    long long launches[NK] = {0, 0, 0, 0, 0};
     cudaEvent_t get() {
         if (pool.empty()) {
             cudaEvent_t e;
@@ -102,22 +105,41 @@ struct KTimer {
         pool.pop_back();
         return e;
     }
+    // bracket a launch: e = start(st) before it, stop(slot, e, st) after it
+    cudaEvent_t start(cudaStream_t st) {
+        cudaEvent_t e = get();
+        if (cudaEventRecord(e, st) != cudaSuccess) throw Error{-2, "cudaEventRecord"};
+        return e;
+    }
+    void stop(int slot, cudaEvent_t a, cudaStream_t st) {
+        cudaEvent_t b = get();
+        if (cudaEventRecord(b, st) != cudaSuccess) throw Error{-2, "cudaEventRecord"};
+        pending.push_back(Rec{slot, a, b});
+    }
     // call after the stream is synchronised
     void harvest() {
-        for (auto &ev : pending) {
-            for (int k = 0; k < 3; ++k) {
-                float t = 0;
-                if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) == cudaSuccess) { ms[k] += t; ++launches[k]; }
-            }
-            for (auto e : ev) pool.push_back(e);
+        for (auto &r : pending) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.slot] += t; ++launches[r.slot]; }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
         }
         pending.clear();
     }
-    void reset() { harvest(); for (int k = 0; k < 3; ++k) { ms[k] = 0; launches[k] = 0; } }
+    void reset() { harvest(); for (int k = 0; k < NK; ++k) { ms[k] = 0; launches[k] = 0; } }
     ~KTimer() {
-        for (auto &ev : pending) for (auto e : ev) cudaEventDestroy(e);
+        for (auto &r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (auto e : pool) cudaEventDestroy(e);
     }
+};
+
+// Active lanes of a wave: `alist` (na lane indices, ascending) and tiles of
+// at most 32 of them sharing a sample slot (tile_lane [ntiles][32]).
+struct LaneList {
+    const int *alist;
+    int na;
+    const int *tile_lane, *tile_si, *tile_cnt;
+    int ntiles;
 };
 
 // ------------------------------------------------------------ launchers
@@ -192,6 +214,12 @@ void gershgorin(cudaStream_t st, const Grid &g, const double *D, const double *d
 template <typename T>
 void ritz_res(cudaStream_t st, const T *AX, const T *X, const double *theta, long long n, long long ld,
               int b, double *res2);
+
+// cg4.cu (float32, Nx % 4 == 0)
+bool cg4_supported(const Grid &g);
+void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *const *diag_of_col,
+                   const float *const *p_ptr, float *const *q_ptr, LaneGeom gm, LaneState ls, LaneList ll, int t,
+                   float *mu, float *beta, KTimer *kt);
 
 // cg.cu
 template <typename T>

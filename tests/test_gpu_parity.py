@@ -104,7 +104,7 @@ def _check_run(name, precision, order, tau, psi_tol, j_tol, wave_samples=0):
         ctx.close()
 
 
-@pytest.mark.parametrize("name", ["t2d_24", "t3d_12", "t2d_37"])
+@pytest.mark.parametrize("name", ["t2d_24", "t3d_12", "t2d_37", "t3d_32"])
 def test_fp64_sequential_matches_oracle(torch_cuda, name):
     from paper_1602_00138_gb300 import rcg
     ctx, out_g, out_o = _check_run(name, rcg.RCG_FP64, rcg.RCG_SEQUENTIAL, 1e-12, 1e-8, 1e-7)
@@ -119,8 +119,10 @@ def test_fp64_wave_matches_oracle(torch_cuda, name):
     _check_run(name, rcg.RCG_FP64, rcg.RCG_WAVE, 1e-9, 1e-8, 1e-7)
 
 
-@pytest.mark.parametrize("name", ["t3d_21", "t3d_33"])
+@pytest.mark.parametrize("name", ["t3d_21", "t3d_33", "t3d_32", "t2d_40"])
 def test_mixed_wave_matches_oracle(torch_cuda, name):
+    # t3d_32 and t2d_40 (Nx % 4 == 0) run the float4 inner iteration; the
+    # others the scalar one
     from paper_1602_00138_gb300 import rcg
     _check_run(name, rcg.RCG_MIXED, rcg.RCG_WAVE, 1e-6, 1e-6, 1e-5)
 
