@@ -108,7 +108,7 @@ typedef struct {
 
 /* Fill *o with defaults: FP64, sequential, tau_rank 1e-12, k_u 10,
  * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-5,
- * check_refine 0 (FP64) / 2 (mixed, set by rcg_create), keep_solutions 0,
+ * check_refine 0, keep_solutions 0,
  * seed_degree 0 (automatic). */
 void rcg_options_default(rcg_options *o);
 

@@ -328,6 +328,15 @@ struct Engine : EngineBase {
         c->sync();
     }
 
+    // Out = V Y (+ beta Out) with float64 accuracy: V is float64 in RCG_FP64; in
+    // RCG_MIXED the float32 basis is lifted with double-float accumulation.
+    void lift(const T *Vb, int k, const double *Y, int ldy, int m, double *Out, long long ldo, double beta) {
+        if (mixed)
+            gemm_nn_df(st, n, (const float *)Vb, ld, k, Y, ldy, m, Out, ldo, beta);
+        else
+            gemm_nn<T, double>(st, n, Vb, ld, k, Y, ldy, m, Out, ldo, 1.0, beta);
+    }
+
     // ----------------------------------------------------- Galerkin matrices
     double *delta_weights(int s) {
         if (!dw[s]) dw[s] = c->alloc<double>(ld);
@@ -486,7 +495,7 @@ struct Engine : EngineBase {
                 trsv_lower_batched(st, L, rmax, r, Yb + (long long)l0 * rmax, rmax, l1 - l0, false);
                 trsv_lower_batched(st, L, rmax, r, Yb + (long long)l0 * rmax, rmax, l1 - l0, true);
             }
-            gemm_nn<T, double>(st, n, Vc, ld, r, Yb, rmax, m, x64, ld, 1.0, first ? 0.0 : 1.0);
+            lift(Vc, r, Yb, rmax, m, x64, ld, first ? 0.0 : 1.0);
         };
         auto residual = [&](std::vector<double> &rr_h, const int *mask) {
             RCG_CUDA_TRY(cudaMemsetAsync(d_rr, 0, sizeof(double) * m, st));
@@ -633,16 +642,15 @@ struct Engine : EngineBase {
             RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * m, st));
             ls.prof = c->ktimer.on ? c->d_prof : nullptr;
             int t = 0;
-            cg_restart<T>(st, g, gm, ls, t, d_mask);
             const int chunk = m > 1 ? 8 : 12;
             std::vector<int> flag_h(m), active_h(m);
-            // active lanes (not yet done) and tiles of <= 32 of them per sample slot
+            // lanes selected by `sel` and tiles of <= 32 of them per sample slot
             const bool vec = mixed && cg4_supported(g);
             LaneList ll{d_alist, 0, d_tlane, d_tsi, d_tcnt, 0};
-            auto build_list = [&]() {
+            auto build_list_of = [&](const std::vector<int> &sel) {
                 std::vector<int> al, tl, tsi, tcnt;
                 for (int l = 0; l < m; ++l)
-                    if (act[l] && !done[l]) al.push_back(l);
+                    if (sel[l]) al.push_back(l);
                 for (size_t q = 0; q < al.size();) {
                     const int s0 = si[al[q]];
                     int cnt = 0;
@@ -661,6 +669,22 @@ struct Engine : EngineBase {
                     c->h2d(d_tcnt, tcnt.data(), tcnt.size());
                 }
             };
+            auto build_list = [&]() {
+                std::vector<int> sel(m, 0);
+                for (int l = 0; l < m; ++l) sel[l] = act[l] && !done[l];
+                build_list_of(sel);
+            };
+            // (re)start the lanes flagged in `mask_h` (also uploaded to d_mask)
+            auto restart = [&](const std::vector<int> &mask_h) {
+                if (vec) {
+                    lane_zero(st, ls, d_mask);
+                    build_list_of(mask_h);
+                    cg_restart4(st, g, gm, ls, ll, t, mu_f, beta_f);
+                } else {
+                    cg_restart<T>(st, g, gm, ls, t, d_mask);
+                }
+            };
+            restart(act);
             if (vec) build_list();
             while (true) {
                 for (int i = 0; i < chunk; ++i) {
@@ -712,7 +736,7 @@ struct Engine : EngineBase {
                         for (int l : Rl) rmask[l] = 1;
                         c->h2d(ls.thresh, thr.data(), m);
                         c->h2d(d_mask, rmask.data(), m);
-                        cg_restart<T>(st, g, gm, ls, t, d_mask);
+                        restart(rmask);
                     }
                 }
                 bool any = false;
@@ -1009,8 +1033,8 @@ struct Engine : EngineBase {
         gemm_tn<double, double>(st, r, Crm, r, nd, Xr, r, ns, Psi, nd, false);
         if (J && dmu) {
             if (!VX) { VX = c->alloc<double>((size_t)ns * ld); VZ = c->alloc<double>((size_t)nd * ld); }
-            gemm_nn<T, double>(st, n, V, ld, r, Xr, r, ns, VX, ld, 1.0, 0.0);
-            gemm_nn<T, double>(st, n, V, ld, r, Zr, r, nd, VZ, ld, 1.0, 0.0);
+            lift(V, r, Xr, r, ns, VX, ld, 0.0);
+            lift(V, r, Zr, r, nd, VZ, ld, 0.0);
             for (int k = 0; k < nparam; ++k) {
                 scaled_diff(st, n, dmu + (long long)k * n, nullptr, -c->h * c->h, wtmp);
                 gemm_tn<double, double>(st, n, VZ, ld, nd, VX, ld, ns, J + (long long)k * nd * ns, nd, false, wtmp);
@@ -1128,7 +1152,7 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
         delete c;
         return RCG_ERR_INVALID;
     }
-    if (c->opt.check_refine < 0) c->opt.check_refine = c->opt.precision == RCG_MIXED ? 2 : 0;
+    if (c->opt.check_refine < 0) c->opt.check_refine = 0;
     if (!(c->opt.inner_eta > 0)) c->opt.inner_eta = 1e-4;
     c->st = (cudaStream_t)stream;
     const int N = gr->N;

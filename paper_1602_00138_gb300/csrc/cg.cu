@@ -337,6 +337,12 @@ void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t
     RCG_CHECK_LAUNCH();
 }
 
+void lane_zero(cudaStream_t st, LaneState ls, const int *mask) {
+    k_lane_zero<<<ls.m, 64, 0, st>>>(ls, mask);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
 template void cg_iteration<double>(cudaStream_t, const Grid &, const double *, const double *const *,
                                    const double *const *, double *const *, LaneGeom, LaneState, int, KTimer *);
 template void cg_iteration<float>(cudaStream_t, const Grid &, const float *, const float *const *,

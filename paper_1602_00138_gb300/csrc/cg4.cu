@@ -172,13 +172,15 @@ constexpr int SN = 128;
 template <int KUT>
 __global__ void __launch_bounds__(kThreads)
 k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane, const int *__restrict__ tile_si,
-         const int *__restrict__ tile_cnt, int sw, long long chunk) {
+         const int *__restrict__ tile_cnt, int sw, long long chunk, int use_w) {
     __shared__ float4 As[KUT][SN / 4];
     __shared__ int lanes[TILE];
     const int t = blockIdx.y;
     const int cnt = tile_cnt[t], ku = gm.k_u;
     if (threadIdx.x < TILE) lanes[threadIdx.x] = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
-    const float *__restrict__ AU = (const float *)gm.awu + (long long)tile_si[t] * ku * gm.ld;
+    // use_w: W = U_0 itself (the shared basis columns), else A~_s U_0 of the tile's sample
+    const float *__restrict__ AU =
+        use_w ? (const float *)gm.wu : (const float *)gm.awu + (long long)tile_si[t] * ku * gm.ld;
     const float *__restrict__ Rb = (const float *)gm.r;
     const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
     float acc[4][KUT];
@@ -231,7 +233,7 @@ k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_la
 // One warp per lane l = alist[blockIdx.x]: decision, beta, mu (float), slot zeroing.
 __global__ void __launch_bounds__(32)
 k_mu(LaneState ls, const int *__restrict__ alist, int sprev, int scur, int snext, int sw, float *__restrict__ mu,
-     float *__restrict__ beta) {
+     float *__restrict__ beta, int restart) {
     const int l = alist[blockIdx.x];
     if (ls.active[l] == 0) return;
     const double rc = ls.rr[scur * ls.m + l];
@@ -239,11 +241,11 @@ k_mu(LaneState ls, const int *__restrict__ alist, int sprev, int scur, int snext
     const bool conv = !broke && sqrt(rc) <= ls.thresh[l];
     __syncwarp();
     if (threadIdx.x == 0) {
-        ls.iters[l] += 1;
+        if (!restart) ls.iters[l] += 1;
         if (broke) { ls.active[l] = 0; ls.flag[l] = 2; }
         else if (conv) { ls.active[l] = 0; ls.flag[l] = 1; }
         ls.rr[snext * ls.m + l] = 0.0;
-        if (ls.prof && !broke && !conv) { atomicAdd(ls.prof + 3, 1ULL); atomicAdd(ls.prof + 4, (unsigned long long)ls.kdef[l]); }
+        if (ls.prof && !restart && !broke && !conv) { atomicAdd(ls.prof + 3, 1ULL); atomicAdd(ls.prof + 4, (unsigned long long)ls.kdef[l]); }
     }
     if (broke || conv) {
         for (int c = threadIdx.x; c < KMAX; c += 32) ls.wv[((long long)(1 - sw) * ls.m + l) * KMAX + c] = 0.0;
@@ -257,7 +259,7 @@ k_mu(LaneState ls, const int *__restrict__ alist, int sprev, int scur, int snext
         for (int jj = 0; jj < k; ++jj) s += G[i + jj * KMAX] * w[jj];
         mu[(long long)l * KMAX + i] = (float)s;
     }
-    if (threadIdx.x == 0) beta[l] = (float)(rc / ls.rr[sprev * ls.m + l]);
+    if (threadIdx.x == 0) beta[l] = restart ? 0.f : (float)(rc / ls.rr[sprev * ls.m + l]);
     __syncwarp();
     for (int c = threadIdx.x; c < KMAX; c += 32) ls.wv[((long long)(1 - sw) * ls.m + l) * KMAX + c] = 0.0;
 }
@@ -332,6 +334,121 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
     }
 }
 
+// Lane l = alist[blockIdx.y]: wv[sw][k_u + c] += (src_c)^T r over the lane's
+// private columns (src = W or A W) and optionally rr[srr] += r^T r.
+__global__ void __launch_bounds__(kThreads)
+k_private_dots4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ alist, int use_aw, int sw,
+                int with_rr, int srr) {
+    const int l = alist[blockIdx.y];
+    const int ku = gm.k_u, kp = gm.kp[l];
+    if (kp == 0 && !with_rr) return;
+    constexpr int NV = 1 + KP_MAX;
+    float acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+    const float4 *__restrict__ R = (const float4 *)((const float *)gm.r + (long long)l * gm.ld);
+    const float *__restrict__ S = (const float *)(use_aw ? gm.awp : gm.wp) + (long long)l * gm.kp_max * gm.ld;
+    const int nv = (int)(n >> 2);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+        const float4 rv = R[v];
+        acc[0] += dot4(rv, rv);
+#pragma unroll
+        for (int c = 0; c < KP_MAX; ++c)
+            if (c < kp) acc[1 + c] += dot4(((const float4 *)(S + (long long)c * gm.ld))[v], rv);
+    }
+    __shared__ double out[NV];
+    block_sum<NV>(acc, out);
+    if (threadIdx.x == 0 && with_rr) atomicAdd(ls.rr + srr * ls.m + l, out[0]);
+    if (threadIdx.x >= 1 && threadIdx.x <= kp)
+        atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + ku + (threadIdx.x - 1), out[threadIdx.x]);
+}
+
+// One warp per lane l = alist[blockIdx.x]: mu = Ginv * wv[sw] (float), no decision.
+__global__ void __launch_bounds__(32)
+k_mu_only(LaneState ls, const int *__restrict__ alist, int sw, float *__restrict__ mu) {
+    const int l = alist[blockIdx.x];
+    const int k = ls.kdef[l];
+    const double *G = ls.gw + (long long)l * KMAX * KMAX;
+    const double *w = ls.wv + ((long long)sw * ls.m + l) * KMAX;
+    for (int i = threadIdx.x; i < k; i += 32) {
+        double s = 0.0;
+        for (int jj = 0; jj < k; ++jj) s += G[i + jj * KMAX] * w[jj];
+        mu[(long long)l * KMAX + i] = (float)s;
+    }
+}
+
+// Restart projection of the lanes of tile blockIdx.y (one sample slot):
+// x = U_0 mu_u + W_p mu_p;  r -= A~_s U_0 mu_u + A~_s W_p mu_p.
+template <int KUT>
+__global__ void __launch_bounds__(kThreads)
+k_project4(long long n, LaneGeom gm, const int *__restrict__ tile_lane, const int *__restrict__ tile_si,
+           const int *__restrict__ tile_cnt, const float *__restrict__ mu, long long chunk) {
+    __shared__ float4 Us[KUT][SN / 4], As_[KUT][SN / 4];
+    __shared__ float smu[TILE][KU_MAX + KP_MAX];
+    __shared__ int slane[TILE], skp[TILE];
+    const int t = blockIdx.y, cnt = tile_cnt[t], ku = gm.k_u;
+    if (threadIdx.x < TILE) {
+        const int l = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
+        slane[threadIdx.x] = l;
+        skp[threadIdx.x] = l >= 0 ? gm.kp[l] : 0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TILE * (KU_MAX + KP_MAX); e += blockDim.x) {
+        const int jj = e / (KU_MAX + KP_MAX), c = e % (KU_MAX + KP_MAX);
+        const int l = slane[jj];
+        smu[jj][c] = (l >= 0 && c < ku + skp[jj]) ? mu[(long long)l * KMAX + c] : 0.f;
+    }
+    const float *__restrict__ WU = (const float *)gm.wu;
+    const float *__restrict__ AU = (const float *)gm.awu + (long long)tile_si[t] * ku * gm.ld;
+    const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    __syncthreads();
+    for (long long base = r0; base < r1; base += SN) {
+        for (int e = threadIdx.x; e < KUT * (SN / 4); e += blockDim.x) {
+            const int c = e / (SN / 4), v4 = e % (SN / 4);
+            const long long p = base + 4 * v4;
+            const bool ok = c < ku && p < r1;
+            Us[c][v4] = ok ? *(const float4 *)(WU + (long long)c * gm.ld + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            As_[c][v4] = ok ? *(const float4 *)(AU + (long long)c * gm.ld + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        const long long p = base + 4 * tl;
+        if (p < r1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jj = warp + 8 * q;
+                const int l = slane[jj];
+                if (l < 0) continue;
+                float4 xs = make_float4(0.f, 0.f, 0.f, 0.f), rs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < KUT; ++c) {
+                    const float m = c < ku ? smu[jj][c] : 0.f;
+                    const float4 u = Us[c][tl], a = As_[c][tl];
+                    xs.x += m * u.x; xs.y += m * u.y; xs.z += m * u.z; xs.w += m * u.w;
+                    rs.x += m * a.x; rs.y += m * a.y; rs.z += m * a.z; rs.w += m * a.w;
+                }
+                const int kp = skp[jj];
+                const float *WP = (const float *)gm.wp + (long long)l * gm.kp_max * gm.ld;
+                const float *AP = (const float *)gm.awp + (long long)l * gm.kp_max * gm.ld;
+                for (int c = 0; c < kp; ++c) {
+                    const float m = smu[jj][ku + c];
+                    const float4 w = *(const float4 *)(WP + (long long)c * gm.ld + p);
+                    const float4 a = *(const float4 *)(AP + (long long)c * gm.ld + p);
+                    xs.x += m * w.x; xs.y += m * w.y; xs.z += m * w.z; xs.w += m * w.w;
+                    rs.x += m * a.x; rs.y += m * a.y; rs.z += m * a.z; rs.w += m * a.w;
+                }
+                const long long o = (long long)l * gm.ld + p;
+                *(float4 *)((float *)gm.x + o) = xs;
+                float4 rv = *(const float4 *)((const float *)gm.r + o);
+                rv.x -= rs.x; rv.y -= rs.y; rv.z -= rs.z; rv.w -= rs.w;
+                *(float4 *)((float *)gm.r + o) = rv;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int gx_for(long long nv, int rows, int per_sm) {
     long long want = ((long long)per_sm * 152 + rows - 1) / rows;
     long long maxb = (nv + kThreads - 1) / kThreads;
@@ -377,14 +494,14 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         long long z;
         const long long chunk = tile_chunk(z);
         dim3 grid((unsigned)z, ll.ntiles);
-#define RCG_U0(K) k_u0dots<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, sw, chunk)
+#define RCG_U0(K) k_u0dots<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, sw, chunk, 0)
         switch (kut) { case 4: RCG_U0(4); break; case 8: RCG_U0(8); break; case 12: RCG_U0(12); break; default: RCG_U0(16); }
 #undef RCG_U0
         count_launch();
         RCG_CHECK_LAUNCH();
     }
     if (tm) { kt->stop(2, e, st); e = kt->start(st); }
-    k_mu<<<ll.na, 32, 0, st>>>(ls, ll.alist, sprev, scur, snext, sw, mu, beta);
+    k_mu<<<ll.na, 32, 0, st>>>(ls, ll.alist, sprev, scur, snext, sw, mu, beta, 0);
     count_launch();
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(3, e, st); e = kt->start(st); }
@@ -399,6 +516,60 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         RCG_CHECK_LAUNCH();
     }
     if (tm) kt->stop(4, e, st);
+}
+
+// (Re)start of the lanes of ll (float32, Nx % 4 == 0) at iteration number t;
+// the same steps as cg_restart in cg.cu.  k_lane_zero has run for these lanes.
+void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, LaneList ll, int t, float *mu,
+                 float *beta) {
+    if (ll.na <= 0) return;
+    const int scur = t % 3, snext = (t + 1) % 3, sprev = (t + 2) % 3;
+    const int sw = t % 2, sA = (t + 1) % 2;
+    const long long nv = g.n >> 2;
+    long long z = (6LL * 152 + ll.ntiles - 1) / ll.ntiles;
+    const long long maxz = (g.n + 4 * SN - 1) / (4 * SN);
+    if (z > maxz) z = maxz;
+    if (z < 1) z = 1;
+    long long chunk = (g.n + z - 1) / z;
+    chunk = (chunk + SN - 1) / SN * SN;
+    z = (g.n + chunk - 1) / chunk;
+    const dim3 tgrid((unsigned)z, ll.ntiles), lgrid(gx_for(nv, ll.na, 8), ll.na);
+    const int kut = gm.k_u <= 4 ? 4 : gm.k_u <= 8 ? 8 : gm.k_u <= 12 ? 12 : 16;
+#define RCG_U0(K, W, SLOT) k_u0dots<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, SLOT, chunk, W)
+#define RCG_U0S(W, SLOT) switch (kut) { case 4: RCG_U0(4, W, SLOT); break; case 8: RCG_U0(8, W, SLOT); break; \
+                                    case 12: RCG_U0(12, W, SLOT); break; default: RCG_U0(16, W, SLOT); }
+    // z = W^T r -> wv[sA]
+    if (gm.k_u > 0) { RCG_U0S(1, sA); count_launch(); RCG_CHECK_LAUNCH(); }
+    k_private_dots4<<<lgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.alist, 0, sA, 0, 0);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    // mu0 = Ginv z; x = W mu0; r -= A W mu0
+    k_mu_only<<<ll.na, 32, 0, st>>>(ls, ll.alist, sA, mu);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+#define RCG_PJ(K) k_project4<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ll.tile_lane, ll.tile_si, ll.tile_cnt, mu, chunk)
+    switch (kut) { case 4: RCG_PJ(4); break; case 8: RCG_PJ(8); break; case 12: RCG_PJ(12); break; default: RCG_PJ(16); }
+#undef RCG_PJ
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    // rr and (A W)^T r -> rr[scur], wv[sw]
+    if (gm.k_u > 0) { RCG_U0S(0, sw); count_launch(); RCG_CHECK_LAUNCH(); }
+#undef RCG_U0S
+#undef RCG_U0
+    k_private_dots4<<<lgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.alist, 1, sw, 1, scur);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    // decision, mu, beta = 0, slot zeroing (wv[sA] is zeroed as wv[1 - sw]); p = r - W mu
+    k_mu<<<ll.na, 32, 0, st>>>(ls, ll.alist, sprev, scur, snext, sw, mu, beta, 1);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    long long zc;
+    (void)zc;
+#define RCG_DIR(K) k_direction4<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk)
+    switch (kut) { case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break; default: RCG_DIR(16); }
+#undef RCG_DIR
+    count_launch();
+    RCG_CHECK_LAUNCH();
 }
 
 }  // namespace rcg

@@ -164,6 +164,8 @@ void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int k
 template <typename TA, typename TO>
 void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k,
              const double *Y, int ldy, int m, TO *Out, long long ldo, double alpha, double beta);
+void gemm_nn_df(cudaStream_t st, long long n, const float *V, long long ldv, int k, const double *Y, int ldy,
+                int m, double *Out, long long ldo, double beta);
 template <typename TV>
 void gather_rows(cudaStream_t st, const TV *V, long long ldv, int r, const int *node,
                  const double *w, int m, double *out, int ldo);
@@ -220,6 +222,9 @@ bool cg4_supported(const Grid &g);
 void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *const *diag_of_col,
                    const float *const *p_ptr, float *const *q_ptr, LaneGeom gm, LaneState ls, LaneList ll, int t,
                    float *mu, float *beta, KTimer *kt);
+void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, LaneList ll, int t, float *mu,
+                 float *beta);
+void lane_zero(cudaStream_t st, LaneState ls, const int *mask);
 
 // cg.cu
 template <typename T>

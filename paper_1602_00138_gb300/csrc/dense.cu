@@ -176,6 +176,65 @@ k_gemm_nn(long long n, const TA *__restrict__ A, long long lda, int k, const dou
     }
 }
 
+// Out_j[p] = beta Out_j[p] + sum_c V_c[p] Y[c + j*ldy] with V float32, Y and
+// Out float64, accumulated as unevaluated float32 pairs (hi + lo): each
+// product v*y_hi is split exactly with an FMA (TwoProd), v*y_lo joins the
+// error term, and the running sum is compensated (TwoSum).  The result is
+// accurate to ~1e-13 relative at float32 instruction cost; a plain float32
+// accumulation would leave ~1e-7 relative noise in the lifted vector, which
+// the operator amplifies into the Galerkin residual.
+template <int MN>
+__global__ void __launch_bounds__(256)
+k_gemm_nn_df(long long n, const float *__restrict__ V, long long ldv, int k, const double *__restrict__ Y, int ldy,
+             int m, double *__restrict__ Out, long long ldo, double beta) {
+    __shared__ float Yh[NN_KC][MN], Yl[NN_KC][MN];
+    const int j0 = blockIdx.y * MN;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float sh[MN], sl[MN];
+#pragma unroll
+    for (int j = 0; j < MN; ++j) { sh[j] = 0.f; sl[j] = 0.f; }
+    for (int c0 = 0; c0 < k; c0 += NN_KC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < NN_KC * MN; e += blockDim.x) {
+            const int cc = e % NN_KC, jj = e / NN_KC;
+            double v = 0.0;
+            if (c0 + cc < k && j0 + jj < m) v = Y[(c0 + cc) + (long long)(j0 + jj) * ldy];
+            const float hi = (float)v;
+            Yh[cc][jj] = hi;
+            Yl[cc][jj] = (float)(v - (double)hi);
+        }
+        __syncthreads();
+        if (p < n) {
+            const int cend = (k - c0) < NN_KC ? (k - c0) : NN_KC;
+            for (int cc = 0; cc < cend; ++cc) {
+                const float a = V[(long long)(c0 + cc) * ldv + p];
+#pragma unroll
+                for (int j = 0; j < MN; ++j) {
+                    // _rn intrinsics keep the compiler from contracting these into FMAs,
+                    // which would break the error-free transformations
+                    const float prod = __fmul_rn(a, Yh[cc][j]);
+                    float err = fmaf(a, Yh[cc][j], -prod);     // exact: a*y_hi = prod + err
+                    err = fmaf(a, Yl[cc][j], err);
+                    const float t = __fadd_rn(sh[j], prod);     // TwoSum(sh, prod)
+                    const float bp = __fsub_rn(t, sh[j]);
+                    const float e2 = __fadd_rn(__fsub_rn(sh[j], __fsub_rn(t, bp)), __fsub_rn(prod, bp));
+                    sh[j] = t;
+                    sl[j] += e2 + err;
+                }
+            }
+        }
+    }
+    if (p < n) {
+#pragma unroll
+        for (int j = 0; j < MN; ++j) {
+            if (j0 + j >= m) break;
+            double *o = Out + (long long)(j0 + j) * ldo + p;
+            const double v = (double)sh[j] + (double)sl[j];
+            *o = (beta != 0.0) ? beta * *o + v : v;
+        }
+    }
+}
+
 template <typename TV>
 __global__ void k_gather_rows(const TV *__restrict__ V, long long ldv, int r, const int *__restrict__ node,
                               const double *__restrict__ w, int m, double *__restrict__ out, int ldo) {
@@ -231,6 +290,20 @@ int blocks_for(long long n, int per_col_cols) {
 }
 
 }  // namespace
+
+void gemm_nn_df(cudaStream_t st, long long n, const float *V, long long ldv, int k, const double *Y, int ldy, int m,
+                double *Out, long long ldo, double beta) {
+    if (m <= 0 || n <= 0) return;
+    if (m <= 4) {
+        dim3 grid((unsigned)((n + 255) / 256), (m + 3) / 4);
+        k_gemm_nn_df<4><<<grid, 256, 0, st>>>(n, V, ldv, k, Y, ldy, m, Out, ldo, beta);
+    } else {
+        dim3 grid((unsigned)((n + 255) / 256), (m + 15) / 16);
+        k_gemm_nn_df<16><<<grid, 256, 0, st>>>(n, V, ldv, k, Y, ldy, m, Out, ldo, beta);
+    }
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
 
 template <typename TA, typename TB, typename AT>
 void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int ka, const TB *B, long long ldb,
