@@ -127,6 +127,15 @@ def test_mixed_wave_matches_oracle(torch_cuda, name):
     _check_run(name, rcg.RCG_MIXED, rcg.RCG_WAVE, 1e-6, 1e-6, 1e-5)
 
 
+def test_config_2d64_fp64_sequential(torch_cuda):
+    """The 2D 64^2 configuration (16 + 16 RHS, 3 samples, tol 1e-10, plain
+    FP64 recycled CG in the paper's order) against the oracle in full."""
+    from paper_1602_00138_gb300 import rcg
+    ctx, out_g, out_o = _check_run("c1_2d64", rcg.RCG_FP64, rcg.RCG_SEQUENTIAL, 1e-12, 1e-8, 1e-7)
+    diffs = [abs(a["iters"] - b["iters"]) for a, b in zip(out_g, out_o)]
+    assert max(diffs) <= 3, diffs
+
+
 def test_heldout_reduced_model_fp64(torch_cuda):
     """At a parameter point not used to build V, the GPU reduced model equals
     the oracle's reduced model built from the oracle's basis."""
