@@ -162,7 +162,9 @@ struct Engine : EngineBase {
     double *Cb = nullptr, *M = nullptr, *S = nullptr, *R = nullptr, *RK = nullptr, *Ri = nullptr, *Rhat = nullptr;
     double *xn2 = nullptr, *ratio_d = nullptr;
     int *kept_d = nullptr, *d_K = nullptr, *d_cand = nullptr;
-    int *d_info = nullptr;
+    int *d_info = nullptr;          // [0] Cholesky info, [1] sticky tensor-core wait timeout
+    float *tc_scr = nullptr;        // split-K slices of the tensor-core products
+    long long tc_cap = 0;
     // rom workspace
     double *Ar = nullptr, *Br = nullptr, *Crm = nullptr, *Xr = nullptr, *Zr = nullptr, *wtmp = nullptr;
     double *VX = nullptr, *VZ = nullptr;
@@ -175,6 +177,7 @@ struct Engine : EngineBase {
         Gs = c->alloc<double>((size_t)rmax * rmax);
         Ls = c->alloc<double>((size_t)rmax * rmax);
         d_info = c->alloc<int>(4);
+        RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, 4 * sizeof(int), st));
         Gw.assign(c->opt.max_samples, nullptr);
         Lw.assign(c->opt.max_samples, nullptr);
         dw.assign(c->opt.max_samples, nullptr);
@@ -280,10 +283,31 @@ struct Engine : EngineBase {
     }
 
     void check_info(const char *what) {
-        int info = 0;
-        c->d2h(&info, d_info, 1);
+        int info[2] = {0, 0};
+        c->d2h(info, d_info, 2);
         c->sync();
-        if (info != 0) throw Error{RCG_ERR_NOT_SPD, std::string(what) + ": float64 Cholesky found a non-positive pivot"};
+        if (info[1] != 0) throw Error{RCG_ERR_TIMEOUT, "tensor-core product: an mbarrier wait ran out"};
+        if (info[0] != 0) throw Error{RCG_ERR_NOT_SPD, std::string(what) + ": float64 Cholesky found a non-positive pivot"};
+    }
+
+    // C (ka x kb, ld ldc) = A^T B for n-long columns of stride ld.  float32
+    // operands of at least 16 columns each go to the tensor cores (3xTF32,
+    // float64 sum of the slices); the rest, and the float64 path, to the
+    // CUDA-core kernels.  sym: A == B, ka == kb (upper tiles, mirrored).
+    void prod_tn(const T *A, int ka, const T *B, int kb, double *C, int ldc, bool sym = false) {
+        if constexpr (sizeof(T) == 4) {
+            if (ka >= 16 && kb >= 16 && tc_gemm_tn_ok(ld, ld, A, B)) {
+                const long long need = tc_gemm_tn_scratch(n, ka, kb, sym, nullptr, nullptr);
+                if (need > tc_cap) {
+                    c->release(tc_scr);
+                    tc_cap = std::max(need, 2 * tc_cap);
+                    tc_scr = c->alloc<float>((size_t)tc_cap);
+                }
+                tc_gemm_tn(st, n, A, ld, ka, B, ld, kb, C, ldc, false, sym, tc_scr, d_info + 1);
+                return;
+            }
+        }
+        gemm_tn<T, T>(st, n, A, ld, ka, B, ld, kb, C, ldc, false);
     }
 
     // A~_s applied to `cnt` columns (pointer lists on the host).
@@ -388,10 +412,10 @@ struct Engine : EngineBase {
         convert_lanes<double, T>(st, n, (const double *const *)p_x64, d_cand, a, Wb, ld);
         norm2_lanes(st, n, (const double *const *)p_x64, d_cand, a, xn2);
         for (int pass = 0; pass < 2 && r > 0; ++pass) {   // W <- (I - V V^T)^2 X
-            gemm_tn<T, T>(st, n, V, ld, r, Wb, ld, a, Cb, r, false);
+            prod_tn(V, r, Wb, a, Cb, r);
             gemm_nn<T, T>(st, n, V, ld, r, Cb, r, a, Wb, ld, -1.0, 1.0);
         }
-        gemm_tn<T, T>(st, n, Wb, ld, a, Wb, ld, a, M, a, false);
+        prod_tn(Wb, a, Wb, a, M, a, true);
         ordered_drop_chol(st, M, a, xn2, S, tau, R, kept_d, ratio_d);
         c->d2h(kept.data(), kept_d, a);
         c->d2h(ratio.data(), ratio_d, a);
@@ -410,10 +434,10 @@ struct Engine : EngineBase {
         gemm_nn<T, T>(st, n, Wb, ld, a, Rhat, a, ak, Qb, ld, 1.0, 0.0);
         // second pass: Q <- (I - V V^T) Q, then Q R2^-1 with R2^T R2 = Q^T Q
         if (r > 0) {
-            gemm_tn<T, T>(st, n, V, ld, r, Qb, ld, ak, Cb, r, false);
+            prod_tn(V, r, Qb, ak, Cb, r);
             gemm_nn<T, T>(st, n, V, ld, r, Cb, r, ak, Qb, ld, -1.0, 1.0);
         }
-        gemm_tn<T, T>(st, n, Qb, ld, ak, Qb, ld, ak, M, ak, false);
+        prod_tn(Qb, ak, Qb, ak, M, ak, true);
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
         chol_inplace(st, M, ak, ak, d_info);
         check_info("append second pass Q^T Q");
@@ -488,7 +512,7 @@ struct Engine : EngineBase {
         auto project = [&](bool first) {
             // Yb = V^T b (first) or V^T r; Y = G^-1 Yb; x64 (+)= V Y
             if (first) gather_rows<T>(st, Vc, ld, r, d_lnode, d_lw, m, Yb, rmax);
-            else gemm_tn<T, T>(st, n, Vc, ld, r, rv, ld, m, Yb, rmax, false);
+            else prod_tn(Vc, r, rv, m, Yb, rmax);
             for (size_t gi = 0; gi + 1 < grp_begin.size(); ++gi) {
                 const int l0 = grp_begin[gi], l1 = grp_begin[gi + 1];
                 double *L = gal[samp[l0]].second;
@@ -798,7 +822,7 @@ struct Engine : EngineBase {
     // CholQR of the b columns of X (twice), using Y as scratch.
     void cholqr(T *X, T *Y, int b) {
         for (int pass = 0; pass < 2; ++pass) {
-            gemm_tn<T, T>(st, n, X, ld, b, X, ld, b, M, b, false);
+            prod_tn(X, b, X, b, M, b, true);
             RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
             chol_inplace(st, M, b, b, d_info);
             check_info("eigen seed CholQR");
@@ -815,7 +839,7 @@ struct Engine : EngineBase {
         std::vector<T *> dst(b);
         for (int i = 0; i < b; ++i) { src[i] = X + (long long)i * ld; dst[i] = AX + (long long)i * ld; }
         apply_cols(src, dst, std::vector<int>(b, s0));
-        gemm_tn<T, T>(st, n, X, ld, b, AX, ld, b, M, b, false);
+        prod_tn(X, b, AX, b, M, b);
         jacobi_eig(st, M, b, b, Rhat, xn2);          // Rhat: eigenvectors, xn2: eigenvalues
         gemm_nn<T, T>(st, n, X, ld, b, Rhat, b, b, Y, ld, 1.0, 0.0);
         RCG_CUDA_TRY(cudaMemcpyAsync(X, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
@@ -928,7 +952,7 @@ struct Engine : EngineBase {
         c->h2d(d_list, all.data(), nrhs);
         convert_lanes<double, T>(st, n, (const double *const *)p_x64, d_list, nrhs, X0, ld);
         RCG_CUDA_TRY(cudaMemsetAsync(sX0, 0, sizeof(double) * rmax * nrhs, st));
-        gemm_tn<T, T>(st, n, V, ld, r, X0, ld, nrhs, sX0, rmax, false);
+        prod_tn(V, r, X0, nrhs, sX0, rmax);
         c->sync();
         priv.assign(nrhs, std::vector<int>{-1});
         priv_seed = priv;

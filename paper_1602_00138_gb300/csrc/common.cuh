@@ -161,6 +161,11 @@ template <typename TA, typename TB, typename AT>
 void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
                  const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
                  const double *wt = nullptr, const int *rows = nullptr, long long nrows = 0);
+// tc.cu: C (+)= A^T B for float32 A, B on the tensor cores (3xTF32)
+long long tc_gemm_tn_scratch(long long n, int ka, int kb, bool symmetric, int *z_out, long long *chunk_out);
+bool tc_gemm_tn_ok(long long lda, long long ldb, const void *A, const void *B);
+void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int ka, const float *B, long long ldb,
+                int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err);
 template <typename TA, typename TO>
 void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k,
              const double *Y, int ldy, int m, TO *Out, long long ldo, double alpha, double beta);

@@ -1,0 +1,387 @@
+// Tall-skinny products C (+)= A^T B on the 5th-generation tensor cores
+// (tcgen05.mma kind::tf32, accumulators in tensor memory), for the basis
+// products of the ordered append (Sec. 5.3 incremental QR: V^T W, W^T W,
+// V^T Q, Q^T Q with n-long columns) and the seed's Gram matrices.
+//
+// A (n x ka) and B (n x kb) are float32, column-major (each column
+// contiguous along n: K-major operands for the MMA).  A CTA owns a 128 x 128
+// output tile and a slice of n (split-K), walked in K-steps of 32 rows:
+//
+//   * cp.async copies the raw 128 x 32 tiles of A and B straight into the
+//     128-byte-swizzled K-major layout (row m = one column of A: 32 floats =
+//     128 B; 16-byte chunk c of row m stored at chunk c ^ (m mod 8)), two
+//     K-steps ahead, into a 3-stage ring;
+//   * every value x is split in place into hi = rn_tf32(x) and, beside it,
+//     lo = rn_tf32(x - hi); three MMAs per 8-deep K-slice (hi hi, hi lo,
+//     lo hi) give products at float32 level ("3xTF32");
+//   * one thread issues the 12 MMAs of a K-step into one of two tensor-memory
+//     accumulators and commits them to an mbarrier;
+//   * while the tensor core runs step k, the CTA drains step k-1's
+//     accumulator into registers.  Each step's accumulator starts from zero,
+//     so the tensor core never adds a small product into a large sum (its
+//     float32 accumulation is not round-to-nearest: a long accumulation of
+//     same-sign products drifts by ~1 ulp per MMA); the registers sum the
+//     per-step partials in two levels (16 steps, then the slice).
+//
+// The float32 tile of every slice goes to a scratch [z][kb][ka]; a second
+// kernel sums the slices in float64 into C.  Symmetric products (A == B)
+// compute the upper tiles only and mirror them.
+//
+// Every mbarrier wait is bounded: on timeout the CTA records RCG_ERR_TIMEOUT
+// in *err, stops issuing work, waits (bounded) for its MMAs and copies,
+// frees its tensor memory and returns.
+#include "common.cuh"
+#include "../../include/rcg.h"
+
+#include <algorithm>
+#include <cstdint>
+
+namespace rcg {
+namespace {
+
+constexpr int TM = 128;                 // output rows per CTA (columns of A)
+constexpr int TNc = 128;                // output columns per CTA (columns of B)
+constexpr int TBK = 32;                 // K rows per step (one 128-byte swizzle row)
+constexpr int NTHR = 256;               // 8 warps
+constexpr int TILE_BYTES = TM * TBK * 4;                 // 16 KiB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;              // A hi, B hi, A lo, B lo
+constexpr int NSTAGE = 3;
+constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + 1024;     // + 1024-byte alignment slack
+constexpr int LEVEL1 = 16;              // K-steps summed before the second level
+constexpr long long SPIN_LIMIT = 1LL << 22;
+constexpr int NUM_SMS = 152;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
+// layout: 8-row groups 1024 B apart (stride byte offset), descriptor
+// version 1 (tcgen05), layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: D f32, A and B tf32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < SPIN_LIMIT; ++i)
+        if (mbar_try_wait(mbar, parity)) return true;
+    return false;
+}
+
+// Round a float32 to the nearest TF32 value (10 explicit mantissa bits),
+// ties away from zero, on the bit pattern: add half of the dropped range to
+// the magnitude bits and clear them (finite inputs; two integer operations,
+// where the conversion instruction would run on a slower pipe).
+__device__ __forceinline__ float rn_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// 16-byte chunk c (K rows 4c..4c+3) of tile row m, 128-byte swizzle.
+__device__ __forceinline__ int sw_off(int m, int c) { return m * 128 + ((c ^ (m & 7)) << 4); }
+
+// Copy the raw 128 x 32 tile of X at rows k0..k0+31 into `dst` (zero-filled
+// outside the matrix and past row k1).  Thread t copies 16-byte chunk t%8 of
+// columns c0 + t/8 + 32 it (it = 0..3); `colp` = X + (c0 + t/8) ldx + 4 (t%8),
+// `ncol` = number of those four columns inside the matrix.
+__device__ __forceinline__ void prefetch_tile(const float *colp, long long step_col, int ncol, long long k0,
+                                              long long k1, char *dst) {
+    const int m0 = threadIdx.x >> 3, c = threadIdx.x & 7;
+    const long long k = k0 + 4 * c;
+    const long long left = k1 - k;
+    const int bytes_row = left >= 4 ? 16 : (left > 0 ? (int)(4 * left) : 0);
+#pragma unroll
+    for (int it = 0; it < TM * (TBK / 4) / NTHR; ++it) {
+        const int bytes = it < ncol ? bytes_row : 0;
+        const float *src = bytes ? colp + it * step_col + k0 : colp;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + sw_off(m0 + 32 * it, c))),
+                     "l"(src), "r"(bytes)
+                     : "memory");
+    }
+}
+
+// hi in place, lo at the same offset in `lo` (the split is elementwise, so
+// the swizzle does not matter here).
+__device__ __forceinline__ void split_tile(char *hi, char *lo) {
+#pragma unroll
+    for (int it = 0; it < TILE_BYTES / 16 / NTHR; ++it) {
+        const int o = (threadIdx.x + it * NTHR) * 16;
+        const float4 v = *(const float4 *)(hi + o);
+        float4 h, l;
+        h.x = rn_tf32(v.x); h.y = rn_tf32(v.y); h.z = rn_tf32(v.z); h.w = rn_tf32(v.w);
+        l.x = rn_tf32(v.x - h.x); l.y = rn_tf32(v.y - h.y); l.z = rn_tf32(v.z - h.z); l.w = rn_tf32(v.w - h.w);
+        *(float4 *)(hi + o) = h;
+        *(float4 *)(lo + o) = l;
+    }
+}
+
+// 32 consecutive accumulator columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__global__ void __launch_bounds__(NTHR, 1)
+k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const float *__restrict__ B, long long ldb,
+        int kb, int symmetric, float *__restrict__ part, long long chunk, int *__restrict__ err) {
+    if (symmetric && blockIdx.x > blockIdx.y) return;        // lower tiles are mirrored by the reduction
+    extern __shared__ __align__(1024) char smem_raw[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok;
+    char *smem = (char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TNc;
+    const long long r0 = (long long)blockIdx.z * chunk;
+    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    const long long nk = (r1 > r0) ? (r1 - r0 + TBK - 1) / TBK : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2 * TNc));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_ok = 1;
+    }
+    // this thread's source columns (see prefetch_tile)
+    const int mt = threadIdx.x >> 3;
+    const float *colA = A + (long long)(i0 + mt < ka ? i0 + mt : 0) * lda + 4 * (threadIdx.x & 7);
+    const float *colB = B + (long long)(j0 + mt < kb ? j0 + mt : 0) * ldb + 4 * (threadIdx.x & 7);
+    const int ncolA = i0 + mt < ka ? min(4, (ka - i0 - mt + 31) / 32) : 0;
+    const int ncolB = j0 + mt < kb ? min(4, (kb - j0 - mt + 31) / 32) : 0;
+    const long long stepA = 32 * lda, stepB = 32 * ldb;
+    // prologue: steps 0 and 1 in flight (one cp.async group per step; empty
+    // groups keep the count uniform)
+    for (int q = 0; q < 2; ++q) {
+        if (q < nk) {
+            char *stg = smem + q * STAGE_BYTES;
+            prefetch_tile(colA, stepA, ncolA, r0 + q * TBK, r1, stg);
+            prefetch_tile(colB, stepB, ncolB, r0 + q * TBK, r1, stg + TILE_BYTES);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = make_idesc_tf32(TM, TNc);
+    // accumulator lane block of this warp and this thread's 64 columns
+    const uint32_t t_lane = (uint32_t)((warp & 3) * 32) << 16;
+    const int col0 = (warp >> 2) * 64;
+    float acc1[64], acc2[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) { acc1[q] = 0.f; acc2[q] = 0.f; }
+    bool ok = true;
+    long long drained = 0;                // steps whose partial is in acc1 / acc2
+    auto drain = [&](long long q) {       // the MMAs of step q are complete
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t base = tmem + t_lane + (uint32_t)((q & 1) * TNc + col0);
+        float v[32];
+        tmem_ld32(base, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc1[c] += v[c];
+        tmem_ld32(base + 32, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc1[32 + c] += v[c];
+        if (((q + 1) % LEVEL1) == 0) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) { acc2[c] += acc1[c]; acc1[c] = 0.f; }
+        }
+        drained = q + 1;
+    };
+    for (long long ks = 0; ks < nk; ++ks) {
+        char *stg = smem + (int)(ks % NSTAGE) * STAGE_BYTES;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");      // step ks has landed (own copies)
+        __syncthreads();                                           // ... everyone's; s_ok is uniform here
+        if (!s_ok) { ok = false; break; }
+        split_tile(stg, stg + 2 * TILE_BYTES);                     // A hi | A lo
+        split_tile(stg + TILE_BYTES, stg + 3 * TILE_BYTES);        // B hi | B lo
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t d = tmem + (uint32_t)((ks & 1) * TNc);
+            const uint32_t a_hi = smem_u32(stg), b_hi = a_hi + TILE_BYTES;
+            const uint32_t a_lo = a_hi + 2 * TILE_BYTES, b_lo = a_hi + 3 * TILE_BYTES;
+#pragma unroll
+            for (int s = 0; s < TBK / 8; ++s) {        // K = 8 per MMA = 32 bytes along the swizzled row
+                const uint32_t o = s * 32;
+                mma_tf32(d, make_desc_sw128(a_hi + o), make_desc_sw128(b_hi + o), idesc, s > 0 ? 1u : 0u);
+                mma_tf32(d, make_desc_sw128(a_hi + o), make_desc_sw128(b_lo + o), idesc, 1u);
+                mma_tf32(d, make_desc_sw128(a_lo + o), make_desc_sw128(b_hi + o), idesc, 1u);
+            }
+            mma_commit(smem_u32(&mbar[ks & 1]));
+        }
+        // step ks-1: its MMAs free the stage that step ks+2 is copied into, and
+        // its accumulator is drained while step ks runs on the tensor core
+        if (ks >= 1) {
+            const long long q = ks - 1;
+            if (mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1))) {
+                drain(q);
+            } else {
+                s_ok = 0;
+                ok = false;
+            }
+        }
+        if (ok && ks + 2 < nk) {
+            char *nxt = smem + (int)((ks + 2) % NSTAGE) * STAGE_BYTES;
+            prefetch_tile(colA, stepA, ncolA, r0 + (ks + 2) * TBK, r1, nxt);
+            prefetch_tile(colB, stepB, ncolB, r0 + (ks + 2) * TBK, r1, nxt + TILE_BYTES);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    // last step: wait for its MMAs (bounded, also after a timeout, so that
+    // nothing runs on the tensor memory when it is freed)
+    if (nk > 0 && drained < nk) {
+        const long long q = drained < nk - 1 ? (ok ? nk - 1 : drained) : nk - 1;
+        const bool done = mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1));
+        if (ok && done && q == nk - 1 && drained == nk - 1) drain(q);
+        else ok = false;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");          // no copy in flight at exit
+    if (!ok) s_ok = 0;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (threadIdx.x == 0 && !s_ok) atomicExch(err, RCG_ERR_TIMEOUT);
+    // this thread's row of the slice: row i0 + (warp&3)*32 + lane, 64 columns
+    float *dst = part + (long long)blockIdx.z * ((long long)kb * ka);
+    const int row = i0 + (warp & 3) * 32 + lane;
+    if (s_ok && row < ka) {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+            const int col = j0 + col0 + c;
+            if (col < kb) dst[(long long)col * ka + row] = acc2[c] + acc1[c];
+        }
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TNc));
+}
+
+// C[i + j*ldc] (+)= sum_z part[z][j][i] in float64; a symmetric product
+// reads the lower tiles from the mirrored upper ones.
+__global__ void k_tc_reduce(const float *__restrict__ part, int z, int ka, int kb, int symmetric,
+                            double *__restrict__ C, int ldc, int accumulate) {
+    const long long tot = (long long)ka * kb;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % ka), j = (int)(e / ka);
+        const long long src = (symmetric && i / TM > j / TNc) ? (long long)i * ka + j : e;
+        double s = 0.0;
+        for (int q = 0; q < z; ++q) s += (double)part[(long long)q * tot + src];
+        double *c = C + i + (long long)j * ldc;
+        *c = accumulate ? *c + s : s;
+    }
+}
+
+}  // namespace
+
+// Slices z of the long dimension for (n, ka, kb) and the float scratch they
+// need: one CTA per SM, z chosen so that the CTAs fill whole waves.
+long long tc_gemm_tn_scratch(long long n, int ka, int kb, bool symmetric, int *z_out, long long *chunk_out) {
+    const long long tx = (ka + TM - 1) / TM, ty = (kb + TNc - 1) / TNc;
+    const long long tiles = symmetric ? tx * (tx + 1) / 2 : tx * ty;
+    long long z = 1;
+    if (n > 0) {
+        const long long zmax = std::max<long long>(1, n / 512);    // at least 512 rows per slice
+        double best = -1.0;
+        for (long long zz = 1; zz <= std::min<long long>(zmax, 4 * NUM_SMS); ++zz) {
+            const long long ctas = tiles * zz;
+            const long long waves = (ctas + NUM_SMS - 1) / NUM_SMS;
+            const double eff = (double)ctas / (double)(waves * NUM_SMS);
+            if (eff > best + 0.02) { best = eff; z = zz; }
+            if (waves > 3) break;
+        }
+    }
+    long long chunk = n > 0 ? (n + z - 1) / z : TBK;
+    chunk = (chunk + TBK - 1) / TBK * TBK;
+    if (n > 0) z = (n + chunk - 1) / chunk;
+    if (z_out) *z_out = (int)z;
+    if (chunk_out) *chunk_out = chunk;
+    return z * (long long)ka * kb;
+}
+
+// The copies need 16-byte aligned columns.
+bool tc_gemm_tn_ok(long long lda, long long ldb, const void *A, const void *B) {
+    return lda % 4 == 0 && ldb % 4 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
+}
+
+// C (ka x kb, ld ldc) = / += A^T B with A, B float32 column-major (n rows,
+// 16-byte aligned, lda and ldb multiples of 4).  symmetric: A == B, ka == kb.
+// scratch: >= tc_gemm_tn_scratch(...) floats; err: device int (0 = ok).
+void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int ka, const float *B, long long ldb,
+                int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err) {
+    if (ka <= 0 || kb <= 0) return;
+    if (!tc_gemm_tn_ok(lda, ldb, A, B)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: operands not 16-byte aligned"};
+    if (symmetric && (A != B || ka != kb || lda != ldb)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: not symmetric"};
+    int z;
+    long long chunk;
+    tc_gemm_tn_scratch(n, ka, kb, symmetric, &z, &chunk);
+    static bool attr[64] = {};          // per device ordinal
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_tc_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    dim3 grid((ka + TM - 1) / TM, (kb + TNc - 1) / TNc, z);
+    k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, B, ldb, kb, symmetric ? 1 : 0, scratch, chunk, err);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    const long long tot = (long long)ka * kb;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 2048);
+    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, z, ka, kb, symmetric ? 1 : 0, C, ldc, accumulate ? 1 : 0);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+}  // namespace rcg
