@@ -3,11 +3,13 @@
 //
 //   k_stencil4   q = A~_s p, float4 along x, one active lane per CTA row,
 //                fused p^T q
+//   k_stencil4z  the same for 3D grids, two lanes per CTA, planes streamed
+//                through a shared-memory ring (each value read about once)
 //   k_update4    x += alpha p, r -= alpha q, fused r^T r and the private
 //                (A W)^T r dots, float4, one active lane per CTA row
-//   k_u0dots     (A~_s U_0)^T r for a tile of <= 32 lanes of one sample:
-//                a shared-memory tiled product, so each A~_s U_0 element is
-//                read once per tile instead of once per lane
+//   k_u0dots     (A~_s U_0)^T r (or U_0^T r at a restart) for a tile of
+//                <= 32 lanes of one sample: a shared-memory tiled product,
+//                so each A~_s U_0 element is read once per tile
 //   k_mu         per lane (one warp): convergence / breakdown decision,
 //                beta, mu = (W^T A W)^-1 (A W)^T r, ring-slot zeroing
 //   k_direction4 p = r + beta p - U_0 mu_u - W_p mu_p for a tile of lanes;
@@ -24,7 +26,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int TILE = 32;       // lanes per tile
-constexpr int BK = 64;         // nodes per shared-memory stage of k_u0dots
 
 __device__ __forceinline__ float dot4(const float4 a, const float4 b) {
     return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
@@ -115,6 +116,161 @@ k_stencil4(Grid g, const float *__restrict__ D, const float *const *__restrict__
     }
 }
 
+// 3D grids with 256 % (Nx / 4) == 0: q = A~ p for ZL lanes per CTA over one
+// (y-tile, z-chunk) block.  The CTA's thread (tx, ty) owns x-nodes 4tx..4tx+3
+// of row y0 + ty; TY = 256 / (Nx / 4) rows form the tile.  Planes of p (each
+// lane) and D, tile rows plus one halo row on either side, stream through a
+// ZR-slot shared-memory ring by cp.async two planes ahead, so every p and D
+// value is read from memory about once (halo rows and planes aside) and the
+// six neighbours come from shared memory.  Fused p^T q per lane.
+constexpr int ZR = 4;    // ring slots: planes z-1, z, z+1 in use, z+2 in flight
+constexpr int ZL = 2;    // lanes per CTA (they share the D planes)
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict__ diag_of_col,
+            const float *const *__restrict__ src, float *const *__restrict__ dst, const int *__restrict__ alist,
+            int na, const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ prof,
+            int zc) {
+    extern __shared__ float4 ring[];                 // [ZR][ZL + 1][TY + 2][nx4]
+    const int nx4 = g.Nx >> 2, TY = kThreads / nx4, rows = TY + 2;
+    const int ytiles = (g.Ny + TY - 1) / TY;
+    const int yt = blockIdx.x % ytiles, zb = blockIdx.x / ytiles;
+    const int y0 = yt * TY, z0 = zb * zc;
+    const int z1 = min(z0 + zc, g.Nz);
+    const int tx = threadIdx.x % nx4, ty = threadIdx.x / nx4;
+    const int y = y0 + ty;
+    int c[ZL];
+    bool on[ZL];
+    int non = 0;
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        const int li = blockIdx.y * ZL + i;
+        c[i] = li < na ? alist[li] : -1;
+        on[i] = c[i] >= 0 && active[c[i]] != 0;
+        non += on[i];
+    }
+    if (non == 0 || z0 >= g.Nz) return;             // uniform over the CTA
+    if (prof && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
+    const float *P[ZL];
+    float4 *Q[ZL];
+    const float4 *DG[ZL];
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        P[i] = on[i] ? src[c[i]] : nullptr;
+        Q[i] = on[i] ? (float4 *)dst[c[i]] : nullptr;
+        DG[i] = on[i] ? (const float4 *)diag_of_col[c[i]] : nullptr;
+    }
+    const int plane4 = nx4 * rows;                   // float4 per array and slot
+    auto slot = [&](int z) { return ring + (size_t)(z % ZR) * (ZL + 1) * plane4; };
+    // Plane z, rows y0-1 .. y0+TY, of each live array into its slot.  Thread
+    // (tx, ty) copies column tx of slot rows ty, ty + TY, ty + 2 TY, ... (256
+    // threads = TY rows of nx4 float4), walking (array, row) without division.
+    auto load_plane = [&](int z) {
+        float4 *sl = slot(z);
+        const long long zoff = (long long)z * g.Ny;
+        int a = 0, ry = ty;
+        for (int R = ty; R < (ZL + 1) * rows; R += TY) {
+            const int yy = y0 - 1 + ry;
+            const float *base = D;
+#pragma unroll
+            for (int i = 0; i < ZL; ++i)
+                if (a == i) base = P[i];
+            if (yy >= 0 && yy < g.Ny && base != nullptr)
+                cp_async16(sl + R * nx4 + tx, (const float4 *)base + (zoff + yy) * nx4 + tx);
+            ry += TY;
+            if (ry >= rows) { ry -= rows; ++a; }
+        }
+    };
+    // prologue: planes z0-1, z0, z0+1 (one cp.async group each)
+    for (int q = -1; q <= 1; ++q) {
+        const int z = z0 + q;
+        if (z >= 0 && z < g.Nz && z <= z1) load_plane(z);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const bool yok = y < g.Ny;
+    const long long row4 = (long long)nx4 * g.Ny;    // float4 per plane in memory
+    float4 dgc[ZL], dgn[ZL];
+#pragma unroll
+    for (int i = 0; i < ZL; ++i)
+        dgc[i] = (on[i] && yok) ? DG[i][(long long)z0 * row4 + (long long)y * nx4 + tx] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc[ZL];
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) acc[i] = 0.f;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int z = z0; z < z1; ++z) {
+        if (z + 2 <= z1 && z + 2 < g.Nz) load_plane(z + 2);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const long long v = (long long)z * row4 + (long long)y * nx4 + tx;
+#pragma unroll
+        for (int i = 0; i < ZL; ++i)
+            dgn[i] = (on[i] && yok && z + 1 < z1) ? DG[i][v + row4] : zero4;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        if (yok) {
+            const float4 *cs = slot(z), *ms = slot(z + ZR - 1), *ps = slot(z + 1);
+            const int rc = (ty + 1) * nx4 + tx, dof = ZL * plane4;
+            const bool xl = tx > 0, xr = tx < nx4 - 1, ym = y > 0, yp = y < g.Ny - 1, zm = z > 0,
+                       zp = z < g.Nz - 1;
+            const float4 Dc = cs[dof + rc];
+            const float Dl = xl ? cs[dof + rc - 1].w : 0.f, Dr = xr ? cs[dof + rc + 1].x : 0.f;
+            const float4 Dym = ym ? cs[dof + rc - nx4] : zero4, Dyp = yp ? cs[dof + rc + nx4] : zero4;
+            const float4 Dzm = zm ? ms[dof + rc] : zero4, Dzp = zp ? ps[dof + rc] : zero4;
+            // face weights (zero where the neighbour is a ghost or eliminated)
+            const float wl = xl ? 0.5f * (Dc.x + Dl) : 0.f, wr = xr ? 0.5f * (Dc.w + Dr) : 0.f;
+            const float w01 = 0.5f * (Dc.x + Dc.y), w12 = 0.5f * (Dc.y + Dc.z), w23 = 0.5f * (Dc.z + Dc.w);
+            auto fw = [&](bool on_, const float4 Dn) {
+                return on_ ? make_float4(0.5f * (Dc.x + Dn.x), 0.5f * (Dc.y + Dn.y), 0.5f * (Dc.z + Dn.z),
+                                         0.5f * (Dc.w + Dn.w))
+                           : zero4;
+            };
+            const float4 wym = fw(ym, Dym), wyp = fw(yp, Dyp), wzm = fw(zm, Dzm), wzp = fw(zp, Dzp);
+#pragma unroll
+            for (int i = 0; i < ZL; ++i) {
+                if (!on[i]) continue;
+                const int po = i * plane4;
+                const float4 xc = cs[po + rc];
+                const float xlv = xl ? cs[po + rc - 1].w : 0.f, xrv = xr ? cs[po + rc + 1].x : 0.f;
+                const float4 xym = ym ? cs[po + rc - nx4] : zero4, xyp = yp ? cs[po + rc + nx4] : zero4;
+                const float4 xzm = zm ? ms[po + rc] : zero4, xzp = zp ? ps[po + rc] : zero4;
+                const float4 dg = dgc[i];
+                float4 o;
+                o.x = dg.x * xc.x - (wl * xlv + w01 * xc.y) - (wym.x * xym.x + wyp.x * xyp.x) - (wzm.x * xzm.x + wzp.x * xzp.x);
+                o.y = dg.y * xc.y - (w01 * xc.x + w12 * xc.z) - (wym.y * xym.y + wyp.y * xyp.y) - (wzm.y * xzm.y + wzp.y * xzp.y);
+                o.z = dg.z * xc.z - (w12 * xc.y + w23 * xc.w) - (wym.z * xym.z + wyp.z * xyp.z) - (wzm.z * xzm.z + wzp.z * xzp.z);
+                o.w = dg.w * xc.w - (w23 * xc.z + wr * xrv) - (wym.w * xym.w + wyp.w * xyp.w) - (wzm.w * xzm.w + wzp.w * xzp.w);
+                Q[i][v] = o;
+                acc[i] += dot4(xc, o);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ZL; ++i) dgc[i] = dgn[i];
+        __syncthreads();                               // slot of plane z-1 is refilled next
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __shared__ double red[kThreads / 32][ZL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        double s = (double)acc[i];
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, o2);
+        if (lane == 0) red[warp][i] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ZL; ++i)
+        if (threadIdx.x == i && on[i]) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w][i];
+            atomicAdd(dots + c[i], t);
+        }
+}
+
 // Lane l = alist[blockIdx.y]: x += alpha p; r -= alpha q; r^T r and the
 // private (A W)^T r dots (the shared ones come from k_u0dots).
 __global__ void __launch_bounds__(kThreads)
@@ -163,70 +319,117 @@ k_update4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ alist,
         atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + ku + (threadIdx.x - 1), out[threadIdx.x]);
 }
 
-// wv[sw][l][c] += (A~_s U_0)_c^T r_l for the lanes of tile blockIdx.y (one
-// sample slot) over this CTA's node range.  The range is walked in stages of
-// SN nodes: the stage of A~_s U_0 (k_u x SN) is staged in shared memory once
-// and used by all lanes of the tile; warp w streams lanes w, w+8, w+16, w+24
-// with coalesced float4 loads (one float4 of r per thread per lane).
-constexpr int SN = 128;
+// wv[sw][l][c] += (A~_s U_0)_c^T r_l (use_w: U_0 itself) for the lanes of
+// tile blockIdx.y (one sample slot) over this CTA's node range.  The range is
+// walked in stages of SN nodes: the r rows of the tile's lanes (32 x SN) and
+// the k_u x SN block of A~_s U_0 stream into a U0_NST-slot shared-memory ring
+// by cp.async, two stages ahead.  Thread (warp w, lane slot l) dots float4
+// nodes 4w..4w+3 of the stage of lane l against every column (the column
+// reads are warp-wide broadcasts); the eight warps' partial sums are added in
+// shared memory at the end.
+constexpr int SN = 128;                 // nodes per stage
+constexpr int SN4 = SN / 4;
+constexpr int RP = SN4 + 1;             // padded float4 stride of an r row (conflict-free reads)
+constexpr int U0_NST = 3;
+template <int KUT>
+__host__ __device__ constexpr int u0_stage4() { return TILE * RP + KUT * SN4; }
+template <int KUT>
+constexpr size_t u0_smem() { return (size_t)U0_NST * u0_stage4<KUT>() * sizeof(float4); }
+
 template <int KUT>
 __global__ void __launch_bounds__(kThreads)
 k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane, const int *__restrict__ tile_si,
          const int *__restrict__ tile_cnt, int sw, long long chunk, int use_w) {
-    __shared__ float4 As[KUT][SN / 4];
+    extern __shared__ float4 u0s[];
     __shared__ int lanes[TILE];
+    constexpr int STG = u0_stage4<KUT>();
     const int t = blockIdx.y;
     const int cnt = tile_cnt[t], ku = gm.k_u;
     if (threadIdx.x < TILE) lanes[threadIdx.x] = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
-    // use_w: W = U_0 itself (the shared basis columns), else A~_s U_0 of the tile's sample
     const float *__restrict__ AU =
         use_w ? (const float *)gm.wu : (const float *)gm.awu + (long long)tile_si[t] * ku * gm.ld;
     const float *__restrict__ Rb = (const float *)gm.r;
-    const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
-    float acc[4][KUT];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int c = 0; c < KUT; ++c) acc[q][c] = 0.f;
     const long long r0 = (long long)blockIdx.x * chunk;
     const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
     __syncthreads();
-    int lq[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) lq[q] = lanes[warp + 8 * q];
-    for (long long base = r0; base < r1; base += SN) {
-        // stage A~_s U_0 (r0 and chunk are multiples of SN; n is a multiple of 4)
-        for (int e = threadIdx.x; e < KUT * (SN / 4); e += blockDim.x) {
-            const int c = e / (SN / 4), v4 = e % (SN / 4);
+    // this thread's copies: r rows (lane e/SN4, float4 e%SN4) and U_0 rows
+    auto issue = [&](int s) {
+        float4 *stg = u0s + (size_t)(s % U0_NST) * STG;
+        const long long base = r0 + (long long)s * SN;
+        for (int e = threadIdx.x; e < TILE * SN4; e += kThreads) {
+            const int l = e / SN4, v4 = e % SN4;
             const long long p = base + 4 * v4;
-            As[c][v4] = (c < ku && p < r1) ? *(const float4 *)(AU + (long long)c * gm.ld + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int ln = lanes[l];
+            const bool ok = ln >= 0 && p < r1;
+            const float *src = ok ? Rb + (long long)ln * gm.ld + p : Rb;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(stg + l * RP + v4)),
+                         "l"(src), "r"(ok ? 16 : 0)
+                         : "memory");
         }
+        for (int e = threadIdx.x; e < KUT * SN4; e += kThreads) {
+            const int c = e / SN4, v4 = e % SN4;
+            const long long p = base + 4 * v4;
+            const bool ok = c < ku && p < r1;
+            const float *src = ok ? AU + (long long)c * gm.ld + p : AU;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(stg + TILE * RP + e)),
+                         "l"(src), "r"(ok ? 16 : 0)
+                         : "memory");
+        }
+    };
+    const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
+    float acc[KUT];
+#pragma unroll
+    for (int c = 0; c < KUT; ++c) acc[c] = 0.f;
+    for (int q = 0; q < 2; ++q) {
+        if (q < nst) issue(q);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int s = 0; s < nst; ++s) {
+        if (s + 2 < nst) issue(s + 2);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 2;" ::: "memory");
         __syncthreads();
-        const long long p = base + 4 * tl;
-        if (p < r1) {
-            float4 rv[4];
+        if (tl < cnt) {
+            const float4 *stg = u0s + (size_t)(s % U0_NST) * STG;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                rv[q] = lq[q] >= 0 ? *(const float4 *)(Rb + (long long)lq[q] * gm.ld + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < 4; ++j) {
+                const int v4 = warp * 4 + j;
+                const float4 rv = stg[tl * RP + v4];
 #pragma unroll
-            for (int c = 0; c < KUT; ++c) {
-                const float4 a = As[c][tl];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q][c] += dot4(a, rv[q]);
+                for (int c = 0; c < KUT; ++c) acc[c] += dot4(stg[TILE * RP + c * SN4 + v4], rv);
             }
         }
         __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // sum the eight warps' partials: red[w][c][l]
+    float *red = (float *)u0s;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int c = 0; c < KUT; ++c) red[(warp * KUT + c) * TILE + tl] = acc[c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < KUT * TILE; e += kThreads) {
+        const int c = e / TILE, l = e % TILE;
+        if (l < cnt && c < ku) {
+            float v = 0.f;
 #pragma unroll
-        for (int c = 0; c < KUT; ++c) {
-            float v = acc[q][c];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (tl == 0 && lq[q] >= 0 && c < ku)
-                atomicAdd(ls.wv + ((long long)sw * ls.m + lq[q]) * KMAX + c, (double)v);
+            for (int w = 0; w < kThreads / 32; ++w) v += red[(w * KUT + c) * TILE + l];
+            atomicAdd(ls.wv + ((long long)sw * ls.m + lanes[l]) * KMAX + c, (double)v);
         }
+    }
+}
+
+template <int KUT>
+void u0dots_attr() {
+    static bool attr[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_u0dots<KUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)u0_smem<KUT>()));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
     }
 }
 
@@ -460,6 +663,13 @@ int gx_for(long long nv, int rows, int per_sm) {
 
 bool cg4_supported(const Grid &g) { return (g.Nx % 4) == 0 && (g.ld % 4) == 0; }
 
+// The plane-streaming stencil: 3D, whole rows of float4 tiling 256 threads.
+bool stencil4z_supported(const Grid &g) {
+    const int nx4 = g.Nx / 4;
+    return g.Ny > 1 && (g.Nx % 4) == 0 && nx4 >= 1 && nx4 <= kThreads && kThreads % nx4 == 0 &&
+           (size_t)ZR * (ZL + 1) * (kThreads / nx4 + 2) * nx4 * sizeof(float4) <= 160 * 1024;
+}
+
 // One float32 iteration t over the active lanes (see the file comment).
 void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *const *diag_of_col,
                    const float *const *p_ptr, float *const *q_ptr, LaneGeom gm, LaneState ls, LaneList ll, int t,
@@ -469,8 +679,31 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     const long long nv = g.n >> 2;
     const bool tm = kt && kt->on;
     cudaEvent_t e = tm ? kt->start(st) : nullptr;
-    k_stencil4<<<dim3(gx_for(nv, ll.na, 8), ll.na), kThreads, 0, st>>>(
-        g, D, diag_of_col, p_ptr, q_ptr, ll.alist, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
+    if (stencil4z_supported(g)) {
+        const int nx4 = g.Nx / 4, TY = kThreads / nx4;
+        const int ytiles = (g.Ny + TY - 1) / TY, pairs = (ll.na + ZL - 1) / ZL;
+        // z-chunks: enough CTAs for ~4 waves at 3 CTAs per SM, chunks of >= 4 planes
+        const long long base = (long long)ytiles * pairs;
+        long long nzc = (12LL * 152 + base - 1) / base;
+        const long long maxc = (g.Nz + 3) / 4;
+        if (nzc > maxc) nzc = maxc;
+        if (nzc < 1) nzc = 1;
+        const int zc = (int)((g.Nz + nzc - 1) / nzc);
+        nzc = (g.Nz + zc - 1) / zc;
+        const size_t smem = (size_t)ZR * (ZL + 1) * (TY + 2) * nx4 * sizeof(float4);
+        static bool attr[64] = {};
+        int dev = 0;
+        RCG_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64 || !attr[dev]) {
+            RCG_CUDA_TRY(cudaFuncSetAttribute(k_stencil4z, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+            if (dev >= 0 && dev < 64) attr[dev] = true;
+        }
+        k_stencil4z<<<dim3((unsigned)(ytiles * nzc), pairs), kThreads, smem, st>>>(
+            g, D, diag_of_col, p_ptr, q_ptr, ll.alist, ll.na, ls.active, ls.pq + (long long)spq * ls.m, ls.prof, zc);
+    } else {
+        k_stencil4<<<dim3(gx_for(nv, ll.na, 8), ll.na), kThreads, 0, st>>>(
+            g, D, diag_of_col, p_ptr, q_ptr, ll.alist, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
+    }
     count_launch();
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(0, e, st); e = kt->start(st); }
@@ -494,7 +727,8 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         long long z;
         const long long chunk = tile_chunk(z);
         dim3 grid((unsigned)z, ll.ntiles);
-#define RCG_U0(K) k_u0dots<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, sw, chunk, 0)
+#define RCG_U0(K) u0dots_attr<K>(); \
+        k_u0dots<K><<<grid, kThreads, u0_smem<K>(), st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, sw, chunk, 0)
         switch (kut) { case 4: RCG_U0(4); break; case 8: RCG_U0(8); break; case 12: RCG_U0(12); break; default: RCG_U0(16); }
 #undef RCG_U0
         count_launch();
@@ -510,7 +744,8 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         const long long chunk = tile_chunk(z);
         dim3 grid((unsigned)z, ll.ntiles);
 #define RCG_DIR(K) k_direction4<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk)
-        switch (kut) { case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break; default: RCG_DIR(16); }
+        switch (kut) { case 0: case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break;
+                       default: RCG_DIR(16); }
 #undef RCG_DIR
         count_launch();
         RCG_CHECK_LAUNCH();
@@ -535,7 +770,8 @@ void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, Lane
     z = (g.n + chunk - 1) / chunk;
     const dim3 tgrid((unsigned)z, ll.ntiles), lgrid(gx_for(nv, ll.na, 8), ll.na);
     const int kut = gm.k_u <= 4 ? 4 : gm.k_u <= 8 ? 8 : gm.k_u <= 12 ? 12 : 16;
-#define RCG_U0(K, W, SLOT) k_u0dots<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, SLOT, chunk, W)
+#define RCG_U0(K, W, SLOT) u0dots_attr<K>(); \
+    k_u0dots<K><<<tgrid, kThreads, u0_smem<K>(), st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, SLOT, chunk, W)
 #define RCG_U0S(W, SLOT) switch (kut) { case 4: RCG_U0(4, W, SLOT); break; case 8: RCG_U0(8, W, SLOT); break; \
                                     case 12: RCG_U0(12, W, SLOT); break; default: RCG_U0(16, W, SLOT); }
     // z = W^T r -> wv[sA]

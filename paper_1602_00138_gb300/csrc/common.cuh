@@ -224,6 +224,7 @@ void ritz_res(cudaStream_t st, const T *AX, const T *X, const double *theta, lon
 
 // cg4.cu (float32, Nx % 4 == 0)
 bool cg4_supported(const Grid &g);
+bool stencil4z_supported(const Grid &g);
 void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *const *diag_of_col,
                    const float *const *p_ptr, float *const *q_ptr, LaneGeom gm, LaneState ls, LaneList ll, int t,
                    float *mu, float *beta, KTimer *kt);

@@ -119,10 +119,11 @@ def test_fp64_wave_matches_oracle(torch_cuda, name):
     _check_run(name, rcg.RCG_FP64, rcg.RCG_WAVE, 1e-9, 1e-8, 1e-7)
 
 
-@pytest.mark.parametrize("name", ["t3d_21", "t3d_33", "t3d_32", "t2d_40"])
+@pytest.mark.parametrize("name", ["t3d_21", "t3d_33", "t3d_32", "t2d_40", "t3d_16"])
 def test_mixed_wave_matches_oracle(torch_cuda, name):
-    # t3d_32 and t2d_40 (Nx % 4 == 0) run the float4 inner iteration; the
-    # others the scalar one
+    # t3d_32, t2d_40 and t3d_16 (Nx % 4 == 0) run the float4 inner iteration
+    # (the 3D ones with the plane-streaming stencil, t3d_16 with a ragged
+    # y-tile); the others the scalar one
     from paper_1602_00138_gb300 import rcg
     _check_run(name, rcg.RCG_MIXED, rcg.RCG_WAVE, 1e-6, 1e-6, 1e-5)
 
