@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--ncu-region", action="store_true",
                     help="profile only the timed steps (cudaProfilerStart/Stop); skip the other legs")
+    ap.add_argument("--products", action="store_true",
+                    help="time the basis product A^T B on the tensor cores and on CUDA cores (one JSON line per shape)")
+    ap.add_argument("--products-shapes", type=int, default=4, help="number of --products shapes to run")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
@@ -352,8 +355,45 @@ def run_oracle_subprocess(args, steps=1, warmup=0):
 
 
 # ---------------------------------------------------------------------- main
+def products_bench(torch, nshapes):
+    """Time rcg_gemm_tn_f32 (the append's orthogonalisation product) on both
+    engines for the bench workload's shapes: 320 lanes / rank ~300 at 64^3 and
+    1280 lanes at 128^3.  Inputs are larger than L2; events on the stream."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_1602_00138_gb300 import rcg
+    shapes = [(262144, 320, 320, False), (262144, 320, 320, True), (262144, 300, 40, False),
+              (2097152, 1280, 1280, True)]
+    for n, ka, kb, sym in shapes[:nshapes]:
+        X = torch.rand((ka + (0 if sym else kb), n), dtype=torch.float32, device="cuda")
+        A = X[:ka]
+        B = A if sym else X[ka:]
+        out = {"n": n, "ka": ka, "kb": kb, "symmetric": sym}
+        for engine, key in ((1, "tensor_core_us"), (0, "cuda_core_us")):
+            reps = 5 if (engine == 1 or ka * kb < 500000) else 2
+            for _ in range(3):
+                rcg.gemm_tn_f32(A, B, engine=engine, symmetric=sym)
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(reps):
+                rcg.gemm_tn_f32(A, B, engine=engine, symmetric=sym)
+            e1.record(st)
+            torch.cuda.synchronize()
+            out[key] = round(e0.elapsed_time(e1) * 1e3 / reps, 1)
+        flops = 2.0 * n * ka * kb / (2 if sym else 1)
+        out["tensor_core_tflops"] = round(flops / out["tensor_core_us"] / 1e6, 1)
+        print(json.dumps(out))
+        del X
+
+
 def main():
     args = parse_args()
+    if args.products:
+        import torch
+        products_bench(torch, args.products_shapes)
+        return
     if args.cpu_worker:
         oracle_worker(args)
         return

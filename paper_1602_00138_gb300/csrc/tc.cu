@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 namespace rcg {
 namespace {
@@ -385,3 +386,57 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
 }
 
 }  // namespace rcg
+
+// ------------------------------------------------------------ C ABI
+namespace {
+// Split-K scratch and timeout flag of rcg_gemm_tn_f32, one per device, grown
+// on demand and kept until exit; the mutex is held for the whole call (which
+// waits for its stream), so concurrent host threads take turns.
+std::mutex g_gemm_mu;
+float *g_gemm_scr[64] = {};
+long long g_gemm_cap[64] = {};
+int *g_gemm_err[64] = {};
+}  // namespace
+
+extern "C" int rcg_gemm_tn_f32(const float *A, long long lda, int ka, const float *B, long long ldb, int kb,
+                               long long n, double *C, int ldc, int engine, int symmetric, void *stream) {
+    using namespace rcg;
+    if ((n > 0 && (!A || !B)) || !C || ka < 0 || kb < 0 || n < 0 || lda < n || ldb < n || ldc < ka ||
+        (engine != 0 && engine != 1))
+        return RCG_ERR_INVALID;
+    if (symmetric && (A != B || ka != kb || lda != ldb)) return RCG_ERR_INVALID;
+    if (engine == 1 && !tc_gemm_tn_ok(lda, ldb, A, B)) return RCG_ERR_INVALID;
+    if (ka == 0 || kb == 0) return RCG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_gemm_mu);
+    int rc = RCG_OK;
+    try {
+        int dev = 0;
+        RCG_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) return RCG_ERR_INVALID;
+        if (engine == 1) {
+            const long long need = tc_gemm_tn_scratch(n, ka, kb, symmetric != 0, nullptr, nullptr);
+            if (need > g_gemm_cap[dev]) {
+                if (g_gemm_scr[dev]) RCG_CUDA_TRY(cudaFree(g_gemm_scr[dev]));
+                g_gemm_scr[dev] = nullptr;
+                g_gemm_cap[dev] = 0;
+                RCG_CUDA_TRY(cudaMalloc(&g_gemm_scr[dev], sizeof(float) * (size_t)need));
+                g_gemm_cap[dev] = need;
+            }
+            if (!g_gemm_err[dev]) RCG_CUDA_TRY(cudaMalloc(&g_gemm_err[dev], sizeof(int)));
+            RCG_CUDA_TRY(cudaMemsetAsync(g_gemm_err[dev], 0, sizeof(int), st));
+            tc_gemm_tn(st, n, A, lda, ka, B, ldb, kb, C, ldc, false, symmetric != 0, g_gemm_scr[dev], g_gemm_err[dev]);
+        } else {
+            gemm_tn<float, float>(st, n, A, lda, ka, B, ldb, kb, C, ldc, false);
+        }
+        RCG_CUDA_TRY(cudaStreamSynchronize(st));
+        if (engine == 1) {
+            int h = 0;
+            RCG_CUDA_TRY(cudaMemcpy(&h, g_gemm_err[dev], sizeof(int), cudaMemcpyDeviceToHost));
+            if (h) rc = RCG_ERR_TIMEOUT;
+        }
+    } catch (const Error &e) {
+        rc = e.code;
+    }
+    return rc;
+}

@@ -96,6 +96,7 @@ def load(path=LIB_PATH):
         "rcg_launch_count": (LL, [P]),
         "rcg_profile_enable": (I, [P, I]),
         "rcg_profile_get": (I, [P, I, C.POINTER(KProf)]),
+        "rcg_gemm_tn_f32": (I, [P, LL, I, P, LL, I, LL, P, I, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,6 +125,24 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return a.data_ptr()
     raise TypeError(type(a))
+
+
+def gemm_tn_f32(A, B, engine=1, symmetric=False, stream=None):
+    """C = A^T B (float64, ka x kb) for float32 CUDA tensors A (n x ka) and B
+    (n x kb) stored column-major, i.e. passed as (ka, n) / (kb, n) row-major
+    views (`A_cols[i]` = column i); see rcg_gemm_tn_f32."""
+    import torch
+    ka, n = A.shape
+    kb, nb = B.shape
+    assert n == nb and A.dtype == torch.float32 and B.dtype == torch.float32
+    assert A.stride(1) == 1 and B.stride(1) == 1
+    Cm = torch.empty((kb, ka), dtype=torch.float64, device=A.device)
+    st = stream if stream is not None else torch.cuda.current_stream(A.device).cuda_stream
+    rc = lib().rcg_gemm_tn_f32(A.data_ptr(), A.stride(0), ka, B.data_ptr(), B.stride(0), kb, n,
+                               Cm.data_ptr(), ka, engine, 1 if symmetric else 0, st)
+    if rc != 0:
+        raise RcgError(rc, lib().rcg_strerror(rc).decode())
+    return Cm.t()
 
 
 def default_options(**kw):
