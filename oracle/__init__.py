@@ -17,6 +17,8 @@ Contents (each function cites the passage of the paper it restates):
                ordered rank-revealing append.
   rom       -- reduced transfer function and Jacobian (Sec. 3.3-3.4, eqs.
                newreduced, newjac) and the full-order plain definitions.
+  cnn       -- the learned augmentation of the private recycle space (not
+               in the paper): coarse 3D CNN forward pass, features, loss.
 
 All arithmetic is float64.  Parity status of each function is recorded in
 its docstring; every function here is pinned by a -m "not gpu" test against
