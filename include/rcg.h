@@ -93,6 +93,9 @@ typedef struct {
     int    keep_solutions;/* keep every delivered x (for rcg_solution_get)  */
     int    seed_degree;   /* Chebyshev filter degree of the eigen seed      */
     long long spin_budget;/* reserved: bound of device-side waits           */
+    int    learned;       /* RCG_MIXED: add the learned network's column to
+                             the private U_j of every CG solve (needs
+                             weights: rcg_learn_set_weights or _train)      */
 } rcg_options;
 
 typedef struct {
@@ -104,12 +107,13 @@ typedef struct {
     double relres0;       /* relres of the Galerkin guess from V            */
     double relres;        /* final relres, float64 residual recomputed      */
     double ratio;         /* ||new part|| / ||x|| at the append decision    */
+    int    augmented;     /* 1 if the learned column joined U_j of this solve */
 } rcg_stat;
 
 /* Fill *o with defaults: FP64, sequential, tau_rank 1e-12, k_u 10,
  * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-5,
  * check_refine 0, keep_solutions 0,
- * seed_degree 0 (automatic). */
+ * seed_degree 0 (automatic), learned 0. */
 void rcg_options_default(rcg_options *o);
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a
@@ -252,6 +256,47 @@ typedef struct {
 } rcg_kprof;
 int rcg_profile_enable(rcg_ctx *c, int on);
 int rcg_profile_get(rcg_ctx *c, int kernel, rcg_kprof *out);
+
+/* ---------------------------------------------------------------- learned
+ * Learned augmentation of the private recycle spaces (not in the paper; the
+ * learned step of this library's mixed-precision contender).  For a
+ * right-hand side whose Galerkin check fails, a 3D CNN on a coarse grid
+ * (block means over f^3 fine nodes, f = 4, 2 or 1) maps the features
+ * [coarse(r0) / max|coarse(r0)|, coarse(mu) / mean(mu) - 1] (bfloat16) of its
+ * check residual r0 and the sample's mu to the shape of the correction
+ * A~^-1 r0; the trilinear upsampling x_hat joins that solve's private U_j
+ * (never V) iff its Galerkin pivot sqrt(s/d) > tau_rank, where d = x_hat^T
+ * A~ x_hat and s = d - c^T (U_j^T A~ U_j)^-1 c, c = U_j^T A~ x_hat.  Network:
+ * channels 2-16-16-16-16-16-1, 3x3x3 zero-padded convolutions with bias, ReLU
+ * between layers, rcg_learn_nparams() parameters laid out per layer as
+ * W [Cout][Cin][27] (offset (dz+1)*9+(dy+1)*3+(dx+1)) then b [Cout].
+ * Inference rounds the weights to bfloat16 (float32 sums); training keeps
+ * float32 master weights (Adam, mean squared error against
+ * coarse(x - x0) / max|coarse(x - x0)| of recorded solves).  All arrays
+ * below are host memory owned by the caller; coarse arrays are
+ * [batch][channel][Gz][Gy][Gx], x fastest. */
+int rcg_learn_nparams(void);
+/* dims[0..3] = Gx, Gy, Gz, f of the context's grid. */
+int rcg_learn_geometry(rcg_ctx *c, int *dims);
+int rcg_learn_set_weights(rcg_ctx *c, const float *theta, int nparam);
+int rcg_learn_get_weights(rcg_ctx *c, float *theta, int nparam);
+/* on != 0: every later rcg_solve_all records one (features, target) pair per
+ * CG solve (held in device memory); *npairs = pairs recorded so far. */
+int rcg_learn_record(rcg_ctx *c, int on);
+int rcg_learn_pairs(rcg_ctx *c, int *npairs);
+/* Adam (beta 0.9 / 0.999) over the recorded pairs: `epochs` passes in
+ * shuffled batches of `batch` (shuffles seeded by `seed`); *loss (may be NULL)
+ * = mean loss of the last epoch.  RCG_ERR_INVALID if nothing was recorded. */
+int rcg_learn_train(rcg_ctx *c, int epochs, int batch, double lr, unsigned long long seed, double *loss);
+/* The network on B inputs in[B][2][V] -> out[B][V]; rounded != 0: bfloat16
+ * weights (inference), else the float32 master weights. */
+int rcg_learn_forward(rcg_ctx *c, const float *in, int B, int rounded, float *out);
+/* Loss and its gradient grad[nparam] with respect to the master weights for
+ * one batch in[B][2][V], targets tg[B][V]. */
+int rcg_learn_gradient(rcg_ctx *c, const float *in, const float *tg, int B, float *grad, double *loss);
+/* Features feat[2][V] (may be NULL) and x_hat[n] (may be NULL) of one
+ * residual r0[n] (float32) at sample slot s, with the bfloat16 weights. */
+int rcg_learn_predict(rcg_ctx *c, int s, const float *r0, float *feat, float *xhat);
 
 #ifdef __cplusplus
 }

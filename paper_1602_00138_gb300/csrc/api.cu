@@ -75,6 +75,11 @@ struct rcg_ctx {
     std::map<std::string, double> phase;
     std::vector<std::vector<double>> solutions;   // per sample, host copies (keep_solutions)
     KTimer ktimer;                                 // optional device timing of the CG kernels
+    std::unique_ptr<Cnn> cnn;                      // learned augmentation (created on first use)
+    Cnn &net() {
+        if (!cnn) cnn.reset(new Cnn(g));
+        return *cnn;
+    }
     unsigned long long *d_prof = nullptr;          // work counters of the CG kernels
 
     template <typename T> T *alloc(size_t count) {
@@ -165,6 +170,28 @@ struct Engine : EngineBase {
     int *d_info = nullptr;          // [0] Cholesky info, [1] sticky tensor-core wait timeout
     float *tc_scr = nullptr;        // split-K slices of the tensor-core products
     long long tc_cap = 0;
+    // learned augmentation: per-lane pointer lists, rows, pivot data
+    const float **d_lr = nullptr;
+    const double **d_lm = nullptr, **d_lx = nullptr;
+    float **d_ldst = nullptr;
+    int *d_arow = nullptr, *d_aug_l = nullptr, *d_kept = nullptr;
+    double *d_cd = nullptr;
+    int lp_cap = 0;
+    void ensure_learn(int m) {
+        if (m <= lp_cap) return;
+        for (void *p : std::vector<void *>{(void *)d_lr, (void *)d_lm, (void *)d_lx, (void *)d_ldst, (void *)d_arow,
+                                           (void *)d_aug_l, (void *)d_kept, (void *)d_cd})
+            c->release(p);
+        lp_cap = m;
+        d_lr = c->alloc<const float *>(m);
+        d_lm = c->alloc<const double *>(m);
+        d_lx = c->alloc<const double *>(m);
+        d_ldst = c->alloc<float *>(m);
+        d_arow = c->alloc<int>(m);
+        d_aug_l = c->alloc<int>(m);
+        d_kept = c->alloc<int>(m);
+        d_cd = c->alloc<double>((size_t)m * (KMAX + 1));
+    }
     // rom workspace
     double *Ar = nullptr, *Br = nullptr, *Crm = nullptr, *Xr = nullptr, *Zr = nullptr, *wtmp = nullptr;
     double *VX = nullptr, *VZ = nullptr;
@@ -555,6 +582,42 @@ struct Engine : EngineBase {
             }
         }
         std::vector<int> iters_h(m, 0);
+        // learned augmentation (float32 engine): features of the check residuals,
+        // the network's coarse prediction, coarse x0 when recording pairs
+        Cnn *net = nullptr;
+        if constexpr (sizeof(T) == 4) {
+            if (!seed_mode && c->cnn && (c->cnn->record || (c->opt.learned && c->cnn->have))) net = c->cnn.get();
+        }
+        const bool use_aug = net && c->opt.learned && net->have;
+        std::vector<int> alanes;
+        if (net && nact) {
+            for (int l = 0; l < m; ++l)
+                if (act[l]) alanes.push_back(l);
+            const int na = (int)alanes.size();
+            const long long Vc = net->geom.V;
+            ensure_learn(m);
+            std::vector<const float *> hr(na);
+            std::vector<const double *> hm(na), hx(na);
+            for (int a = 0; a < na; ++a) {
+                const int l = alanes[a];
+                hr[a] = (const float *)(rv + (long long)l * ld);
+                hm[a] = c->mu64 + (long long)samp[l] * ld;
+                hx[a] = x64 + (long long)l * ld;
+            }
+            c->h2d(d_lr, hr.data(), na);
+            c->h2d(d_lm, hm.data(), na);
+            c->h2d(d_lx, hx.data(), na);
+            net->ensure(net->feat, net->feat_cap, (long long)na * 2 * Vc);
+            net->features(st, d_lr, d_lm, na, net->feat);
+            if (net->record) {
+                net->ensure(net->x0c, net->x0c_cap, (long long)na * Vc);
+                net->pool64(st, d_lx, net->x0c, na, -1.f, false);
+            }
+            if (use_aug) {
+                net->ensure(net->outc, net->outc_cap, (long long)na * Vc);
+                net->forward(st, net->feat, na, net->outc, true);
+            }
+        }
         if (nact) {
             // deflation spaces: U_j = [V(:, 0:k_u), X_0(:, j), V(:, priv_j)] (seed: V(:, 0:k_u))
             std::vector<int> spec((size_t)m * KMAX, 0), kdef(m, 0), kp(m, 0), si(m, 0);
@@ -606,7 +669,15 @@ struct Engine : EngineBase {
                 sxp[l] = sX0 ? sX0 + (long long)lanes[l].j * rmax : nullptr;
                 gsl[l] = gal.count(samp[l]) ? gal[samp[l]].first : nullptr;
             }
-            const long long npriv = (long long)m * kp_max;
+            // one more private slot for the network's column where it fits
+            std::vector<int> aug(m, 0);
+            int kps = kp_max;
+            if (use_aug)
+                for (int l = 0; l < m; ++l) {
+                    aug[l] = act[l] && kp[l] < KP_MAX;
+                    kps = std::max(kps, kp[l] + aug[l]);
+                }
+            const long long npriv = (long long)m * kps;
             if (npriv > awp_cap) {
                 c->release(awp);
                 c->release(wpb);
@@ -621,16 +692,38 @@ struct Engine : EngineBase {
                 for (int q = 0; q < kp[l]; ++q) {
                     const int e = spec[(size_t)l * KMAX + ku + q];
                     psrc.push_back(e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld);
-                    T *w = wpb + ((long long)l * kp_max + q) * ld;
+                    T *w = wpb + ((long long)l * kps + q) * ld;
                     pdst.push_back(w);
                     asrc.push_back(w);
-                    adst.push_back(awp + ((long long)l * kp_max + q) * ld);
+                    adst.push_back(awp + ((long long)l * kps + q) * ld);
                     asamp.push_back(samp[l]);
                 }
             if (!psrc.empty()) {
                 for (size_t i = 0; i < psrc.size(); ++i)
                     RCG_CUDA_TRY(cudaMemcpyAsync(pdst[i], psrc[i], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
                 c->sync();
+            }
+            // the network's column x_hat in slot kp[l] of the lane, then A~ x_hat with the others
+            std::vector<int> aug_l;
+            if (use_aug) {
+                std::vector<float *> hd;
+                std::vector<int> rows;
+                for (size_t a = 0; a < alanes.size(); ++a) {
+                    const int l = alanes[a];
+                    if (!aug[l]) continue;
+                    T *w = wpb + ((long long)l * kps + kp[l]) * ld;
+                    hd.push_back((float *)w);
+                    rows.push_back((int)a);
+                    aug_l.push_back(l);
+                    asrc.push_back(w);
+                    adst.push_back(awp + ((long long)l * kps + kp[l]) * ld);
+                    asamp.push_back(samp[l]);
+                }
+                if (!hd.empty()) {
+                    c->h2d(d_ldst, hd.data(), hd.size());
+                    c->h2d(d_arow, rows.data(), rows.size());
+                    net->upsample(st, net->outc, d_ldst, d_arow, (int)hd.size());
+                }
             }
             apply_cols(asrc, adst, asamp);
             c->h2d(d_spec, spec.data(), (size_t)m * KMAX);
@@ -642,7 +735,7 @@ struct Engine : EngineBase {
             LaneGeom gm{};
             gm.ld = ld;
             gm.k_u = ku;
-            gm.kp_max = std::max(kp_max, 1);
+            gm.kp_max = std::max(kps, 1);
             gm.x = xc; gm.r = rv; gm.p = pv; gm.q = qv;
             gm.wu = V; gm.awu = au0; gm.wp = wpb; gm.awp = awp;
             gm.si = d_si; gm.kp = d_kp;
@@ -651,6 +744,18 @@ struct Engine : EngineBase {
                 RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
                 lane_inverse(st, ls.gw, ls.kdef, m, d_info);
                 check_info("deflation matrix U_j^T A U_j");
+            }
+            if (!aug_l.empty()) {
+                // Galerkin pivot of x_hat against U_j; kept columns border G_W^-1 on the device
+                const int nq = (int)aug_l.size();
+                c->h2d(d_aug_l, aug_l.data(), nq);
+                aug_dots(st, n, ld, (const float *)V, ku, (const float *)wpb, (const float *)awp, kps, d_kp, d_aug_l, nq,
+                         d_cd);
+                aug_border(st, ls.gw, ls.kdef, d_kp, d_aug_l, nq, d_cd, c->opt.tau_rank, d_kept);
+                std::vector<int> kh(nq);
+                c->d2h(kh.data(), d_kept, nq);
+                c->sync();
+                for (int i = 0; i < nq; ++i) out[aug_l[i]].augmented = kh[i];
             }
             // thresholds and the first (re)start
             std::vector<double> thr(m, 0.0);
@@ -771,6 +876,13 @@ struct Engine : EngineBase {
             }
             c->d2h(iters_h.data(), ls.iters, m);
             c->sync();
+            if (net && net->record && !alanes.empty()) {
+                // training pairs: features of r0 and coarse(x - x0) / max, x the delivered solution
+                const int na = (int)alanes.size();
+                net->pool64(st, d_lx, net->x0c, na, 1.f, true);
+                net->normalise(st, net->x0c, na);
+                net->add_pairs(st, net->feat, net->x0c, na);
+            }
         }
         RCG_CUDA_TRY(cudaEventRecord(e2, st));
 
@@ -1436,6 +1548,131 @@ double rcg_phase_ms(const rcg_ctx *c, const char *phase) {
 }
 
 long long rcg_launch_count(const rcg_ctx *c) { return c ? c->launches : -1; }
+
+// ------------------------------------------------------------ learned
+int rcg_learn_nparams(void) { return cnn_nparams(); }
+
+int rcg_learn_geometry(rcg_ctx *c, int *dims) {
+    return guarded(c, [&]() {
+        if (!dims) throw Error{RCG_ERR_INVALID, "rcg_learn_geometry: dims is NULL"};
+        const CnnGeom cg = cnn_geom(c->g);
+        dims[0] = cg.Gx; dims[1] = cg.Gy; dims[2] = cg.Gz; dims[3] = cg.f;
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_set_weights(rcg_ctx *c, const float *theta, int nparam) {
+    return guarded(c, [&]() {
+        if (!theta || nparam != cnn_nparams()) throw Error{RCG_ERR_INVALID, "rcg_learn_set_weights: nparam mismatch"};
+        for (int i = 0; i < nparam; ++i)
+            if (!std::isfinite(theta[i])) throw Error{RCG_ERR_INVALID, "rcg_learn_set_weights: non-finite weight"};
+        c->net().set_weights(c->st, theta);
+        c->sync();
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_get_weights(rcg_ctx *c, float *theta, int nparam) {
+    return guarded(c, [&]() {
+        if (!theta || nparam != cnn_nparams()) throw Error{RCG_ERR_INVALID, "rcg_learn_get_weights: nparam mismatch"};
+        if (!c->cnn || !c->cnn->have) throw Error{RCG_ERR_INVALID, "rcg_learn_get_weights: no weights yet"};
+        c->d2h(theta, c->cnn->theta, nparam);
+        c->sync();
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_record(rcg_ctx *c, int on) {
+    return guarded(c, [&]() {
+        if (c->opt.precision != RCG_MIXED) throw Error{RCG_ERR_INVALID, "rcg_learn_record: RCG_MIXED only"};
+        c->net().record = on != 0;
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_pairs(rcg_ctx *c, int *npairs) {
+    return guarded(c, [&]() {
+        if (!npairs) throw Error{RCG_ERR_INVALID, "rcg_learn_pairs: NULL"};
+        *npairs = c->cnn ? c->cnn->npairs : 0;
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_train(rcg_ctx *c, int epochs, int batch, double lr, unsigned long long seed, double *loss) {
+    return guarded(c, [&]() {
+        if (epochs < 0 || batch < 1 || !(lr > 0.0)) throw Error{RCG_ERR_INVALID, "rcg_learn_train: bad arguments"};
+        if (!c->cnn || !c->cnn->have) throw Error{RCG_ERR_INVALID, "rcg_learn_train: set initial weights first"};
+        const double l = c->cnn->train(c->st, epochs, batch, lr, seed);
+        if (loss) *loss = l;
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_forward(rcg_ctx *c, const float *in, int B, int rounded, float *out) {
+    return guarded(c, [&]() {
+        if (!in || !out || B < 1) throw Error{RCG_ERR_INVALID, "rcg_learn_forward: bad arguments"};
+        Cnn &net = c->net();
+        if (!net.have) throw Error{RCG_ERR_INVALID, "rcg_learn_forward: no weights"};
+        const long long V = net.geom.V;
+        float *din = c->alloc<float>((size_t)B * 2 * V), *dout = c->alloc<float>((size_t)B * V);
+        c->h2d(din, in, (size_t)B * 2 * V);
+        net.forward(c->st, din, B, dout, rounded != 0);
+        c->d2h(out, dout, (size_t)B * V);
+        c->sync();
+        c->release(din);
+        c->release(dout);
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_gradient(rcg_ctx *c, const float *in, const float *tg, int B, float *grad, double *loss) {
+    return guarded(c, [&]() {
+        if (!in || !tg || !grad || B < 1) throw Error{RCG_ERR_INVALID, "rcg_learn_gradient: bad arguments"};
+        Cnn &net = c->net();
+        if (!net.have) throw Error{RCG_ERR_INVALID, "rcg_learn_gradient: no weights"};
+        const long long V = net.geom.V;
+        float *din = c->alloc<float>((size_t)B * 2 * V), *dtg = c->alloc<float>((size_t)B * V);
+        c->h2d(din, in, (size_t)B * 2 * V);
+        c->h2d(dtg, tg, (size_t)B * V);
+        const double l = net.gradient(c->st, din, dtg, B);
+        c->d2h(grad, net.grad, net.P);
+        c->sync();
+        c->release(din);
+        c->release(dtg);
+        if (loss) *loss = l;
+        return RCG_OK;
+    });
+}
+
+int rcg_learn_predict(rcg_ctx *c, int s, const float *r0, float *feat, float *xhat) {
+    return guarded(c, [&]() {
+        if (!r0 || s < 0 || s >= c->opt.max_samples || !c->sample_set[s])
+            throw Error{RCG_ERR_INVALID, "rcg_learn_predict: bad arguments or sample slot not set"};
+        Cnn &net = c->net();
+        if (!net.have) throw Error{RCG_ERR_INVALID, "rcg_learn_predict: no weights"};
+        const long long V = net.geom.V;
+        float *dr = c->alloc<float>((size_t)c->ld), *df = c->alloc<float>((size_t)2 * V), *dout = c->alloc<float>(V);
+        float *dx = c->alloc<float>((size_t)c->ld);
+        const float **pr = c->alloc<const float *>(1);
+        const double **pm = c->alloc<const double *>(1);
+        float **px = c->alloc<float *>(1);
+        const float *hr = dr;
+        const double *hm = c->mu64 + (long long)s * c->ld;
+        float *hx = dx;
+        c->h2d(dr, r0, (size_t)c->n);
+        c->h2d(pr, &hr, 1);
+        c->h2d(pm, &hm, 1);
+        c->h2d(px, &hx, 1);
+        net.features(c->st, pr, pm, 1, df);
+        net.forward(c->st, df, 1, dout, true);
+        net.upsample(c->st, dout, px, nullptr, 1);
+        if (feat) c->d2h(feat, df, (size_t)2 * V);
+        if (xhat) c->d2h(xhat, dx, (size_t)c->n);
+        c->sync();
+        for (void *p : std::vector<void *>{dr, df, dout, dx, (void *)pr, (void *)pm, (void *)px}) c->release(p);
+        return RCG_OK;
+    });
+}
 
 int rcg_profile_enable(rcg_ctx *c, int on) {
     return guarded(c, [&]() {

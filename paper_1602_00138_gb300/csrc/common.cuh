@@ -142,6 +142,73 @@ struct LaneList {
     int ntiles;
 };
 
+// ------------------------------------------------------------ learned augmentation (cnn.cu)
+struct CnnGeom {
+    int Nx, Ny, Nz;      // fine grid
+    int f;               // pooling factor (4, 2 or 1; y is not pooled in 2D)
+    int Gx, Gy, Gz;      // coarse grid
+    long long V;         // coarse nodes
+};
+constexpr int CNN_LAYERS = 6;
+extern const int CNN_CH[CNN_LAYERS + 1];
+CnnGeom cnn_geom(const Grid &g);
+int cnn_nparams();
+
+// The network, its Adam state, the recorded training pairs and work buffers
+// (device memory owned here).
+class Cnn {
+  public:
+    explicit Cnn(const Grid &g);
+    ~Cnn();
+    Cnn(const Cnn &) = delete;
+    Cnn &operator=(const Cnn &) = delete;
+
+    void set_weights(cudaStream_t st, const float *host);
+    void refresh_bf16(cudaStream_t st);
+    void features(cudaStream_t st, const float *const *r0, const double *const *mu, int nl, float *out);
+    void forward(cudaStream_t st, const float *in, int B, float *out, bool rounded);
+    double gradient(cudaStream_t st, const float *in, const float *tg, int B);
+    void add_pairs(cudaStream_t st, const float *feat, const float *tgt, int cnt);
+    double train(cudaStream_t st, int epochs, int B, double lr, unsigned long long seed);
+    void upsample(cudaStream_t st, const float *out, float *const *dst, const int *rows, int B);
+    void pool64(cudaStream_t st, const double *const *src, float *out, int B, float sign, bool accumulate);
+    void normalise(cudaStream_t st, float *a, int B);
+    void ensure(float *&p, long long &cap, long long need);
+
+    CnnGeom geom;
+    int P;
+    bool have = false;       // weights set or trained
+    bool record = false;     // record (features, target) pairs from solves
+    int npairs = 0;
+    float *theta = nullptr, *theta16 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+    double *d_loss = nullptr;
+    long long t_adam = 0;
+    int woff[CNN_LAYERS], boff[CNN_LAYERS];
+    // work buffers of the solver integration (grown on demand)
+    float *feat = nullptr, *outc = nullptr, *x0c = nullptr;
+    long long feat_cap = 0, outc_cap = 0, x0c_cap = 0;
+
+  private:
+    void conv(cudaStream_t st, int l, const float *in, float *out, int B, bool relu, bool rounded);
+    void forward_backward(cudaStream_t st, const float *in, const float *tg, int B);
+    float *act = nullptr, *dact0 = nullptr, *dact1 = nullptr;
+    long long act_cap = 0, dact0_cap = 0, dact1_cap = 0;
+    float *pin = nullptr, *ptg = nullptr;
+    long long pair_cap = 0;
+    float *bin = nullptr, *btg = nullptr;
+    long long bin_cap = 0, btg_cap = 0;
+    int *d_idx = nullptr;
+    long long idx_cap = 0;
+};
+
+// Augmentation of the private deflation spaces by the network's columns:
+// dots of A~ x_hat with every deflation column and x_hat, then the Galerkin
+// pivot test and the bordered inverse (see cnn.cu).
+void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku, const float *wpb,
+              const float *awp, int kps, const int *kp, const int *alist, int na, double *cd);
+void aug_border(cudaStream_t st, double *gw, int *kdef, int *kp, const int *alist, int na, const double *cd,
+                double tau, int *kept);
+
 // ------------------------------------------------------------ launchers
 // stencil.cu
 template <typename T>

@@ -33,6 +33,9 @@ EXPORTED = [
     "rcg_set_sample_device", "rcg_apply", "rcg_seed", "rcg_reset_to_seed", "rcg_solve_all",
     "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device",
     "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
+    "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
+    "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
+    "rcg_learn_gradient", "rcg_learn_predict",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
 
@@ -46,13 +49,13 @@ class Options(C.Structure):
                 ("tau_rank", C.c_double), ("k_u", C.c_int), ("k_cap", C.c_int), ("r_max", C.c_int),
                 ("max_samples", C.c_int), ("maxit", C.c_int), ("inner_eta", C.c_double),
                 ("check_refine", C.c_int), ("keep_solutions", C.c_int), ("seed_degree", C.c_int),
-                ("spin_budget", C.c_longlong)]
+                ("spin_budget", C.c_longlong), ("learned", C.c_int)]
 
 
 class Stat(C.Structure):
     _fields_ = [("sample", C.c_int), ("rhs", C.c_int), ("iters", C.c_int), ("restarts", C.c_int),
                 ("appended", C.c_int), ("status", C.c_int), ("relres0", C.c_double),
-                ("relres", C.c_double), ("ratio", C.c_double)]
+                ("relres", C.c_double), ("ratio", C.c_double), ("augmented", C.c_int)]
 
 
 class KProf(C.Structure):
@@ -97,6 +100,16 @@ def load(path=LIB_PATH):
         "rcg_profile_enable": (I, [P, I]),
         "rcg_profile_get": (I, [P, I, C.POINTER(KProf)]),
         "rcg_gemm_tn_f32": (I, [P, LL, I, P, LL, I, LL, P, I, I, I, P]),
+        "rcg_learn_nparams": (I, []),
+        "rcg_learn_geometry": (I, [P, P]),
+        "rcg_learn_set_weights": (I, [P, P, I]),
+        "rcg_learn_get_weights": (I, [P, P, I]),
+        "rcg_learn_record": (I, [P, I]),
+        "rcg_learn_pairs": (I, [P, C.POINTER(I)]),
+        "rcg_learn_train": (I, [P, I, I, D, C.c_ulonglong, C.POINTER(D)]),
+        "rcg_learn_forward": (I, [P, P, I, I, P]),
+        "rcg_learn_gradient": (I, [P, P, P, I, P, C.POINTER(D)]),
+        "rcg_learn_predict": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -157,7 +170,8 @@ def default_options(**kw):
 
 def stats_to_dicts(arr):
     return [dict(sample=s.sample, rhs=s.rhs, iters=s.iters, restarts=s.restarts, appended=s.appended,
-                 status=s.status, relres0=s.relres0, relres=s.relres, ratio=s.ratio) for s in arr]
+                 status=s.status, relres0=s.relres0, relres=s.relres, ratio=s.ratio, augmented=s.augmented)
+            for s in arr]
 
 
 class Context:
@@ -289,3 +303,54 @@ class Context:
         k = KProf()
         self._check(self.L.rcg_profile_get(self.h, kernel, C.byref(k)))
         return dict(launches=k.launches, ms=k.ms, lane_units=k.lane_units, defl_cols=k.defl_cols)
+
+    # ---- learned augmentation (rcg_learn_*)
+    def learn_geometry(self):
+        d = np.zeros(4, dtype=np.int32)
+        self._check(self.L.rcg_learn_geometry(self.h, _ptr(d)))
+        return tuple(int(v) for v in d)          # Gx, Gy, Gz, f
+
+    def learn_set_weights(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        return self._check(self.L.rcg_learn_set_weights(self.h, _ptr(t), t.size))
+
+    def learn_get_weights(self):
+        t = np.zeros(self.L.rcg_learn_nparams(), dtype=np.float32)
+        self._check(self.L.rcg_learn_get_weights(self.h, _ptr(t), t.size))
+        return t
+
+    def learn_record(self, on=True):
+        return self._check(self.L.rcg_learn_record(self.h, 1 if on else 0))
+
+    def learn_pairs(self):
+        v = C.c_int()
+        self._check(self.L.rcg_learn_pairs(self.h, C.byref(v)))
+        return v.value
+
+    def learn_train(self, epochs, batch=16, lr=1e-3, seed=0):
+        loss = C.c_double()
+        self._check(self.L.rcg_learn_train(self.h, epochs, batch, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def learn_forward(self, inp, rounded=True):
+        x = np.ascontiguousarray(inp, dtype=np.float32)
+        B = x.shape[0]
+        out = np.zeros((B,) + x.shape[2:], dtype=np.float32)
+        self._check(self.L.rcg_learn_forward(self.h, _ptr(x), B, 1 if rounded else 0, _ptr(out)))
+        return out
+
+    def learn_gradient(self, inp, tg):
+        x = np.ascontiguousarray(inp, dtype=np.float32)
+        t = np.ascontiguousarray(tg, dtype=np.float32)
+        g = np.zeros(self.L.rcg_learn_nparams(), dtype=np.float32)
+        loss = C.c_double()
+        self._check(self.L.rcg_learn_gradient(self.h, _ptr(x), _ptr(t), x.shape[0], _ptr(g), C.byref(loss)))
+        return loss.value, g
+
+    def learn_predict(self, s, r0):
+        Gx, Gy, Gz, _ = self.learn_geometry()
+        r = np.ascontiguousarray(r0, dtype=np.float32)
+        feat = np.zeros((2, Gz, Gy, Gx), dtype=np.float32)
+        xhat = np.zeros(self.n, dtype=np.float32)
+        self._check(self.L.rcg_learn_predict(self.h, s, _ptr(r), _ptr(feat), _ptr(xhat)))
+        return feat, xhat

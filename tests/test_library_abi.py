@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     txt = open(os.path.join(ROOT, "include", "rcg.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(rcg_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(rcg_[a-z_0-9]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
