@@ -18,6 +18,7 @@ workload on this machine's host cores.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -33,10 +34,12 @@ if ROOT not in sys.path:
 
 WORKLOAD = "c2_3d64"
 METRIC = "full-order solves/s at relres 1e-8: learned+mixed batched RCG vs plain FP64 RCG"
-CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0)   # mixed, one wave
+CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0, learned=1)  # learned + mixed, one wave
+MIXED_PLAIN = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0)          # the same without the network
+NTRAIN, EPOCHS, BATCH, LR = 8, 40, 16, 1e-3     # training solves (held-out parameter points), Adam schedule
 BASELINE = dict(precision=0, order=0, tau_rank=1e-12)                    # FP64, paper order
-ORACLE_RHS = (0, 1, 2, 3, 32, 33, 34, 35)                                # CPU sample: 4 src + 4 det
-ORACLE_SAMPLES = (1,)
+ORACLE_RHS = (0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39)    # CPU sample: 8 src + 8 det
+ORACLE_SAMPLES = (1, 2)
 
 
 def parse_args():
@@ -115,7 +118,7 @@ class Clocks:
 def make_ctx(rcg, inp, opts, torch, device_inputs=True):
     wl = inp["wl"]
     stream = torch.cuda.current_stream().cuda_stream
-    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, stream=stream, k_u=wl.k_u, max_samples=wl.K + 2,
+    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, stream=stream, k_u=wl.k_u, max_samples=wl.K + 2 + NTRAIN,
                       r_max=1024, **opts)
     ctx.set_diffusion(inp["D"])
     ctx.set_sources_detectors(inp["src_ij"], inp["det_ij"])
@@ -140,6 +143,32 @@ def run_ours(args, rank, world, torch):
     dmu_dev = torch.tensor(dmu_ho, dtype=torch.float64, device=dev)
     psi_dev = torch.empty(wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
     J_dev = torch.empty(wl.nparam * wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
+    # training samples of the learned augmentation: parameter points of the same
+    # jitter law, disjoint from the timed samples and the held-out ROM point
+    mu_tr = [pals_mu(p, inp["X"], wl.mu_bg) for p in heldout_params(wl, NTRAIN, seed_offset=2000)]
+    learn_info = {}
+
+    def train_network(ctx):
+        """Offline (untimed, like the seed): solve the training samples with
+        pair recording, then Adam on the recorded pairs."""
+        from synthetic.cnn_init import init_weights
+        for i, m in enumerate(mu_tr):
+            ctx.set_sample(K + 1 + i, m)
+        ctx.learn_set_weights(init_weights(0))
+        ctx.learn_record(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_all(K + 1, NTRAIN)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss0 = ctx.learn_train(1, BATCH, LR, 1)
+        loss = ctx.learn_train(EPOCHS - 1, BATCH, LR, 2)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ctx.learn_record(False)
+        learn_info.update(pairs=ctx.learn_pairs(), epochs=EPOCHS, batch=BATCH, lr=LR, loss_first_epoch=loss0,
+                          loss_last_epoch=loss, data_s=round(t1 - t0, 3), train_s=round(t2 - t1, 3),
+                          training_samples=NTRAIN, params=len(ctx.learn_get_weights()))
 
     def prepare(opts):
         ctx = make_ctx(rcg, inp, opts, torch)
@@ -149,6 +178,8 @@ def run_ours(args, rank, world, torch):
         seed_stats = ctx.seed(0, None)
         torch.cuda.synchronize()
         seed_s = time.perf_counter() - t0
+        if opts.get("learned"):
+            train_network(ctx)
         return ctx, seed_stats, seed_s
 
     def step(ctx):
@@ -211,6 +242,8 @@ def run_ours(args, rank, world, torch):
     phases = {k: ctx.phase_ms(k) for k in ("check", "cg", "append", "rom")}
     rank_V = ctx.rank()
     mean_iters = float(np.mean([s["iters"] for s in all_stats[-1]]))
+    learn_info["augmented_last_step"] = int(sum(s["augmented"] for s in all_stats[-1]))
+    trained = ctx.learn_get_weights()
 
     # ---- roofline of the dominant inner-CG kernel (device events over the timed region)
     names = ["k_stencil4 (q = A p)", "k_update4 (x, r)", "k_u0dots (shared deflation dots)", "k_mu (lane scalars)",
@@ -258,7 +291,7 @@ def run_ours(args, rank, world, torch):
         ctx.close()
         return dict(value=value, ms=ms_max / args.steps, launches=launches, roofline=roofline, e2e=None,
                     clocks=clk, base=None, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
-                    seed_s=seed_s, solves_per_step=solves_per_step)
+                    seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=None)
 
     # ---- end to end through the public API with host buffers
     ctx_e = make_ctx(rcg, inp, CONTENDER, torch)
@@ -269,6 +302,7 @@ def run_ours(args, rank, world, torch):
     for s in range(K + 1):
         ctx_e.set_sample(s, pinned[s].numpy())
     ctx_e.seed(0, None)
+    ctx_e.learn_set_weights(trained)          # the network trained above (untimed)
 
     def e2e_step():
         for s in range(1, K + 1):
@@ -286,11 +320,21 @@ def run_ours(args, rank, world, torch):
         check(e2e_step())
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    stat_bytes = 56
+    stat_bytes = ctypes.sizeof(rcg.Stat)
     e2e = {"value": round(world * solves_per_step / e2e_s, 2), "unit": "solves/s",
            "h2d_bytes_per_step": (K + 1 + wl.nparam) * n * 8,
            "d2h_bytes_per_step": K * wl.nrhs * stat_bytes + wl.ndet * wl.nsrc * 8 * (1 + wl.nparam)}
     ctx_e.close()
+
+    # ---- the same mixed wave without the network (the learned step's effect)
+    nolearn = None
+    if not args.no_baseline and rank == 0:
+        ctx_m, _, _ = prepare(MIXED_PLAIN)
+        ms_m, _, stats_m, _ = timed(ctx_m, args.steps, args.warmup)
+        nolearn = {"value": round(solves_per_step * args.steps / (ms_m / 1e3), 2), "unit": "solves/s",
+                   "ms_per_step": round(ms_m / args.steps, 3), "rank_V": ctx_m.rank(),
+                   "mean_cg_iters": float(np.mean([s["iters"] for s in stats_m[-1]]))}
+        ctx_m.close()
 
     # ---- plain FP64 recycled CG in the paper's order, same library and inputs
     base = None
@@ -307,7 +351,7 @@ def run_ours(args, rank, world, torch):
     ctx.close()
     return dict(value=value, ms=ms_max / args.steps, launches=launches, roofline=roofline, e2e=e2e,
                 clocks=clk, base=base, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
-                seed_s=seed_s, solves_per_step=solves_per_step)
+                seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=nolearn)
 
 
 # ------------------------------------------------------------- CPU oracle leg
@@ -340,7 +384,7 @@ def oracle_worker(args):
     print(json.dumps({"value": nsolve * len(times) / sum(times), "unit": "solves/s", "cores": 1,
                       "kind": "oracle", "seconds": sum(times),
                       "sample": f"{args.workload}: samples {list(ORACLE_SAMPLES)}, RHS {cols} "
-                                f"(4 sources + 4 detectors), sequential FP64, seed untimed"}))
+                                f"(8 sources + 8 detectors), sequential FP64, seed untimed"}))
 
 
 def run_oracle_subprocess(args, steps=1, warmup=0):
@@ -447,8 +491,10 @@ def main():
                        "precision": "f32 inner CG / stencil / basis, f64 refinement residuals, "
                                     "Galerkin matrices and decisions",
                        "order": "wave (all samples and RHS in one batch)", "tau_rank": CONTENDER["tau_rank"],
-                       "learned": False, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "working set > L2 (320 lanes x 262144 nodes x 24 B = 2.0 GB)",
+                       "learned": True, "learning": res["learn"],
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"working set > L2 ({res['solves_per_step']} lanes x {wl.n} nodes x 24 B = "
+                             f"{res['solves_per_step'] * wl.n * 24 / 1e9:.1f} GB)",
                        "rank_V_after_step": res["rank_V"], "mean_cg_iters": res["mean_iters"],
                        "phases_ms_last_step": {k: round(v, 2) for k, v in res["phases"].items()},
                        "seed_s_untimed": round(res["seed_s"], 3)},
@@ -458,6 +504,7 @@ def main():
             "clocks": res["clocks"],
             "gpu_launches": res["launches"],
             "baseline_fp64_sequential": res["base"],
+            "mixed_without_learning": res["nolearn"],
         }
         print(json.dumps(line))
     if world > 1:
