@@ -172,13 +172,18 @@ int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_de
 
 /* The basis product of the orthogonalisation in the append (Sec. 5.3
  * incremental QR: V^T W, W^T W, V^T Q, Q^T Q), exposed for testing and
- * timing: C = A^T B with A (n x ka) and B (n x kb) float32, column-major with
+ * timing: C = A^T diag(w) B (w == NULL: C = A^T B; w != NULL is the weighted
+ * Gram V^T Delta V of the check and the reduced model, eq. newreduced, with
+ * w = h^2 (mu - mu_*) of finite support) with A (n x ka) and B (n x kb)
+ * float32, column-major with
  * leading dimensions lda, ldb, and C (ka x kb, leading dimension ldc)
  * float64, all three in device memory and owned by the caller.
  *   - engine 0: CUDA-core kernel (float32 products, float64 partial sums);
  *     engine 1: tensor cores (tcgen05 kind::tf32, three MMAs per product,
  *     float64 sum of the split-K slices), which needs A and B 16-byte
- *     aligned and lda, ldb multiples of 4 (else RCG_ERR_INVALID).
+ *     aligned and lda, ldb multiples of 4 (else RCG_ERR_INVALID); with w it
+ *     visits only the 32-row blocks where w does not vanish.  w (float64,
+ *     n, device, 16-byte aligned) scales the rows of A in float32.
  *   - n == 0 gives C = 0 (A and B may then be NULL).
  *   - symmetric != 0: A == B, ka == kb, lda == ldb (engine 1 computes the
  *     upper tiles and mirrors them).
@@ -189,7 +194,7 @@ int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_de
  *   - RCG_ERR_INVALID for bad sizes or pointers, RCG_ERR_CUDA for a CUDA
  *     error, RCG_ERR_TIMEOUT if a tensor-core wait ran out (C undefined). */
 int rcg_gemm_tn_f32(const float *A, long long lda, int ka, const float *B, long long ldb, int kb, long long n,
-                    double *C, int ldc, int engine, int symmetric, void *stream);
+                    const double *w, double *C, int ldc, int engine, int symmetric, void *stream);
 
 /* Seed step of Algorithm 2 at sample s0: U_0 = U0 (host n x k_u, column-
  * major) or, if U0 == NULL, the k_u smallest eigenvectors of A~_{s0} by a

@@ -136,6 +136,9 @@ struct Engine : EngineBase {
     // per-sample wave Galerkin matrices and Delta weights
     std::vector<double *> Gw, Lw, dw;
     std::vector<int> dw_star;
+    std::vector<int *> dwl;            // per sample: 32-row blocks where Delta does not vanish
+    int *dwc = nullptr;                // their counts (device, one per sample slot)
+    int *rom_bl = nullptr, *rom_bc = nullptr;
     // lanes workspace
     int mcap = 0;
     double *x64 = nullptr;
@@ -209,6 +212,8 @@ struct Engine : EngineBase {
         Lw.assign(c->opt.max_samples, nullptr);
         dw.assign(c->opt.max_samples, nullptr);
         dw_star.assign(c->opt.max_samples, -1);
+        dwl.assign(c->opt.max_samples, nullptr);
+        dwc = c->alloc<int>(c->opt.max_samples);
     }
 
     const T *diagT(int s) const { return mixed ? (const T *)c->diag32_of(s) : (const T *)c->diag64_of(s); }
@@ -393,16 +398,41 @@ struct Engine : EngineBase {
         if (!dw[s]) dw[s] = c->alloc<double>(ld);
         if (dw_star[s] != s_star) {
             scaled_diff(st, n, c->mu64 + (long long)s * ld, c->mu64 + (long long)s_star * ld, c->h * c->h, dw[s]);
+            if (mixed) {
+                if (!dwl[s]) dwl[s] = c->alloc<int>((size_t)(n + 31) / 32);
+                tc_block_list(st, n, dw[s], dwl[s], dwc + s);
+            }
             dw_star[s] = s_star;
         }
         return dw[s];
+    }
+
+    // C (ka x ka, ld ldc) += A^T diag(w) A: the weighted Gram of the check and the
+    // reduced model; tensor cores (only the 32-row blocks in blist) for float32.
+    void gram_w_acc(const T *A, int ka, double *C, int ldc, const double *w, const int *blist, const int *bcount) {
+        if constexpr (sizeof(T) == 4) {
+            if (ka >= 16 && blist && tc_gemm_tn_ok(ld, ld, A, A)) {
+                const long long need = tc_gemm_tn_scratch(n, ka, ka, true, nullptr, nullptr);
+                if (need > tc_cap) {
+                    c->release(tc_scr);
+                    tc_cap = std::max(need, 2 * tc_cap);
+                    tc_scr = c->alloc<float>((size_t)tc_cap);
+                }
+                tc_gemm_tn(st, n, A, ld, ka, A, ld, ka, C, ldc, true, true, tc_scr, d_info + 1, w, blist, bcount);
+                return;
+            }
+        }
+        gemm_tn_acc<T, T, double>(st, n, A, ld, ka, A, ld, ka, C, ldc, true, w);
     }
 
     // G = C_* + V^T diag(h^2 (mu_s - mu_*)) V (r x r) and its Cholesky factor L.
     void galerkin(int s, double *G, double *L) {
         RCG_CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * rmax, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        if (s != s_star) gemm_tn_acc<T, T, double>(st, n, V, ld, r, V, ld, r, G, rmax, true, delta_weights(s));
+        if (s != s_star) {
+            const double *w = delta_weights(s);
+            gram_w_acc(V, r, G, rmax, w, mixed ? dwl[s] : nullptr, mixed ? dwc + s : nullptr);
+        }
         RCG_CUDA_TRY(cudaMemcpy2DAsync(L, sizeof(double) * rmax, G, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -1152,7 +1182,11 @@ struct Engine : EngineBase {
         scaled_diff(st, n, mu, c->mu64 + (long long)s_star * ld, c->h * c->h, wtmp);
         RCG_CUDA_TRY(cudaMemcpy2DAsync(Ar, sizeof(double) * r, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        gemm_tn_acc<T, T, double>(st, n, V, ld, r, V, ld, r, Ar, r, true, wtmp);
+        if (mixed) {
+            if (!rom_bl) { rom_bl = c->alloc<int>((size_t)(n + 31) / 32); rom_bc = c->alloc<int>(1); }
+            tc_block_list(st, n, wtmp, rom_bl, rom_bc);
+        }
+        gram_w_acc(V, r, Ar, r, wtmp, mixed ? rom_bl : nullptr, mixed ? rom_bc : nullptr);
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
         chol_inplace(st, Ar, r, r, d_info);
         check_info("reduced matrix V^T A(p) V");

@@ -97,10 +97,10 @@ k_cnn_features(CnnGeom cg, const float *const *__restrict__ r0, const double *co
 }
 
 // out[b][co][p] = bias[co] + sum_ci sum_d W[co][ci][d] in[b][ci][p + d]  (zero
-// padding), optional ReLU.  One thread per output node, all COUT outputs; the
-// weights sit in shared memory as [ci][27][COUT] so a (ci, d) step reads them
-// as float4 broadcasts.
-template <int COUT>
+// padding), optional ReLU.  One thread per VX consecutive x nodes (Gx % VX ==
+// 0), all COUT outputs; the weights sit in shared memory as [ci][27][COUT] so
+// that a (ci, d) step reads them as float4 broadcasts and uses each for VX nodes.
+template <int COUT, int VX>
 __global__ void __launch_bounds__(CT)
 k_conv3_fwd(const float *__restrict__ in, int Cin, float *__restrict__ out, const float *__restrict__ W,
             const float *__restrict__ bias, int relu, int Gx, int Gy, int Gz, long long V) {
@@ -111,42 +111,62 @@ k_conv3_fwd(const float *__restrict__ in, int Cin, float *__restrict__ out, cons
         wsm[rem * COUT + co] = W[e];
     }
     __syncthreads();
-    const long long v = (long long)blockIdx.x * CT + threadIdx.x;
-    if (v >= V) return;
+    const long long v0 = ((long long)blockIdx.x * CT + threadIdx.x) * VX;
+    if (v0 >= V) return;
     const int b = blockIdx.y;
     int x, y, z;
-    coords(v, Gx, Gy, x, y, z);
-    float acc[COUT];
+    coords(v0, Gx, Gy, x, y, z);
+    float acc[VX][COUT];
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[co] = bias[co];
+    for (int j = 0; j < VX; ++j)
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[j][co] = bias[co];
     for (int ci = 0; ci < Cin; ++ci) {
         const float *__restrict__ src = in + ((long long)b * Cin + ci) * V;
-        for (int d = 0; d < 27; ++d) {
-            const int xx = x + d % 3 - 1, yy = y + (d / 3) % 3 - 1, zz = z + d / 9 - 1;
-            if (xx < 0 || xx >= Gx || yy < 0 || yy >= Gy || zz < 0 || zz >= Gz) continue;
-            const float val = src[((long long)zz * Gy + yy) * Gx + xx];
-            const float *w = wsm + (ci * 27 + d) * COUT;
-            if constexpr (COUT % 4 == 0) {
+        for (int dzy = 0; dzy < 9; ++dzy) {
+            const int yy = y + dzy % 3 - 1, zz = z + dzy / 3 - 1;
+            if (yy < 0 || yy >= Gy || zz < 0 || zz >= Gz) continue;
+            const float *row = src + ((long long)zz * Gy + yy) * Gx;
+            // x - 1 .. x + VX: the row segment every tap of this (dz, dy) needs
+            float seg[VX + 2];
 #pragma unroll
-                for (int q = 0; q < COUT / 4; ++q) {
-                    const float4 w4 = ((const float4 *)w)[q];
-                    acc[4 * q] += w4.x * val;
-                    acc[4 * q + 1] += w4.y * val;
-                    acc[4 * q + 2] += w4.z * val;
-                    acc[4 * q + 3] += w4.w * val;
+            for (int j = 0; j < VX + 2; ++j) {
+                const int xx = x + j - 1;
+                seg[j] = (xx >= 0 && xx < Gx) ? row[xx] : 0.f;
+            }
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const float *w = wsm + (ci * 27 + dzy * 3 + dx) * COUT;
+                if constexpr (COUT % 4 == 0) {
+#pragma unroll
+                    for (int q = 0; q < COUT / 4; ++q) {
+                        const float4 w4 = ((const float4 *)w)[q];
+#pragma unroll
+                        for (int j = 0; j < VX; ++j) {
+                            const float val = seg[j + dx];
+                            acc[j][4 * q] += w4.x * val;
+                            acc[j][4 * q + 1] += w4.y * val;
+                            acc[j][4 * q + 2] += w4.z * val;
+                            acc[j][4 * q + 3] += w4.w * val;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int co = 0; co < COUT; ++co)
+#pragma unroll
+                        for (int j = 0; j < VX; ++j) acc[j][co] += w[co] * seg[j + dx];
                 }
-            } else {
-#pragma unroll
-                for (int co = 0; co < COUT; ++co) acc[co] += w[co] * val;
             }
         }
     }
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-        float a = acc[co];
-        if (relu) a = fmaxf(a, 0.f);
-        out[((long long)b * COUT + co) * V + v] = a;
-    }
+    for (int co = 0; co < COUT; ++co)
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+            float a = acc[j][co];
+            if (relu) a = fmaxf(a, 0.f);
+            out[((long long)b * COUT + co) * V + v0 + j] = a;
+        }
 }
 
 // din[b][ci][q] = (sum_co sum_d W[co][ci][d] dout[b][co][q - d]) * (act[b][ci][q] > 0):
@@ -360,26 +380,30 @@ __global__ void __launch_bounds__(256)
 k_aug_dots(long long n, long long ld, const float *__restrict__ V, int ku, const float *__restrict__ wpb,
            const float *__restrict__ awp, int kps, const int *__restrict__ kp, const int *__restrict__ alist,
            double *__restrict__ cd, long long chunk) {
+    constexpr int NQ = KU_MAX + KP_MAX + 1;
+    __shared__ const float *cols[NQ];
     const int a = blockIdx.y, l = alist[a];
     const int kpl = kp[l], nq = ku + kpl + 1;
+    if (threadIdx.x < NQ) {
+        const int q = threadIdx.x;
+        cols[q] = q < ku ? V + (long long)q * ld : wpb + ((long long)l * kps + (q - ku)) * ld;
+    }
+    __syncthreads();
     const float *__restrict__ y = awp + ((long long)l * kps + kpl) * ld;
     const long long r0 = (long long)blockIdx.x * chunk, r1 = min(r0 + chunk, n);
-    float acc[KU_MAX + KP_MAX + 1];
+    float acc[NQ];
 #pragma unroll
-    for (int q = 0; q < KU_MAX + KP_MAX + 1; ++q) acc[q] = 0.f;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
     for (long long p = r0 + threadIdx.x; p < r1; p += blockDim.x) {
         const float yv = y[p];
 #pragma unroll
-        for (int q = 0; q < KU_MAX + KP_MAX + 1; ++q) {
-            if (q >= nq) break;
-            const float *w = q < ku ? V + (long long)q * ld : wpb + ((long long)l * kps + (q - ku)) * ld;
-            acc[q] += yv * w[p];
-        }
+        for (int q = 0; q < NQ; ++q)
+            if (q < nq) acc[q] += yv * cols[q][p];
     }
-    __shared__ float red[8][KU_MAX + KP_MAX + 1];
+    __shared__ float red[8][NQ];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < KU_MAX + KP_MAX + 1; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         float v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][q] = v;
@@ -525,13 +549,19 @@ void Cnn::conv(cudaStream_t st, int l, const float *in, float *out, int B, bool 
     const float *Wt = (rounded ? theta16 : theta) + woff[l];
     const float *bt = (rounded ? theta16 : theta) + boff[l];
     const size_t sm = sizeof(float) * (size_t)Cout * Cin * 27;
-    dim3 grid((unsigned)((geom.V + CT - 1) / CT), (unsigned)B);
+    const int vx = geom.Gx % 4 == 0 ? 4 : 1;
+    const long long thr = (geom.V + vx - 1) / vx;
+    dim3 grid((unsigned)((thr + CT - 1) / CT), (unsigned)B);
+#define RCG_CONV(CO, VXT) k_conv3_fwd<CO, VXT><<<grid, CT, sm, st>>>(in, Cin, out, Wt, bt, relu ? 1 : 0, geom.Gx, \
+                                                                     geom.Gy, geom.Gz, geom.V)
     if (Cout == 16) {
-        set_smem(k_conv3_fwd<16>, sm);
-        k_conv3_fwd<16><<<grid, CT, sm, st>>>(in, Cin, out, Wt, bt, relu ? 1 : 0, geom.Gx, geom.Gy, geom.Gz, geom.V);
+        if (vx == 4) RCG_CONV(16, 4);
+        else RCG_CONV(16, 1);
     } else {
-        k_conv3_fwd<1><<<grid, CT, sm, st>>>(in, Cin, out, Wt, bt, relu ? 1 : 0, geom.Gx, geom.Gy, geom.Gz, geom.V);
+        if (vx == 4) RCG_CONV(1, 4);
+        else RCG_CONV(1, 1);
     }
+#undef RCG_CONV
     count_launch();
     RCG_CHECK_LAUNCH();
 }
@@ -713,9 +743,8 @@ void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku
               const float *awp, int kps, const int *kp, const int *alist, int na, double *cd) {
     if (na <= 0) return;
     RCG_CUDA_TRY(cudaMemsetAsync(cd, 0, sizeof(double) * (size_t)na * (KMAX + 1), st));
-    long long z = std::max<long long>(1, (4LL * 152 + na - 1) / na);
-    z = std::min<long long>(z, (n + 4095) / 4096);
-    if (z < 1) z = 1;
+    // chunks of ~8192 nodes: thousands of CTAs over the lanes
+    long long z = std::max<long long>(1, (n + 8191) / 8192);
     const long long chunk = (n + z - 1) / z;
     k_aug_dots<<<dim3((unsigned)z, (unsigned)na), 256, 0, st>>>(n, ld, V, ku, wpb, awp, kps, kp, alist, cd, chunk);
     count_launch();

@@ -232,7 +232,9 @@ void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int k
 long long tc_gemm_tn_scratch(long long n, int ka, int kb, bool symmetric, int *z_out, long long *chunk_out);
 bool tc_gemm_tn_ok(long long lda, long long ldb, const void *A, const void *B);
 void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int ka, const float *B, long long ldb,
-                int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err);
+                int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err,
+                const double *wt = nullptr, const int *blist = nullptr, const int *bcount = nullptr);
+void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count);
 template <typename TA, typename TO>
 void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k,
              const double *Y, int ldy, int m, TO *Out, long long ldo, double alpha, double beta);

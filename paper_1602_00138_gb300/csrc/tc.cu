@@ -47,7 +47,8 @@ constexpr int NTHR = 256;               // 8 warps
 constexpr int TILE_BYTES = TM * TBK * 4;                 // 16 KiB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;              // A hi, B hi, A lo, B lo
 constexpr int NSTAGE = 3;
-constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + 1024;     // + 1024-byte alignment slack
+constexpr int WBYTES = TBK * 8;                          // the step's float64 row weights
+constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + NSTAGE * WBYTES + 1024;   // + 1024-byte alignment slack
 constexpr int LEVEL1 = 16;              // K-steps summed before the second level
 constexpr long long SPIN_LIMIT = 1LL << 22;
 constexpr int NUM_SMS = 152;
@@ -137,13 +138,30 @@ __device__ __forceinline__ void prefetch_tile(const float *colp, long long step_
     }
 }
 
-// hi in place, lo at the same offset in `lo` (the split is elementwise, so
-// the swizzle does not matter here).
-__device__ __forceinline__ void split_tile(char *hi, char *lo) {
+// The step's 32 row weights (float64) into `dst` (zero past row n).
+__device__ __forceinline__ void prefetch_w(const double *wt, long long k0, long long n, char *dst) {
+    if (threadIdx.x < WBYTES / 16) {
+        const long long k = k0 + 2 * threadIdx.x;
+        const int bytes = k + 2 <= n ? 16 : (k < n ? 8 : 0);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + 16 * threadIdx.x)),
+                     "l"(bytes ? wt + k : wt), "r"(bytes)
+                     : "memory");
+    }
+}
+
+// hi in place, lo at the same offset in `lo`; with row weights w (the step's
+// 32 float64 weights in shared memory) every value is first scaled by its
+// row's weight.  16-byte chunk o of the tile holds rows 4 c .. 4 c + 3 with
+// c = ((o / 16) mod 8) xor (m mod 8), m = o / 128 (the 128-byte swizzle).
+__device__ __forceinline__ void split_tile(char *hi, char *lo, const double *w = nullptr) {
 #pragma unroll
     for (int it = 0; it < TILE_BYTES / 16 / NTHR; ++it) {
         const int o = (threadIdx.x + it * NTHR) * 16;
-        const float4 v = *(const float4 *)(hi + o);
+        float4 v = *(const float4 *)(hi + o);
+        if (w) {
+            const int m = o >> 7, c = ((o >> 4) & 7) ^ (m & 7);
+            v.x *= (float)w[4 * c]; v.y *= (float)w[4 * c + 1]; v.z *= (float)w[4 * c + 2]; v.w *= (float)w[4 * c + 3];
+        }
         float4 h, l;
         h.x = rn_tf32(v.x); h.y = rn_tf32(v.y); h.z = rn_tf32(v.z); h.w = rn_tf32(v.w);
         l.x = rn_tf32(v.x - h.x); l.y = rn_tf32(v.y - h.y); l.z = rn_tf32(v.z - h.z); l.w = rn_tf32(v.w - h.w);
@@ -170,17 +188,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 
 __global__ void __launch_bounds__(NTHR, 1)
 k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const float *__restrict__ B, long long ldb,
-        int kb, int symmetric, float *__restrict__ part, long long chunk, int *__restrict__ err) {
+        int kb, int symmetric, float *__restrict__ part, long long chunk, int *__restrict__ err,
+        const double *__restrict__ wt, const int *__restrict__ blist, const int *__restrict__ bcount) {
     if (symmetric && blockIdx.x > blockIdx.y) return;        // lower tiles are mirrored by the reduction
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_ok;
     char *smem = (char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    char *wsm = smem + NSTAGE * STAGE_BYTES;
     const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TNc;
-    const long long r0 = (long long)blockIdx.z * chunk;
-    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
-    const long long nk = (r1 > r0) ? (r1 - r0 + TBK - 1) / TBK : 0;
+    // K-steps of this slice: steps s_begin .. s_begin + nk - 1 (chunk = steps per
+    // slice); step s covers rows 32 s .. 32 s + 31, or rows 32 blist[s] .. with a
+    // block list (the blocks where the weights do not vanish)
+    const long long nsteps = blist ? (long long)*bcount : (n + TBK - 1) / TBK;
+    const long long s_begin = (long long)blockIdx.z * chunk;
+    const long long s_end = s_begin + chunk < nsteps ? s_begin + chunk : nsteps;
+    const long long nk = s_end > s_begin ? s_end - s_begin : 0;
+    auto step_row = [&](long long ks) -> long long {
+        return (long long)TBK * (blist ? (long long)blist[s_begin + ks] : s_begin + ks);
+    };
+    auto step_end = [&](long long k0) -> long long { return k0 + TBK < n ? k0 + TBK : n; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -205,8 +233,10 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
     for (int q = 0; q < 2; ++q) {
         if (q < nk) {
             char *stg = smem + q * STAGE_BYTES;
-            prefetch_tile(colA, stepA, ncolA, r0 + q * TBK, r1, stg);
-            prefetch_tile(colB, stepB, ncolB, r0 + q * TBK, r1, stg + TILE_BYTES);
+            const long long k0 = step_row(q);
+            prefetch_tile(colA, stepA, ncolA, k0, step_end(k0), stg);
+            prefetch_tile(colB, stepB, ncolB, k0, step_end(k0), stg + TILE_BYTES);
+            if (wt) prefetch_w(wt, k0, n, wsm + q * WBYTES);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
@@ -244,7 +274,8 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
         asm volatile("cp.async.wait_group 1;" ::: "memory");      // step ks has landed (own copies)
         __syncthreads();                                           // ... everyone's; s_ok is uniform here
         if (!s_ok) { ok = false; break; }
-        split_tile(stg, stg + 2 * TILE_BYTES);                     // A hi | A lo
+        split_tile(stg, stg + 2 * TILE_BYTES,                      // A hi | A lo (weighted rows)
+                   wt ? (const double *)(wsm + (int)(ks % NSTAGE) * WBYTES) : nullptr);
         split_tile(stg + TILE_BYTES, stg + 3 * TILE_BYTES);        // B hi | B lo
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -276,8 +307,10 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
         }
         if (ok && ks + 2 < nk) {
             char *nxt = smem + (int)((ks + 2) % NSTAGE) * STAGE_BYTES;
-            prefetch_tile(colA, stepA, ncolA, r0 + (ks + 2) * TBK, r1, nxt);
-            prefetch_tile(colB, stepB, ncolB, r0 + (ks + 2) * TBK, r1, nxt + TILE_BYTES);
+            const long long k0 = step_row(ks + 2);
+            prefetch_tile(colA, stepA, ncolA, k0, step_end(k0), nxt);
+            prefetch_tile(colB, stepB, ncolB, k0, step_end(k0), nxt + TILE_BYTES);
+            if (wt) prefetch_w(wt, k0, n, wsm + (int)((ks + 2) % NSTAGE) * WBYTES);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -307,6 +340,37 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TNc));
+}
+
+// Ascending list of the 32-row blocks where w does not vanish (one CTA, the
+// order is deterministic): thread t scans a contiguous range of blocks.
+__global__ void __launch_bounds__(1024) k_block_list(long long n, const double *__restrict__ w, int *__restrict__ list,
+                                                     int *__restrict__ count) {
+    const long long nb = (n + TBK - 1) / TBK;
+    const long long per = (nb + blockDim.x - 1) / blockDim.x;
+    const long long b0 = threadIdx.x * per, b1 = b0 + per < nb ? b0 + per : nb;
+    int cnt = 0;
+    for (long long b = b0; b < b1; ++b) {
+        bool nz = false;
+        for (long long k = b * TBK; k < (b + 1) * TBK && k < n; ++k) nz |= (w[k] != 0.0);
+        cnt += nz;
+    }
+    __shared__ int scan[1024];
+    scan[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {       // inclusive scan
+        const int v = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int pos = scan[threadIdx.x] - cnt;
+    for (long long b = b0; b < b1; ++b) {
+        bool nz = false;
+        for (long long k = b * TBK; k < (b + 1) * TBK && k < n; ++k) nz |= (w[k] != 0.0);
+        if (nz) list[pos++] = (int)b;
+    }
+    if (threadIdx.x == blockDim.x - 1) *count = scan[threadIdx.x];
 }
 
 // C[i + j*ldc] (+)= sum_z part[z][j][i] in float64; a symmetric product
@@ -343,12 +407,19 @@ long long tc_gemm_tn_scratch(long long n, int ka, int kb, bool symmetric, int *z
             if (waves > 3) break;
         }
     }
-    long long chunk = n > 0 ? (n + z - 1) / z : TBK;
-    chunk = (chunk + TBK - 1) / TBK * TBK;
-    if (n > 0) z = (n + chunk - 1) / chunk;
+    const long long steps = (n + TBK - 1) / TBK;
+    long long chunk = steps > 0 ? (steps + z - 1) / z : 1;      // K-steps per slice
+    if (steps > 0) z = (steps + chunk - 1) / chunk;
     if (z_out) *z_out = (int)z;
     if (chunk_out) *chunk_out = chunk;
     return z * (long long)ka * kb;
+}
+
+// Blocks of 32 rows where w is not zero (list: (n + 31) / 32 ints; count: 1 int).
+void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count) {
+    k_block_list<<<1, 1024, 0, st>>>(n, w, list, count);
+    count_launch();
+    RCG_CHECK_LAUNCH();
 }
 
 // The copies need 16-byte aligned columns.
@@ -360,7 +431,8 @@ bool tc_gemm_tn_ok(long long lda, long long ldb, const void *A, const void *B) {
 // 16-byte aligned, lda and ldb multiples of 4).  symmetric: A == B, ka == kb.
 // scratch: >= tc_gemm_tn_scratch(...) floats; err: device int (0 = ok).
 void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int ka, const float *B, long long ldb,
-                int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err) {
+                int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err,
+                const double *wt, const int *blist, const int *bcount) {
     if (ka <= 0 || kb <= 0) return;
     if (!tc_gemm_tn_ok(lda, ldb, A, B)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: operands not 16-byte aligned"};
     if (symmetric && (A != B || ka != kb || lda != ldb)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: not symmetric"};
@@ -375,7 +447,9 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     dim3 grid((ka + TM - 1) / TM, (kb + TNc - 1) / TNc, z);
-    k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, B, ldb, kb, symmetric ? 1 : 0, scratch, chunk, err);
+    if ((blist != nullptr) != (bcount != nullptr) || (blist && !wt)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: block list"};
+    k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, B, ldb, kb, symmetric ? 1 : 0, scratch, chunk, err, wt, blist,
+                                         bcount);
     count_launch();
     RCG_CHECK_LAUNCH();
     const long long tot = (long long)ka * kb;
@@ -396,16 +470,20 @@ std::mutex g_gemm_mu;
 float *g_gemm_scr[64] = {};
 long long g_gemm_cap[64] = {};
 int *g_gemm_err[64] = {};
+int *g_gemm_bl[64] = {};
+long long g_gemm_blcap[64] = {};
 }  // namespace
 
 extern "C" int rcg_gemm_tn_f32(const float *A, long long lda, int ka, const float *B, long long ldb, int kb,
-                               long long n, double *C, int ldc, int engine, int symmetric, void *stream) {
+                               long long n, const double *w, double *C, int ldc, int engine, int symmetric,
+                               void *stream) {
     using namespace rcg;
     if ((n > 0 && (!A || !B)) || !C || ka < 0 || kb < 0 || n < 0 || lda < n || ldb < n || ldc < ka ||
         (engine != 0 && engine != 1))
         return RCG_ERR_INVALID;
     if (symmetric && (A != B || ka != kb || lda != ldb)) return RCG_ERR_INVALID;
     if (engine == 1 && !tc_gemm_tn_ok(lda, ldb, A, B)) return RCG_ERR_INVALID;
+    if (w && ((uintptr_t)w & 15)) return RCG_ERR_INVALID;
     if (ka == 0 || kb == 0) return RCG_OK;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_gemm_mu);
@@ -425,7 +503,23 @@ extern "C" int rcg_gemm_tn_f32(const float *A, long long lda, int ka, const floa
             }
             if (!g_gemm_err[dev]) RCG_CUDA_TRY(cudaMalloc(&g_gemm_err[dev], sizeof(int)));
             RCG_CUDA_TRY(cudaMemsetAsync(g_gemm_err[dev], 0, sizeof(int), st));
-            tc_gemm_tn(st, n, A, lda, ka, B, ldb, kb, C, ldc, false, symmetric != 0, g_gemm_scr[dev], g_gemm_err[dev]);
+            int *bl = nullptr;
+            if (w) {
+                const long long nb = (n + TBK - 1) / TBK;
+                if (nb + 1 > g_gemm_blcap[dev]) {
+                    if (g_gemm_bl[dev]) RCG_CUDA_TRY(cudaFree(g_gemm_bl[dev]));
+                    g_gemm_bl[dev] = nullptr;
+                    g_gemm_blcap[dev] = 0;
+                    RCG_CUDA_TRY(cudaMalloc(&g_gemm_bl[dev], sizeof(int) * (size_t)(nb + 1)));
+                    g_gemm_blcap[dev] = nb + 1;
+                }
+                bl = g_gemm_bl[dev];
+                tc_block_list(st, n, w, bl + 1, bl);
+            }
+            tc_gemm_tn(st, n, A, lda, ka, B, ldb, kb, C, ldc, false, symmetric != 0, g_gemm_scr[dev], g_gemm_err[dev],
+                       w, bl ? bl + 1 : nullptr, bl);
+        } else if (w) {
+            gemm_tn_acc<float, float, double>(st, n, A, lda, ka, B, ldb, kb, C, ldc, false, w);
         } else {
             gemm_tn<float, float>(st, n, A, lda, ka, B, ldb, kb, C, ldc, false);
         }

@@ -99,7 +99,7 @@ def load(path=LIB_PATH):
         "rcg_launch_count": (LL, [P]),
         "rcg_profile_enable": (I, [P, I]),
         "rcg_profile_get": (I, [P, I, C.POINTER(KProf)]),
-        "rcg_gemm_tn_f32": (I, [P, LL, I, P, LL, I, LL, P, I, I, I, P]),
+        "rcg_gemm_tn_f32": (I, [P, LL, I, P, LL, I, LL, P, P, I, I, I, P]),
         "rcg_learn_nparams": (I, []),
         "rcg_learn_geometry": (I, [P, P]),
         "rcg_learn_set_weights": (I, [P, P, I]),
@@ -140,10 +140,11 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
-def gemm_tn_f32(A, B, engine=1, symmetric=False, stream=None):
-    """C = A^T B (float64, ka x kb) for float32 CUDA tensors A (n x ka) and B
-    (n x kb) stored column-major, i.e. passed as (ka, n) / (kb, n) row-major
-    views (`A_cols[i]` = column i); see rcg_gemm_tn_f32."""
+def gemm_tn_f32(A, B, engine=1, symmetric=False, stream=None, w=None):
+    """C = A^T diag(w) B (float64, ka x kb) for float32 CUDA tensors A (n x ka)
+    and B (n x kb) stored column-major, i.e. passed as (ka, n) / (kb, n)
+    row-major views (`A_cols[i]` = column i); w: float64 CUDA tensor (n) or
+    None; see rcg_gemm_tn_f32."""
     import torch
     ka, n = A.shape
     kb, nb = B.shape
@@ -151,8 +152,11 @@ def gemm_tn_f32(A, B, engine=1, symmetric=False, stream=None):
     assert A.stride(1) == 1 and B.stride(1) == 1
     Cm = torch.empty((kb, ka), dtype=torch.float64, device=A.device)
     st = stream if stream is not None else torch.cuda.current_stream(A.device).cuda_stream
+    if w is not None:
+        assert w.dtype == torch.float64 and w.numel() >= n and w.is_contiguous()
     rc = lib().rcg_gemm_tn_f32(A.data_ptr(), A.stride(0), ka, B.data_ptr(), B.stride(0), kb, n,
-                               Cm.data_ptr(), ka, engine, 1 if symmetric else 0, st)
+                               None if w is None else w.data_ptr(), Cm.data_ptr(), ka, engine,
+                               1 if symmetric else 0, st)
     if rc != 0:
         raise RcgError(rc, lib().rcg_strerror(rc).decode())
     return Cm.t()

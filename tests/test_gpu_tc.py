@@ -85,3 +85,27 @@ def test_empty_and_invalid_arguments(rcg):
     # symmetric with different operands
     with pytest.raises(rcg.RcgError):
         rcg.gemm_tn_f32(A, A.clone(), engine=1, symmetric=True)
+
+
+@pytest.mark.parametrize("engine", [1, 0])
+def test_weighted_product_with_finite_support(rcg, engine):
+    """C = A^T diag(w) A with w zero outside a few scattered ranges (the check's
+    Delta weights have finite support): the tensor cores visit only the
+    32-row blocks where w does not vanish."""
+    import torch
+    n, k = 100003, 130
+    rng = np.random.default_rng(21)
+    ld = (n + 63) // 64 * 64
+    A = np.zeros((k, ld), dtype=np.float32)
+    A[:, :n] = rng.random((k, n), dtype=np.float32)
+    w = np.zeros(ld)
+    for a, b in [(5, 40), (1000, 1031), (50000, 57777), (99990, 100003)]:
+        w[a:b] = rng.random(b - a) * 1e-3
+    dA = torch.from_numpy(A).cuda()
+    dw = torch.from_numpy(w).cuda()
+    C = rcg.gemm_tn_f32(dA[:, :n], dA[:, :n], engine=engine, symmetric=(engine == 1), w=dw).cpu().numpy()
+    A64 = A[:, :n].astype(np.float64)
+    ref = (A64 * w[:n]) @ A64.T
+    scale = np.outer(np.linalg.norm(A64 * np.sqrt(w[:n]), axis=1), np.linalg.norm(A64 * np.sqrt(w[:n]), axis=1))
+    err = np.max(np.abs(C - ref) / scale)
+    assert err <= (5e-7 if engine == 1 else 1e-7), err
