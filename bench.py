@@ -126,6 +126,17 @@ def make_ctx(rcg, inp, opts, torch, device_inputs=True):
     return ctx
 
 
+def replica_value(torch, ms_local, world, solves_per_step, steps, dev):
+    """Whole-job throughput of N independent replicas (the path does not shard:
+    every rank solves the whole workload): the slowest rank's time over the
+    units all ranks processed.  Returns (solves/s, max ms over ranks)."""
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * solves_per_step * steps / (ms_max / 1e3), ms_max
+
+
 def run_ours(args, rank, world, torch):
     import numpy as np
     from paper_1602_00138_gb300 import rcg
@@ -233,12 +244,8 @@ def run_ours(args, rank, world, torch):
     clocks.start()
     ms, launches, all_stats, prof = timed(ctx, args.steps, args.warmup, profile=True)
     clk = clocks.stop()
-    ms_tensor = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_tensor, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_tensor.item())
     solves_per_step = K * wl.nrhs
-    value = world * solves_per_step * args.steps / (ms_max / 1e3)
+    value, ms_max = replica_value(torch, ms, world, solves_per_step, args.steps, dev)
     phases = {k: ctx.phase_ms(k) for k in ("check", "cg", "append", "rom")}
     rank_V = ctx.rank()
     mean_iters = float(np.mean([s["iters"] for s in all_stats[-1]]))
@@ -271,15 +278,19 @@ def run_ours(args, rank, world, torch):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = per_launch_bytes / per_launch_s / 1e9
+    # DRAM traffic of the dominant kernel from an ncu capture, valid only while
+    # the kernel's source text is the one that was measured
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path):
         tr = json.load(open(tr_path))
-        src = open(os.path.join(ROOT, "paper_1602_00138_gb300", "csrc",
-                                "cg4.cu"), "rb").read()
+        src = open(os.path.join(ROOT, "paper_1602_00138_gb300", "csrc", "cg4.cu")).read()
         ent = tr.get(["stencil", "update", "u0dots", "mu", "direction"][kdom])
-        if ent and ent.get("source_sha256") == hashlib.sha256(src).hexdigest():
-            traffic = ent["dram_bytes_per_lane_node"] * n * P["lane_units"] / max(P["launches"], 1)
+        if ent and ("\n" + ent["kernel"] + "(") in src:
+            i = src.index("\n" + ent["kernel"] + "(")
+            text = src[src.rindex("__global__", 0, i):src.index("\n}\n", i) + 3]
+            if ent.get("kernel_sha256") == hashlib.sha256(text.encode()).hexdigest():
+                traffic = round(ent["dram_bytes_per_lane_node"] * n * P["lane_units"] / max(P["launches"], 1))
     roofline = {"bound": "hbm", "kernel": names[kdom], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
@@ -465,7 +476,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))   # barrier and the max of the timings
     import __graft_entry__ as g
     if rank == 0:
         g.build()

@@ -230,6 +230,25 @@ int rcg_solution_get(rcg_ctx *c, int s, double *X);
 int rcg_rom_eval(rcg_ctx *c, const double *mu, int nparam, const double *dmu,
                  double *Psi, double *J);
 
+/* The full-order transfer function and Jacobian of sample s from its
+ * delivered solutions (needs options.keep_solutions): Psi = C~^T X (Sec. 3.1)
+ * with X the source columns, and, if dmu != NULL (host, n x nparam),
+ * J[d + ndet*(s' + nsrc*k)] = -Z^T diag(h^2 dmu_k) X (eq. newjac) with Z the
+ * detector columns; same layouts as rcg_rom_eval.  For comparing the reduced
+ * model against the full one (the interpolation property of Sec. 3.4). */
+int rcg_full_eval(rcg_ctx *c, int s, int nparam, const double *dmu, double *Psi, double *J);
+
+/* Save the recycling state (V, C_* = V^T A~_* V and the mu_* it belongs to,
+ * X_0 and V^T X_0, the private recycle lists, the state right after the seed,
+ * the learned network's weights if any) to a file, and load it into a
+ * context created with the same grid, precision, D and sources/detectors
+ * (checked: RCG_ERR_INVALID otherwise).  The paper reuses the basis across
+ * optimisation steps (Sec. 4.2.2); this lets a later process continue from
+ * it.  The seed sample slot is set to the saved mu_*; rcg_reset_to_seed
+ * returns to the saved seed state. */
+int rcg_save(rcg_ctx *c, const char *path);
+int rcg_load(rcg_ctx *c, const char *path);
+
 /* Device-resident variant of rcg_rom_eval: mu_dev (n), dmu_dev (n x nparam),
  * Psi_dev, J_dev device float64. */
 int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const double *dmu_dev,

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -47,7 +48,33 @@ struct EngineBase {
     virtual void basis_get(double *V) = 0;
     virtual void rom_eval(const double *mu, int nparam, const double *dmu, double *Psi, double *J) = 0;
     virtual void sample_changed(int s) = 0;
+    virtual void save(std::FILE *f) = 0;
+    virtual void load(std::FILE *f) = 0;
 };
+
+// ---------------------------------------------------------- state file I/O
+// Binary layout of rcg_save: magic, a header of int64 fields, then arrays
+// (each: int64 count, raw elements).  Little-endian host order.
+constexpr char kMagic[8] = {'R', 'C', 'G', 'S', 'T', 'A', 'T', '1'};
+inline void wr(std::FILE *f, const void *p, size_t bytes) {
+    if (bytes && std::fwrite(p, 1, bytes, f) != bytes) throw Error{RCG_ERR_INVALID, "rcg_save: write failed"};
+}
+inline void rd(std::FILE *f, void *p, size_t bytes) {
+    if (bytes && std::fread(p, 1, bytes, f) != bytes) throw Error{RCG_ERR_INVALID, "rcg_load: truncated file"};
+}
+template <typename V> void wr_vec(std::FILE *f, const std::vector<V> &v) {
+    const long long c = (long long)v.size();
+    wr(f, &c, sizeof(c));
+    wr(f, v.data(), sizeof(V) * v.size());
+}
+template <typename V> std::vector<V> rd_vec(std::FILE *f, long long max_count) {
+    long long c = 0;
+    rd(f, &c, sizeof(c));
+    if (c < 0 || c > max_count) throw Error{RCG_ERR_INVALID, "rcg_load: bad array length"};
+    std::vector<V> v((size_t)c);
+    rd(f, v.data(), sizeof(V) * v.size());
+    return v;
+}
 
 struct rcg_ctx {
     rcg_grid grid{};
@@ -68,6 +95,7 @@ struct rcg_ctx {
     std::vector<char> sample_set;
     // device coefficient fields
     double *D64 = nullptr, *dstar = nullptr, *mu64 = nullptr, *diag64 = nullptr;
+    double *W64 = nullptr;             // face weights (D_p + D_q)/2 towards +x, +y, +z (3 columns)
     float *D32 = nullptr, *diag32 = nullptr;
     int *d_rhs_node = nullptr;
     double *d_rhs_w = nullptr;
@@ -139,6 +167,10 @@ struct Engine : EngineBase {
     std::vector<int *> dwl;            // per sample: 32-row blocks where Delta does not vanish
     int *dwc = nullptr;                // their counts (device, one per sample slot)
     int *rom_bl = nullptr, *rom_bc = nullptr;
+    // reduced Jacobian: per-parameter weights, block lists, G_k and G_k X_r
+    double *jk_w = nullptr, *jk_G = nullptr, *jk_T = nullptr;
+    int *jk_bl = nullptr, *jk_bc = nullptr;
+    int jk_cap = 0;
     // lanes workspace
     int mcap = 0;
     double *x64 = nullptr;
@@ -455,6 +487,13 @@ struct Engine : EngineBase {
         return {Gw[s], Lw[s]};
     }
 
+    // Cb = [V Q]^T (A~ Q) with A~ Q in float64 (the border of C_* or G_s):
+    // double-float products for the float32 basis, float64 otherwise.
+    void border_tn(const double *AQ, int ak) {
+        if constexpr (sizeof(T) == 4) gemm_tn_df(st, n, (const float *)V, ld, r + ak, AQ, ld, ak, Cb, r + ak, false);
+        else gemm_tn<T, double>(st, n, V, ld, r + ak, AQ, ld, ak, Cb, r + ak, false);
+    }
+
     // ------------------------------------------------------------ append
     // Ordered rank-revealing append of the solutions in lanes `cand` (order
     // = priority).  Returns per-candidate kept flags and ratios.
@@ -508,11 +547,11 @@ struct Engine : EngineBase {
         ensure_aq64(ak);
         convert_cols<T, double>(st, n, V + (long long)r * ld, ld, Q64, ld, ak);
         apply_cols64(Q64, AQ64, ak, s_star);
-        gemm_tn<T, double>(st, n, V, ld, r + ak, AQ64, ld, ak, Cb, r + ak, false);
+        border_tn(AQ64, ak);
         border_write(st, Cstar, rmax, r, ak, Cb, r + ak);
         if (border_sample >= 0 && gs_sample == border_sample && gs_r == r) {
             if (border_sample != s_star) apply_cols64(Q64, AQ64, ak, border_sample);
-            gemm_tn<T, double>(st, n, V, ld, r + ak, AQ64, ld, ak, Cb, r + ak, false);
+            border_tn(AQ64, ak);
             border_write(st, Gs, rmax, r, ak, Cb, r + ak);
             copy_new_rows(st, Gs, Ls, rmax, r, ak);
             RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -580,7 +619,7 @@ struct Engine : EngineBase {
         };
         auto residual = [&](std::vector<double> &rr_h, const int *mask) {
             RCG_CUDA_TRY(cudaMemsetAsync(d_rr, 0, sizeof(double) * m, st));
-            residual64(st, g, c->D64, (const double *const *)p_diag64, (const double *const *)p_x64,
+            residual64(st, g, c->W64, (const double *const *)p_diag64, (const double *const *)p_x64,
                        mixed ? nullptr : (double *const *)p_r, mixed ? (float *const *)p_r : nullptr, m, d_lnode, d_lw,
                        d_rr, mask);
             rr_h.resize(m);
@@ -1143,6 +1182,87 @@ struct Engine : EngineBase {
         return rc;
     }
 
+    // ---------------------------------------------------------- state I/O
+    // The recycling state: V (r columns), C_* = V^T A~_* V, X_0 and V^T X_0,
+    // the private recycle lists and the state right after the seed.
+    void save(std::FILE *f) override {
+        if (!seeded) throw Error{RCG_ERR_INVALID, "rcg_save before rcg_seed"};
+        const long long hdr[6] = {(long long)sizeof(T), r, r_seed, s_star, k_u, c->nrhs};
+        wr(f, hdr, sizeof(hdr));
+        std::vector<T> hv((size_t)r * n);
+        for (int q = 0; q < r; ++q) c->d2h(hv.data() + (size_t)q * n, V + (long long)q * ld, (size_t)n);
+        std::vector<double> hc((size_t)r * r);
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(hc.data(), sizeof(double) * r, Cstar, sizeof(double) * rmax, sizeof(double) * r,
+                                       r, cudaMemcpyDeviceToHost, st));
+        std::vector<T> hx((size_t)c->nrhs * n);
+        for (int j = 0; j < c->nrhs; ++j) c->d2h(hx.data() + (size_t)j * n, X0 + (long long)j * ld, (size_t)n);
+        std::vector<double> hs((size_t)r * c->nrhs);
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(hs.data(), sizeof(double) * r, sX0, sizeof(double) * rmax, sizeof(double) * r,
+                                       c->nrhs, cudaMemcpyDeviceToHost, st));
+        c->sync();
+        wr_vec(f, hv);
+        wr_vec(f, hc);
+        wr_vec(f, hx);
+        wr_vec(f, hs);
+        for (auto *pl : {&priv, &priv_seed})
+            for (int j = 0; j < c->nrhs; ++j) wr_vec(f, (*pl)[j]);
+        // mu_* of the seed sample, which C_* belongs to
+        std::vector<double> mu((size_t)n);
+        c->d2h(mu.data(), c->mu64 + (long long)s_star * ld, (size_t)n);
+        c->sync();
+        wr_vec(f, mu);
+    }
+
+    void load(std::FILE *f) override {
+        long long hdr[6];
+        rd(f, hdr, sizeof(hdr));
+        if (hdr[0] != (long long)sizeof(T) || hdr[5] != c->nrhs || hdr[1] < 0 || hdr[1] > rmax || hdr[2] < 0 ||
+            hdr[2] > hdr[1] || hdr[3] < 0 || hdr[3] >= c->opt.max_samples)
+            throw Error{RCG_ERR_INVALID, "rcg_load: precision, RHS count or basis size does not match the context"};
+        const int rr = (int)hdr[1], nrhs = c->nrhs;
+        auto hv = rd_vec<T>(f, (long long)rr * n);
+        auto hc = rd_vec<double>(f, (long long)rr * rr);
+        auto hx = rd_vec<T>(f, (long long)nrhs * n);
+        auto hs = rd_vec<double>(f, (long long)rr * nrhs);
+        if ((long long)hv.size() != (long long)rr * n || (long long)hc.size() != (long long)rr * rr ||
+            (long long)hx.size() != (long long)nrhs * n || (long long)hs.size() != (long long)rr * nrhs)
+            throw Error{RCG_ERR_INVALID, "rcg_load: array sizes do not match the context"};
+        std::vector<std::vector<int>> p1(nrhs), p2(nrhs);
+        for (auto *pl : {&p1, &p2})
+            for (int j = 0; j < nrhs; ++j) {
+                (*pl)[j] = rd_vec<int>(f, KP_MAX + 1);
+                for (int e : (*pl)[j])
+                    if (e < -1 || e >= rr) throw Error{RCG_ERR_INVALID, "rcg_load: bad recycle list"};
+            }
+        auto mu = rd_vec<double>(f, n);
+        if ((long long)mu.size() != n) throw Error{RCG_ERR_INVALID, "rcg_load: mu_* size"};
+        ensure_lanes(std::max(nrhs, 1));
+        if (!X0) { X0 = c->alloc<T>((size_t)nrhs * ld); sX0 = c->alloc<double>((size_t)rmax * nrhs); }
+        // the seed sample slot gets mu_* back (its diagonal too)
+        const int ss = (int)hdr[3];
+        c->h2d(c->mu64 + (long long)ss * ld, mu.data(), (size_t)n);
+        diag_sample(st, n, c->dstar, c->mu64 + (long long)ss * ld, c->h * c->h, c->diag64_of(ss), c->diag32_of(ss));
+        c->sample_set[ss] = 1;
+        for (int q = 0; q < rr; ++q) c->h2d(V + (long long)q * ld, hv.data() + (size_t)q * n, (size_t)n);
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(Cstar, sizeof(double) * rmax, hc.data(), sizeof(double) * rr, sizeof(double) * rr,
+                                       rr, cudaMemcpyHostToDevice, st));
+        for (int j = 0; j < nrhs; ++j) c->h2d(X0 + (long long)j * ld, hx.data() + (size_t)j * n, (size_t)n);
+        RCG_CUDA_TRY(cudaMemsetAsync(sX0, 0, sizeof(double) * rmax * nrhs, st));
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(sX0, sizeof(double) * rmax, hs.data(), sizeof(double) * rr, sizeof(double) * rr,
+                                       nrhs, cudaMemcpyHostToDevice, st));
+        c->sync();
+        r = rr;
+        r_seed = (int)hdr[2];
+        s_star = (int)hdr[3];
+        k_u = (int)hdr[4];
+        priv = p1;
+        priv_seed = p2;
+        gs_sample = -1;
+        au0_valid = false;
+        for (auto &d : dw_star) d = -1;
+        seeded = true;
+    }
+
     int rank() const override { return r; }
 
     // caches derived from mu_s: Delta weights, A~_s U_0, the sequential G_s
@@ -1201,7 +1321,28 @@ struct Engine : EngineBase {
         trsv_lower_batched(st, Ar, r, r, Zr, r, nd, true);
         // Psi_r = C~_r^T X_r  (ndet x nsrc)
         gemm_tn<double, double>(st, r, Crm, r, nd, Xr, r, ns, Psi, nd, false);
-        if (J && dmu) {
+        if (J && dmu && mixed && r >= 16) {
+            // J_k = Z_r^T G_k X_r with G_k = V^T diag(-h^2 dmu_k) V: the weighted Grams on the
+            // tensor cores over the support of dmu_k, then two small float64 products
+            const long long nbl = (n + 31) / 32;
+            if (nparam > jk_cap) {
+                for (void *p : std::vector<void *>{(void *)jk_w, (void *)jk_bl, (void *)jk_bc}) c->release(p);
+                jk_cap = nparam;
+                jk_w = c->alloc<double>((size_t)nparam * ld);
+                jk_bl = c->alloc<int>((size_t)nparam * nbl);
+                jk_bc = c->alloc<int>(nparam);
+            }
+            if (!jk_G) { jk_G = c->alloc<double>((size_t)rmax * rmax); jk_T = c->alloc<double>((size_t)rmax * ns); }
+            for (int k = 0; k < nparam; ++k)
+                scaled_diff(st, n, dmu + (long long)k * n, nullptr, -c->h * c->h, jk_w + (long long)k * ld);
+            tc_block_list(st, n, jk_w, jk_bl, jk_bc, nparam, ld, nbl);
+            for (int k = 0; k < nparam; ++k) {
+                RCG_CUDA_TRY(cudaMemsetAsync(jk_G, 0, sizeof(double) * (size_t)r * r, st));
+                gram_w_acc(V, r, jk_G, r, jk_w + (long long)k * ld, jk_bl + (long long)k * nbl, jk_bc + k);
+                gemm_tn<double, double>(st, r, jk_G, r, r, Xr, r, ns, jk_T, r, false);     // G_k X_r (G_k symmetric)
+                gemm_tn<double, double>(st, r, Zr, r, nd, jk_T, r, ns, J + (long long)k * nd * ns, nd, false);
+            }
+        } else if (J && dmu) {
             if (!VX) { VX = c->alloc<double>((size_t)ns * ld); VZ = c->alloc<double>((size_t)nd * ld); }
             lift(V, r, Xr, r, ns, VX, ld, 0.0);
             lift(V, r, Zr, r, nd, VZ, ld, 0.0);
@@ -1371,6 +1512,8 @@ int rcg_set_diffusion(rcg_ctx *c, const double *D) {
         c->h2d(c->D64, D, c->n);
         convert_cols<double, float>(c->st, c->n, c->D64, c->ld, c->D32, c->ld, 1);
         diag_star(c->st, c->g, c->D64, c->h, c->grid.robin_A, c->dstar);
+        if (!c->W64) c->W64 = c->alloc<double>((size_t)3 * c->ld);
+        face_weights(c->st, c->g, c->D64, c->W64);
         c->sync();
         c->have_D = true;
         c->have_rhs = false;          // effective source weights depend on D: set them again
@@ -1540,6 +1683,113 @@ int rcg_solution_get(rcg_ctx *c, int s, double *X) {
         if (!c->opt.keep_solutions || s < 0 || s >= c->opt.max_samples || !X || c->solutions[s].empty())
             return fail(c, RCG_ERR_INVALID, "no kept solutions for this sample");
         std::memcpy(X, c->solutions[s].data(), sizeof(double) * c->solutions[s].size());
+        return RCG_OK;
+    });
+}
+
+int rcg_full_eval(rcg_ctx *c, int s, int nparam, const double *dmu, double *Psi, double *J) {
+    return guarded(c, [&]() {
+        if (!c->opt.keep_solutions || s < 0 || s >= c->opt.max_samples || !Psi || c->solutions[s].empty())
+            return fail(c, RCG_ERR_INVALID, "rcg_full_eval: no kept solutions for this sample");
+        if (dmu && (nparam < 1 || !J)) return fail(c, RCG_ERR_INVALID, "rcg_full_eval: nparam / J");
+        const int ns = c->nsrc, nd = c->ndet;
+        const long long n = c->n, ld = c->ld;
+        const std::vector<double> &X = c->solutions[s];       // n x nrhs, sources then detectors
+        // Psi[d, j] = c~_d^T x_j: the receivers are point functionals w_d e_{node_d}
+        for (int j = 0; j < ns; ++j)
+            for (int d = 0; d < nd; ++d)
+                Psi[d + (long long)nd * j] = c->rhs_w[ns + d] * X[(size_t)j * n + c->rhs_node[ns + d]];
+        if (dmu) {
+            double *dX = c->alloc<double>((size_t)c->nrhs * ld), *dw = c->alloc<double>((size_t)ld);
+            double *dm = c->alloc<double>((size_t)ld), *dJ = c->alloc<double>((size_t)nparam * nd * ns);
+            for (int j = 0; j < c->nrhs; ++j) c->h2d(dX + (long long)j * ld, X.data() + (size_t)j * n, (size_t)n);
+            for (int k = 0; k < nparam; ++k) {
+                c->h2d(dm, dmu + (size_t)k * n, (size_t)n);
+                scaled_diff(c->st, n, dm, nullptr, -c->h * c->h, dw);
+                gemm_tn<double, double>(c->st, n, dX + (long long)ns * ld, ld, nd, dX, ld, ns,
+                                        dJ + (long long)k * nd * ns, nd, false, dw);
+            }
+            c->d2h(J, dJ, (size_t)nparam * nd * ns);
+            c->sync();
+            for (void *p : std::vector<void *>{dX, dw, dm, dJ}) c->release(p);
+        }
+        return RCG_OK;
+    });
+}
+
+int rcg_save(rcg_ctx *c, const char *path) {
+    return guarded(c, [&]() {
+        if (!path || !c->eng) return fail(c, RCG_ERR_INVALID, "rcg_save: no path or nothing to save");
+        std::FILE *f = std::fopen(path, "wb");
+        if (!f) return fail(c, RCG_ERR_INVALID, std::string("rcg_save: cannot open ") + path);
+        try {
+            wr(f, kMagic, sizeof(kMagic));
+            const long long g[6] = {c->grid.dim, c->grid.N, c->n, c->opt.precision, c->nsrc, c->ndet};
+            wr(f, g, sizeof(g));
+            std::vector<double> D((size_t)c->n);
+            c->d2h(D.data(), c->D64, (size_t)c->n);
+            c->sync();
+            wr_vec(f, D);
+            wr_vec(f, c->rhs_node);
+            wr_vec(f, c->rhs_w);
+            c->eng->save(f);
+            const bool have_net = c->cnn && c->cnn->have;
+            const long long nn = have_net ? c->cnn->P : 0;
+            wr(f, &nn, sizeof(nn));
+            if (have_net) {
+                std::vector<float> th((size_t)nn);
+                c->d2h(th.data(), c->cnn->theta, (size_t)nn);
+                c->sync();
+                wr(f, th.data(), sizeof(float) * th.size());
+            }
+        } catch (...) {
+            std::fclose(f);
+            throw;
+        }
+        if (std::fclose(f) != 0) return fail(c, RCG_ERR_INVALID, "rcg_save: close failed");
+        return RCG_OK;
+    });
+}
+
+int rcg_load(rcg_ctx *c, const char *path) {
+    return guarded(c, [&]() {
+        if (!path) return fail(c, RCG_ERR_INVALID, "rcg_load: no path");
+        if (!c->have_D || !c->have_rhs) return fail(c, RCG_ERR_INVALID, "rcg_load: set D and the sources first");
+        std::FILE *f = std::fopen(path, "rb");
+        if (!f) return fail(c, RCG_ERR_INVALID, std::string("rcg_load: cannot open ") + path);
+        try {
+            char m[8];
+            rd(f, m, sizeof(m));
+            if (std::memcmp(m, kMagic, sizeof(m)) != 0) throw Error{RCG_ERR_INVALID, "rcg_load: not an rcg state file"};
+            long long g[6];
+            rd(f, g, sizeof(g));
+            if (g[0] != c->grid.dim || g[1] != c->grid.N || g[2] != c->n || g[3] != c->opt.precision ||
+                g[4] != c->nsrc || g[5] != c->ndet)
+                throw Error{RCG_ERR_INVALID, "rcg_load: grid, precision or source/detector counts differ"};
+            auto D = rd_vec<double>(f, c->n);
+            auto node = rd_vec<int>(f, c->nrhs);
+            auto w = rd_vec<double>(f, c->nrhs);
+            std::vector<double> Dc((size_t)c->n);
+            c->d2h(Dc.data(), c->D64, (size_t)c->n);
+            c->sync();
+            if (D != Dc || node != c->rhs_node || w != c->rhs_w)
+                throw Error{RCG_ERR_INVALID, "rcg_load: D or the sources / detectors differ from the saved state"};
+            if (!c->eng) throw Error{RCG_ERR_INVALID, "rcg_load: context has no engine"};
+            c->eng->load(f);
+            long long nn = 0;
+            rd(f, &nn, sizeof(nn));
+            if (nn) {
+                if (nn != cnn_nparams()) throw Error{RCG_ERR_INVALID, "rcg_load: network size differs"};
+                std::vector<float> th((size_t)nn);
+                rd(f, th.data(), sizeof(float) * th.size());
+                c->net().set_weights(c->st, th.data());
+                c->sync();
+            }
+        } catch (...) {
+            std::fclose(f);
+            throw;
+        }
+        std::fclose(f);
         return RCG_OK;
     });
 }

@@ -215,7 +215,8 @@ template <typename T>
 void apply_op(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_of_col,
               const T *const *src, T *const *dst, int ncols, const int *active,
               double *dots, unsigned long long *act_count = nullptr);
-void residual64(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
+void face_weights(cudaStream_t st, const Grid &g, const double *D, double *W);
+void residual64(cudaStream_t st, const Grid &g, const double *W, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,
                 const int *node, const double *bw, double *rr, const int *active);
 
@@ -224,6 +225,8 @@ template <typename TA, typename TB>
 void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
              const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
              const double *wt = nullptr, const int *rows = nullptr, long long nrows = 0);
+void gemm_tn_df(cudaStream_t st, long long n, const float *A, long long lda, int ka, const double *B, long long ldb,
+                int kb, double *C, int ldc, bool accumulate);
 template <typename TA, typename TB, typename AT>
 void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
                  const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
@@ -234,7 +237,10 @@ bool tc_gemm_tn_ok(long long lda, long long ldb, const void *A, const void *B);
 void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int ka, const float *B, long long ldb,
                 int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err,
                 const double *wt = nullptr, const int *blist = nullptr, const int *bcount = nullptr);
-void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count);
+// Blocks of 32 rows where w does not vanish, for nvec weight vectors (w + v ldw
+// -> list + v ldl, count[v]).
+void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count, int nvec = 1,
+                   long long ldw = 0, long long ldl = 0);
 template <typename TA, typename TO>
 void gemm_nn(cudaStream_t st, long long n, const TA *A, long long lda, int k,
              const double *Y, int ldy, int m, TO *Out, long long ldo, double alpha, double beta);

@@ -235,6 +235,68 @@ k_gemm_nn_df(long long n, const float *__restrict__ V, long long ldv, int k, con
     }
 }
 
+// C (+)= A^T B with A float32 and B float64 (the float32 basis against float64
+// stencil images: the border of the cached Galerkin matrix), in double-float
+// arithmetic on float32 units: B is split into hi + lo when staged, each
+// product a*b_hi is split exactly (TwoProd), a*b_lo joins the error term,
+// and the running sums are compensated (TwoSum).  ~1e-13 relative; GB300's
+// float64 units are ~1/64 of its float32 rate.  Partial sums of the CTA's
+// row range go to C by float64 atomics.
+__global__ void __launch_bounds__(256)
+k_gemm_tn_df(long long n, const float *__restrict__ A, long long lda, int ka, const double *__restrict__ B,
+             long long ldb, int kb, double *__restrict__ C, int ldc, long long chunk) {
+    __shared__ float As[TN_BK][TN_T + 1], Bh[TN_BK][TN_T + 1], Bl[TN_BK][TN_T + 1];
+    const int i0 = blockIdx.x * TN_T, j0 = blockIdx.y * TN_T;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long long r0 = (long long)blockIdx.z * chunk;
+    const long long r1 = (r0 + chunk < n) ? r0 + chunk : n;
+    float sh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, sl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (long long base = r0; base < r1; base += TN_BK) {
+        for (int e = threadIdx.x; e < TN_BK * TN_T; e += 256) {
+            const int rr = e % TN_BK, cc = e / TN_BK;
+            const long long q = base + rr;
+            float av = 0.f, bh = 0.f, bl = 0.f;
+            if (q < r1) {
+                if (i0 + cc < ka) av = A[(long long)(i0 + cc) * lda + q];
+                if (j0 + cc < kb) {
+                    const double bv = B[(long long)(j0 + cc) * ldb + q];
+                    bh = (float)bv;
+                    bl = (float)(bv - (double)bh);
+                }
+            }
+            As[rr][cc] = av;
+            Bh[rr][cc] = bh;
+            Bl[rr][cc] = bl;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < TN_BK; ++kk) {
+            const float a[2] = {As[kk][ty], As[kk][ty + 16]};
+            const float h[2] = {Bh[kk][tx], Bh[kk][tx + 16]}, l[2] = {Bl[kk][tx], Bl[kk][tx + 16]};
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const float prod = __fmul_rn(a[u], h[v]);
+                    float err = fmaf(a[u], h[v], -prod);          // exact: a*b_hi = prod + err
+                    err = fmaf(a[u], l[v], err);
+                    const float t = __fadd_rn(sh[u][v], prod);     // TwoSum(sh, prod)
+                    const float bp = __fsub_rn(t, sh[u][v]);
+                    const float e2 = __fadd_rn(__fsub_rn(sh[u][v], __fsub_rn(t, bp)), __fsub_rn(prod, bp));
+                    sh[u][v] = t;
+                    sl[u][v] = __fadd_rn(sl[u][v], __fadd_rn(e2, err));
+                }
+        }
+        __syncthreads();
+    }
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) {
+            const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+            const double val = (double)sh[u][v] + (double)sl[u][v];
+            if (i < ka && j < kb && val != 0.0) atomicAdd(C + i + (long long)j * ldc, val);
+        }
+}
+
 template <typename TV>
 __global__ void k_gather_rows(const TV *__restrict__ V, long long ldv, int r, const int *__restrict__ node,
                               const double *__restrict__ w, int m, double *__restrict__ out, int ldo) {
@@ -310,8 +372,8 @@ void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int k
                  int kb, double *C, int ldc, bool accumulate, const double *wt, const int *rows, long long nrows) {
     if (ka <= 0 || kb <= 0) return;
     if (!accumulate) {
-        for (int j = 0; j < kb; ++j)
-            RCG_CUDA_TRY(cudaMemsetAsync(C + (long long)j * ldc, 0, sizeof(double) * ka, st));
+        if (ldc == ka) RCG_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)ka * kb, st));
+        else RCG_CUDA_TRY(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * ka, kb, st));
     }
     const long long len = rows ? nrows : n;
     if (len <= 0) return;
@@ -347,6 +409,26 @@ void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int k
     z = (len + chunk - 1) / chunk;
     dim3 grid(gx, gy, (unsigned)z);
     k_gemm_tn<TA, TB, AT><<<grid, 256, 0, st>>>(n, A, lda, ka, B, ldb, kb, C, ldc, wt, rows, nrows, chunk);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void gemm_tn_df(cudaStream_t st, long long n, const float *A, long long lda, int ka, const double *B, long long ldb,
+                int kb, double *C, int ldc, bool accumulate) {
+    if (ka <= 0 || kb <= 0) return;
+    if (!accumulate) RCG_CUDA_TRY(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * ka, kb, st));
+    if (n <= 0) return;
+    const int gx = (ka + TN_T - 1) / TN_T, gy = (kb + TN_T - 1) / TN_T;
+    const long long tiles = (long long)gx * gy;
+    long long z = (6LL * 152 + tiles - 1) / tiles;
+    const long long maxz = (n + 1023) / 1024;
+    if (z > maxz) z = maxz;
+    if (z < 1) z = 1;
+    if (z > 65535) z = 65535;
+    long long chunk = (n + z - 1) / z;
+    chunk = (chunk + TN_BK - 1) / TN_BK * TN_BK;
+    z = (n + chunk - 1) / chunk;
+    k_gemm_tn_df<<<dim3(gx, gy, (unsigned)z), 256, 0, st>>>(n, A, lda, ka, B, ldb, kb, C, ldc, chunk);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

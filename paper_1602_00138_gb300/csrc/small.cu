@@ -103,10 +103,17 @@ __global__ void __launch_bounds__(256) k_trsv(const double *L, int ldl, int r, d
 __global__ void __launch_bounds__(1024)
 k_ordered_drop(const double *M, int a, const double *xnorm2, double tau, double *S, double *R, int *kept,
                double *ratio) {
+    // S holds the trailing Schur complement; only its upper triangle (i <= j)
+    // is kept up to date.  Row c of R is staged in shared memory.
+    extern __shared__ double rowc[];
     __shared__ double piv;
     __shared__ int keep;
-    const long long tot = (long long)a * a;
-    for (long long e = threadIdx.x; e < tot; e += blockDim.x) { S[e] = M[e]; R[e] = 0.0; }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < a; j += nw)
+        for (int i = lane; i < a; i += 32) {
+            S[i + (long long)j * a] = M[i + (long long)j * a];
+            R[i + (long long)j * a] = 0.0;
+        }
     __syncthreads();
     for (int c = 0; c < a; ++c) {
         if (threadIdx.x == 0) {
@@ -120,14 +127,16 @@ k_ordered_drop(const double *M, int a, const double *xnorm2, double tau, double 
         }
         __syncthreads();
         if (keep) {
-            for (int j = c + 1 + threadIdx.x; j < a; j += blockDim.x)
-                R[c + (long long)j * a] = S[c + (long long)j * a] / piv;
+            for (int j = c + 1 + threadIdx.x; j < a; j += blockDim.x) {
+                const double v = S[c + (long long)j * a] / piv;
+                R[c + (long long)j * a] = v;
+                rowc[j] = v;
+            }
             __syncthreads();
-            const int m = a - c - 1;
-            const long long t2 = (long long)m * m;
-            for (long long e = threadIdx.x; e < t2; e += blockDim.x) {
-                const int i = c + 1 + (int)(e % m), j = c + 1 + (int)(e / m);
-                S[i + (long long)j * a] -= R[c + (long long)i * a] * R[c + (long long)j * a];
+            // S(i, j) -= R(c, i) R(c, j) for c < i <= j: warps over columns, lanes over rows
+            for (int j = c + 1 + warp; j < a; j += nw) {
+                const double rj = rowc[j];
+                for (int i = c + 1 + lane; i <= j; i += 32) S[i + (long long)j * a] -= rowc[i] * rj;
             }
         }
         __syncthreads();
@@ -292,7 +301,9 @@ void trsv_lower_batched(cudaStream_t st, const double *L, int ldl, int r, double
 void ordered_drop_chol(cudaStream_t st, const double *M, int a, const double *xnorm2, double *S, double tau,
                        double *R, int *kept, double *ratio) {
     if (a <= 0) return;
-    k_ordered_drop<<<1, 1024, 0, st>>>(M, a, xnorm2, tau, S, R, kept, ratio);
+    const size_t sm = sizeof(double) * (size_t)a;
+    if (sm > 48 * 1024) RCG_CUDA_TRY(cudaFuncSetAttribute(k_ordered_drop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_ordered_drop<<<1, 1024, sm, st>>>(M, a, xnorm2, tau, S, R, kept, ratio);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

@@ -100,10 +100,12 @@ k_apply(Grid g, const T *__restrict__ D, const T *const *__restrict__ diag_of_co
 // r_c = b_c - A~_{s(c)} x_c in float64, b_c = bw_c e_{node_c}; optional float32 copy; rr_c += r^T r.
 template <int NB>
 __global__ void __launch_bounds__(kThreads)
-k_residual64(Grid g, const double *__restrict__ D, const double *const *__restrict__ diag_of_col,
+k_residual64(Grid g, const double *__restrict__ W, const double *const *__restrict__ diag_of_col,
              const double *const *__restrict__ xsrc, double *const *__restrict__ rdst,
              float *const *__restrict__ r32dst, int ncols, const int *__restrict__ node,
              const double *__restrict__ bw, double *__restrict__ rr, const int *__restrict__ active) {
+    // W: face weights (D_p + D_q)/2 towards the +x, +y, +z neighbour (0 on the
+    // last layer of each axis), three columns of stride g.ld
     const int c0 = blockIdx.y * NB;
     bool act[NB];
     bool any = false;
@@ -117,21 +119,14 @@ k_residual64(Grid g, const double *__restrict__ D, const double *const *__restri
     double acc[NB];
 #pragma unroll
     for (int t = 0; t < NB; ++t) acc[t] = 0.0;
-    const long long sxy = (long long)g.Nx * g.Ny;
-    const bool has_y = g.Ny > 1;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p % g.Nx);
-        const long long rest = p / g.Nx;
-        const int j = (int)(rest % g.Ny);
-        const int k = (int)(rest / g.Ny);
-        const double Dp = D[p];
-        const double wxm = i > 0 ? 0.5 * (Dp + D[p - 1]) : 0.0;
-        const double wxp = i < g.Nx - 1 ? 0.5 * (Dp + D[p + 1]) : 0.0;
-        const double wym = (has_y && j > 0) ? 0.5 * (Dp + D[p - g.Nx]) : 0.0;
-        const double wyp = (has_y && j < g.Ny - 1) ? 0.5 * (Dp + D[p + g.Nx]) : 0.0;
-        const double wzm = k > 0 ? 0.5 * (Dp + D[p - sxy]) : 0.0;
-        const double wzp = k < g.Nz - 1 ? 0.5 * (Dp + D[p + sxy]) : 0.0;
+    const int sxy = g.Nx * g.Ny, n = (int)g.n;
+    const double *__restrict__ Wx = W, *__restrict__ Wy = W + g.ld, *__restrict__ Wz = W + 2 * g.ld;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int i = p % g.Nx, rest = p / g.Nx;
+        const int j = rest % g.Ny, k = rest / g.Ny;
+        const double wxm = i > 0 ? Wx[p - 1] : 0.0, wxp = Wx[p];
+        const double wym = j > 0 ? Wy[p - g.Nx] : 0.0, wyp = Wy[p];
+        const double wzm = k > 0 ? Wz[p - sxy] : 0.0, wzp = Wz[p];
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
             if (!act[t]) continue;
@@ -140,11 +135,11 @@ k_residual64(Grid g, const double *__restrict__ D, const double *const *__restri
             double v = diag_of_col[c][p] * x[p];
             if (i > 0) v -= wxm * x[p - 1];
             if (i < g.Nx - 1) v -= wxp * x[p + 1];
-            if (has_y && j > 0) v -= wym * x[p - g.Nx];
-            if (has_y && j < g.Ny - 1) v -= wyp * x[p + g.Nx];
+            if (j > 0) v -= wym * x[p - g.Nx];
+            if (j < g.Ny - 1) v -= wyp * x[p + g.Nx];
             if (k > 0) v -= wzm * x[p - sxy];
             if (k < g.Nz - 1) v -= wzp * x[p + sxy];
-            const double b = (p == (long long)node[c]) ? bw[c] : 0.0;
+            const double b = (p == node[c]) ? bw[c] : 0.0;
             const double res = b - v;
             if (rdst) rdst[c][p] = res;
             if (r32dst) r32dst[c][p] = (float)res;
@@ -152,6 +147,19 @@ k_residual64(Grid g, const double *__restrict__ D, const double *const *__restri
         }
     }
     if (rr) block_reduce_add<NB>(acc, rr + c0, act);
+}
+
+// W[a * ld + p] = (D_p + D_q) / 2 with q the +a neighbour of p (0 if p is on
+// the last layer of axis a): the off-diagonal couplings of A~ (Sec. 3).
+__global__ void k_face_weights(Grid g, const double *__restrict__ D, double *__restrict__ W) {
+    const int sxy = g.Nx * g.Ny;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)p;
+        const int i = pi % g.Nx, rest = pi / g.Nx, j = rest % g.Ny, k = rest / g.Ny;
+        W[p] = i < g.Nx - 1 ? 0.5 * (D[p] + D[p + 1]) : 0.0;
+        W[g.ld + p] = j < g.Ny - 1 ? 0.5 * (D[p] + D[p + g.Nx]) : 0.0;
+        W[2 * g.ld + p] = k < g.Nz - 1 ? 0.5 * (D[p] + D[p + sxy]) : 0.0;
+    }
 }
 
 int grid_x_for(long long n, int groups) {
@@ -199,14 +207,20 @@ template void apply_op<float>(cudaStream_t, const Grid &, const float *, const f
                               const float *const *, float *const *, int, const int *, double *,
                               unsigned long long *);
 
-void residual64(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
+void residual64(cudaStream_t st, const Grid &g, const double *W, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,
                 const int *node, const double *bw, double *rr, const int *active) {
     if (ncols <= 0) return;
-    constexpr int NB = 4;
+    constexpr int NB = 8;
     const int groups = (ncols + NB - 1) / NB;
     dim3 grid(grid_x_for(g.n, groups), groups);
-    k_residual64<NB><<<grid, kThreads, 0, st>>>(g, D, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
+    k_residual64<NB><<<grid, kThreads, 0, st>>>(g, W, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void face_weights(cudaStream_t st, const Grid &g, const double *D, double *W) {
+    k_face_weights<<<(unsigned)std::min<long long>((g.n + 255) / 256, 4096), 256, 0, st>>>(g, D, W);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

@@ -345,7 +345,11 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
 // Ascending list of the 32-row blocks where w does not vanish (one CTA, the
 // order is deterministic): thread t scans a contiguous range of blocks.
 __global__ void __launch_bounds__(1024) k_block_list(long long n, const double *__restrict__ w, int *__restrict__ list,
-                                                     int *__restrict__ count) {
+                                                     int *__restrict__ count, long long ldw, long long ldl) {
+    // CTA b handles weight vector b: w + b ldw -> list + b ldl, count[b]
+    w += blockIdx.x * ldw;
+    list += blockIdx.x * ldl;
+    count += blockIdx.x;
     const long long nb = (n + TBK - 1) / TBK;
     const long long per = (nb + blockDim.x - 1) / blockDim.x;
     const long long b0 = threadIdx.x * per, b1 = b0 + per < nb ? b0 + per : nb;
@@ -416,8 +420,10 @@ long long tc_gemm_tn_scratch(long long n, int ka, int kb, bool symmetric, int *z
 }
 
 // Blocks of 32 rows where w is not zero (list: (n + 31) / 32 ints; count: 1 int).
-void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count) {
-    k_block_list<<<1, 1024, 0, st>>>(n, w, list, count);
+void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count, int nvec, long long ldw,
+                   long long ldl) {
+    if (nvec <= 0) return;
+    k_block_list<<<nvec, 1024, 0, st>>>(n, w, list, count, ldw, ldl);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

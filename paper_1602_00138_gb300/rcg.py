@@ -35,7 +35,7 @@ EXPORTED = [
     "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
     "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
-    "rcg_learn_gradient", "rcg_learn_predict",
+    "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
 
@@ -110,6 +110,9 @@ def load(path=LIB_PATH):
         "rcg_learn_forward": (I, [P, P, I, I, P]),
         "rcg_learn_gradient": (I, [P, P, P, I, P, C.POINTER(D)]),
         "rcg_learn_predict": (I, [P, I, P, P, P]),
+        "rcg_full_eval": (I, [P, I, I, P, P, P]),
+        "rcg_save": (I, [P, C.c_char_p]),
+        "rcg_load": (I, [P, C.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -289,6 +292,24 @@ class Context:
         J = np.zeros((k, self.nsrc, self.ndet), dtype=np.float64)   # C order = J[d + ndet*(s + nsrc*k)]
         self._check(self.L.rcg_rom_eval(self.h, _ptr(mu), k, _ptr(dmu), _ptr(Psi), _ptr(J)))
         return Psi, np.transpose(J, (0, 2, 1))
+
+    def save(self, path):
+        return self._check(self.L.rcg_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        return self._check(self.L.rcg_load(self.h, os.fsencode(path)))
+
+    def full_eval(self, s, dmu=None):
+        """Psi (ndet x nsrc) and J (nparam x ndet x nsrc) from the kept solutions of sample s."""
+        Psi = np.zeros((self.ndet, self.nsrc), dtype=np.float64, order="F")
+        J = None
+        k = 0
+        if dmu is not None:
+            dmu = np.ascontiguousarray(dmu, dtype=np.float64)      # (nparam, n) -> n x nparam column-major
+            k = dmu.shape[0]
+            J = np.zeros((k, self.nsrc, self.ndet), dtype=np.float64)
+        self._check(self.L.rcg_full_eval(self.h, s, k, _ptr(dmu), _ptr(Psi), _ptr(J)))
+        return Psi, (None if J is None else np.transpose(J, (0, 2, 1)))
 
     def rom_eval_device(self, mu_dev, dmu_dev, Psi_dev, J_dev, nparam):
         return self._check(self.L.rcg_rom_eval_device(self.h, _ptr(mu_dev), nparam, _ptr(dmu_dev),
