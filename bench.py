@@ -37,6 +37,7 @@ METRIC = "full-order solves/s at relres 1e-8: learned+mixed batched RCG vs plain
 CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0, learned=1)  # learned + mixed, one wave
 MIXED_PLAIN = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0)          # the same without the network
 NTRAIN, EPOCHS, BATCH, LR = 8, 40, 16, 1e-3     # training solves (held-out parameter points), Adam schedule
+MAX_TRAIN = 32
 BASELINE = dict(precision=0, order=0, tau_rank=1e-12)                    # FP64, paper order
 ORACLE_RHS = (0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39)    # CPU sample: 8 src + 8 det
 ORACLE_SAMPLES = (1, 2)
@@ -53,6 +54,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--ncu-region", action="store_true",
                     help="profile only the timed steps (cudaProfilerStart/Stop); skip the other legs")
+    ap.add_argument("--train-samples", type=int, default=NTRAIN,
+                    help="parameter points solved (untimed) to train the learned augmentation")
+    ap.add_argument("--epochs", type=int, default=EPOCHS, help="Adam epochs over the recorded pairs")
     ap.add_argument("--products", action="store_true",
                     help="time the basis product A^T B on the tensor cores and on CUDA cores (one JSON line per shape)")
     ap.add_argument("--products-shapes", type=int, default=4, help="number of --products shapes to run")
@@ -118,7 +122,7 @@ class Clocks:
 def make_ctx(rcg, inp, opts, torch, device_inputs=True):
     wl = inp["wl"]
     stream = torch.cuda.current_stream().cuda_stream
-    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, stream=stream, k_u=wl.k_u, max_samples=wl.K + 2 + NTRAIN,
+    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, stream=stream, k_u=wl.k_u, max_samples=wl.K + 2 + MAX_TRAIN,
                       r_max=1024, **opts)
     ctx.set_diffusion(inp["D"])
     ctx.set_sources_detectors(inp["src_ij"], inp["det_ij"])
@@ -156,7 +160,8 @@ def run_ours(args, rank, world, torch):
     J_dev = torch.empty(wl.nparam * wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
     # training samples of the learned augmentation: parameter points of the same
     # jitter law, disjoint from the timed samples and the held-out ROM point
-    mu_tr = [pals_mu(p, inp["X"], wl.mu_bg) for p in heldout_params(wl, NTRAIN, seed_offset=2000)]
+    ntrain, epochs = min(args.train_samples, MAX_TRAIN), args.epochs
+    mu_tr = [pals_mu(p, inp["X"], wl.mu_bg) for p in heldout_params(wl, ntrain, seed_offset=2000)]
     learn_info = {}
 
     def train_network(ctx):
@@ -169,17 +174,17 @@ def run_ours(args, rank, world, torch):
         ctx.learn_record(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.solve_all(K + 1, NTRAIN)
+        ctx.solve_all(K + 1, ntrain)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         loss0 = ctx.learn_train(1, BATCH, LR, 1)
-        loss = ctx.learn_train(EPOCHS - 1, BATCH, LR, 2)
+        loss = ctx.learn_train(max(epochs - 1, 0), BATCH, LR, 2) if epochs > 1 else loss0
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         ctx.learn_record(False)
-        learn_info.update(pairs=ctx.learn_pairs(), epochs=EPOCHS, batch=BATCH, lr=LR, loss_first_epoch=loss0,
+        learn_info.update(pairs=ctx.learn_pairs(), epochs=epochs, batch=BATCH, lr=LR, loss_first_epoch=loss0,
                           loss_last_epoch=loss, data_s=round(t1 - t0, 3), train_s=round(t2 - t1, 3),
-                          training_samples=NTRAIN, params=len(ctx.learn_get_weights()))
+                          training_samples=ntrain, params=len(ctx.learn_get_weights()))
 
     def prepare(opts):
         ctx = make_ctx(rcg, inp, opts, torch)

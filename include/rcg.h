@@ -238,6 +238,17 @@ int rcg_rom_eval(rcg_ctx *c, const double *mu, int nparam, const double *dmu,
  * model against the full one (the interpolation property of Sec. 3.4). */
 int rcg_full_eval(rcg_ctx *c, int s, int nparam, const double *dmu, double *Psi, double *J);
 
+/* The basis update of the append (Sec. 5.3: W - V (V^T W), Q = W R^-1,
+ * V <- Q R2^-1), exposed for testing and timing: Out = alpha V C + beta Out
+ * with V (n x k, ld ldv) float32, C (k x m, ld ldc) float64 and Out (n x m,
+ * ld ldo) float32, all in device memory and owned by the caller.  engine 0:
+ * CUDA cores (float32); engine 1: tensor cores (3xTF32; V 16-byte aligned
+ * with ldv a multiple of 4, else RCG_ERR_INVALID).  Runs on `stream` and
+ * returns after it has finished; RCG_ERR_TIMEOUT if a tensor-core wait ran
+ * out (Out undefined). */
+int rcg_gemm_nn_f32(const float *V, long long ldv, int k, const double *C, int ldc, int m, long long n, float *Out,
+                    long long ldo, double alpha, double beta, int engine, void *stream);
+
 /* Save the recycling state (V, C_* = V^T A~_* V and the mu_* it belongs to,
  * X_0 and V^T X_0, the private recycle lists, the state right after the seed,
  * the learned network's weights if any) to a file, and load it into a

@@ -312,6 +312,20 @@ struct Engine : EngineBase {
         c->h2d(p_r, hr.data(), m);
         c->h2d(p_p, hp.data(), m);
         c->h2d(p_q, hq.data(), m);
+        // lane state starts inactive over the whole capacity (fresh device memory
+        // holds whatever an earlier allocation left there)
+        RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * m, st));
+        RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * m, st));
+        RCG_CUDA_TRY(cudaMemsetAsync(ls.kdef, 0, sizeof(int) * m, st));
+        RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * m, st));
+        RCG_CUDA_TRY(cudaMemsetAsync(d_mask, 0, sizeof(int) * m, st));
+        // diagonal pointers of unused lanes point at a valid column (sample slot 0)
+        {
+            std::vector<double *> hd64(m, c->diag64_of(0));
+            std::vector<T *> hdt(m, (T *)diagT(0));
+            c->h2d(p_diag64, hd64.data(), m);
+            c->h2d(p_diag, hdt.data(), m);
+        }
         c->sync();
     }
 
@@ -439,6 +453,24 @@ struct Engine : EngineBase {
         return dw[s];
     }
 
+    // Out (n x m) = alpha A C + beta Out with A (n x k, stride ld) and C (k x m,
+    // float64): tensor cores for float32 with k, m >= 16, CUDA cores otherwise.
+    void prod_nn(const T *A, int k, const double *C, int ldc, int m, T *Out, double alpha, double beta) {
+        if constexpr (sizeof(T) == 4) {
+            if (k >= 16 && m >= 16 && ld % 4 == 0 && ((uintptr_t)A & 15) == 0) {
+                const long long need = tc_gemm_nn_scratch(k, m);
+                if (need > tc_cap) {
+                    c->release(tc_scr);
+                    tc_cap = std::max(need, 2 * tc_cap);
+                    tc_scr = c->alloc<float>((size_t)tc_cap);
+                }
+                tc_gemm_nn(st, n, A, ld, k, C, ldc, m, Out, ld, alpha, beta, tc_scr, d_info + 1);
+                return;
+            }
+        }
+        gemm_nn<T, T>(st, n, A, ld, k, C, ldc, m, Out, ld, alpha, beta);
+    }
+
     // C (ka x ka, ld ldc) += A^T diag(w) A: the weighted Gram of the check and the
     // reduced model; tensor cores (only the 32-row blocks in blist) for float32.
     void gram_w_acc(const T *A, int ka, double *C, int ldc, const double *w, const int *blist, const int *bcount) {
@@ -509,7 +541,7 @@ struct Engine : EngineBase {
         norm2_lanes(st, n, (const double *const *)p_x64, d_cand, a, xn2);
         for (int pass = 0; pass < 2 && r > 0; ++pass) {   // W <- (I - V V^T)^2 X
             prod_tn(V, r, Wb, a, Cb, r);
-            gemm_nn<T, T>(st, n, V, ld, r, Cb, r, a, Wb, ld, -1.0, 1.0);
+            prod_nn(V, r, Cb, r, a, Wb, -1.0, 1.0);
         }
         prod_tn(Wb, a, Wb, a, M, a, true);
         ordered_drop_chol(st, M, a, xn2, S, tau, R, kept_d, ratio_d);
@@ -527,11 +559,11 @@ struct Engine : EngineBase {
         gather_sub(st, R, a, d_K, ak, RK);
         tri_upper_inverse(st, RK, ak, ak, Ri);
         scatter_rows(st, Ri, ak, d_K, a, Rhat);
-        gemm_nn<T, T>(st, n, Wb, ld, a, Rhat, a, ak, Qb, ld, 1.0, 0.0);
+        prod_nn(Wb, a, Rhat, a, ak, Qb, 1.0, 0.0);
         // second pass: Q <- (I - V V^T) Q, then Q R2^-1 with R2^T R2 = Q^T Q
         if (r > 0) {
             prod_tn(V, r, Qb, ak, Cb, r);
-            gemm_nn<T, T>(st, n, V, ld, r, Cb, r, ak, Qb, ld, -1.0, 1.0);
+            prod_nn(V, r, Cb, r, ak, Qb, -1.0, 1.0);
         }
         prod_tn(Qb, ak, Qb, ak, M, ak, true);
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -539,7 +571,7 @@ struct Engine : EngineBase {
         check_info("append second pass Q^T Q");
         lower_to_upper(st, M, ak, ak, RK);
         tri_upper_inverse(st, RK, ak, ak, Ri);
-        gemm_nn<T, T>(st, n, Qb, ld, ak, Ri, ak, ak, V + (long long)r * ld, ld, 1.0, 0.0);
+        prod_nn(Qb, ak, Ri, ak, ak, V + (long long)r * ld, 1.0, 0.0);
         // C_* bordered with [V Q]^T A~_* Q.  The stencil and the products are
         // float64 in both modes: for smooth columns A~ Q cancels to ~lambda_min
         // |Q|, so a float32 stencil would lose 3 digits of the Galerkin matrix
@@ -834,10 +866,14 @@ struct Engine : EngineBase {
             };
             for (int l = 0; l < m; ++l)
                 if (act[l]) set_thresh(l, std::sqrt(rr_h[l]));
+            // the whole capacity: the scalar iteration launches over ls.m lanes and
+            // skips those whose active / mask entry is 0 (lanes m.. of a smaller wave)
+            RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * ls.m, st));
+            RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * ls.m, st));
+            RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * ls.m, st));
+            RCG_CUDA_TRY(cudaMemsetAsync(d_mask, 0, sizeof(int) * ls.m, st));
             c->h2d(ls.thresh, thr.data(), m);
             c->h2d(d_mask, act.data(), m);
-            RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * m, st));
-            RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * m, st));
             ls.prof = c->ktimer.on ? c->d_prof : nullptr;
             int t = 0;
             const int chunk = m > 1 ? 8 : 12;
@@ -1009,7 +1045,7 @@ struct Engine : EngineBase {
             check_info("eigen seed CholQR");
             lower_to_upper(st, M, b, b, RK);
             tri_upper_inverse(st, RK, b, b, Ri);
-            gemm_nn<T, T>(st, n, X, ld, b, Ri, b, b, Y, ld, 1.0, 0.0);
+            prod_nn(X, b, Ri, b, b, Y, 1.0, 0.0);
             RCG_CUDA_TRY(cudaMemcpyAsync(X, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
         }
     }
@@ -1022,9 +1058,9 @@ struct Engine : EngineBase {
         apply_cols(src, dst, std::vector<int>(b, s0));
         prod_tn(X, b, AX, b, M, b);
         jacobi_eig(st, M, b, b, Rhat, xn2);          // Rhat: eigenvectors, xn2: eigenvalues
-        gemm_nn<T, T>(st, n, X, ld, b, Rhat, b, b, Y, ld, 1.0, 0.0);
+        prod_nn(X, b, Rhat, b, b, Y, 1.0, 0.0);
         RCG_CUDA_TRY(cudaMemcpyAsync(X, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
-        gemm_nn<T, T>(st, n, AX, ld, b, Rhat, b, b, Y, ld, 1.0, 0.0);
+        prod_nn(AX, b, Rhat, b, b, Y, 1.0, 0.0);
         RCG_CUDA_TRY(cudaMemcpyAsync(AX, Y, sizeof(T) * (size_t)b * ld, cudaMemcpyDeviceToDevice, st));
         theta.resize(b);
         c->d2h(theta.data(), xn2, b);

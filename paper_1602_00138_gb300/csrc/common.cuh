@@ -15,18 +15,22 @@ struct Error {
     std::string msg;
 };
 
+#define RCG_STR2(x) #x
+#define RCG_STR(x) RCG_STR2(x)
+#define RCG_WHERE " (" __FILE__ ":" RCG_STR(__LINE__) ")"
+
 #define RCG_CUDA_TRY(expr)                                                          \
     do {                                                                            \
         cudaError_t e_ = (expr);                                                    \
         if (e_ != cudaSuccess)                                                      \
-            throw ::rcg::Error{-2, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+            throw ::rcg::Error{-2, std::string(#expr) + ": " + cudaGetErrorString(e_) + RCG_WHERE}; \
     } while (0)
 
 #define RCG_CHECK_LAUNCH()                                                          \
     do {                                                                            \
         cudaError_t e_ = cudaGetLastError();                                        \
         if (e_ != cudaSuccess)                                                      \
-            throw ::rcg::Error{-2, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+            throw ::rcg::Error{-2, std::string("kernel launch: ") + cudaGetErrorString(e_) + RCG_WHERE}; \
     } while (0)
 
 // Launch counter shared by all launchers of a context (set by the caller).
@@ -239,6 +243,9 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
                 const double *wt = nullptr, const int *blist = nullptr, const int *bcount = nullptr);
 // Blocks of 32 rows where w does not vanish, for nvec weight vectors (w + v ldw
 // -> list + v ldl, count[v]).
+long long tc_gemm_nn_scratch(int k, int m);
+void tc_gemm_nn(cudaStream_t st, long long n, const float *V, long long ldv, int k, const double *C, int ldc, int m,
+                float *Out, long long ldo, double alpha, double beta, float *scratch, int *err);
 void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count, int nvec = 1,
                    long long ldw = 0, long long ldl = 0);
 template <typename TA, typename TO>

@@ -377,6 +377,196 @@ __global__ void __launch_bounds__(1024) k_block_list(long long n, const double *
     if (threadIdx.x == blockDim.x - 1) *count = scan[threadIdx.x];
 }
 
+// ------------------------------------------------------------------ NN
+// Out (n x m, float32) = alpha V C + beta Out with V (n x k, float32,
+// column-major) and C (k x m, float64): the basis updates of the append
+// (W -= V (V^T W), Q = W R^-1, V <- Q R2^-1).  A CTA owns 128 rows x 128
+// columns of Out and walks k in steps of 32.  C is split once per call into
+// TF32 hi / lo rows (k_nn_prep_b, rows of ldb floats) that cp.async copies
+// straight into the swizzled K-major B operand; the V tile arrives in its
+// natural row-major-in-n layout and is transposed into the K-major A operand
+// while it is split.  Accumulation and drains as in k_tc_tn.
+constexpr int NN_RAW = TBK * TM * 4;                                   // raw V tile: [32 k][128 rows]
+constexpr int NN_SMEM = NSTAGE * STAGE_BYTES + 2 * NN_RAW + 1024;
+
+__global__ void k_nn_prep_b(const double *__restrict__ C, int ldc, int k, int m, float *__restrict__ Bh,
+                            float *__restrict__ Bl, int ldb) {
+    const long long tot = (long long)m * ldb;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ldb), kk = (int)(e % ldb);
+        const float b = kk < k ? (float)C[kk + (long long)j * ldc] : 0.f;
+        const float h = rn_tf32(b);
+        Bh[e] = h;
+        Bl[e] = rn_tf32(b - h);
+    }
+}
+
+__global__ void __launch_bounds__(NTHR, 1)
+k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const float *__restrict__ Bh,
+        const float *__restrict__ Bl, int ldb, int m, float *__restrict__ Out, long long ldo, float alpha, float beta,
+        int *__restrict__ err) {
+    extern __shared__ __align__(1024) char smem_raw[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok;
+    char *smem = (char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    char *rawA = smem + NSTAGE * STAGE_BYTES;
+    const long long i0 = (long long)blockIdx.x * TM;
+    const int j0 = blockIdx.y * TNc;
+    const long long nk = (k + TBK - 1) / TBK;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2 * TNc));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_ok = 1;
+    }
+    // this thread's B rows (columns j0 + t/8 + 32 it of Out) in the prepared hi / lo arrays
+    const int mt = threadIdx.x >> 3;
+    const long long stepB = 32LL * ldb;
+    const float *colBh = Bh + (long long)(j0 + mt < m ? j0 + mt : 0) * ldb + 4 * (threadIdx.x & 7);
+    const float *colBl = Bl + (long long)(j0 + mt < m ? j0 + mt : 0) * ldb + 4 * (threadIdx.x & 7);
+    const int ncolB = j0 + mt < m ? min(4, (m - j0 - mt + 31) / 32) : 0;
+    auto prefetch = [&](long long q) {
+        const long long k0 = q * TBK;
+        // V tile: [kk][128 rows], 32 16-byte chunks per k column
+        char *ra = rawA + (int)(q & 1) * NN_RAW;
+#pragma unroll
+        for (int it = 0; it < (TBK * TM / 4) / NTHR; ++it) {
+            const int e = threadIdx.x + it * NTHR;
+            const int kk = e >> 5, c = e & 31;
+            const long long row = i0 + 4 * c, col = k0 + kk;
+            int bytes = 0;
+            const float *src = V;
+            if (col < k && row < n) {
+                src = V + col * ldv + row;
+                bytes = n - row >= 4 ? 16 : (int)(4 * (n - row));
+            }
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(ra + kk * 512 + c * 16)),
+                         "l"(src), "r"(bytes)
+                         : "memory");
+        }
+        // B hi / lo rows straight into the operand stage (128-byte swizzle)
+        char *stg = smem + (int)(q % NSTAGE) * STAGE_BYTES;
+        prefetch_tile(colBh, stepB, ncolB, k0, (long long)ldb, stg + TILE_BYTES);
+        prefetch_tile(colBl, stepB, ncolB, k0, (long long)ldb, stg + 3 * TILE_BYTES);
+    };
+    for (int q = 0; q < 2; ++q) {
+        if (q < nk) prefetch(q);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = make_idesc_tf32(TM, TNc);
+    const uint32_t t_lane = (uint32_t)((warp & 3) * 32) << 16;
+    const int col0 = (warp >> 2) * 64;
+    float acc1[64], acc2[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) { acc1[q] = 0.f; acc2[q] = 0.f; }
+    bool ok = true;
+    long long drained = 0;
+    auto drain = [&](long long q) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t base = tmem + t_lane + (uint32_t)((q & 1) * TNc + col0);
+        float v[32];
+        tmem_ld32(base, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc1[c] += v[c];
+        tmem_ld32(base + 32, v);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc1[32 + c] += v[c];
+        if (((q + 1) % LEVEL1) == 0) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) { acc2[c] += acc1[c]; acc1[c] = 0.f; }
+        }
+        drained = q + 1;
+    };
+    for (long long ks = 0; ks < nk; ++ks) {
+        char *stg = smem + (int)(ks % NSTAGE) * STAGE_BYTES;
+        const char *ra = rawA + (int)(ks & 1) * NN_RAW;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        if (!s_ok) { ok = false; break; }
+        // split and transpose: thread (t, row) takes k = 4t..4t+3 of one row
+#pragma unroll
+        for (int it = 0; it < (TBK / 4) * TM / NTHR; ++it) {
+            const int e = threadIdx.x + it * NTHR;
+            const int row = e & 127, t = e >> 7;
+            float4 h, l;
+            float x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = *(const float *)(ra + (4 * t + q) * 512 + row * 4);
+            h.x = rn_tf32(x[0]); h.y = rn_tf32(x[1]); h.z = rn_tf32(x[2]); h.w = rn_tf32(x[3]);
+            l.x = rn_tf32(x[0] - h.x); l.y = rn_tf32(x[1] - h.y); l.z = rn_tf32(x[2] - h.z); l.w = rn_tf32(x[3] - h.w);
+            *(float4 *)(stg + sw_off(row, t)) = h;
+            *(float4 *)(stg + 2 * TILE_BYTES + sw_off(row, t)) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t d = tmem + (uint32_t)((ks & 1) * TNc);
+            const uint32_t a_hi = smem_u32(stg), b_hi = a_hi + TILE_BYTES;
+            const uint32_t a_lo = a_hi + 2 * TILE_BYTES, b_lo = a_hi + 3 * TILE_BYTES;
+#pragma unroll
+            for (int s = 0; s < TBK / 8; ++s) {
+                const uint32_t o = s * 32;
+                mma_tf32(d, make_desc_sw128(a_hi + o), make_desc_sw128(b_hi + o), idesc, s > 0 ? 1u : 0u);
+                mma_tf32(d, make_desc_sw128(a_hi + o), make_desc_sw128(b_lo + o), idesc, 1u);
+                mma_tf32(d, make_desc_sw128(a_lo + o), make_desc_sw128(b_hi + o), idesc, 1u);
+            }
+            mma_commit(smem_u32(&mbar[ks & 1]));
+        }
+        if (ks >= 1) {
+            const long long q = ks - 1;
+            if (mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1))) {
+                drain(q);
+            } else {
+                s_ok = 0;
+                ok = false;
+            }
+        }
+        // step ks+2: the raw V stage of step ks (split above) and the operand
+        // stage of step ks-1 (its MMAs are complete) are free
+        if (ok && ks + 2 < nk) prefetch(ks + 2);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    if (nk > 0 && drained < nk) {
+        const long long q = drained < nk - 1 ? (ok ? nk - 1 : drained) : nk - 1;
+        const bool done = mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1));
+        if (ok && done && q == nk - 1 && drained == nk - 1) drain(q);
+        else ok = false;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok) s_ok = 0;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (threadIdx.x == 0 && !s_ok) atomicExch(err, RCG_ERR_TIMEOUT);
+    const long long row = i0 + (warp & 3) * 32 + lane;
+    if (s_ok && row < n) {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+            const int col = j0 + col0 + c;
+            if (col < m) {
+                float *o = Out + (long long)col * ldo + row;
+                const float v = alpha * (acc2[c] + acc1[c]);
+                *o = beta != 0.f ? v + beta * *o : v;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TNc));
+}
+
 // C[i + j*ldc] (+)= sum_z part[z][j][i] in float64; a symmetric product
 // reads the lower tiles from the mirrored upper ones.
 __global__ void k_tc_reduce(const float *__restrict__ part, int z, int ka, int kb, int symmetric,
@@ -465,6 +655,34 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
     RCG_CHECK_LAUNCH();
 }
 
+// Prepared-B float32 scratch of tc_gemm_nn: 2 m ldb floats, ldb = k rounded up to 32.
+long long tc_gemm_nn_scratch(int k, int m) { return 2LL * m * ((k + TBK - 1) / TBK * TBK); }
+
+// Out (n x m, ld ldo) = alpha V C + beta Out on the tensor cores (3xTF32).
+// V: float32 n x k (ld ldv, 16-byte aligned columns); C: float64 k x m (ld ldc).
+void tc_gemm_nn(cudaStream_t st, long long n, const float *V, long long ldv, int k, const double *C, int ldc, int m,
+                float *Out, long long ldo, double alpha, double beta, float *scratch, int *err) {
+    if (m <= 0 || n <= 0) return;
+    if (k <= 0 || ldv % 4 != 0 || ((uintptr_t)V & 15)) throw Error{RCG_ERR_INVALID, "tc_gemm_nn: bad operands"};
+    const int ldb = (k + TBK - 1) / TBK * TBK;
+    float *Bh = scratch, *Bl = scratch + (long long)m * ldb;
+    const long long tot = (long long)m * ldb;
+    k_nn_prep_b<<<(unsigned)std::min<long long>((tot + 255) / 256, 2048), 256, 0, st>>>(C, ldc, k, m, Bh, Bl, ldb);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    static bool attr[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_tc_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, NN_SMEM));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)((m + TNc - 1) / TNc));
+    k_tc_nn<<<grid, NTHR, NN_SMEM, st>>>(n, V, ldv, k, Bh, Bl, ldb, m, Out, ldo, (float)alpha, (float)beta, err);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
 }  // namespace rcg
 
 // ------------------------------------------------------------ C ABI
@@ -531,6 +749,48 @@ extern "C" int rcg_gemm_tn_f32(const float *A, long long lda, int ka, const floa
         }
         RCG_CUDA_TRY(cudaStreamSynchronize(st));
         if (engine == 1) {
+            int h = 0;
+            RCG_CUDA_TRY(cudaMemcpy(&h, g_gemm_err[dev], sizeof(int), cudaMemcpyDeviceToHost));
+            if (h) rc = RCG_ERR_TIMEOUT;
+        }
+    } catch (const Error &e) {
+        rc = e.code;
+    }
+    return rc;
+}
+
+extern "C" int rcg_gemm_nn_f32(const float *V, long long ldv, int k, const double *C, int ldc, int m, long long n,
+                               float *Out, long long ldo, double alpha, double beta, int engine, void *stream) {
+    using namespace rcg;
+    if ((n > 0 && k > 0 && (!V || !C)) || (n > 0 && m > 0 && !Out) || k < 0 || m < 0 || n < 0 || ldv < n || ldo < n ||
+        ldc < k || (engine != 0 && engine != 1))
+        return RCG_ERR_INVALID;
+    if (engine == 1 && (ldv % 4 != 0 || ((uintptr_t)V & 15))) return RCG_ERR_INVALID;
+    if (m == 0 || n == 0) return RCG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_gemm_mu);
+    int rc = RCG_OK;
+    try {
+        int dev = 0;
+        RCG_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) return RCG_ERR_INVALID;
+        if (engine == 1 && k > 0) {
+            const long long need = tc_gemm_nn_scratch(k, m);
+            if (need > g_gemm_cap[dev]) {
+                if (g_gemm_scr[dev]) RCG_CUDA_TRY(cudaFree(g_gemm_scr[dev]));
+                g_gemm_scr[dev] = nullptr;
+                g_gemm_cap[dev] = 0;
+                RCG_CUDA_TRY(cudaMalloc(&g_gemm_scr[dev], sizeof(float) * (size_t)need));
+                g_gemm_cap[dev] = need;
+            }
+            if (!g_gemm_err[dev]) RCG_CUDA_TRY(cudaMalloc(&g_gemm_err[dev], sizeof(int)));
+            RCG_CUDA_TRY(cudaMemsetAsync(g_gemm_err[dev], 0, sizeof(int), st));
+            tc_gemm_nn(st, n, V, ldv, k, C, ldc, m, Out, ldo, alpha, beta, g_gemm_scr[dev], g_gemm_err[dev]);
+        } else {
+            gemm_nn<float, float>(st, n, V, ldv, k, C, ldc, m, Out, ldo, alpha, beta);
+        }
+        RCG_CUDA_TRY(cudaStreamSynchronize(st));
+        if (engine == 1 && k > 0) {
             int h = 0;
             RCG_CUDA_TRY(cudaMemcpy(&h, g_gemm_err[dev], sizeof(int), cudaMemcpyDeviceToHost));
             if (h) rc = RCG_ERR_TIMEOUT;

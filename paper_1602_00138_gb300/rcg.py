@@ -35,7 +35,7 @@ EXPORTED = [
     "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
     "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
-    "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load",
+    "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load", "rcg_gemm_nn_f32",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
 
@@ -113,6 +113,7 @@ def load(path=LIB_PATH):
         "rcg_full_eval": (I, [P, I, I, P, P, P]),
         "rcg_save": (I, [P, C.c_char_p]),
         "rcg_load": (I, [P, C.c_char_p]),
+        "rcg_gemm_nn_f32": (I, [P, LL, I, P, I, I, LL, P, LL, D, D, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -163,6 +164,24 @@ def gemm_tn_f32(A, B, engine=1, symmetric=False, stream=None, w=None):
     if rc != 0:
         raise RcgError(rc, lib().rcg_strerror(rc).decode())
     return Cm.t()
+
+
+def gemm_nn_f32(V, Cmat, Out, alpha=1.0, beta=0.0, engine=1, stream=None):
+    """Out = alpha V C + beta Out in place.  V: float32 CUDA tensor (k, n) holding
+    the k columns of length n; Cmat: float64 CUDA tensor (m, k) holding the m
+    columns of C; Out: float32 CUDA tensor (m, n) holding the m columns of Out."""
+    import torch
+    k, n = V.shape
+    m, k2 = Cmat.shape
+    assert k == k2 and Out.shape[0] == m and Out.shape[1] == n
+    assert V.dtype == torch.float32 and Cmat.dtype == torch.float64 and Out.dtype == torch.float32
+    assert V.stride(1) == 1 and Cmat.stride(1) == 1 and Out.stride(1) == 1
+    st = stream if stream is not None else torch.cuda.current_stream(V.device).cuda_stream
+    rc = lib().rcg_gemm_nn_f32(V.data_ptr(), V.stride(0), k, Cmat.data_ptr(), Cmat.stride(0), m, n,
+                               Out.data_ptr(), Out.stride(0), alpha, beta, engine, st)
+    if rc != 0:
+        raise RcgError(rc, lib().rcg_strerror(rc).decode())
+    return Out
 
 
 def default_options(**kw):

@@ -109,3 +109,33 @@ def test_weighted_product_with_finite_support(rcg, engine):
     scale = np.outer(np.linalg.norm(A64 * np.sqrt(w[:n]), axis=1), np.linalg.norm(A64 * np.sqrt(w[:n]), axis=1))
     err = np.max(np.abs(C - ref) / scale)
     assert err <= (5e-7 if engine == 1 else 1e-7), err
+
+
+NN_CASES = [(100003, 150, 70, False, 0.0), (70001, 7, 300, True, 1.0), (40, 33, 20, False, -1.0),
+            (262144, 130, 129, True, 1.0), (4096, 128, 128, True, 0.0)]
+
+
+@pytest.mark.parametrize("n,k,m,positive,beta", NN_CASES)
+@pytest.mark.parametrize("engine", [1, 0])
+def test_update_product_matches_float64(rcg, n, k, m, positive, beta, engine):
+    """Out = alpha V C + beta Out (the append's basis updates) against float64."""
+    import torch
+    rng = np.random.default_rng(100 * k + m)
+    ld = (n + 63) // 64 * 64 + 4
+    V = _cols(rng, k, n, ld, positive)
+    Cm = rng.standard_normal((m, k)) * (1.0 if not positive else 0.1)
+    O = _cols(rng, m, n, ld, positive)
+    dV = torch.from_numpy(V).cuda()
+    dC = torch.from_numpy(Cm).cuda()
+    dO = torch.from_numpy(O.copy()).cuda()
+    alpha = -0.75
+    rcg.gemm_nn_f32(dV[:, :n], dC, dO[:, :n], alpha=alpha, beta=beta, engine=engine)
+    out = dO.cpu().numpy()[:, :n].astype(np.float64)
+    V64 = V[:, :n].astype(np.float64)
+    ref = alpha * (Cm.astype(np.float32).astype(np.float64) @ V64) + beta * O[:, :n].astype(np.float64)
+    # rounding scale of entry (j, p): |alpha| sum_i |C_ij V_ip| + |beta O_jp|
+    scale = abs(alpha) * (np.abs(Cm) @ np.abs(V64)) + abs(beta) * np.abs(O[:, :n]) + 1e-30
+    err = np.max(np.abs(out - ref) / scale)
+    assert err <= 4e-6, err
+    # the padding beyond n is untouched
+    assert np.array_equal(dO.cpu().numpy()[:, n:], O[:, n:])
