@@ -51,6 +51,7 @@ constexpr int WBYTES = TBK * 8;                          // the step's float64 r
 constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + NSTAGE * WBYTES + 1024;   // + 1024-byte alignment slack
 constexpr int LEVEL1 = 16;              // K-steps summed before the second level
 constexpr long long SPIN_LIMIT = 1LL << 22;
+constexpr long long LIST_MIN_CHUNK = 8;  // fewest K-steps per slice when a block list sets the length
 constexpr int NUM_SMS = 152;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -186,6 +187,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// K-steps per slice when the weights' block list (nsteps blocks) is spread
+// over z slices; slices past the last block hold no partial.
+__device__ __forceinline__ long long list_chunk(long long nsteps, int z) {
+    const long long c = (nsteps + z - 1) / z;
+    return c < LIST_MIN_CHUNK ? LIST_MIN_CHUNK : c;
+}
+
 __global__ void __launch_bounds__(NTHR, 1)
 k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const float *__restrict__ B, long long ldb,
         int kb, int symmetric, float *__restrict__ part, long long chunk, int *__restrict__ err,
@@ -202,6 +210,10 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
     // slice); step s covers rows 32 s .. 32 s + 31, or rows 32 blist[s] .. with a
     // block list (the blocks where the weights do not vanish)
     const long long nsteps = blist ? (long long)*bcount : (n + TBK - 1) / TBK;
+    if (blist) {                       // the support, not n, sets the slice length
+        chunk = list_chunk(nsteps, (int)gridDim.z);
+        if ((long long)blockIdx.z * chunk >= nsteps) return;    // empty slice: the reduction skips it
+    }
     const long long s_begin = (long long)blockIdx.z * chunk;
     const long long s_end = s_begin + chunk < nsteps ? s_begin + chunk : nsteps;
     const long long nk = s_end > s_begin ? s_end - s_begin : 0;
@@ -553,15 +565,22 @@ k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const fl
     if (threadIdx.x == 0 && !s_ok) atomicExch(err, RCG_ERR_TIMEOUT);
     const long long row = i0 + (warp & 3) * 32 + lane;
     if (s_ok && row < n) {
+        // all loads of Out before the first store: a store between them would
+        // serialise one DRAM latency per column (the columns may alias for
+        // all the compiler knows)
+        const int ncol = min(64, m - j0 - col0);
+        float *o = Out + (long long)(j0 + col0) * ldo + row;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            const int col = j0 + col0 + c;
-            if (col < m) {
-                float *o = Out + (long long)col * ldo + row;
-                const float v = alpha * (acc2[c] + acc1[c]);
-                *o = beta != 0.f ? v + beta * *o : v;
-            }
+        for (int c = 0; c < 64; ++c) acc2[c] = alpha * (acc2[c] + acc1[c]);
+        if (beta != 0.f) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) acc1[c] = c < ncol ? o[(long long)c * ldo] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 64; ++c) acc2[c] += beta * acc1[c];
         }
+#pragma unroll
+        for (int c = 0; c < 64; ++c)
+            if (c < ncol) o[(long long)c * ldo] = acc2[c];
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TNc));
@@ -570,7 +589,12 @@ k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const fl
 // C[i + j*ldc] (+)= sum_z part[z][j][i] in float64; a symmetric product
 // reads the lower tiles from the mirrored upper ones.
 __global__ void k_tc_reduce(const float *__restrict__ part, int z, int ka, int kb, int symmetric,
-                            double *__restrict__ C, int ldc, int accumulate) {
+                            double *__restrict__ C, int ldc, int accumulate, const int *__restrict__ bcount) {
+    if (bcount) {                      // only the slices that held blocks of the list
+        const long long nsteps = *bcount;
+        const long long chunk = list_chunk(nsteps, z);
+        z = (int)((nsteps + chunk - 1) / chunk);
+    }
     const long long tot = (long long)ka * kb;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(e % ka), j = (int)(e / ka);
@@ -650,7 +674,7 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
     RCG_CHECK_LAUNCH();
     const long long tot = (long long)ka * kb;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 2048);
-    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, z, ka, kb, symmetric ? 1 : 0, C, ldc, accumulate ? 1 : 0);
+    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, z, ka, kb, symmetric ? 1 : 0, C, ldc, accumulate ? 1 : 0, bcount);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
