@@ -258,14 +258,16 @@ def run_ours(args, rank, world, torch):
     trained = ctx.learn_get_weights()
 
     # ---- roofline of the dominant inner-CG kernel (device events over the timed region)
-    names = ["k_stencil4 (q = A p)", "k_update4 (x, r)", "k_u0dots (shared deflation dots)", "k_mu (lane scalars)",
-             "k_direction4 (p)"]
+    names = ["k_stencil4 (q = A p)", "k_update4 (r)", "k_u0dots (shared deflation dots)", "k_mu (lane scalars)",
+             "k_direction4 (x, p)"]
     s_bytes = 4
     # Algorithmic bytes (unique DRAM bytes a launch must move), per node per active lane:
     #   stencil    read p, write q; D and the sample diagonal once per sample: 2 + 2/nrhs
-    #   update     read x, p, r, q, write x, r, the lane's private A~W columns: 6 + k_priv
+    #   update     read r, q, write r, the lane's private A~W columns: 3 + k_priv
     #   u0dots     read r; the k_u shared A~_s U_0 columns once per tile of 32 lanes: 1 + k_u/32
     #   direction  read r, p, write p, private W columns, U_0 once per tile: 3 + k_priv + k_u/32
+    #              per continuing lane; read x, write x (the step x += alpha p) per updated lane,
+    #              and read p for an updated lane that stopped
     kdom = max((0, 1, 2, 4), key=lambda k: prof[k]["ms"])
     P = prof[kdom]
     A = P["lane_units"]
@@ -273,10 +275,13 @@ def run_ours(args, rank, world, torch):
         alg = A * n * (2 + 2 / wl.nrhs) * s_bytes
     elif kdom == 2:
         alg = A * n * (1 + wl.k_u / 32) * s_bytes
-    else:
-        base = 6 if kdom == 1 else 3
+    elif kdom == 1:
         kpriv = P["defl_cols"] - wl.k_u * A
-        alg = ((base + (0 if kdom == 1 else wl.k_u / 32)) * A + kpriv) * n * s_bytes
+        alg = (3 * A + kpriv) * n * s_bytes
+    else:
+        kpriv = P["defl_cols"] - wl.k_u * A
+        A_upd = prof[1]["lane_units"]
+        alg = ((3 + wl.k_u / 32) * A + kpriv + 2 * A_upd + max(A_upd - A, 0)) * n * s_bytes
     per_launch_bytes = alg / max(P["launches"], 1)
     per_launch_s = P["ms"] / 1e3 / max(P["launches"], 1)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

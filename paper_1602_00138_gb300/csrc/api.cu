@@ -254,7 +254,7 @@ struct Engine : EngineBase {
     void ensure_lanes(int m) {
         if (m <= mcap) return;
         for (void *p : std::vector<void *>{x64, xc, rv, pv, qv, ls.rr, ls.pq, ls.wv, ls.gw, ls.kdef, ls.active, ls.flag,
-                                           ls.iters, ls.thresh, d_mask, d_lnode, d_list, d_lw, d_rr,
+                                           ls.iters, ls.thresh, ls.xa, ls.xt, d_mask, d_lnode, d_list, d_lw, d_rr,
                                            p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb, d_si, d_kp,
                                            mu_f, beta_f, d_alist, d_tlane, d_tsi, d_tcnt})
             c->release(p);
@@ -274,6 +274,8 @@ struct Engine : EngineBase {
         ls.flag = c->alloc<int>(m);
         ls.iters = c->alloc<int>(m);
         ls.thresh = c->alloc<double>(m);
+        ls.xa = c->alloc<float>(m);
+        ls.xt = c->alloc<int>(m);
         d_si = c->alloc<int>(m);
         d_kp = c->alloc<int>(m);
         mu_f = c->alloc<float>((size_t)m * KMAX);
@@ -318,6 +320,7 @@ struct Engine : EngineBase {
         RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * m, st));
         RCG_CUDA_TRY(cudaMemsetAsync(ls.kdef, 0, sizeof(int) * m, st));
         RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * m, st));
+        RCG_CUDA_TRY(cudaMemsetAsync(ls.xt, 0xFF, sizeof(int) * m, st));
         RCG_CUDA_TRY(cudaMemsetAsync(d_mask, 0, sizeof(int) * m, st));
         // diagonal pointers of unused lanes point at a valid column (sample slot 0)
         {
@@ -871,6 +874,7 @@ struct Engine : EngineBase {
             RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * ls.m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * ls.m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * ls.m, st));
+            RCG_CUDA_TRY(cudaMemsetAsync(ls.xt, 0xFF, sizeof(int) * ls.m, st));    // no pending x step
             RCG_CUDA_TRY(cudaMemsetAsync(d_mask, 0, sizeof(int) * ls.m, st));
             c->h2d(ls.thresh, thr.data(), m);
             c->h2d(d_mask, act.data(), m);

@@ -6,13 +6,15 @@
 //   k_stencil4z  the same for 3D grids, two lanes per CTA, planes streamed
 //                through a shared-memory ring (each value read about once)
 //   k_update4    x += alpha p, r -= alpha q, fused r^T r and the private
-//                (A W)^T r dots, float4, one active lane per CTA row
+//                (A W)^T r dots, float4; whole waves of CTAs over the
+//                flattened (lane, node block) range
 //   k_u0dots     (A~_s U_0)^T r (or U_0^T r at a restart) for a tile of
 //                <= 32 lanes of one sample: a shared-memory tiled product,
 //                so each A~_s U_0 element is read once per tile
 //   k_mu         per lane (one warp): convergence / breakdown decision,
 //                beta, mu = (W^T A W)^-1 (A W)^T r, ring-slot zeroing
-//   k_direction4 p = r + beta p - U_0 mu_u - W_p mu_p for a tile of lanes;
+//   k_direction4 x += alpha p (the step left by k_update4), then
+//                p = r + beta p - U_0 mu_u - W_p mu_p for a tile of lanes;
 //                the thread keeps its U_0 values in registers across the
 //                tile's lanes
 //
@@ -21,11 +23,14 @@
 // to 32 active lanes of one sample slot.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace rcg {
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int TILE = 32;       // lanes per tile
+constexpr int UPD_WAVES = 1;   // waves of resident CTAs in a k_update4 launch
 
 __device__ __forceinline__ float dot4(const float4 a, const float4 b) {
     return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
@@ -271,52 +276,115 @@ k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict_
         }
 }
 
-// Lane l = alist[blockIdx.y]: x += alpha p; r -= alpha q; r^T r and the
-// private (A W)^T r dots (the shared ones come from k_u0dots).
-__global__ void __launch_bounds__(kThreads)
-k_update4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ alist, int sprev, int scur, int spq,
-          int sw) {
-    const int l = alist[blockIdx.y];
-    if (ls.active[l] == 0) return;
-    const double pq = ls.pq[spq * ls.m + l];
-    const double rrp = ls.rr[sprev * ls.m + l];
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rrp)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) ls.flag[l] = 2;
-        return;
-    }
-    const float alpha = (float)(rrp / pq);
-    const int ku = gm.k_u, kp = gm.kp[l];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ls.pq[(1 - spq) * ls.m + l] = 0.0;
-        if (ls.prof) { atomicAdd(ls.prof + 1, 1ULL); atomicAdd(ls.prof + 2, (unsigned long long)(ku + kp)); }
-    }
-    constexpr int NV = 1 + KP_MAX;
-    float acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
-    const long long o = (long long)l * gm.ld;
-    float4 *__restrict__ X = (float4 *)((float *)gm.x + o);
-    float4 *__restrict__ R = (float4 *)((float *)gm.r + o);
-    const float4 *__restrict__ P = (const float4 *)((const float *)gm.p + o);
-    const float4 *__restrict__ Q = (const float4 *)((const float *)gm.q + o);
-    const float *__restrict__ AP = (const float *)gm.awp + (long long)l * gm.kp_max * gm.ld;
-    const int nv = (int)(n >> 2);
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
-        const float4 pv = P[v], qv = Q[v], xv = X[v], rv0 = R[v];
-        const float4 rv = make_float4(rv0.x - alpha * qv.x, rv0.y - alpha * qv.y, rv0.z - alpha * qv.z,
-                                      rv0.w - alpha * qv.w);
-        X[v] = make_float4(xv.x + alpha * pv.x, xv.y + alpha * pv.y, xv.z + alpha * pv.z, xv.w + alpha * pv.w);
-        R[v] = rv;
-        acc[0] += dot4(rv, rv);
-#pragma unroll
-        for (int c = 0; c < KP_MAX; ++c)
-            if (c < kp) acc[1 + c] += dot4(((const float4 *)(AP + (long long)c * gm.ld))[v], rv);
-    }
+// r -= alpha q; r^T r and the private (A W)^T r dots (the shared ones come
+// from k_u0dots) for the active lanes alist[0 .. na-1].  The step
+// x += alpha p is left to k_direction4 of the same iteration, which reads p
+// anyway: alpha and the iteration number go to xa / xt.
+// The work is flattened: lane li has nb units of kThreads float4, and CTA c
+// takes the contiguous units [U c / G, U (c+1) / G) of the U = na nb units
+// (G = gridDim.x, one wave of resident CTAs), so every CTA moves the same
+// bytes whatever na is.  The dots of each lane segment a CTA crosses are
+// summed in the CTA and added atomically; the CTA that holds a lane's first
+// unit does the lane's one-off work.  KPM bounds the lanes' private columns;
+// a thread loads UNR float4 of every stream before it uses any (the loads in
+// flight per SM are what bounds this kernel).
+template <int KPM>
+__host__ __device__ constexpr int upd_unroll() { return KPM <= 2 ? 4 : KPM <= 4 ? 2 : 1; }
+
+template <int KPM>
+__global__ void __launch_bounds__(kThreads, 2)
+k_update4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ alist, int na, int t, int sprev,
+          int scur, int spq, int sw) {
+    constexpr int NV = 1 + KPM;
+    constexpr int UNR = upd_unroll<KPM>();
     __shared__ double out[NV];
-    block_sum<NV>(acc, out);
-    if (threadIdx.x == 0) atomicAdd(ls.rr + scur * ls.m + l, out[0]);
-    if (threadIdx.x >= 1 && threadIdx.x <= kp)
-        atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + ku + (threadIdx.x - 1), out[threadIdx.x]);
+    const long long nv = n >> 2;
+    const long long nb = (nv + kThreads - 1) / kThreads;
+    const long long U = (long long)na * nb;
+    const long long u_end = U * (blockIdx.x + 1) / gridDim.x;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long u = U * blockIdx.x / gridDim.x; u < u_end;) {
+        const int li = (int)(u / nb);
+        const long long lane0 = (long long)li * nb;
+        const long long seg_end = u_end < lane0 + nb ? u_end : lane0 + nb;
+        const bool owner = u == lane0;
+        const int l = alist[li];
+        const long long v0 = (u - lane0) * kThreads, v1 = (seg_end - lane0) * kThreads;
+        u = seg_end;
+        if (ls.active[l] == 0) continue;
+        const double pq = ls.pq[spq * ls.m + l];
+        const double rrp = ls.rr[sprev * ls.m + l];
+        if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rrp)) {
+            if (owner && threadIdx.x == 0) ls.flag[l] = 2;
+            continue;
+        }
+        const float alpha = (float)(rrp / pq);
+        const int ku = gm.k_u, kp = gm.kp[l];
+        if (owner && threadIdx.x == 0) {
+            ls.xa[l] = alpha;
+            ls.xt[l] = t;
+            ls.pq[(1 - spq) * ls.m + l] = 0.0;
+            if (ls.prof) { atomicAdd(ls.prof + 1, 1ULL); atomicAdd(ls.prof + 2, (unsigned long long)(ku + kp)); }
+        }
+        float acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+        const long long o = (long long)l * gm.ld;
+        float4 *__restrict__ R = (float4 *)((float *)gm.r + o);
+        const float4 *__restrict__ Q = (const float4 *)((const float *)gm.q + o);
+        const float *__restrict__ AP = (const float *)gm.awp + (long long)l * gm.kp_max * gm.ld;
+        const long long vend = v1 < nv ? v1 : nv;
+        for (long long v = v0 + threadIdx.x; v < vend; v += (long long)UNR * kThreads) {
+            float4 qv[UNR], rv[UNR], av[UNR][KPM];
+#pragma unroll
+            for (int e = 0; e < UNR; ++e) {
+                const long long w = v + (long long)e * kThreads;
+                const bool ok = w < vend;
+                qv[e] = ok ? Q[w] : z4;
+                rv[e] = ok ? R[w] : z4;
+#pragma unroll
+                for (int c = 0; c < KPM; ++c)
+                    av[e][c] = (ok && c < kp) ? ((const float4 *)(AP + (long long)c * gm.ld))[w] : z4;
+            }
+#pragma unroll
+            for (int e = 0; e < UNR; ++e) {
+                const long long w = v + (long long)e * kThreads;
+                const float4 r1 = make_float4(rv[e].x - alpha * qv[e].x, rv[e].y - alpha * qv[e].y,
+                                              rv[e].z - alpha * qv[e].z, rv[e].w - alpha * qv[e].w);
+                if (w < vend) R[w] = r1;
+                acc[0] += dot4(r1, r1);
+#pragma unroll
+                for (int c = 0; c < KPM; ++c) acc[1 + c] += dot4(av[e][c], r1);
+            }
+        }
+        block_sum<NV>(acc, out);
+        if (threadIdx.x == 0) atomicAdd(ls.rr + scur * ls.m + l, out[0]);
+        if (threadIdx.x >= 1 && threadIdx.x <= kp)
+            atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + ku + (threadIdx.x - 1), out[threadIdx.x]);
+    }
+}
+
+// One wave of resident k_update4<KPM> CTAs for lanes with at most KPM
+// private columns (occupancy cached per device ordinal).
+template <int KPM>
+void launch_update4(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const LaneList &ll,
+                    int t, int sprev, int scur, int spq, int sw) {
+    static int slots[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    int g = 2 * 152;
+    if (dev >= 0 && dev < 64) {
+        if (!slots[dev]) {
+            int occ = 0, sms = 0;
+            RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update4<KPM>, kThreads, 0));
+            RCG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            slots[dev] = std::max(1, occ * sms);
+        }
+        g = slots[dev];
+    }
+    const long long units = (long long)ll.na * (((n >> 2) + kThreads - 1) / kThreads);
+    const int grid = (int)std::min<long long>(units, (long long)UPD_WAVES * g);
+    k_update4<KPM><<<grid, kThreads, 0, st>>>(n, gm, ls, ll.alist, ll.na, t, sprev, scur, spq, sw);
 }
 
 // wv[sw][l][c] += (A~_s U_0)_c^T r_l (use_w: U_0 itself) for the lanes of
@@ -467,31 +535,37 @@ k_mu(LaneState ls, const int *__restrict__ alist, int sprev, int scur, int snext
     for (int c = threadIdx.x; c < KMAX; c += 32) ls.wv[((long long)(1 - sw) * ls.m + l) * KMAX + c] = 0.0;
 }
 
-// p = r + beta p - U_0 mu_u - W_p mu_p for the active lanes of tile
-// blockIdx.y over this CTA's node range; U_0 is staged per stage of SN nodes
+// Iteration it over the lanes of tile blockIdx.y and this CTA's node range:
+// x += alpha p (the step k_update4 left, for every lane whose xt is it, also
+// one that stopped in this iteration), then, for the active lanes,
+// p = r + beta p - U_0 mu_u - W_p mu_p.  U_0 is staged per stage of SN nodes
 // in shared memory and shared by the tile's lanes (warp w: lanes w + 8q).
 template <int KUT>
 __global__ void __launch_bounds__(kThreads)
 k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane,
              const int *__restrict__ tile_cnt, const float *__restrict__ mu, const float *__restrict__ beta,
-             long long chunk) {
+             long long chunk, int it) {
     __shared__ float4 Us[KUT][SN / 4];
     __shared__ float smu[TILE][KU_MAX + KP_MAX];
-    __shared__ float sbeta[TILE];
-    __shared__ int slane[TILE], skp[TILE];
+    __shared__ float sbeta[TILE], salpha[TILE];
+    __shared__ int slane[TILE], skp[TILE], sdir[TILE];
     const int t = blockIdx.y, cnt = tile_cnt[t], ku = gm.k_u;
     if (threadIdx.x < TILE) {
         int l = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
-        if (l >= 0 && ls.active[l] == 0) l = -1;
+        const bool step = l >= 0 && ls.xt[l] == it;
+        const bool dir = l >= 0 && ls.active[l] != 0;
+        if (!step && !dir) l = -1;
         slane[threadIdx.x] = l;
-        skp[threadIdx.x] = l >= 0 ? gm.kp[l] : 0;
-        sbeta[threadIdx.x] = l >= 0 ? beta[l] : 0.f;
+        sdir[threadIdx.x] = dir ? 1 : 0;
+        salpha[threadIdx.x] = step ? ls.xa[l] : 0.f;
+        skp[threadIdx.x] = dir ? gm.kp[l] : 0;
+        sbeta[threadIdx.x] = dir ? beta[l] : 0.f;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < TILE * (KU_MAX + KP_MAX); e += blockDim.x) {
         const int jj = e / (KU_MAX + KP_MAX), c = e % (KU_MAX + KP_MAX);
         const int l = slane[jj];
-        smu[jj][c] = (l >= 0 && c < ku + skp[jj]) ? mu[(long long)l * KMAX + c] : 0.f;
+        smu[jj][c] = (l >= 0 && sdir[jj] && c < ku + skp[jj]) ? mu[(long long)l * KMAX + c] : 0.f;
     }
     const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
     const float *__restrict__ WU = (const float *)gm.wu;
@@ -513,8 +587,15 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
                 const int l = slane[jj];
                 if (l < 0) continue;
                 const long long o = (long long)l * gm.ld + p;
-                const float4 rv = *(const float4 *)((const float *)gm.r + o);
                 const float4 pv = *(const float4 *)((const float *)gm.p + o);
+                const float a = salpha[jj];
+                if (a != 0.f) {
+                    float4 *xp = (float4 *)((float *)gm.x + o);
+                    const float4 xv = *xp;
+                    *xp = make_float4(xv.x + a * pv.x, xv.y + a * pv.y, xv.z + a * pv.z, xv.w + a * pv.w);
+                }
+                if (!sdir[jj]) continue;
+                const float4 rv = *(const float4 *)((const float *)gm.r + o);
                 const float b = sbeta[jj];
                 float4 sres = make_float4(rv.x + b * pv.x, rv.y + b * pv.y, rv.z + b * pv.z, rv.w + b * pv.w);
 #pragma unroll
@@ -707,7 +788,10 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     count_launch();
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(0, e, st); e = kt->start(st); }
-    k_update4<<<dim3(gx_for(nv, ll.na, 8), ll.na), kThreads, 0, st>>>(g.n, gm, ls, ll.alist, sprev, scur, spq, sw);
+    if (gm.kp_max <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else if (gm.kp_max <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else if (gm.kp_max <= 4) launch_update4<4>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else launch_update4<KP_MAX>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
     count_launch();
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(1, e, st); e = kt->start(st); }
@@ -743,7 +827,7 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         long long z;
         const long long chunk = tile_chunk(z);
         dim3 grid((unsigned)z, ll.ntiles);
-#define RCG_DIR(K) k_direction4<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk)
+#define RCG_DIR(K) k_direction4<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, t)
         switch (kut) { case 0: case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break;
                        default: RCG_DIR(16); }
 #undef RCG_DIR
@@ -801,7 +885,9 @@ void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, Lane
     RCG_CHECK_LAUNCH();
     long long zc;
     (void)zc;
-#define RCG_DIR(K) k_direction4<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk)
+    // no x step is pending at a restart (x = W mu0 was just set): iteration
+    // number -2 matches no stamp
+#define RCG_DIR(K) k_direction4<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, -2)
     switch (kut) { case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break; default: RCG_DIR(16); }
 #undef RCG_DIR
     count_launch();

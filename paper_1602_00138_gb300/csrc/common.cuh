@@ -70,6 +70,8 @@ struct LaneState {
     int *iters;             // [m]
     double *thresh;         // [m] stop threshold on ||r|| of the current cycle
     unsigned long long *prof;  // optional work counters (see KTimer), or null
+    float *xa;              // [m] alpha of the step x += alpha p still to apply (float32 iteration)
+    int *xt;                // [m] iteration that set xa (-1: none); applied by that iteration's direction kernel
 };
 
 // Arithmetic addressing of the lanes of a wave (all columns ld apart):
