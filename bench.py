@@ -60,6 +60,10 @@ def parse_args():
     ap.add_argument("--products", action="store_true",
                     help="time the basis product A^T B on the tensor cores and on CUDA cores (one JSON line per shape)")
     ap.add_argument("--products-shapes", type=int, default=4, help="number of --products shapes to run")
+    ap.add_argument("--rom-sweep", type=int, default=16,
+                    help="held-out parameter points for the reduced-model sweep (Psi_r and J through the "
+                         "last step's basis; 0 skips it)")
+    ap.add_argument("--rom-batch", type=int, default=8, help="points per rcg_rom_eval_batch call in the sweep")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
@@ -314,6 +318,54 @@ def run_ours(args, rank, world, torch):
                     clocks=clk, base=None, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
                     seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=None)
 
+    # ---- reduced-model sweep: Psi_r and its Jacobian at held-out points through
+    # the basis of the last timed step, batched, against one point per call
+    sweep = None
+    if args.rom_sweep > 0 and rank == 0:
+        Q, Bq = args.rom_sweep, max(1, min(args.rom_batch, args.rom_sweep))
+        ps = heldout_params(wl, Q, seed_offset=3000)
+        mus_sw = torch.tensor(np.stack([pals_mu(p, inp["X"], wl.mu_bg) for p in ps]), dtype=torch.float64,
+                              device=dev)
+        dmus_sw = torch.empty((Q, wl.nparam, n), dtype=torch.float64, device=dev)
+        for q, p in enumerate(ps):
+            dmus_sw[q].copy_(torch.from_numpy(np.ascontiguousarray(pals_dmu(p, inp["X"], wl.mu_bg))))
+        nd_ns = wl.ndet * wl.nsrc
+        psi_sw = torch.empty((Q, nd_ns), dtype=torch.float64, device=dev)
+        J_sw = torch.empty((Q, wl.nparam * nd_ns), dtype=torch.float64, device=dev)
+        psi_1 = torch.empty((Q, nd_ns), dtype=torch.float64, device=dev)
+        J_1 = torch.empty((Q, wl.nparam * nd_ns), dtype=torch.float64, device=dev)
+
+        def sweep_batched():
+            for b in range(0, Q, Bq):
+                m = min(Bq, Q - b)
+                ctx.rom_eval_batch_device(m, mus_sw[b], dmus_sw[b], psi_sw[b], J_sw[b], wl.nparam)
+
+        def sweep_single():
+            for q in range(Q):
+                ctx.rom_eval_device(mus_sw[q], dmus_sw[q], psi_1[q], J_1[q], wl.nparam)
+
+        st_ = torch.cuda.current_stream()
+        times = {}
+        for name, fn in (("batched", sweep_batched), ("single", sweep_single)):
+            fn()                                  # warm-up (buffers, attributes)
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st_)
+            for _ in range(3):
+                fn()
+            b_.record(st_)
+            torch.cuda.synchronize()
+            times[name] = a.elapsed_time(b_) / 3
+        dpsi = float(((psi_sw - psi_1).norm() / psi_1.norm()).item())
+        dJ = float(((J_sw - J_1).norm() / J_1.norm()).item())
+        sweep = {"points": Q, "batch": Bq, "nparam": wl.nparam, "rank_V": rank_V,
+                 "evals_per_s": round(Q / (times["batched"] / 1e3), 1),
+                 "ms_per_point": round(times["batched"] / Q, 4),
+                 "single_call_ms_per_point": round(times["single"] / Q, 4),
+                 "rel_diff_vs_single": {"psi": dpsi, "J": dJ},
+                 "what": "Psi_r (ndet x nsrc) and J (nparam x ndet x nsrc) per point, inputs resident"}
+        del mus_sw, dmus_sw, psi_sw, J_sw, psi_1, J_1
+
     # ---- end to end through the public API with host buffers
     ctx_e = make_ctx(rcg, inp, CONTENDER, torch)
     pinned = torch.empty((K + 1, n), dtype=torch.float64).pin_memory()
@@ -372,7 +424,8 @@ def run_ours(args, rank, world, torch):
     ctx.close()
     return dict(value=value, ms=ms_max / args.steps, launches=launches, roofline=roofline, e2e=e2e,
                 clocks=clk, base=base, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
-                seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=nolearn)
+                seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=nolearn,
+                rom_sweep=sweep)
 
 
 # ------------------------------------------------------------- CPU oracle leg
@@ -526,6 +579,7 @@ def main():
             "gpu_launches": res["launches"],
             "baseline_fp64_sequential": res["base"],
             "mixed_without_learning": res["nolearn"],
+            "rom_sweep": res.get("rom_sweep"),
         }
         print(json.dumps(line))
     if world > 1:

@@ -265,8 +265,22 @@ int rcg_load(rcg_ctx *c, const char *path);
 int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const double *dmu_dev,
                         double *Psi_dev, double *J_dev);
 
+/* The reduced model at nq parameter points in one call (Sec. 4.2.2: the
+ * optimisation evaluates Psi_r and its Jacobian at many p through the same
+ * V).  Device float64 arrays: mu_dev nq x n (point q at mu_dev + q n),
+ * dmu_dev nq x nparam x n (d mu / d p_k of point q at dmu_dev + (q nparam + k) n)
+ * or NULL, Psi_dev nq x ndet x nsrc (point q as in rcg_rom_eval at
+ * Psi_dev + q ndet nsrc), J_dev nq x nparam x ndet x nsrc or NULL (needs
+ * dmu_dev).  Each point's values equal rcg_rom_eval's at that point up to
+ * rounding.  The caller owns every array; the call returns after the results
+ * are written.  RCG_ERR_INVALID for nq < 0, missing arrays or an empty basis,
+ * RCG_ERR_NOT_SPD if a reduced matrix is not positive definite. */
+int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, const double *dmu_dev,
+                       double *Psi_dev, double *J_dev);
+
 /* Elapsed device milliseconds of the named phase in the last call that ran
- * it ("check", "cg", "append", "seed_eig", "seed_x0", "rom"); -1 if none. */
+ * it ("check", "cg", "append", "seed_eig", "seed_x0", "rom", "rom_batch");
+ * -1 if none. */
 double rcg_phase_ms(const rcg_ctx *c, const char *phase);
 
 /* Number of kernel launches issued by this context since creation. */

@@ -11,6 +11,7 @@
 #include "../../include/rcg.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,7 @@ struct EngineBase {
     virtual int rank() const = 0;
     virtual void basis_get(double *V) = 0;
     virtual void rom_eval(const double *mu, int nparam, const double *dmu, double *Psi, double *J) = 0;
+    virtual void rom_eval_batch(int nq, const double *mu, int nparam, const double *dmu, double *Psi, double *J) = 0;
     virtual void sample_changed(int s) = 0;
     virtual void save(std::FILE *f) = 0;
     virtual void load(std::FILE *f) = 0;
@@ -168,8 +170,13 @@ struct Engine : EngineBase {
     int *dwc = nullptr;                // their counts (device, one per sample slot)
     int *rom_bl = nullptr, *rom_bc = nullptr;
     // reduced Jacobian: per-parameter weights, block lists, G_k and G_k X_r
-    double *jk_w = nullptr, *jk_G = nullptr, *jk_T = nullptr;
+    double *jk_w = nullptr, *jk_G = nullptr;
+    long long jk_gcap = 0;
     int *jk_bl = nullptr, *jk_bc = nullptr;
+    // rom_eval_batch: per-point reduced matrices, weights, block lists, solves, Jacobian Grams
+    double *rb_A = nullptr, *rb_w = nullptr, *rb_X = nullptr, *rb_Z = nullptr, *rb_G = nullptr;
+    int *rb_bl = nullptr, *rb_bc = nullptr, *rb_jbl = nullptr, *rb_jbc = nullptr;
+    long long rb_cap[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int jk_cap = 0;
     // lanes workspace
     int mcap = 0;
@@ -1361,9 +1368,9 @@ struct Engine : EngineBase {
         trsv_lower_batched(st, Ar, r, r, Zr, r, nd, true);
         // Psi_r = C~_r^T X_r  (ndet x nsrc)
         gemm_tn<double, double>(st, r, Crm, r, nd, Xr, r, ns, Psi, nd, false);
-        if (J && dmu && mixed && r >= 16) {
+        if (J && dmu && mixed && r >= 16 && tc_gemm_tn_ok(ld, ld, V, V)) {
             // J_k = Z_r^T G_k X_r with G_k = V^T diag(-h^2 dmu_k) V: the weighted Grams on the
-            // tensor cores over the support of dmu_k, then two small float64 products
+            // tensor cores over the support of dmu_k (one launch for all k), then all J_k in one float64 launch
             const long long nbl = (n + 31) / 32;
             if (nparam > jk_cap) {
                 for (void *p : std::vector<void *>{(void *)jk_w, (void *)jk_bl, (void *)jk_bc}) c->release(p);
@@ -1372,16 +1379,25 @@ struct Engine : EngineBase {
                 jk_bl = c->alloc<int>((size_t)nparam * nbl);
                 jk_bc = c->alloc<int>(nparam);
             }
-            if (!jk_G) { jk_G = c->alloc<double>((size_t)rmax * rmax); jk_T = c->alloc<double>((size_t)rmax * ns); }
+            const long long gsz = (long long)nparam * r * r;
+            if (gsz > jk_gcap) {
+                c->release(jk_G);
+                jk_gcap = std::max(gsz, 2 * jk_gcap);
+                jk_G = c->alloc<double>((size_t)jk_gcap);
+            }
             for (int k = 0; k < nparam; ++k)
                 scaled_diff(st, n, dmu + (long long)k * n, nullptr, -c->h * c->h, jk_w + (long long)k * ld);
             tc_block_list(st, n, jk_w, jk_bl, jk_bc, nparam, ld, nbl);
-            for (int k = 0; k < nparam; ++k) {
-                RCG_CUDA_TRY(cudaMemsetAsync(jk_G, 0, sizeof(double) * (size_t)r * r, st));
-                gram_w_acc(V, r, jk_G, r, jk_w + (long long)k * ld, jk_bl + (long long)k * nbl, jk_bc + k);
-                gemm_tn<double, double>(st, r, jk_G, r, r, Xr, r, ns, jk_T, r, false);     // G_k X_r (G_k symmetric)
-                gemm_tn<double, double>(st, r, Zr, r, nd, jk_T, r, ns, J + (long long)k * nd * ns, nd, false);
+            // all G_k in one tensor-core launch, then all J_k in one float64 launch
+            const long long need = tc_gram_w_batched_scratch(r, nparam, nullptr);
+            if (need > tc_cap) {
+                c->release(tc_scr);
+                tc_cap = std::max(need, 2 * tc_cap);
+                tc_scr = c->alloc<float>((size_t)tc_cap);
             }
+            tc_gram_w_batched(st, n, (const float *)V, ld, r, jk_G, r, (long long)r * r, nparam, jk_w, ld, jk_bl, nbl,
+                              jk_bc, tc_scr, d_info + 1);
+            rom_jac(st, r, nparam, jk_G, Xr, ns, Zr, nd, J);
         } else if (J && dmu) {
             if (!VX) { VX = c->alloc<double>((size_t)ns * ld); VZ = c->alloc<double>((size_t)nd * ld); }
             lift(V, r, Xr, r, ns, VX, ld, 0.0);
@@ -1396,6 +1412,101 @@ struct Engine : EngineBase {
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
         c->phase["rom"] = ms;
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+    }
+
+    // Psi_r and J at nq points in one pass (device pointers: mu nq x n,
+    // dmu nq x nparam x n or null, Psi nq x nd x ns, J nq x nparam x nd x ns):
+    // the reduced matrices of all points from one tensor-core launch over the
+    // supports of mu_q - mu_*, one batched Cholesky, batched solves, and, with
+    // dmu, all points' Jacobian Grams in one more launch.  Where the batched
+    // tensor-core path does not apply (float64 basis, r < 16, weights that
+    // are not 16-byte aligned) the points run one by one through rom_eval.
+    void rom_eval_batch(int nq, const double *mu, int nparam, const double *dmu, double *Psi, double *J) override {
+        if (r == 0) throw Error{RCG_ERR_INVALID, "rcg_rom_eval_batch with an empty basis"};
+        if (nq <= 0) return;
+        const int ns = c->nsrc, nd = c->ndet;
+        const bool jac = J && dmu && nparam > 0;
+        const bool batched = mixed && r >= 16 && tc_gemm_tn_ok(ld, ld, V, V) &&
+                             (!jac || ((((uintptr_t)dmu) & 15) == 0 && (n & 1) == 0));
+        if (!batched) {
+            for (int q = 0; q < nq; ++q)
+                rom_eval(mu + (long long)q * n, jac ? nparam : 0, jac ? dmu + (long long)q * nparam * n : nullptr,
+                         Psi + (long long)q * nd * ns, jac ? J + (long long)q * nparam * nd * ns : nullptr);
+            return;
+        }
+        cudaEvent_t e0, e1;
+        RCG_CUDA_TRY(cudaEventCreate(&e0)); RCG_CUDA_TRY(cudaEventCreate(&e1));
+        RCG_CUDA_TRY(cudaEventRecord(e0, st));
+        if (!Ar) {
+            Ar = c->alloc<double>((size_t)rmax * rmax);
+            Br = c->alloc<double>((size_t)rmax * ns);
+            Crm = c->alloc<double>((size_t)rmax * nd);
+            Xr = c->alloc<double>((size_t)rmax * ns);
+            Zr = c->alloc<double>((size_t)rmax * nd);
+            wtmp = c->alloc<double>(ld);
+        }
+        const long long nbl = (n + 31) / 32, rr2 = (long long)r * r;
+        auto grow = [&](int slot, auto *&p, long long need) {
+            if (need <= rb_cap[slot]) return;
+            c->release(p);
+            rb_cap[slot] = std::max(need, 2 * rb_cap[slot]);
+            p = c->alloc<std::remove_reference_t<decltype(*p)>>((size_t)rb_cap[slot]);
+        };
+        grow(0, rb_A, nq * rr2);
+        grow(1, rb_w, (long long)nq * ld);
+        grow(2, rb_bl, nq * nbl);
+        grow(3, rb_bc, (long long)nq);
+        grow(4, rb_X, (long long)nq * r * ns);
+        grow(5, rb_Z, (long long)nq * r * nd);
+        // A~_r(q) = C_* + V^T diag(h^2 (mu_q - mu_*)) V for all q
+        for (int q = 0; q < nq; ++q) {
+            scaled_diff(st, n, mu + (long long)q * n, c->mu64 + (long long)s_star * ld, c->h * c->h, rb_w + (long long)q * ld);
+            RCG_CUDA_TRY(cudaMemcpy2DAsync(rb_A + q * rr2, sizeof(double) * r, Cstar, sizeof(double) * rmax,
+                                           sizeof(double) * r, r, cudaMemcpyDeviceToDevice, st));
+        }
+        tc_block_list(st, n, rb_w, rb_bl, rb_bc, nq, ld, nbl);
+        const long long need = tc_gram_w_batched_scratch(r, std::max(nq, jac ? nq * nparam : 0), nullptr);
+        if (need > tc_cap) {
+            c->release(tc_scr);
+            tc_cap = std::max(need, 2 * tc_cap);
+            tc_scr = c->alloc<float>((size_t)tc_cap);
+        }
+        tc_gram_w_batched(st, n, (const float *)V, ld, r, rb_A, r, rr2, nq, rb_w, ld, rb_bl, nbl, rb_bc, tc_scr,
+                          d_info + 1, true, 1.0);
+        RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+        chol_batched(st, rb_A, r, rr2, r, nq, d_info);
+        check_info("reduced matrices V^T A(p_q) V");
+        // B~_r, C~_r (the same for every point), then X_q = A~_r(q)^-1 B~_r, Z_q likewise
+        gather_rows<T>(st, V, ld, r, c->d_rhs_node, c->d_rhs_w, ns, Br, r);
+        gather_rows<T>(st, V, ld, r, c->d_rhs_node + ns, c->d_rhs_w + ns, nd, Crm, r);
+        for (int q = 0; q < nq; ++q) {
+            RCG_CUDA_TRY(cudaMemcpyAsync(rb_X + (long long)q * r * ns, Br, sizeof(double) * r * ns,
+                                         cudaMemcpyDeviceToDevice, st));
+            RCG_CUDA_TRY(cudaMemcpyAsync(rb_Z + (long long)q * r * nd, Crm, sizeof(double) * r * nd,
+                                         cudaMemcpyDeviceToDevice, st));
+        }
+        trsv_multi(st, rb_A, r, rr2, r, rb_X, r, (long long)r * ns, ns, nq, false);
+        trsv_multi(st, rb_A, r, rr2, r, rb_X, r, (long long)r * ns, ns, nq, true);
+        trsv_multi(st, rb_A, r, rr2, r, rb_Z, r, (long long)r * nd, nd, nq, false);
+        trsv_multi(st, rb_A, r, rr2, r, rb_Z, r, (long long)r * nd, nd, nq, true);
+        rom_psi(st, r, nq, Crm, rb_X, ns, nd, Psi);
+        if (jac) {
+            // G_qk = V^T diag(-h^2 dmu_qk) V straight from dmu (scale in the split), then J_qk = Z_q^T G_qk X_q
+            const long long nv = (long long)nq * nparam;
+            grow(6, rb_G, nv * rr2);
+            grow(7, rb_jbl, nv * nbl);
+            grow(8, rb_jbc, nv);
+            tc_block_list(st, n, dmu, rb_jbl, rb_jbc, (int)nv, n, nbl);
+            tc_gram_w_batched(st, n, (const float *)V, ld, r, rb_G, r, rr2, (int)nv, dmu, n, rb_jbl, nbl, rb_jbc,
+                              tc_scr, d_info + 1, false, -c->h * c->h);
+            rom_jac(st, r, nparam, rb_G, rb_X, ns, rb_Z, nd, J, nq);
+        }
+        RCG_CUDA_TRY(cudaEventRecord(e1, st));
+        c->sync();
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->phase["rom_batch"] = ms;
         cudaEventDestroy(e0); cudaEventDestroy(e1);
     }
 };
@@ -1839,6 +1950,16 @@ int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const doub
     return guarded(c, [&]() {
         if (!mu_dev || !Psi_dev || nparam < 0) return fail(c, RCG_ERR_INVALID, "bad rom arguments");
         c->eng->rom_eval(mu_dev, nparam, dmu_dev, Psi_dev, J_dev);
+        return RCG_OK;
+    });
+}
+
+int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, const double *dmu_dev,
+                       double *Psi_dev, double *J_dev) {
+    return guarded(c, [&]() {
+        if (nq < 0 || nparam < 0 || (nq > 0 && (!mu_dev || !Psi_dev)) || (J_dev && !dmu_dev))
+            return fail(c, RCG_ERR_INVALID, "bad rom batch arguments");
+        c->eng->rom_eval_batch(nq, mu_dev, nparam, dmu_dev, Psi_dev, J_dev);
         return RCG_OK;
     });
 }

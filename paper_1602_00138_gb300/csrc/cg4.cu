@@ -15,8 +15,8 @@
 //                beta, mu = (W^T A W)^-1 (A W)^T r, ring-slot zeroing
 //   k_direction4 x += alpha p (the step left by k_update4), then
 //                p = r + beta p - U_0 mu_u - W_p mu_p for a tile of lanes;
-//                the thread keeps its U_0 values in registers across the
-//                tile's lanes
+//                the U_0 rows of a stage arrive in a shared-memory ring by
+//                cp.async two stages ahead and serve all the tile's lanes
 //
 // Lanes are addressed through the active list `alist` (rebuilt by the host
 // at every synchronisation) so converged lanes cost no work; tiles group up
@@ -399,6 +399,7 @@ constexpr int SN = 128;                 // nodes per stage
 constexpr int SN4 = SN / 4;
 constexpr int RP = SN4 + 1;             // padded float4 stride of an r row (conflict-free reads)
 constexpr int U0_NST = 3;
+constexpr int DIR_NST = 3;              // U_0 stage ring of k_direction4
 template <int KUT>
 __host__ __device__ constexpr int u0_stage4() { return TILE * RP + KUT * SN4; }
 template <int KUT>
@@ -539,13 +540,14 @@ k_mu(LaneState ls, const int *__restrict__ alist, int sprev, int scur, int snext
 // x += alpha p (the step k_update4 left, for every lane whose xt is it, also
 // one that stopped in this iteration), then, for the active lanes,
 // p = r + beta p - U_0 mu_u - W_p mu_p.  U_0 is staged per stage of SN nodes
-// in shared memory and shared by the tile's lanes (warp w: lanes w + 8q).
+// in a shared-memory ring and shared by the tile's lanes (warp w: lanes
+// w + 8q); one barrier per stage.
 template <int KUT>
 __global__ void __launch_bounds__(kThreads)
 k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane,
              const int *__restrict__ tile_cnt, const float *__restrict__ mu, const float *__restrict__ beta,
              long long chunk, int it) {
-    __shared__ float4 Us[KUT][SN / 4];
+    __shared__ float4 Us[DIR_NST][KUT][SN / 4];
     __shared__ float smu[TILE][KU_MAX + KP_MAX];
     __shared__ float sbeta[TILE], salpha[TILE];
     __shared__ int slane[TILE], skp[TILE], sdir[TILE];
@@ -571,14 +573,35 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
     const float *__restrict__ WU = (const float *)gm.wu;
     const long long r0 = (long long)blockIdx.x * chunk;
     const long long r1 = r0 + chunk < n ? r0 + chunk : n;
-    __syncthreads();
-    for (long long base = r0; base < r1; base += SN) {
-        for (int e = threadIdx.x; e < KUT * (SN / 4); e += blockDim.x) {
-            const int c = e / (SN / 4), v4 = e % (SN / 4);
-            const long long p = base + 4 * v4;
-            Us[c][v4] = (c < ku && p < r1) ? *(const float4 *)(WU + (long long)c * gm.ld + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
+    // U_0 rows of stage st into ring slot st % DIR_NST (cp.async, one group per
+    // stage; rows past r1 and columns past k_u are zeros written directly)
+    auto stage_u = [&](int st) {
+        if (st < nst) {
+            const long long base = r0 + (long long)st * SN;
+            for (int e = threadIdx.x; e < KUT * (SN / 4); e += blockDim.x) {
+                const int c = e / (SN / 4), v4 = e % (SN / 4);
+                const long long p = base + 4 * v4;
+                float4 *dst = &Us[st % DIR_NST][c][v4];
+                if (c < ku && p < r1)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                     (uint32_t)__cvta_generic_to_shared(dst)),
+                                 "l"(WU + (long long)c * gm.ld + p)
+                                 : "memory");
+                else
+                    *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        __syncthreads();
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    stage_u(0);
+    stage_u(1);
+    for (int st = 0; st < nst; ++st) {
+        const long long base = r0 + (long long)st * SN;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");      // stage st: this thread's copies
+        __syncthreads();                                           // everyone's; stage st-1 is done
+        stage_u(st + 2);                                           // into the slot stage st-1 used
+        const float4(&Uc)[KUT][SN / 4] = Us[st % DIR_NST];
         const long long p = base + 4 * tl;
         if (p < r1) {
 #pragma unroll
@@ -601,7 +624,7 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
 #pragma unroll
                 for (int c = 0; c < KUT; ++c) {
                     const float m = c < ku ? smu[jj][c] : 0.f;
-                    const float4 u = Us[c][tl];
+                    const float4 u = Uc[c][tl];
                     sres.x -= m * u.x; sres.y -= m * u.y; sres.z -= m * u.z; sres.w -= m * u.w;
                 }
                 const int kp = skp[jj];
@@ -614,8 +637,24 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
                 *(float4 *)((float *)gm.p + o) = sres;
             }
         }
-        __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Resident k_direction4<KUT> CTAs on the whole GPU (cached per device ordinal).
+template <int KUT>
+int dir_slots() {
+    static int slots[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return 5 * 152;
+    if (!slots[dev]) {
+        int occ = 0, sms = 0;
+        RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direction4<KUT>, kThreads, 0));
+        RCG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        slots[dev] = std::max(1, occ * sms);
+    }
+    return slots[dev];
 }
 
 // Lane l = alist[blockIdx.y]: wv[sw][k_u + c] += (src_c)^T r over the lane's
@@ -795,9 +834,9 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     count_launch();
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(1, e, st); e = kt->start(st); }
-    // node range per CTA for the tile kernels: a multiple of SN, ~6 CTAs per SM in total
-    auto tile_chunk = [&](long long &z) {
-        z = (6LL * 152 + ll.ntiles - 1) / ll.ntiles;
+    // node range per CTA for the tile kernels: a multiple of SN, `slots` CTAs in total
+    auto tile_chunk = [&](long long &z, long long slots = 6LL * 152) {
+        z = std::max<long long>(1, slots / ll.ntiles);
         const long long maxz = (g.n + 4 * SN - 1) / (4 * SN);
         if (z > maxz) z = maxz;
         if (z < 1) z = 1;
@@ -824,8 +863,11 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(3, e, st); e = kt->start(st); }
     {
+        // one wave of resident CTAs (a partial second wave would hold the whole launch)
+        const int slots = kut <= 4 ? dir_slots<4>() : kut == 8 ? dir_slots<8>() : kut == 12 ? dir_slots<12>()
+                                                                                            : dir_slots<16>();
         long long z;
-        const long long chunk = tile_chunk(z);
+        const long long chunk = tile_chunk(z, slots);
         dim3 grid((unsigned)z, ll.ntiles);
 #define RCG_DIR(K) k_direction4<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, t)
         switch (kut) { case 0: case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break;

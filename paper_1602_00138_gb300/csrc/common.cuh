@@ -233,6 +233,12 @@ void gemm_tn(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
              const double *wt = nullptr, const int *rows = nullptr, long long nrows = 0);
 void gemm_tn_df(cudaStream_t st, long long n, const float *A, long long lda, int ka, const double *B, long long ldb,
                 int kb, double *C, int ldc, bool accumulate);
+// J_qk = Z_q^T G_qk X_q for k < nparam, q < nq (G: [q][k] r x r symmetric,
+// X_q = X + q r ns, Z_q = Z + q r nd, ld r; J_qk = J + (q nparam + k) nd ns)
+void rom_jac(cudaStream_t st, int r, int nparam, const double *G, const double *X, int ns, const double *Z, int nd,
+             double *J, int nq = 1);
+// Psi_q = Crm^T X_q (nd x ns) for q < nq (Crm r x nd, X_q = X + q r ns, ld r)
+void rom_psi(cudaStream_t st, int r, int nq, const double *Crm, const double *X, int ns, int nd, double *Psi);
 template <typename TA, typename TB, typename AT>
 void gemm_tn_acc(cudaStream_t st, long long n, const TA *A, long long lda, int ka,
                  const TB *B, long long ldb, int kb, double *C, int ldc, bool accumulate,
@@ -243,11 +249,16 @@ bool tc_gemm_tn_ok(long long lda, long long ldb, const void *A, const void *B);
 void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int ka, const float *B, long long ldb,
                 int kb, double *C, int ldc, bool accumulate, bool symmetric, float *scratch, int *err,
                 const double *wt = nullptr, const int *blist = nullptr, const int *bcount = nullptr);
-// Blocks of 32 rows where w does not vanish, for nvec weight vectors (w + v ldw
-// -> list + v ldl, count[v]).
+// C_b = A^T diag(w_b) A for nbatch weight vectors in one launch (see tc.cu).
+long long tc_gram_w_batched_scratch(int ka, int nbatch, int *zper_out);
+void tc_gram_w_batched(cudaStream_t st, long long n, const float *A, long long lda, int ka, double *C, int ldc,
+                       long long ldcb, int nbatch, const double *wt, long long ldw, const int *blist, long long ldl,
+                       const int *bcount, float *scratch, int *err, bool accumulate = false, double wscale = 1.0);
 long long tc_gemm_nn_scratch(int k, int m);
 void tc_gemm_nn(cudaStream_t st, long long n, const float *V, long long ldv, int k, const double *C, int ldc, int m,
                 float *Out, long long ldo, double alpha, double beta, float *scratch, int *err);
+// Blocks of 32 rows where w does not vanish, for nvec weight vectors (w + v ldw
+// -> list + v ldl, count[v]).
 void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count, int nvec = 1,
                    long long ldw = 0, long long ldl = 0);
 template <typename TA, typename TO>
@@ -272,6 +283,11 @@ void chol_inplace(cudaStream_t st, double *A, int lda, int r, int *info);
 void chol_border(cudaStream_t st, double *L, int ldl, int r_old, int a, int *info);
 void trsv_lower_batched(cudaStream_t st, const double *L, int ldl, int r, double *B, int ldb,
                         int m, bool transpose);
+// nbatch independent systems: factor b at A + b strideA (failure: *info = max first bad pivot + 1)
+void chol_batched(cudaStream_t st, double *A, int lda, long long strideA, int r, int nbatch, int *info);
+// nbatch factors L + b strideL, each with m right-hand sides B + b strideB
+void trsv_multi(cudaStream_t st, const double *L, int ldl, long long strideL, int r, double *B, int ldb,
+                long long strideB, int m, int nbatch, bool transpose);
 void ordered_drop_chol(cudaStream_t st, const double *M, int a, const double *xnorm2, double *S,
                        double tau, double *R, int *kept, double *ratio);
 void tri_upper_inverse(cudaStream_t st, const double *R, int ldr, int a, double *Ri);

@@ -5,6 +5,7 @@
 // space"), the ordered append (Sec. 5.3 incremental QR of the basis) and
 // the reduced model (eq. newreduced).
 #include "common.cuh"
+#include "../../include/rcg.h"
 
 #include <type_traits>
 
@@ -343,6 +344,54 @@ __global__ void k_add_f32_f64(long long n, double *__restrict__ x, long long ldx
         x[(long long)l * ldx + p] += (double)d[(long long)l * ldd + p];
 }
 
+// J_k[:, s] = Z^T (G_k X[:, s]) for CTA (s, k): the reduced Jacobian of the
+// transfer function (CS-3: dPsi_r/dp_k = -Z_r^T V^T diag(h^2 dmu_k) V X_r,
+// with the sign and h^2 folded into G_k).  G_k r x r (ld r, symmetric),
+// X r x ns, Z r x nd (ld r), J_k nd x ns.  One column of G_k X per CTA in
+// shared memory; float64 (few FMAs per CTA, spread over the whole GPU).
+__global__ void __launch_bounds__(256)
+k_rom_jac(int r, const double *__restrict__ G, const double *__restrict__ X, int ns, const double *__restrict__ Z,
+          int nd, double *__restrict__ J) {
+    extern __shared__ double t[];             // r + r: x column, then G_k x
+    const int s = blockIdx.x, k = blockIdx.y, q = blockIdx.z, nparam = gridDim.y;
+    const double *Gk = G + ((long long)q * nparam + k) * r * r;
+    X += (long long)q * r * ns;
+    Z += (long long)q * r * nd;
+    J += (long long)q * nparam * nd * ns;
+    double *xs = t, *gx = t + r;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) xs[i] = X[(long long)s * r + i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < r; i += nw) {      // (G_k x)_i = G_k[:, i] . x (G_k symmetric: a contiguous column)
+        double a = 0.0;
+        for (int j = lane; j < r; j += 32) a += Gk[(long long)i * r + j] * xs[j];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) gx[i] = a;
+    }
+    __syncthreads();
+    for (int d = warp; d < nd; d += nw) {
+        double a = 0.0;
+        for (int j = lane; j < r; j += 32) a += Z[(long long)d * r + j] * gx[j];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) J[((long long)k * ns + s) * nd + d] = a;
+    }
+}
+
+// Psi_q[d + nd s] = Crm[:, d] . X_q[:, s] for CTA (s, q), one warp per d.
+__global__ void __launch_bounds__(256)
+k_rom_psi(int r, const double *__restrict__ Crm, const double *__restrict__ X, int ns, int nd,
+          double *__restrict__ Psi) {
+    const int s = blockIdx.x, q = blockIdx.y;
+    const double *x = X + ((long long)q * ns + s) * r;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int d = warp; d < nd; d += nw) {
+        double a = 0.0;
+        for (int j = lane; j < r; j += 32) a += Crm[(long long)d * r + j] * x[j];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) Psi[((long long)q * ns + s) * nd + d] = a;
+    }
+}
+
 int blocks_for(long long n, int per_col_cols) {
     long long b = (n + 255) / 256;
     long long cap = (long long)(4 * 152) / (per_col_cols > 0 ? per_col_cols : 1);
@@ -352,6 +401,25 @@ int blocks_for(long long n, int per_col_cols) {
 }
 
 }  // namespace
+
+void rom_psi(cudaStream_t st, int r, int nq, const double *Crm, const double *X, int ns, int nd, double *Psi) {
+    if (r <= 0 || nq <= 0 || ns <= 0 || nd <= 0) return;
+    k_rom_psi<<<dim3(ns, nq), 256, 0, st>>>(r, Crm, X, ns, nd, Psi);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void rom_jac(cudaStream_t st, int r, int nparam, const double *G, const double *X, int ns, const double *Z, int nd,
+             double *J, int nq) {
+    if (r <= 0 || nparam <= 0 || ns <= 0 || nd <= 0 || nq <= 0) return;
+    const size_t smem = sizeof(double) * 2 * (size_t)r;
+    if (smem > 200 * 1024) throw Error{RCG_ERR_INVALID, "rom_jac: reduced dimension too large"};
+    if (smem > 48 * 1024)
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_rom_jac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rom_jac<<<dim3(ns, nparam, nq), 256, smem, st>>>(r, G, X, ns, Z, nd, J);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
 
 void gemm_nn_df(cudaStream_t st, long long n, const float *V, long long ldv, int k, const double *Y, int ldy, int m,
                 double *Out, long long ldo, double beta) {

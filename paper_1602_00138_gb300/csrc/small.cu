@@ -10,6 +10,9 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 namespace rcg {
 namespace {
@@ -45,6 +48,44 @@ __global__ void __launch_bounds__(1024) k_chol(double *A, int lda, int k0, int r
         __syncthreads();
     }
     if (threadIdx.x == 0 && info) *info = fail;
+}
+
+// The same factorisation with the lower triangle staged in shared memory
+// (r x r, ld r; r <= SM_R), for matrix b = blockIdx.x at A + b strideA: the
+// r sequential steps then touch only shared memory.  Warp w updates trailing
+// columns w, w + nw, ...; failure (first bad pivot + 1) goes to *info by
+// atomicMax.
+constexpr int SM_R = 160;
+__global__ void __launch_bounds__(1024) k_chol_sm(double *A, int lda, long long strideA, int k0, int r, int *info) {
+    extern __shared__ double S[];
+    __shared__ double piv;
+    __shared__ int fail;
+    A += blockIdx.x * strideA;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < r; j += nw)
+        for (int i = j + lane; i < r; i += 32) S[i + j * r] = A[i + (long long)j * lda];
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int k = k0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = S[k + k * r];
+            if (bad(d)) fail = k + 1;
+            else { piv = sqrt(d); S[k + k * r] = piv; }
+        }
+        __syncthreads();
+        if (fail) break;
+        const double inv = 1.0 / piv;
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + k * r] *= inv;
+        __syncthreads();
+        for (int j = k + 1 + warp; j < r; j += nw) {
+            const double ljk = S[j + k * r];
+            for (int i = j + lane; i < r; i += 32) S[i + j * r] -= S[i + k * r] * ljk;
+        }
+        __syncthreads();
+    }
+    for (int j = warp; j < r; j += nw)
+        for (int i = j + lane; i < r; i += 32) A[i + (long long)j * lda] = S[i + j * r];
+    if (threadIdx.x == 0 && info && fail) atomicMax(info, fail);
 }
 
 // New rows r_old..r_old+a-1 of A hold the Gram entries (lower part).  Apply
@@ -94,6 +135,49 @@ __global__ void __launch_bounds__(256) k_trsv(const double *L, int ldl, int r, d
         }
     }
     for (int i = threadIdx.x; i < r; i += blockDim.x) b[i] = y[i];
+}
+
+// Batched triangular solves with L staged in shared memory (r <= SM_R):
+// system b = blockIdx.y has factor L + b strideL and right-hand sides
+// B + b strideB; warp w of CTA blockIdx.x solves column 8 blockIdx.x + w in
+// place (forward L y = b, or backward L^T y = b), synchronising only itself.
+// The diagonal's reciprocals are formed once per CTA.
+__global__ void __launch_bounds__(256) k_trsv_sm(const double *L, int ldl, long long strideL, int r, double *B,
+                                                 int ldb, long long strideB, int m, int trans) {
+    extern __shared__ double sh[];
+    double *Ls = sh, *dinv = sh + (long long)r * r, *ys = dinv + r;
+    L += blockIdx.y * strideL;
+    B += blockIdx.y * strideB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < r; j += 8)
+        for (int i = j + lane; i < r; i += 32) Ls[i + j * r] = L[i + (long long)j * ldl];
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) dinv[j] = 1.0 / Ls[j + j * r];
+    const int col = blockIdx.x * 8 + warp;
+    double *y = ys + warp * r;
+    double *b = B + (long long)col * ldb;
+    if (col < m)
+        for (int i = lane; i < r; i += 32) y[i] = b[i];
+    __syncthreads();
+    if (col >= m) return;
+    if (!trans) {
+        for (int j = 0; j < r; ++j) {
+            const double yj = y[j] * dinv[j];
+            __syncwarp();
+            if (lane == 0) y[j] = yj;
+            for (int k = j + 1 + lane; k < r; k += 32) y[k] -= Ls[k + j * r] * yj;
+            __syncwarp();
+        }
+    } else {
+        for (int j = r - 1; j >= 0; --j) {
+            const double yj = y[j] * dinv[j];
+            __syncwarp();
+            if (lane == 0) y[j] = yj;
+            for (int k = lane; k < j; k += 32) y[k] -= Ls[j + k * r] * yj;
+            __syncwarp();
+        }
+    }
+    for (int i = lane; i < r; i += 32) b[i] = y[i];
 }
 
 // Ordered pivot-free Cholesky of the candidate Gram M (a x a) with drop test:
@@ -268,11 +352,48 @@ __global__ void k_jacobi(double *A, int lda, int k, double *Q, double *w) {
 
 }  // namespace
 
+// Shared-memory attribute for the staged kernels (per device ordinal).
+void sm_attr(const void *f, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void *, int>, int>> done;   // (func, dev) -> bytes set
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    for (auto &e : done)
+        if (e.first.first == f && e.first.second == dev) {
+            if (e.second >= bytes) return;
+            RCG_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            e.second = bytes;
+            return;
+        }
+    RCG_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.push_back({{f, dev}, bytes});
+}
+
+void chol_run(cudaStream_t st, double *A, int lda, long long strideA, int k0, int r, int *info, int nbatch) {
+    if (r <= SM_R) {
+        const int bytes = (int)(sizeof(double) * (size_t)r * r);
+        if (bytes > 48 * 1024) sm_attr((const void *)k_chol_sm, bytes);
+        k_chol_sm<<<nbatch, 1024, bytes, st>>>(A, lda, strideA, k0, r, info);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+        return;
+    }
+    for (int b = 0; b < nbatch; ++b) {
+        k_chol<<<1, 1024, 0, st>>>(A + b * strideA, lda, k0, r, info);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+    }
+}
+
 void chol_inplace(cudaStream_t st, double *A, int lda, int r, int *info) {
     if (r <= 0) return;
-    k_chol<<<1, 1024, 0, st>>>(A, lda, 0, r, info);
-    count_launch();
-    RCG_CHECK_LAUNCH();
+    chol_run(st, A, lda, 0, 0, r, info, 1);
+}
+
+void chol_batched(cudaStream_t st, double *A, int lda, long long strideA, int r, int nbatch, int *info) {
+    if (r <= 0 || nbatch <= 0) return;
+    chol_run(st, A, lda, strideA, 0, r, info, nbatch);
 }
 
 void chol_border(cudaStream_t st, double *L, int ldl, int r_old, int a, int *info) {
@@ -282,14 +403,31 @@ void chol_border(cudaStream_t st, double *L, int ldl, int r_old, int a, int *inf
         count_launch();
         RCG_CHECK_LAUNCH();
     }
-    k_chol<<<1, 1024, 0, st>>>(L, ldl, r_old, r_old + a, info);
-    count_launch();
-    RCG_CHECK_LAUNCH();
+    chol_run(st, L, ldl, 0, r_old, r_old + a, info, 1);
+}
+
+void trsv_multi(cudaStream_t st, const double *L, int ldl, long long strideL, int r, double *B, int ldb,
+                long long strideB, int m, int nbatch, bool transpose) {
+    if (r <= 0 || m <= 0 || nbatch <= 0) return;
+    if (r <= SM_R) {
+        const int bytes = (int)(sizeof(double) * ((size_t)r * r + r + 8 * (size_t)r));
+        if (bytes > 48 * 1024) sm_attr((const void *)k_trsv_sm, bytes);
+        k_trsv_sm<<<dim3((m + 7) / 8, nbatch), 256, bytes, st>>>(L, ldl, strideL, r, B, ldb, strideB, m,
+                                                                transpose ? 1 : 0);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+        return;
+    }
+    for (int b = 0; b < nbatch; ++b) trsv_lower_batched(st, L + b * strideL, ldl, r, B + b * strideB, ldb, m, transpose);
 }
 
 void trsv_lower_batched(cudaStream_t st, const double *L, int ldl, int r, double *B, int ldb, int m,
                         bool transpose) {
     if (r <= 0 || m <= 0) return;
+    if (r <= SM_R) {
+        trsv_multi(st, L, ldl, 0, r, B, ldb, 0, m, 1, transpose);
+        return;
+    }
     const size_t sh = sizeof(double) * (size_t)r;
     if (sh > 48 * 1024)
         RCG_CUDA_TRY(cudaFuncSetAttribute(k_trsv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));

@@ -154,14 +154,15 @@ __device__ __forceinline__ void prefetch_w(const double *wt, long long k0, long 
 // 32 float64 weights in shared memory) every value is first scaled by its
 // row's weight.  16-byte chunk o of the tile holds rows 4 c .. 4 c + 3 with
 // c = ((o / 16) mod 8) xor (m mod 8), m = o / 128 (the 128-byte swizzle).
-__device__ __forceinline__ void split_tile(char *hi, char *lo, const double *w = nullptr) {
+__device__ __forceinline__ void split_tile(char *hi, char *lo, const double *w = nullptr, double wscale = 1.0) {
 #pragma unroll
     for (int it = 0; it < TILE_BYTES / 16 / NTHR; ++it) {
         const int o = (threadIdx.x + it * NTHR) * 16;
         float4 v = *(const float4 *)(hi + o);
         if (w) {
             const int m = o >> 7, c = ((o >> 4) & 7) ^ (m & 7);
-            v.x *= (float)w[4 * c]; v.y *= (float)w[4 * c + 1]; v.z *= (float)w[4 * c + 2]; v.w *= (float)w[4 * c + 3];
+            v.x *= (float)(wscale * w[4 * c]); v.y *= (float)(wscale * w[4 * c + 1]);
+            v.z *= (float)(wscale * w[4 * c + 2]); v.w *= (float)(wscale * w[4 * c + 3]);
         }
         float4 h, l;
         h.x = rn_tf32(v.x); h.y = rn_tf32(v.y); h.z = rn_tf32(v.z); h.w = rn_tf32(v.w);
@@ -197,7 +198,8 @@ __device__ __forceinline__ long long list_chunk(long long nsteps, int z) {
 __global__ void __launch_bounds__(NTHR, 1)
 k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const float *__restrict__ B, long long ldb,
         int kb, int symmetric, float *__restrict__ part, long long chunk, int *__restrict__ err,
-        const double *__restrict__ wt, const int *__restrict__ blist, const int *__restrict__ bcount) {
+        const double *__restrict__ wt, const int *__restrict__ blist, const int *__restrict__ bcount, int zper,
+        long long ldw_b, long long ldl_b, double wscale) {
     if (symmetric && blockIdx.x > blockIdx.y) return;        // lower tiles are mirrored by the reduction
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar[2];
@@ -209,12 +211,17 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
     // K-steps of this slice: steps s_begin .. s_begin + nk - 1 (chunk = steps per
     // slice); step s covers rows 32 s .. 32 s + 31, or rows 32 blist[s] .. with a
     // block list (the blocks where the weights do not vanish)
+    // batch bk = blockIdx.z / zper (weights wt + bk ldw_b, block list
+    // blist + bk ldl_b with count bcount[bk]), slice bz = blockIdx.z mod zper
+    const int bk = blockIdx.z / zper, bz = blockIdx.z % zper;
+    if (wt) wt += bk * ldw_b;
+    if (blist) { blist += bk * ldl_b; bcount += bk; }
     const long long nsteps = blist ? (long long)*bcount : (n + TBK - 1) / TBK;
     if (blist) {                       // the support, not n, sets the slice length
-        chunk = list_chunk(nsteps, (int)gridDim.z);
-        if ((long long)blockIdx.z * chunk >= nsteps) return;    // empty slice: the reduction skips it
+        chunk = list_chunk(nsteps, zper);
+        if ((long long)bz * chunk >= nsteps) return;            // empty slice: the reduction skips it
     }
-    const long long s_begin = (long long)blockIdx.z * chunk;
+    const long long s_begin = (long long)bz * chunk;
     const long long s_end = s_begin + chunk < nsteps ? s_begin + chunk : nsteps;
     const long long nk = s_end > s_begin ? s_end - s_begin : 0;
     auto step_row = [&](long long ks) -> long long {
@@ -287,7 +294,7 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
         __syncthreads();                                           // ... everyone's; s_ok is uniform here
         if (!s_ok) { ok = false; break; }
         split_tile(stg, stg + 2 * TILE_BYTES,                      // A hi | A lo (weighted rows)
-                   wt ? (const double *)(wsm + (int)(ks % NSTAGE) * WBYTES) : nullptr);
+                   wt ? (const double *)(wsm + (int)(ks % NSTAGE) * WBYTES) : nullptr, wscale);
         split_tile(stg + TILE_BYTES, stg + 3 * TILE_BYTES);        // B hi | B lo
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -354,39 +361,58 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TNc));
 }
 
-// Ascending list of the 32-row blocks where w does not vanish (one CTA, the
-// order is deterministic): thread t scans a contiguous range of blocks.
-__global__ void __launch_bounds__(1024) k_block_list(long long n, const double *__restrict__ w, int *__restrict__ list,
-                                                     int *__restrict__ count, long long ldw, long long ldl) {
-    // CTA b handles weight vector b: w + b ldw -> list + b ldl, count[b]
-    w += blockIdx.x * ldw;
-    list += blockIdx.x * ldl;
-    count += blockIdx.x;
+// Ascending list of the 32-row blocks where w does not vanish, in two
+// passes.  k_block_flags: one warp per (vector, block) writes 1 / 0 into the
+// list slot of the block (one coalesced 256-byte read per block).
+__global__ void k_block_flags(long long n, const double *__restrict__ w, int *__restrict__ list, int nvec,
+                              long long ldw, long long ldl) {
     const long long nb = (n + TBK - 1) / TBK;
-    const long long per = (nb + blockDim.x - 1) / blockDim.x;
-    const long long b0 = threadIdx.x * per, b1 = b0 + per < nb ? b0 + per : nb;
-    int cnt = 0;
-    for (long long b = b0; b < b1; ++b) {
-        bool nz = false;
-        for (long long k = b * TBK; k < (b + 1) * TBK && k < n; ++k) nz |= (w[k] != 0.0);
-        cnt += nz;
+    const long long total = nb * nvec;
+    const int lane = threadIdx.x & 31;
+    for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < total;
+         gw += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long v = gw / nb, b = gw % nb;
+        const long long k = b * TBK + lane;
+        const bool nz = k < n && w[v * ldw + k] != 0.0;
+        const unsigned any = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) list[v * ldl + b] = any != 0u;
     }
+}
+
+// k_block_compact: CTA v compacts the flags of vector v in place, in chunks
+// of 1024 x 8 flags: every flag of a chunk is in registers before any index
+// of it is written, and an index never lands past its own flag's slot.
+__global__ void __launch_bounds__(1024) k_block_compact(long long n, int *__restrict__ list, int *__restrict__ count,
+                                                        long long ldl) {
+    constexpr int PER = 8;
     __shared__ int scan[1024];
-    scan[threadIdx.x] = cnt;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {       // inclusive scan
-        const int v = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
+    list += blockIdx.x * ldl;
+    const long long nb = (n + TBK - 1) / TBK;
+    int base = 0;
+    for (long long c0 = 0; c0 < nb; c0 += 1024 * PER) {
+        const long long b0 = c0 + (long long)threadIdx.x * PER;
+        int f[PER], cnt = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            f[i] = b0 + i < nb ? list[b0 + i] : 0;
+            cnt += f[i];
+        }
+        scan[threadIdx.x] = cnt;
         __syncthreads();
-        scan[threadIdx.x] += v;
+        for (int o = 1; o < 1024; o <<= 1) {       // inclusive scan
+            const int v = threadIdx.x >= (unsigned)o ? scan[threadIdx.x - o] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int pos = base + scan[threadIdx.x] - cnt;
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (f[i]) list[pos++] = (int)(b0 + i);
+        base += scan[1023];
         __syncthreads();
     }
-    int pos = scan[threadIdx.x] - cnt;
-    for (long long b = b0; b < b1; ++b) {
-        bool nz = false;
-        for (long long k = b * TBK; k < (b + 1) * TBK && k < n; ++k) nz |= (w[k] != 0.0);
-        if (nz) list[pos++] = (int)b;
-    }
-    if (threadIdx.x == blockDim.x - 1) *count = scan[threadIdx.x];
+    if (threadIdx.x == 0) count[blockIdx.x] = base;
 }
 
 // ------------------------------------------------------------------ NN
@@ -588,20 +614,27 @@ k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const fl
 
 // C[i + j*ldc] (+)= sum_z part[z][j][i] in float64; a symmetric product
 // reads the lower tiles from the mirrored upper ones.
-__global__ void k_tc_reduce(const float *__restrict__ part, int z, int ka, int kb, int symmetric,
-                            double *__restrict__ C, int ldc, int accumulate, const int *__restrict__ bcount) {
-    if (bcount) {                      // only the slices that held blocks of the list
-        const long long nsteps = *bcount;
-        const long long chunk = list_chunk(nsteps, z);
-        z = (int)((nsteps + chunk - 1) / chunk);
-    }
+// Batch bk of nbatch: C + bk ldcb from the partials part + bk zper tot.
+__global__ void k_tc_reduce(const float *__restrict__ part, int zper, int ka, int kb, int symmetric,
+                            double *__restrict__ C, int ldc, int accumulate, const int *__restrict__ bcount,
+                            int nbatch, long long ldcb) {
     const long long tot = (long long)ka * kb;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % ka), j = (int)(e / ka);
-        const long long src = (symmetric && i / TM > j / TNc) ? (long long)i * ka + j : e;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot * nbatch;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int bk = (int)(e / tot);
+        const long long el = e % tot;
+        int z = zper;
+        if (bcount) {                  // only the slices that held blocks of the list
+            const long long nsteps = bcount[bk];
+            const long long chunk = list_chunk(nsteps, zper);
+            z = (int)((nsteps + chunk - 1) / chunk);
+        }
+        const int i = (int)(el % ka), j = (int)(el / ka);
+        const long long src = (symmetric && i / TM > j / TNc) ? (long long)i * ka + j : el;
+        const float *pb = part + (long long)bk * zper * tot;
         double s = 0.0;
-        for (int q = 0; q < z; ++q) s += (double)part[(long long)q * tot + src];
-        double *c = C + i + (long long)j * ldc;
+        for (int q = 0; q < z; ++q) s += (double)pb[(long long)q * tot + src];
+        double *c = C + bk * ldcb + i + (long long)j * ldc;
         *c = accumulate ? *c + s : s;
     }
 }
@@ -637,7 +670,12 @@ long long tc_gemm_tn_scratch(long long n, int ka, int kb, bool symmetric, int *z
 void tc_block_list(cudaStream_t st, long long n, const double *w, int *list, int *count, int nvec, long long ldw,
                    long long ldl) {
     if (nvec <= 0) return;
-    k_block_list<<<nvec, 1024, 0, st>>>(n, w, list, count, ldw, ldl);
+    const long long warps = ((n + TBK - 1) / TBK) * nvec;
+    k_block_flags<<<(unsigned)std::min<long long>((warps * 32 + 255) / 256, 8 * NUM_SMS), 256, 0, st>>>(
+        n, w, list, nvec, ldw, ldl ? ldl : (n + TBK - 1) / TBK);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    k_block_compact<<<nvec, 1024, 0, st>>>(n, list, count, ldl ? ldl : (n + TBK - 1) / TBK);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
@@ -669,12 +707,56 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
     dim3 grid((ka + TM - 1) / TM, (kb + TNc - 1) / TNc, z);
     if ((blist != nullptr) != (bcount != nullptr) || (blist && !wt)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: block list"};
     k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, B, ldb, kb, symmetric ? 1 : 0, scratch, chunk, err, wt, blist,
-                                         bcount);
+                                         bcount, z, 0, 0, 1.0);
     count_launch();
     RCG_CHECK_LAUNCH();
     const long long tot = (long long)ka * kb;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 2048);
-    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, z, ka, kb, symmetric ? 1 : 0, C, ldc, accumulate ? 1 : 0, bcount);
+    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, z, ka, kb, symmetric ? 1 : 0, C, ldc, accumulate ? 1 : 0, bcount, 1,
+                                        0);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+// Slices per batch and float scratch of tc_gram_w_batched.
+long long tc_gram_w_batched_scratch(int ka, int nbatch, int *zper_out) {
+    const long long tx = (ka + TM - 1) / TM;
+    const long long tiles = tx * (tx + 1) / 2;
+    long long zper = (4LL * NUM_SMS + tiles * nbatch - 1) / (tiles * nbatch);
+    if (zper < 1) zper = 1;
+    if (zper_out) *zper_out = (int)zper;
+    return zper * nbatch * (long long)ka * ka;
+}
+
+// C_b (+)= A^T diag(wscale w_b) A (ka x ka, ld ldc, C_b = C + b ldcb) for
+// b < nbatch in one launch: w_b = wt + b ldw with block lists blist + b ldl,
+// counts bcount[b] (tc_block_list); the slices of each batch follow its
+// support.  The weights are copied 16 bytes at a time: wt 16-byte aligned,
+// ldw even.
+void tc_gram_w_batched(cudaStream_t st, long long n, const float *A, long long lda, int ka, double *C, int ldc,
+                       long long ldcb, int nbatch, const double *wt, long long ldw, const int *blist, long long ldl,
+                       const int *bcount, float *scratch, int *err, bool accumulate, double wscale) {
+    if (ka <= 0 || nbatch <= 0) return;
+    if (!tc_gemm_tn_ok(lda, lda, A, A) || !wt || !blist || !bcount || ((uintptr_t)wt & 15) || (ldw & 1))
+        throw Error{RCG_ERR_INVALID, "tc_gram_w_batched: bad operands"};
+    int zper;
+    tc_gram_w_batched_scratch(ka, nbatch, &zper);
+    static bool attr[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_tc_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    const unsigned tx = (unsigned)((ka + TM - 1) / TM);
+    dim3 grid(tx, tx, (unsigned)(zper * nbatch));
+    k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, A, lda, ka, 1, scratch, 1, err, wt, blist, bcount, zper, ldw,
+                                         ldl, wscale);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    const long long tot = (long long)ka * ka * nbatch;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, zper, ka, ka, 1, C, ldc, accumulate ? 1 : 0, bcount, nbatch, ldcb);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

@@ -31,7 +31,7 @@ EXPORTED = [
     "rcg_options_default", "rcg_create", "rcg_destroy", "rcg_last_error", "rcg_strerror",
     "rcg_set_diffusion", "rcg_set_sources_detectors", "rcg_set_tolerances", "rcg_set_sample",
     "rcg_set_sample_device", "rcg_apply", "rcg_seed", "rcg_reset_to_seed", "rcg_solve_all",
-    "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device",
+    "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device", "rcg_rom_eval_batch",
     "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
     "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
@@ -95,6 +95,7 @@ def load(path=LIB_PATH):
         "rcg_solution_get": (I, [P, I, P]),
         "rcg_rom_eval": (I, [P, P, I, P, P, P]),
         "rcg_rom_eval_device": (I, [P, P, I, P, P, P]),
+        "rcg_rom_eval_batch": (I, [P, I, P, I, P, P, P]),
         "rcg_phase_ms": (D, [P, C.c_char_p]),
         "rcg_launch_count": (LL, [P]),
         "rcg_profile_enable": (I, [P, I]),
@@ -333,6 +334,33 @@ class Context:
     def rom_eval_device(self, mu_dev, dmu_dev, Psi_dev, J_dev, nparam):
         return self._check(self.L.rcg_rom_eval_device(self.h, _ptr(mu_dev), nparam, _ptr(dmu_dev),
                                                       _ptr(Psi_dev), _ptr(J_dev)))
+
+    def rom_eval_batch_device(self, nq, mu_dev, dmu_dev, Psi_dev, J_dev, nparam):
+        """rcg_rom_eval_batch on device arrays (see rcg.h for the layouts)."""
+        return self._check(self.L.rcg_rom_eval_batch(self.h, nq, _ptr(mu_dev), nparam, _ptr(dmu_dev),
+                                                     _ptr(Psi_dev), _ptr(J_dev)))
+
+    def rom_eval_batch(self, mus, dmus=None):
+        """Psi (nq, ndet, nsrc) and J (nq, nparam, ndet, nsrc) or None at the
+        rows of mus (nq, n), through device copies made with torch."""
+        import torch
+        mus = np.ascontiguousarray(mus, dtype=np.float64)
+        nq = mus.shape[0]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        mu_d = torch.from_numpy(mus).to(dev)
+        Psi_d = torch.empty((nq, self.nsrc, self.ndet), dtype=torch.float64, device=dev)
+        dmu_d = J_d = None
+        k = 0
+        if dmus is not None:
+            dmus = np.ascontiguousarray(dmus, dtype=np.float64)
+            k = dmus.shape[1]
+            dmu_d = torch.from_numpy(dmus).to(dev)
+            J_d = torch.empty((nq, k, self.nsrc, self.ndet), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        self.rom_eval_batch_device(nq, mu_d, dmu_d, Psi_d, J_d, k)
+        Psi = Psi_d.cpu().numpy().transpose(0, 2, 1)
+        J = None if J_d is None else J_d.cpu().numpy().transpose(0, 1, 3, 2)
+        return Psi, J
 
     def phase_ms(self, name):
         return self.L.rcg_phase_ms(self.h, name.encode())
