@@ -542,8 +542,8 @@ k_mu(LaneState ls, const int *__restrict__ alist, int sprev, int scur, int snext
 // p = r + beta p - U_0 mu_u - W_p mu_p.  U_0 is staged per stage of SN nodes
 // in a shared-memory ring and shared by the tile's lanes (warp w: lanes
 // w + 8q); one barrier per stage.
-template <int KUT>
-__global__ void __launch_bounds__(kThreads)
+template <int KUT, int KPM>
+__global__ void __launch_bounds__(kThreads, 2)
 k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane,
              const int *__restrict__ tile_cnt, const float *__restrict__ mu, const float *__restrict__ beta,
              long long chunk, int it) {
@@ -604,57 +604,110 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
         const float4(&Uc)[KUT][SN / 4] = Us[st % DIR_NST];
         const long long p = base + 4 * tl;
         if (p < r1) {
+            // the loads of G lanes before any of their stores (a store to one
+            // lane's p or x would otherwise hold back the next lane's loads)
+            constexpr int G = KPM <= 2 ? 4 : KPM <= 4 ? 2 : 1;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int jj = warp + 8 * q;
-                const int l = slane[jj];
-                if (l < 0) continue;
-                const long long o = (long long)l * gm.ld + p;
-                const float4 pv = *(const float4 *)((const float *)gm.p + o);
-                const float a = salpha[jj];
-                if (a != 0.f) {
-                    float4 *xp = (float4 *)((float *)gm.x + o);
-                    const float4 xv = *xp;
-                    *xp = make_float4(xv.x + a * pv.x, xv.y + a * pv.y, xv.z + a * pv.z, xv.w + a * pv.w);
-                }
-                if (!sdir[jj]) continue;
-                const float4 rv = *(const float4 *)((const float *)gm.r + o);
-                const float b = sbeta[jj];
-                float4 sres = make_float4(rv.x + b * pv.x, rv.y + b * pv.y, rv.z + b * pv.z, rv.w + b * pv.w);
+            for (int q0 = 0; q0 < 4; q0 += G) {
+                float4 pv[G], xv[G], rv[G], wv[G][KPM];
 #pragma unroll
-                for (int c = 0; c < KUT; ++c) {
-                    const float m = c < ku ? smu[jj][c] : 0.f;
-                    const float4 u = Uc[c][tl];
-                    sres.x -= m * u.x; sres.y -= m * u.y; sres.z -= m * u.z; sres.w -= m * u.w;
+                for (int g = 0; g < G; ++g) {
+                    const int jj = warp + 8 * (q0 + g);
+                    const int l = slane[jj];
+                    const bool dir = l >= 0 && sdir[jj] != 0;
+                    const long long o = (long long)(l < 0 ? 0 : l) * gm.ld + p;
+                    pv[g] = l >= 0 ? *(const float4 *)((const float *)gm.p + o) : z4;
+                    xv[g] = (l >= 0 && salpha[jj] != 0.f) ? *(const float4 *)((const float *)gm.x + o) : z4;
+                    rv[g] = dir ? *(const float4 *)((const float *)gm.r + o) : z4;
+                    const float *WP = (const float *)gm.wp + (long long)(l < 0 ? 0 : l) * gm.kp_max * gm.ld + p;
+                    const int kp = skp[jj];
+#pragma unroll
+                    for (int c = 0; c < KPM; ++c)
+                        wv[g][c] = (dir && c < kp) ? *(const float4 *)(WP + (long long)c * gm.ld) : z4;
                 }
-                const int kp = skp[jj];
-                const float *WP = (const float *)gm.wp + (long long)l * gm.kp_max * gm.ld;
-                for (int c = 0; c < kp; ++c) {
-                    const float m = smu[jj][ku + c];
-                    const float4 w = *(const float4 *)(WP + (long long)c * gm.ld + p);
-                    sres.x -= m * w.x; sres.y -= m * w.y; sres.z -= m * w.z; sres.w -= m * w.w;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int jj = warp + 8 * (q0 + g);
+                    const int l = slane[jj];
+                    if (l < 0) continue;
+                    const long long o = (long long)l * gm.ld + p;
+                    const float a = salpha[jj];
+                    if (a != 0.f)
+                        *(float4 *)((float *)gm.x + o) = make_float4(xv[g].x + a * pv[g].x, xv[g].y + a * pv[g].y,
+                                                                     xv[g].z + a * pv[g].z, xv[g].w + a * pv[g].w);
+                    if (!sdir[jj]) continue;
+                    const float b = sbeta[jj];
+                    float4 sres = make_float4(rv[g].x + b * pv[g].x, rv[g].y + b * pv[g].y, rv[g].z + b * pv[g].z,
+                                              rv[g].w + b * pv[g].w);
+#pragma unroll
+                    for (int c = 0; c < KUT; ++c) {
+                        const float m = c < ku ? smu[jj][c] : 0.f;
+                        const float4 u = Uc[c][tl];
+                        sres.x -= m * u.x; sres.y -= m * u.y; sres.z -= m * u.z; sres.w -= m * u.w;
+                    }
+                    const int kp = skp[jj];
+#pragma unroll
+                    for (int c = 0; c < KPM; ++c) {
+                        if (c >= kp) break;
+                        const float m = smu[jj][ku + c];
+                        sres.x -= m * wv[g][c].x; sres.y -= m * wv[g][c].y;
+                        sres.z -= m * wv[g][c].z; sres.w -= m * wv[g][c].w;
+                    }
+                    *(float4 *)((float *)gm.p + o) = sres;
                 }
-                *(float4 *)((float *)gm.p + o) = sres;
             }
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// Resident k_direction4<KUT> CTAs on the whole GPU (cached per device ordinal).
-template <int KUT>
-int dir_slots() {
+// k_direction4<KUT, KPM> over the tiles of ll in one wave of resident CTAs
+// (occupancy cached per device ordinal): a partial second wave would hold
+// the whole launch.  Node ranges are multiples of SN.
+template <int KUT, int KPM>
+void dir_launch(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const LaneList &ll,
+                const float *mu, const float *beta, int it) {
     static int slots[64] = {};
     int dev = 0;
     RCG_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return 5 * 152;
-    if (!slots[dev]) {
-        int occ = 0, sms = 0;
-        RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direction4<KUT>, kThreads, 0));
-        RCG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        slots[dev] = std::max(1, occ * sms);
+    int sl = 2 * 152;
+    if (dev >= 0 && dev < 64) {
+        if (!slots[dev]) {
+            int occ = 0, sms = 0;
+            RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_direction4<KUT, KPM>, kThreads, 0));
+            RCG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            slots[dev] = std::max(1, occ * sms);
+        }
+        sl = slots[dev];
     }
-    return slots[dev];
+    long long z = std::max<long long>(1, sl / std::max(ll.ntiles, 1));
+    const long long maxz = (n + 4 * SN - 1) / (4 * SN);
+    if (z > maxz) z = maxz;
+    long long chunk = (n + z - 1) / z;
+    chunk = (chunk + SN - 1) / SN * SN;
+    z = (n + chunk - 1) / chunk;
+    k_direction4<KUT, KPM><<<dim3((unsigned)z, ll.ntiles), kThreads, 0, st>>>(n, gm, ls, ll.tile_lane, ll.tile_cnt,
+                                                                             mu, beta, chunk, it);
+}
+
+template <int KUT>
+void dir_launch_kp(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const LaneList &ll,
+                   const float *mu, const float *beta, int it) {
+    if (gm.kp_max <= 1) dir_launch<KUT, 1>(st, n, gm, ls, ll, mu, beta, it);
+    else if (gm.kp_max <= 2) dir_launch<KUT, 2>(st, n, gm, ls, ll, mu, beta, it);
+    else if (gm.kp_max <= 4) dir_launch<KUT, 4>(st, n, gm, ls, ll, mu, beta, it);
+    else dir_launch<KUT, KP_MAX>(st, n, gm, ls, ll, mu, beta, it);
+}
+
+void direction_launch(cudaStream_t st, int kut, long long n, const LaneGeom &gm, const LaneState &ls,
+                      const LaneList &ll, const float *mu, const float *beta, int it) {
+    switch (kut) {
+        case 0: case 4: dir_launch_kp<4>(st, n, gm, ls, ll, mu, beta, it); break;
+        case 8: dir_launch_kp<8>(st, n, gm, ls, ll, mu, beta, it); break;
+        case 12: dir_launch_kp<12>(st, n, gm, ls, ll, mu, beta, it); break;
+        default: dir_launch_kp<16>(st, n, gm, ls, ll, mu, beta, it);
+    }
 }
 
 // Lane l = alist[blockIdx.y]: wv[sw][k_u + c] += (src_c)^T r over the lane's
@@ -863,16 +916,7 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     RCG_CHECK_LAUNCH();
     if (tm) { kt->stop(3, e, st); e = kt->start(st); }
     {
-        // one wave of resident CTAs (a partial second wave would hold the whole launch)
-        const int slots = kut <= 4 ? dir_slots<4>() : kut == 8 ? dir_slots<8>() : kut == 12 ? dir_slots<12>()
-                                                                                            : dir_slots<16>();
-        long long z;
-        const long long chunk = tile_chunk(z, slots);
-        dim3 grid((unsigned)z, ll.ntiles);
-#define RCG_DIR(K) k_direction4<K><<<grid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, t)
-        switch (kut) { case 0: case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break;
-                       default: RCG_DIR(16); }
-#undef RCG_DIR
+        direction_launch(st, kut, g.n, gm, ls, ll, mu, beta, t);
         count_launch();
         RCG_CHECK_LAUNCH();
     }
@@ -929,9 +973,7 @@ void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, Lane
     (void)zc;
     // no x step is pending at a restart (x = W mu0 was just set): iteration
     // number -2 matches no stamp
-#define RCG_DIR(K) k_direction4<K><<<tgrid, kThreads, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, -2)
-    switch (kut) { case 4: RCG_DIR(4); break; case 8: RCG_DIR(8); break; case 12: RCG_DIR(12); break; default: RCG_DIR(16); }
-#undef RCG_DIR
+    direction_launch(st, kut, g.n, gm, ls, ll, mu, beta, -2);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
