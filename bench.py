@@ -64,6 +64,8 @@ def parse_args():
                     help="held-out parameter points for the reduced-model sweep (Psi_r and J through the "
                          "last step's basis; 0 skips it)")
     ap.add_argument("--rom-batch", type=int, default=8, help="points per rcg_rom_eval_batch call in the sweep")
+    ap.add_argument("--alg1-tau", type=float, default=1e-6,
+                    help="relative singular-value cut of the Algorithm 1 comparison (untimed; <= 0 skips it)")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
@@ -366,6 +368,42 @@ def run_ours(args, rank, world, torch):
                  "what": "Psi_r (ndet x nsrc) and J (nparam x ndet x nsrc) per point, inputs resident"}
         del mus_sw, dmus_sw, psi_sw, J_sw, psi_1, J_1
 
+    # ---- Algorithm 1 against Algorithm 2 (untimed): one pass of Algorithm 2 with
+    # the solutions kept, then the truncated SVD of the concatenated solutions
+    # (rcg_basis_compress); ranks, the compression time, and the reduced model
+    # of both bases at the sampled points (against the plain definition on the
+    # delivered solutions) and at held-out points (against each other)
+    alg1 = None
+    if args.alg1_tau > 0 and rank == 0:
+        ctx_a = make_ctx(rcg, inp, dict(MIXED_PLAIN, keep_solutions=1), torch)
+        for s in range(K + 1):
+            ctx_a.set_sample(s, mu_dev[s])
+        ctx_a.seed(0, None)
+        ctx_a.solve_all(1, K)
+        r2 = ctx_a.rank()
+        ps_ho = heldout_params(wl, 4, seed_offset=4000)
+        mus_ho = [pals_mu(p, inp["X"], wl.mu_bg) for p in ps_ho]
+
+        def rom_errors(c):
+            smp = []
+            for s in range(1, K + 1):
+                P_r, _ = c.rom_eval(inp["mu"][s])
+                P_f, _ = c.full_eval(s)
+                smp.append(float(np.linalg.norm(P_r - P_f) / np.linalg.norm(P_f)))
+            return max(smp), [c.rom_eval(m)[0] for m in mus_ho]
+
+        # the plain definition uses the delivered solutions of Algorithm 2, kept in the context
+        e2_smp, P2_ho = rom_errors(ctx_a)
+        r1, sig = ctx_a.basis_compress(0, args.alg1_tau)
+        e1_smp, P1_ho = rom_errors(ctx_a)
+        d_ho = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(P1_ho, P2_ho))
+        alg1 = {"snapshot_columns": len(sig), "tau": args.alg1_tau, "rank_alg2": r2, "rank_alg1": r1,
+                "compress_ms": round(ctx_a.phase_ms("compress"), 2),
+                "sigma_ratio_at_rank_alg2": float(sig[min(r2, len(sig)) - 1] / sig[0]),
+                "psi_r_rel_err_sampled": {"alg2": e2_smp, "alg1": e1_smp},
+                "psi_r_rel_diff_heldout_alg1_vs_alg2": d_ho}
+        ctx_a.close()
+
     # ---- end to end through the public API with host buffers
     ctx_e = make_ctx(rcg, inp, CONTENDER, torch)
     pinned = torch.empty((K + 1, n), dtype=torch.float64).pin_memory()
@@ -425,7 +463,7 @@ def run_ours(args, rank, world, torch):
     return dict(value=value, ms=ms_max / args.steps, launches=launches, roofline=roofline, e2e=e2e,
                 clocks=clk, base=base, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
                 seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=nolearn,
-                rom_sweep=sweep)
+                rom_sweep=sweep, alg1=alg1)
 
 
 # ------------------------------------------------------------- CPU oracle leg
@@ -580,6 +618,7 @@ def main():
             "baseline_fp64_sequential": res["base"],
             "mixed_without_learning": res["nolearn"],
             "rom_sweep": res.get("rom_sweep"),
+            "alg1_vs_alg2": res.get("alg1"),
         }
         print(json.dumps(line))
     if world > 1:

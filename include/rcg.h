@@ -218,6 +218,23 @@ int rcg_solve_all(rcg_ctx *c, int s_first, int s_count, rcg_stat *stats);
 int rcg_basis_rank(const rcg_ctx *c, int *r);
 int rcg_basis_get(rcg_ctx *c, double *V);
 
+/* Algorithm 1 (Sec. 4.2.2, "Generate Symmetric Global Basis via Truncated
+ * SVD"), steps 2-3, on the delivered solutions kept so far (needs
+ * options.keep_solutions): S = [X_s1, X_s2, ...], the kept samples in
+ * ascending order, each X_s = the n x nrhs solutions of sample s; V becomes
+ * the first r left singular vectors of S with
+ * r = min(r_max, #{i : sigma_i > tau sigma_1}) (r_max <= 0: options.r_max).
+ * The singular values come from the float64 Gram S^T S (parallel Jacobi), so
+ * values below ~1e-7 sigma_1 are not resolved.  Afterwards C_* is rebuilt for
+ * the new V, the leading min(k_u, r) columns of V serve as the shared
+ * deflation space, the private recycle lists restart empty, and
+ * rcg_reset_to_seed returns to the compressed basis.  sigma (host, may be
+ * NULL): the first min(sigma_len, m) singular values, descending; nsnap (may
+ * be NULL): m, the number of columns of S.  RCG_ERR_INVALID before rcg_seed,
+ * without kept solutions, for tau < 0, or if no singular value exceeds
+ * tau sigma_1 (V is unchanged then). */
+int rcg_basis_compress(rcg_ctx *c, int r_max, double tau, double *sigma, int sigma_len, int *nsnap);
+
 /* Delivered solutions of sample s (host, n x nrhs float64) from the last
  * rcg_solve_all (or rcg_seed for s0); needs options.keep_solutions. */
 int rcg_solution_get(rcg_ctx *c, int s, double *X);
@@ -279,7 +296,8 @@ int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, con
                        double *Psi_dev, double *J_dev);
 
 /* Elapsed device milliseconds of the named phase in the last call that ran
- * it ("check", "cg", "append", "seed_eig", "seed_x0", "rom", "rom_batch");
+ * it ("check", "cg", "append", "seed_eig", "seed_x0", "rom", "rom_batch",
+ * "compress");
  * -1 if none. */
 double rcg_phase_ms(const rcg_ctx *c, const char *phase);
 

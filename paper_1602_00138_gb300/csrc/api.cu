@@ -44,6 +44,7 @@ struct EngineBase {
     virtual ~EngineBase() {}
     virtual void seed(int s0, const double *U0, rcg_stat *stats) = 0;
     virtual void reset() = 0;
+    virtual int compress(int r_cap, double tau, std::vector<double> &sigma) = 0;
     virtual int solve_all(int s_first, int s_count, rcg_stat *stats) = 0;
     virtual int rank() const = 0;
     virtual void basis_get(double *V) = 0;
@@ -1196,6 +1197,94 @@ struct Engine : EngineBase {
         gs_sample = -1;
     }
 
+    // ---------------------------------------------------------- Algorithm 1
+    // Steps 2-3 of Algorithm 1 on the delivered solutions kept so far
+    // (samples in ascending order): S = [X_s1, X_s2, ...] (n x m), the Gram
+    // S^T S in float64, its eigen-decomposition by the parallel Jacobi method,
+    // sigma_i = sqrt(lambda_i), and V <- S W_r diag(sigma)^-1 for the r =
+    // min(r_cap, #{sigma_i > tau sigma_1}) leading pairs, passed through the
+    // ordered append (re-orthonormalised, C_* rebuilt).  The shared deflation
+    // space becomes the leading min(k_u, r) columns and the private recycle
+    // lists restart empty (X_0 need not lie in the truncated range(V), and a
+    // private column's deflation matrix is formed through V^T x); the seed
+    // state becomes the compressed basis.
+    // Returns the number of snapshot columns m; sigma gets all m values.
+    int compress(int r_cap, double tau, std::vector<double> &sigma) override {
+        if (!seeded) throw Error{RCG_ERR_INVALID, "rcg_basis_compress before rcg_seed"};
+        if (!c->opt.keep_solutions) throw Error{RCG_ERR_INVALID, "rcg_basis_compress needs options.keep_solutions"};
+        std::vector<int> samp;
+        for (int s = 0; s < c->opt.max_samples; ++s)
+            if (!c->solutions[s].empty()) samp.push_back(s);
+        if (samp.empty()) throw Error{RCG_ERR_INVALID, "rcg_basis_compress: no delivered solutions are kept"};
+        const int nrhs = c->nrhs;
+        const int m = (int)samp.size() * nrhs, m2 = m + (m & 1);
+        if (r_cap <= 0 || r_cap > rmax) r_cap = rmax;
+        cudaEvent_t e0, e1;
+        RCG_CUDA_TRY(cudaEventCreate(&e0)); RCG_CUDA_TRY(cudaEventCreate(&e1));
+        RCG_CUDA_TRY(cudaEventRecord(e0, st));
+        double *S = c->alloc<double>((size_t)m * ld);
+        double *M = c->alloc<double>((size_t)m2 * m2), *E = c->alloc<double>((size_t)m2 * m2);
+        double *cs = c->alloc<double>((size_t)m2), *red = c->alloc<double>(2);
+        double *Wr = nullptr;
+        try {
+            for (size_t b = 0; b < samp.size(); ++b)
+                for (int j = 0; j < nrhs; ++j)
+                    c->h2d(S + ((long long)b * nrhs + j) * ld, c->solutions[samp[b]].data() + (size_t)j * n, (size_t)n);
+            RCG_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * (size_t)m2 * m2, st));   // odd m: zero last row / column
+            gemm_tn<double, double>(st, n, S, ld, m, S, ld, m, M, m2, false);
+            jacobi_parallel(st, M, m2, m2, E, m2, cs, red, 1e-14, 40);
+            std::vector<double> lam((size_t)m2), Eh((size_t)m2 * m2);
+            RCG_CUDA_TRY(cudaMemcpy2DAsync(lam.data(), sizeof(double), M, sizeof(double) * (m2 + 1), sizeof(double), m2,
+                                           cudaMemcpyDeviceToHost, st));
+            c->d2h(Eh.data(), E, (size_t)m2 * m2);
+            c->sync();
+            std::vector<int> idx((size_t)m2);
+            for (int i = 0; i < m2; ++i) idx[i] = i;
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+            sigma.assign((size_t)m, 0.0);
+            for (int i = 0; i < m; ++i) sigma[i] = std::sqrt(std::max(lam[idx[i]], 0.0));
+            int rn = 0;
+            if (sigma[0] > 0.0)
+                while (rn < m && sigma[rn] > tau * sigma[0]) ++rn;
+            rn = std::min(rn, r_cap);
+            if (rn == 0) throw Error{RCG_ERR_INVALID, "rcg_basis_compress: no singular value above tau sigma_1"};
+            // W_r diag(sigma)^-1 (m x rn), then the new columns into the lane buffers
+            std::vector<double> wr((size_t)m * rn);
+            for (int q = 0; q < rn; ++q)
+                for (int i = 0; i < m; ++i) wr[(size_t)q * m + i] = Eh[(size_t)idx[q] * m2 + i] / sigma[q];
+            Wr = c->alloc<double>((size_t)m * rn);
+            c->h2d(Wr, wr.data(), wr.size());
+            ensure_lanes(rn);
+            gemm_nn<double, double>(st, n, S, ld, m, Wr, m, rn, x64, ld, 1.0, 0.0);
+            // rebuild V (and C_*) from these columns
+            r = 0;
+            gs_sample = -1;
+            au0_valid = false;
+            std::vector<int> cand((size_t)rn), kept;
+            std::vector<double> ratio;
+            for (int q = 0; q < rn; ++q) cand[q] = q;
+            append(cand, 1e-12, -1, kept, ratio);
+            k_u = std::min(k_u, r);
+            RCG_CUDA_TRY(cudaMemsetAsync(sX0, 0, sizeof(double) * rmax * nrhs, st));
+            prod_tn(V, r, X0, nrhs, sX0, rmax);
+            priv.assign(nrhs, std::vector<int>{});
+            priv_seed = priv;
+            r_seed = r;
+        } catch (...) {
+            for (void *q : std::vector<void *>{S, M, E, cs, red, Wr}) c->release(q);
+            cudaEventDestroy(e0); cudaEventDestroy(e1);
+            throw;
+        }
+        RCG_CUDA_TRY(cudaEventRecord(e1, st));
+        c->sync();
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->phase["compress"] = ms;
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+        for (void *q : std::vector<void *>{S, M, E, cs, red, Wr}) c->release(q);
+        return m;
+    }
+
     int solve_all(int s_first, int s_count, rcg_stat *stats) override {
         if (!seeded) throw Error{RCG_ERR_INVALID, "rcg_solve_all before rcg_seed"};
         const int nrhs = c->nrhs;
@@ -1950,6 +2039,18 @@ int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const doub
     return guarded(c, [&]() {
         if (!mu_dev || !Psi_dev || nparam < 0) return fail(c, RCG_ERR_INVALID, "bad rom arguments");
         c->eng->rom_eval(mu_dev, nparam, dmu_dev, Psi_dev, J_dev);
+        return RCG_OK;
+    });
+}
+
+int rcg_basis_compress(rcg_ctx *c, int r_max, double tau, double *sigma, int sigma_len, int *nsnap) {
+    return guarded(c, [&]() {
+        if (!(tau >= 0.0) || sigma_len < 0 || (sigma_len > 0 && !sigma))
+            return fail(c, RCG_ERR_INVALID, "bad compress arguments");
+        std::vector<double> sg;
+        const int m = c->eng->compress(r_max, tau, sg);
+        for (int i = 0; i < std::min(sigma_len, m); ++i) sigma[i] = sg[i];
+        if (nsnap) *nsnap = m;
         return RCG_OK;
     });
 }

@@ -293,6 +293,9 @@ void ordered_drop_chol(cudaStream_t st, const double *M, int a, const double *xn
 void tri_upper_inverse(cudaStream_t st, const double *R, int ldr, int a, double *Ri);
 void lane_inverse(cudaStream_t st, double *gw, const int *kdef, int m, int *info);
 void jacobi_eig(cudaStream_t st, double *A, int lda, int k, double *Q, double *w);
+// parallel cyclic Jacobi (m2 even): eigenvalues on diag(A), eigenvectors in Q; returns sweeps
+int jacobi_parallel(cudaStream_t st, double *A, int lda, int m2, double *Q, int ldq, double *cs, double *red,
+                    double tol, int max_sweeps);
 
 // misc.cu
 void diag_star(cudaStream_t st, const Grid &g, const double *D, double h, double A, double *out);

@@ -8,7 +8,9 @@
 // These run on one CTA (or one CTA per independent system): the matrices
 // are at most a few thousand wide and live in global memory / L2.
 #include "common.cuh"
+#include "../../include/rcg.h"
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <utility>
@@ -350,6 +352,101 @@ __global__ void k_jacobi(double *A, int lda, int k, double *Q, double *w) {
     }
 }
 
+// ---------------------------------------------------------------- parallel Jacobi
+// Cyclic Jacobi for a symmetric m2 x m2 matrix (m2 even), all disjoint pairs of
+// a round at once (round-robin / circle ordering): round t pairs index t with
+// m2 - 1 and (t + k) mod (m2 - 1) with (t - k) mod (m2 - 1), k = 1 .. m2/2 - 1;
+// the m2 - 1 rounds of a sweep meet every pair once.  Each pair's rotation is
+// the symmetric 2 x 2 Schur rotation of Golub and Van Loan (Matrix
+// Computations, Sec. 8.5: "sym.schur2"), which zeroes A(p, q).
+__device__ __forceinline__ void jac_pair(int m2, int t, int k, int &p, int &q) {
+    const int half = m2 - 1;
+    int i, j;
+    if (k == 0) { i = t; j = m2 - 1; }
+    else { i = (t + k) % half; j = (t - k + half) % half; }
+    p = i < j ? i : j;
+    q = i < j ? j : i;
+}
+
+__global__ void k_jac_params(const double *__restrict__ A, int lda, int m2, int t, double *__restrict__ cs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m2 / 2) return;
+    int p, q;
+    jac_pair(m2, t, k, p, q);
+    const double apq = A[p + (long long)q * lda];
+    double c = 1.0, sn = 0.0;
+    if (apq != 0.0) {
+        const double tau = (A[q + (long long)q * lda] - A[p + (long long)p * lda]) / (2.0 * apq);
+        const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        c = 1.0 / sqrt(1.0 + tt * tt);
+        sn = tt * c;
+    }
+    cs[2 * k] = c;
+    cs[2 * k + 1] = sn;
+}
+
+// A <- J^T A J and Q <- Q J for the round's rotations J (block-diagonal in the
+// pairs): one thread per 2 x 2 block (pair a, pair b) of A, read and written in
+// place, then one per (row of Q, pair).
+__global__ void k_jac_apply(double *__restrict__ A, int lda, int m2, int t, const double *__restrict__ cs,
+                            double *__restrict__ Q, int ldq) {
+    const int np = m2 / 2;
+    const long long nb = (long long)np * np, tot = nb + (long long)m2 * np;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < nb) {
+            const int a = (int)(e % np), b = (int)(e / np);
+            int pa, qa, pb, qb;
+            jac_pair(m2, t, a, pa, qa);
+            jac_pair(m2, t, b, pb, qb);
+            const double ca = cs[2 * a], sa = cs[2 * a + 1], cb = cs[2 * b], sb = cs[2 * b + 1];
+            double *a11 = A + pa + (long long)pb * lda, *a12 = A + pa + (long long)qb * lda;
+            double *a21 = A + qa + (long long)pb * lda, *a22 = A + qa + (long long)qb * lda;
+            const double t11 = ca * *a11 - sa * *a21, t12 = ca * *a12 - sa * *a22;   // J_a^T A_ab
+            const double t21 = sa * *a11 + ca * *a21, t22 = sa * *a12 + ca * *a22;
+            *a11 = t11 * cb - t12 * sb;                                              // ... J_b
+            *a12 = t11 * sb + t12 * cb;
+            *a21 = t21 * cb - t22 * sb;
+            *a22 = t21 * sb + t22 * cb;
+        } else {
+            const long long f = e - nb;
+            const int row = (int)(f % m2), b = (int)(f / m2);
+            int pb, qb;
+            jac_pair(m2, t, b, pb, qb);
+            const double cb = cs[2 * b], sb = cs[2 * b + 1];
+            double *qp = Q + row + (long long)pb * ldq, *qq = Q + row + (long long)qb * ldq;
+            const double x = *qp, y = *qq;
+            *qp = x * cb - y * sb;
+            *qq = x * sb + y * cb;
+        }
+    }
+}
+
+// out[0] += sum of squares off the diagonal, out[1] += all squares.
+__global__ void k_jac_offnorm(const double *__restrict__ A, int lda, int m2, double *__restrict__ out) {
+    double off = 0.0, all = 0.0;
+    const long long tot = (long long)m2 * m2;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m2), j = (int)(e / m2);
+        const double v = A[i + (long long)j * lda];
+        all += v * v;
+        if (i != j) off += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_down_sync(0xffffffffu, off, o);
+        all += __shfl_down_sync(0xffffffffu, all, o);
+    }
+    if ((threadIdx.x & 31) == 0) { atomicAdd(out, off); atomicAdd(out + 1, all); }
+}
+
+__global__ void k_eye(double *__restrict__ Q, int ldq, int m2) {
+    const long long tot = (long long)m2 * m2;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x)
+        Q[(e % m2) + (e / m2) * (long long)ldq] = (e % m2 == e / m2) ? 1.0 : 0.0;
+}
+
 }  // namespace
 
 // Shared-memory attribute for the staged kernels (per device ordinal).
@@ -384,6 +481,42 @@ void chol_run(cudaStream_t st, double *A, int lda, long long strideA, int k0, in
         count_launch();
         RCG_CHECK_LAUNCH();
     }
+}
+
+// Eigen-decomposition of the symmetric m2 x m2 matrix A (m2 even; ld lda):
+// on return diag(A) holds the eigenvalues and Q (ld ldq) the eigenvectors.
+// Sweeps until the off-diagonal mass is below tol^2 of the total (at most
+// max_sweeps); cs: m2 doubles, red: 2 doubles of device scratch.  Returns the
+// number of sweeps (host synchronisation once per sweep).
+int jacobi_parallel(cudaStream_t st, double *A, int lda, int m2, double *Q, int ldq, double *cs, double *red,
+                    double tol, int max_sweeps) {
+    if (m2 <= 0) return 0;
+    if (m2 & 1) throw Error{RCG_ERR_INVALID, "jacobi_parallel: odd order"};
+    const long long work = (long long)(m2 / 2) * (m2 / 2) + (long long)m2 * (m2 / 2);
+    const int blocks = (int)std::min<long long>((work + 255) / 256, 4 * 152);
+    const unsigned gsq = (unsigned)std::min<long long>(((long long)m2 * m2 + 255) / 256, 1024);
+    k_eye<<<gsq, 256, 0, st>>>(Q, ldq, m2);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    double h[2];
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        RCG_CUDA_TRY(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
+        k_jac_offnorm<<<gsq, 256, 0, st>>>(A, lda, m2, red);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+        RCG_CUDA_TRY(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
+        RCG_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!(h[0] > tol * tol * h[1])) break;
+        for (int t = 0; t < m2 - 1; ++t) {
+            k_jac_params<<<(m2 / 2 + 127) / 128, 128, 0, st>>>(A, lda, m2, t, cs);
+            k_jac_apply<<<blocks, 256, 0, st>>>(A, lda, m2, t, cs, Q, ldq);
+            count_launch();
+            count_launch();
+        }
+        RCG_CHECK_LAUNCH();
+    }
+    return sweep;
 }
 
 void chol_inplace(cudaStream_t st, double *A, int lda, int r, int *info) {

@@ -31,7 +31,8 @@ EXPORTED = [
     "rcg_options_default", "rcg_create", "rcg_destroy", "rcg_last_error", "rcg_strerror",
     "rcg_set_diffusion", "rcg_set_sources_detectors", "rcg_set_tolerances", "rcg_set_sample",
     "rcg_set_sample_device", "rcg_apply", "rcg_seed", "rcg_reset_to_seed", "rcg_solve_all",
-    "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device", "rcg_rom_eval_batch",
+    "rcg_basis_rank", "rcg_basis_get", "rcg_solution_get", "rcg_rom_eval", "rcg_rom_eval_device",
+    "rcg_rom_eval_batch", "rcg_basis_compress",
     "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
     "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
@@ -96,6 +97,7 @@ def load(path=LIB_PATH):
         "rcg_rom_eval": (I, [P, P, I, P, P, P]),
         "rcg_rom_eval_device": (I, [P, P, I, P, P, P]),
         "rcg_rom_eval_batch": (I, [P, I, P, I, P, P, P]),
+        "rcg_basis_compress": (I, [P, I, C.c_double, P, I, C.POINTER(I)]),
         "rcg_phase_ms": (D, [P, C.c_char_p]),
         "rcg_launch_count": (LL, [P]),
         "rcg_profile_enable": (I, [P, I]),
@@ -334,6 +336,13 @@ class Context:
     def rom_eval_device(self, mu_dev, dmu_dev, Psi_dev, J_dev, nparam):
         return self._check(self.L.rcg_rom_eval_device(self.h, _ptr(mu_dev), nparam, _ptr(dmu_dev),
                                                       _ptr(Psi_dev), _ptr(J_dev)))
+
+    def basis_compress(self, r_max=0, tau=1e-8, sigma_len=1 << 16):
+        """rcg_basis_compress: returns (new rank, singular values of the snapshot matrix)."""
+        sig = np.zeros(sigma_len, dtype=np.float64)
+        m = C.c_int(0)
+        self._check(self.L.rcg_basis_compress(self.h, int(r_max), float(tau), _ptr(sig), sigma_len, C.byref(m)))
+        return self.rank(), sig[: min(m.value, sigma_len)].copy()
 
     def rom_eval_batch_device(self, nq, mu_dev, dmu_dev, Psi_dev, J_dev, nparam):
         """rcg_rom_eval_batch on device arrays (see rcg.h for the layouts)."""

@@ -40,8 +40,9 @@ def gpu_run(name, precision, order, tau, wave_samples=0, k_cap=256, **kw):
     inp = workload(name)
     wl = inp["wl"]
     U0, _, _, _ = oracle_seed_inputs(name)
-    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, precision=precision, order=order, tau_rank=tau,
-                      k_u=wl.k_u, keep_solutions=1, wave_samples=wave_samples, k_cap=k_cap, **kw)
+    opts = dict(k_u=wl.k_u, keep_solutions=1, wave_samples=wave_samples, k_cap=k_cap)
+    opts.update(kw)
+    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, precision=precision, order=order, tau_rank=tau, **opts)
     ctx.set_diffusion(inp["D"])
     ctx.set_sources_detectors(inp["src_ij"], inp["det_ij"])
     ctx.set_tolerances(inp["tol"])
