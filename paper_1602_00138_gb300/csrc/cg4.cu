@@ -128,12 +128,25 @@ k_stencil4(Grid g, const float *__restrict__ D, const float *const *__restrict__
 // ZR-slot shared-memory ring by cp.async two planes ahead, so every p and D
 // value is read from memory about once (halo rows and planes aside) and the
 // six neighbours come from shared memory.  Fused p^T q per lane.
+//
+// Every halo a neighbour read can touch holds zeros: a zero pad float4 at
+// both ends of each slot row (x ghosts), and the rows and planes outside the
+// grid are copied with zero source bytes (y, z ghosts).  A ghost's p is 0, so
+// its coupling term vanishes whatever the weight, and the neighbour reads
+// need no boundary predicates (the ghosts' share of the diagonal is in the
+// precomputed diagonal).
 constexpr int ZR = 4;    // ring slots: planes z-1, z, z+1 in use, z+2 in flight
 constexpr int ZL = 2;    // lanes per CTA (they share the D planes)
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
                  : "memory");
+}
+
+// Shared-memory bytes of k_stencil4z for an x extent of nx4 float4.
+__host__ __device__ constexpr size_t stencil4z_smem(int nx4) {
+    return (size_t)ZR * (ZL + 1) * (kThreads / nx4 + 2) * (nx4 + 2) * sizeof(float4);
 }
 
 __global__ void __launch_bounds__(kThreads, 3)
@@ -141,8 +154,8 @@ k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict_
             const float *const *__restrict__ src, float *const *__restrict__ dst, const int *__restrict__ alist,
             int na, const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ prof,
             int zc) {
-    extern __shared__ float4 ring[];                 // [ZR][ZL + 1][TY + 2][nx4]
-    const int nx4 = g.Nx >> 2, TY = kThreads / nx4, rows = TY + 2;
+    extern __shared__ float4 ring[];                 // [ZR][ZL + 1][TY + 2][nx4 + 2]
+    const int nx4 = g.Nx >> 2, TY = kThreads / nx4, rows = TY + 2, RW = nx4 + 2;
     const int ytiles = (g.Ny + TY - 1) / TY;
     const int yt = blockIdx.x % ytiles, zb = blockIdx.x / ytiles;
     const int y0 = yt * TY, z0 = zb * zc;
@@ -170,14 +183,22 @@ k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict_
         Q[i] = on[i] ? (float4 *)dst[c[i]] : nullptr;
         DG[i] = on[i] ? (const float4 *)diag_of_col[c[i]] : nullptr;
     }
-    const int plane4 = nx4 * rows;                   // float4 per array and slot
-    auto slot = [&](int z) { return ring + (size_t)(z % ZR) * (ZL + 1) * plane4; };
-    // Plane z, rows y0-1 .. y0+TY, of each live array into its slot.  Thread
-    // (tx, ty) copies column tx of slot rows ty, ty + TY, ty + 2 TY, ... (256
-    // threads = TY rows of nx4 float4), walking (array, row) without division.
+    const int plane4 = RW * rows;                    // float4 per array and slot
+    // slot of plane z (z >= -1)
+    auto slot = [&](int z) { return ring + (size_t)((z + ZR) % ZR) * (ZL + 1) * plane4; };
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // zero pads at both ends of every slot row (never written again)
+    for (int e = threadIdx.x; e < ZR * (ZL + 1) * rows; e += kThreads) {
+        ring[(size_t)e * RW] = zero4;
+        ring[(size_t)e * RW + RW - 1] = zero4;
+    }
+    // Plane z, rows y0-1 .. y0+TY, of each array into its slot; rows and
+    // planes outside the grid, and arrays of inactive lanes, as zeros.  Thread
+    // (tx, ty) copies column tx of slot rows ty, ty + TY, ... (256 threads =
+    // TY rows of nx4 float4), walking (array, row) without division.
     auto load_plane = [&](int z) {
         float4 *sl = slot(z);
-        const long long zoff = (long long)z * g.Ny;
+        const bool zin = z >= 0 && z < g.Nz;
         int a = 0, ry = ty;
         for (int R = ty; R < (ZL + 1) * rows; R += TY) {
             const int yy = y0 - 1 + ry;
@@ -185,63 +206,60 @@ k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict_
 #pragma unroll
             for (int i = 0; i < ZL; ++i)
                 if (a == i) base = P[i];
-            if (yy >= 0 && yy < g.Ny && base != nullptr)
-                cp_async16(sl + R * nx4 + tx, (const float4 *)base + (zoff + yy) * nx4 + tx);
+            const bool ok = zin && yy >= 0 && yy < g.Ny && base != nullptr;
+            const float4 *s4 = ok ? (const float4 *)base + ((long long)z * g.Ny + yy) * nx4 + tx : (const float4 *)D;
+            cp_async16(sl + R * RW + 1 + tx, s4, ok ? 16 : 0);
             ry += TY;
             if (ry >= rows) { ry -= rows; ++a; }
         }
     };
+    __syncthreads();                                 // pads before the first cp.async lands beside them
     // prologue: planes z0-1, z0, z0+1 (one cp.async group each)
     for (int q = -1; q <= 1; ++q) {
-        const int z = z0 + q;
-        if (z >= 0 && z < g.Nz && z <= z1) load_plane(z);
+        if (z0 + q <= z1) load_plane(z0 + q);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     const bool yok = y < g.Ny;
-    const long long row4 = (long long)nx4 * g.Ny;    // float4 per plane in memory
+    const int row4 = nx4 * g.Ny;                     // float4 per plane in memory
     float4 dgc[ZL], dgn[ZL];
 #pragma unroll
     for (int i = 0; i < ZL; ++i)
-        dgc[i] = (on[i] && yok) ? DG[i][(long long)z0 * row4 + (long long)y * nx4 + tx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dgc[i] = (on[i] && yok) ? DG[i][(long long)z0 * row4 + y * nx4 + tx] : zero4;
     float acc[ZL];
 #pragma unroll
     for (int i = 0; i < ZL; ++i) acc[i] = 0.f;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int rc = (ty + 1) * RW + 1 + tx, dof = ZL * plane4;
     for (int z = z0; z < z1; ++z) {
-        if (z + 2 <= z1 && z + 2 < g.Nz) load_plane(z + 2);
+        if (z + 2 <= z1) load_plane(z + 2);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        const long long v = (long long)z * row4 + (long long)y * nx4 + tx;
+        const long long v = (long long)z * row4 + y * nx4 + tx;
 #pragma unroll
         for (int i = 0; i < ZL; ++i)
             dgn[i] = (on[i] && yok && z + 1 < z1) ? DG[i][v + row4] : zero4;
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();
         if (yok) {
-            const float4 *cs = slot(z), *ms = slot(z + ZR - 1), *ps = slot(z + 1);
-            const int rc = (ty + 1) * nx4 + tx, dof = ZL * plane4;
-            const bool xl = tx > 0, xr = tx < nx4 - 1, ym = y > 0, yp = y < g.Ny - 1, zm = z > 0,
-                       zp = z < g.Nz - 1;
+            const float4 *cs = slot(z), *ms = slot(z - 1), *ps = slot(z + 1);
             const float4 Dc = cs[dof + rc];
-            const float Dl = xl ? cs[dof + rc - 1].w : 0.f, Dr = xr ? cs[dof + rc + 1].x : 0.f;
-            const float4 Dym = ym ? cs[dof + rc - nx4] : zero4, Dyp = yp ? cs[dof + rc + nx4] : zero4;
-            const float4 Dzm = zm ? ms[dof + rc] : zero4, Dzp = zp ? ps[dof + rc] : zero4;
-            // face weights (zero where the neighbour is a ghost or eliminated)
-            const float wl = xl ? 0.5f * (Dc.x + Dl) : 0.f, wr = xr ? 0.5f * (Dc.w + Dr) : 0.f;
+            const float Dl = cs[dof + rc - 1].w, Dr = cs[dof + rc + 1].x;
+            const float4 Dym = cs[dof + rc - RW], Dyp = cs[dof + rc + RW];
+            const float4 Dzm = ms[dof + rc], Dzp = ps[dof + rc];
+            // face weights (D_p + D_q) / 2; towards a ghost they meet p = 0
+            const float wl = 0.5f * (Dc.x + Dl), wr = 0.5f * (Dc.w + Dr);
             const float w01 = 0.5f * (Dc.x + Dc.y), w12 = 0.5f * (Dc.y + Dc.z), w23 = 0.5f * (Dc.z + Dc.w);
-            auto fw = [&](bool on_, const float4 Dn) {
-                return on_ ? make_float4(0.5f * (Dc.x + Dn.x), 0.5f * (Dc.y + Dn.y), 0.5f * (Dc.z + Dn.z),
-                                         0.5f * (Dc.w + Dn.w))
-                           : zero4;
+            auto fw = [&](const float4 Dn) {
+                return make_float4(0.5f * (Dc.x + Dn.x), 0.5f * (Dc.y + Dn.y), 0.5f * (Dc.z + Dn.z),
+                                   0.5f * (Dc.w + Dn.w));
             };
-            const float4 wym = fw(ym, Dym), wyp = fw(yp, Dyp), wzm = fw(zm, Dzm), wzp = fw(zp, Dzp);
+            const float4 wym = fw(Dym), wyp = fw(Dyp), wzm = fw(Dzm), wzp = fw(Dzp);
 #pragma unroll
             for (int i = 0; i < ZL; ++i) {
                 if (!on[i]) continue;
                 const int po = i * plane4;
                 const float4 xc = cs[po + rc];
-                const float xlv = xl ? cs[po + rc - 1].w : 0.f, xrv = xr ? cs[po + rc + 1].x : 0.f;
-                const float4 xym = ym ? cs[po + rc - nx4] : zero4, xyp = yp ? cs[po + rc + nx4] : zero4;
-                const float4 xzm = zm ? ms[po + rc] : zero4, xzp = zp ? ps[po + rc] : zero4;
+                const float xlv = cs[po + rc - 1].w, xrv = cs[po + rc + 1].x;
+                const float4 xym = cs[po + rc - RW], xyp = cs[po + rc + RW];
+                const float4 xzm = ms[po + rc], xzp = ps[po + rc];
                 const float4 dg = dgc[i];
                 float4 o;
                 o.x = dg.x * xc.x - (wl * xlv + w01 * xc.y) - (wym.x * xym.x + wyp.x * xyp.x) - (wzm.x * xzm.x + wzp.x * xzp.x);
@@ -840,7 +858,7 @@ bool cg4_supported(const Grid &g) { return (g.Nx % 4) == 0 && (g.ld % 4) == 0; }
 bool stencil4z_supported(const Grid &g) {
     const int nx4 = g.Nx / 4;
     return g.Ny > 1 && (g.Nx % 4) == 0 && nx4 >= 1 && nx4 <= kThreads && kThreads % nx4 == 0 &&
-           (size_t)ZR * (ZL + 1) * (kThreads / nx4 + 2) * nx4 * sizeof(float4) <= 160 * 1024;
+           stencil4z_smem(nx4) <= 160 * 1024 && g.n < (1LL << 31);
 }
 
 // One float32 iteration t over the active lanes (see the file comment).
@@ -863,7 +881,7 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         if (nzc < 1) nzc = 1;
         const int zc = (int)((g.Nz + nzc - 1) / nzc);
         nzc = (g.Nz + zc - 1) / zc;
-        const size_t smem = (size_t)ZR * (ZL + 1) * (TY + 2) * nx4 * sizeof(float4);
+        const size_t smem = stencil4z_smem(nx4);
         static bool attr[64] = {};
         int dev = 0;
         RCG_CUDA_TRY(cudaGetDevice(&dev));
