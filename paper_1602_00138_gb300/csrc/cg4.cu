@@ -467,9 +467,9 @@ k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_la
         }
     };
     const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
-    float acc[KUT];
+    float acc[KUT], acc2[KUT];                     // lanes tl mod 16 and tl mod 16 + 16
 #pragma unroll
-    for (int c = 0; c < KUT; ++c) acc[c] = 0.f;
+    for (int c = 0; c < KUT; ++c) { acc[c] = 0.f; acc2[c] = 0.f; }
     for (int q = 0; q < 2; ++q) {
         if (q < nst) issue(q);
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -479,31 +479,42 @@ k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_la
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 2;" ::: "memory");
         __syncthreads();
-        if (tl < cnt) {
+        {
+            // thread (warp w, tl): lanes la = tl mod 16 and la + 16, float4 4w + 2 (tl / 16) + {0, 1};
+            // each U_0 float4 read serves both lanes
             const float4 *stg = u0s + (size_t)(s % U0_NST) * STG;
+            const int la = tl & 15, vb = warp * 4 + 2 * (tl >> 4);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int v4 = warp * 4 + j;
-                const float4 rv = stg[tl * RP + v4];
+            for (int j = 0; j < 2; ++j) {
+                const int v4 = vb + j;
+                const float4 r0 = stg[la * RP + v4], r1 = stg[(la + 16) * RP + v4];
 #pragma unroll
-                for (int c = 0; c < KUT; ++c) acc[c] += dot4(stg[TILE * RP + c * SN4 + v4], rv);
+                for (int c = 0; c < KUT; ++c) {
+                    const float4 u = stg[TILE * RP + c * SN4 + v4];
+                    acc[c] = fmaf(u.x, r0.x, fmaf(u.y, r0.y, fmaf(u.z, r0.z, fmaf(u.w, r0.w, acc[c]))));
+                    acc2[c] = fmaf(u.x, r1.x, fmaf(u.y, r1.y, fmaf(u.z, r1.z, fmaf(u.w, r1.w, acc2[c]))));
+                }
             }
         }
         __syncthreads();
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    // sum the eight warps' partials: red[w][c][l]
+    // sum the partials: red[h][w][c][l], h = half-warp (tl / 16), lane l = tl mod 16 (+16 for acc2)
     float *red = (float *)u0s;
+    const int h = tl >> 4, la = tl & 15;
 #pragma unroll
-    for (int c = 0; c < KUT; ++c) red[(warp * KUT + c) * TILE + tl] = acc[c];
+    for (int c = 0; c < KUT; ++c) {
+        red[((h * (kThreads / 32) + warp) * KUT + c) * TILE + la] = acc[c];
+        red[((h * (kThreads / 32) + warp) * KUT + c) * TILE + la + 16] = acc2[c];
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < KUT * TILE; e += kThreads) {
         const int c = e / TILE, l = e % TILE;
         if (l < cnt && c < ku) {
             float v = 0.f;
 #pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) v += red[(w * KUT + c) * TILE + l];
+            for (int w = 0; w < 2 * (kThreads / 32); ++w) v += red[(w * KUT + c) * TILE + l];
             atomicAdd(ls.wv + ((long long)sw * ls.m + lanes[l]) * KMAX + c, (double)v);
         }
     }
