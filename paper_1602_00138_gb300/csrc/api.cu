@@ -411,7 +411,8 @@ struct Engine : EngineBase {
         c->h2d(d_ptrC, hg.data(), cnt);
         apply_op<T>(st, g, D, (const T *const *)d_ptrC, (const T *const *)d_ptrA, (T *const *)d_ptrB, cnt, nullptr,
                     nullptr);
-        c->sync();   // the pointer scratch is reused by the next call
+        // no synchronisation: the next call's copies into the pointer scratch
+        // follow this kernel on the stream
     }
 
     // float64 scratch for the new basis columns and their images
@@ -438,7 +439,6 @@ struct Engine : EngineBase {
         c->h2d(d_ptrC, hg.data(), cnt);
         apply_op<double>(st, g, c->D64, (const double *const *)d_ptrC, (const double *const *)d_ptrA,
                          (double *const *)d_ptrB, cnt, nullptr, nullptr);
-        c->sync();
     }
 
     // Out = V Y (+ beta Out) with float64 accuracy: V is float64 in RCG_FP64; in
@@ -501,7 +501,7 @@ struct Engine : EngineBase {
     }
 
     // G = C_* + V^T diag(h^2 (mu_s - mu_*)) V (r x r) and its Cholesky factor L.
-    void galerkin(int s, double *G, double *L) {
+    void galerkin(int s, double *G, double *L, bool reset_info = true) {
         RCG_CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * rmax, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
         if (s != s_star) {
@@ -510,11 +510,13 @@ struct Engine : EngineBase {
         }
         RCG_CUDA_TRY(cudaMemcpy2DAsync(L, sizeof(double) * rmax, G, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+        if (reset_info) RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
         chol_inplace(st, L, rmax, r, d_info);
     }
 
-    std::pair<double *, double *> galerkin_for(int s, bool seq) {
+    // check: false leaves the factorisation's status in d_info for one
+    // check_info after several samples (the wave order)
+    std::pair<double *, double *> galerkin_for(int s, bool seq, bool check = true) {
         if (seq) {
             if (gs_sample != s || gs_r != r) {
                 galerkin(s, Gs, Ls);
@@ -525,8 +527,8 @@ struct Engine : EngineBase {
             return {Gs, Ls};
         }
         if (!Gw[s]) { Gw[s] = c->alloc<double>((size_t)rmax * rmax); Lw[s] = c->alloc<double>((size_t)rmax * rmax); }
-        galerkin(s, Gw[s], Lw[s]);
-        check_info("Galerkin matrix V^T A V");
+        galerkin(s, Gw[s], Lw[s], check);
+        if (check) check_info("Galerkin matrix V^T A V");
         return {Gw[s], Lw[s]};
     }
 
@@ -642,10 +644,13 @@ struct Engine : EngineBase {
         grp_begin.push_back(m);
         std::map<int, std::pair<double *, double *>> gal;
         if (r > 0) {
+            // wave order: all samples' matrices and factors, then one status check
+            if (!seq) RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
             for (size_t gi = 0; gi + 1 < grp_begin.size(); ++gi) {
                 const int s = samp[grp_begin[gi]];
-                if (!gal.count(s)) gal[s] = galerkin_for(s, seq);
+                if (!gal.count(s)) gal[s] = galerkin_for(s, seq, seq);
             }
+            if (!seq) check_info("Galerkin matrix V^T A V");
         }
         const T *Vc = V;
         auto project = [&](bool first) {
@@ -810,10 +815,12 @@ struct Engine : EngineBase {
                     adst.push_back(awp + ((long long)l * kps + q) * ld);
                     asamp.push_back(samp[l]);
                 }
-            if (!psrc.empty()) {
-                for (size_t i = 0; i < psrc.size(); ++i)
-                    RCG_CUDA_TRY(cudaMemcpyAsync(pdst[i], psrc[i], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
-                c->sync();
+            if (!psrc.empty()) {            // one gather launch (stream-ordered before apply_cols reuses the scratch)
+                const int cnt = (int)psrc.size();
+                ensure_ptr(cnt);
+                c->h2d(d_ptrA, (const void **)psrc.data(), cnt);
+                c->h2d(d_ptrB, (const void **)pdst.data(), cnt);
+                copy_cols<T>(st, n, (const T *const *)d_ptrA, (T *const *)d_ptrB, cnt);
             }
             // the network's column x_hat in slot kp[l] of the lane, then A~ x_hat with the others
             std::vector<int> aug_l;

@@ -237,6 +237,10 @@ void gemm_tn_df(cudaStream_t st, long long n, const float *A, long long lda, int
 // X_q = X + q r ns, Z_q = Z + q r nd, ld r; J_qk = J + (q nparam + k) nd ns)
 void rom_jac(cudaStream_t st, int r, int nparam, const double *G, const double *X, int ns, const double *Z, int nd,
              double *J, int nq = 1);
+// dst[c] <- src[c] (n elements) for c < cnt, one launch (device pointer lists;
+// 16-byte aligned columns)
+template <typename T>
+void copy_cols(cudaStream_t st, long long n, const T *const *src, T *const *dst, int cnt);
 // Psi_q = Crm^T X_q (nd x ns) for q < nq (Crm r x nd, X_q = X + q r ns, ld r)
 void rom_psi(cudaStream_t st, int r, int nq, const double *Crm, const double *X, int ns, int nd, double *Psi);
 template <typename TA, typename TB, typename AT>

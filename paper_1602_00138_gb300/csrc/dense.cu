@@ -392,6 +392,23 @@ k_rom_psi(int r, const double *__restrict__ Crm, const double *__restrict__ X, i
     }
 }
 
+// dst[c][0 .. n) = src[c][0 .. n) for c = blockIdx.y (columns 16-byte aligned
+// when vec4: float4 body, scalar tail).
+template <typename T>
+__global__ void k_copy_cols(long long n, const T *const *__restrict__ src, T *const *__restrict__ dst, int vec4) {
+    const T *s = src[blockIdx.y];
+    T *d = dst[blockIdx.y];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long p0 = 0;
+    if (vec4 && sizeof(T) == 4) {
+        const long long n4 = n >> 2;
+        for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += stride)
+            ((float4 *)d)[v] = ((const float4 *)s)[v];
+        p0 = n4 << 2;
+    }
+    for (long long p = p0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) d[p] = s[p];
+}
+
 int blocks_for(long long n, int per_col_cols) {
     long long b = (n + 255) / 256;
     long long cap = (long long)(4 * 152) / (per_col_cols > 0 ? per_col_cols : 1);
@@ -401,6 +418,19 @@ int blocks_for(long long n, int per_col_cols) {
 }
 
 }  // namespace
+
+template <typename T>
+void copy_cols(cudaStream_t st, long long n, const T *const *src, T *const *dst, int cnt) {
+    if (cnt <= 0 || n <= 0) return;
+    const long long units = sizeof(T) == 4 ? (n + 3) / 4 : n;
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((units + 255) / 256,
+                                                                             std::max(1, 8 * 152 / cnt)));
+    k_copy_cols<T><<<dim3(gx, cnt), 256, 0, st>>>(n, src, dst, 1);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+template void copy_cols<float>(cudaStream_t, long long, const float *const *, float *const *, int);
+template void copy_cols<double>(cudaStream_t, long long, const double *const *, double *const *, int);
 
 void rom_psi(cudaStream_t st, int r, int nq, const double *Crm, const double *X, int ns, int nd, double *Psi) {
     if (r <= 0 || nq <= 0 || ns <= 0 || nd <= 0) return;

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(1024) k_chol(double *A, int lda, int k0, int r
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && info) *info = fail;
+    if (threadIdx.x == 0 && info && fail) atomicMax(info, fail);
 }
 
 // The same factorisation with the lower triangle staged in shared memory
