@@ -38,7 +38,7 @@ CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0, learned=1)
 MIXED_PLAIN = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0)          # the same without the network
 NTRAIN, EPOCHS, BATCH, LR = 8, 40, 16, 1e-3     # training solves (held-out parameter points), Adam schedule
 MAX_TRAIN = 32
-BASELINE = dict(precision=0, order=0, tau_rank=1e-12)                    # FP64, paper order
+FP64_PAPER = dict(precision=0, order=0, tau_rank=1e-12)                  # FP64, paper order
 ORACLE_RHS = (0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39)    # CPU sample: 8 src + 8 det
 ORACLE_SAMPLES = (1, 2)
 
@@ -450,7 +450,7 @@ def run_ours(args, rank, world, torch):
     # ---- plain FP64 recycled CG in the paper's order, same library and inputs
     base = None
     if not args.no_baseline and rank == 0:
-        ctx_b, _, seed_b = prepare(BASELINE)
+        ctx_b, _, seed_b = prepare(FP64_PAPER)
         ms_b, _, stats_b, _ = timed(ctx_b, 1, 1)
         base = {"value": round(solves_per_step / (ms_b / 1e3), 2), "unit": "solves/s",
                 "ms_per_step": round(ms_b, 1), "rank_V": ctx_b.rank(),
