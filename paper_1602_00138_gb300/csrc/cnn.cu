@@ -390,11 +390,23 @@ k_aug_dots(long long n, long long ld, const float *__restrict__ V, int ku, const
     }
     __syncthreads();
     const float *__restrict__ y = awp + ((long long)l * kps + kpl) * ld;
+    // chunk is a multiple of 4 and every column starts 16-byte aligned: float4
+    // loads up to the last full group of four, scalar loads for a ragged end
     const long long r0 = (long long)blockIdx.x * chunk, r1 = min(r0 + chunk, n);
+    const long long r4 = r0 + ((r1 - r0) & ~3LL);
     float acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
-    for (long long p = r0 + threadIdx.x; p < r1; p += blockDim.x) {
+    for (long long p = r0 + 4 * (long long)threadIdx.x; p < r4; p += 4 * (long long)blockDim.x) {
+        const float4 yv = *(const float4 *)(y + p);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (q < nq) {
+                const float4 w = *(const float4 *)(cols[q] + p);
+                acc[q] = fmaf(yv.x, w.x, fmaf(yv.y, w.y, fmaf(yv.z, w.z, fmaf(yv.w, w.w, acc[q]))));
+            }
+    }
+    for (long long p = r4 + threadIdx.x; p < r1; p += blockDim.x) {
         const float yv = y[p];
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -743,9 +755,12 @@ void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku
               const float *awp, int kps, const int *kp, const int *alist, int na, double *cd) {
     if (na <= 0) return;
     RCG_CUDA_TRY(cudaMemsetAsync(cd, 0, sizeof(double) * (size_t)na * (KMAX + 1), st));
-    // chunks of ~8192 nodes: thousands of CTAs over the lanes
+    // chunks of ~8192 nodes (a multiple of 4): thousands of CTAs over the lanes
     long long z = std::max<long long>(1, (n + 8191) / 8192);
-    const long long chunk = (n + z - 1) / z;
+    long long chunk = (n + z - 1) / z;
+    chunk = (chunk + 3) / 4 * 4;
+    z = (n + chunk - 1) / chunk;
+    if (ld % 4 != 0) throw Error{RCG_ERR_INVALID, "aug_dots: leading dimension not a multiple of 4"};
     k_aug_dots<<<dim3((unsigned)z, (unsigned)na), 256, 0, st>>>(n, ld, V, ku, wpb, awp, kps, kp, alist, cd, chunk);
     count_launch();
     RCG_CHECK_LAUNCH();
