@@ -231,8 +231,9 @@ int rcg_basis_get(rcg_ctx *c, double *V);
  * rcg_reset_to_seed returns to the compressed basis.  sigma (host, may be
  * NULL): the first min(sigma_len, m) singular values, descending; nsnap (may
  * be NULL): m, the number of columns of S.  RCG_ERR_INVALID before rcg_seed,
- * without kept solutions, for tau < 0, or if no singular value exceeds
- * tau sigma_1 (V is unchanged then). */
+ * without kept solutions, for tau < 0, for m > RCG_COMPRESS_MAX_COLS, or if
+ * no singular value exceeds tau sigma_1 (V is unchanged then). */
+#define RCG_COMPRESS_MAX_COLS 4096
 int rcg_basis_compress(rcg_ctx *c, int r_max, double tau, double *sigma, int sigma_len, int *nsnap);
 
 /* Delivered solutions of sample s (host, n x nrhs float64) from the last

@@ -1225,6 +1225,9 @@ struct Engine : EngineBase {
         if (samp.empty()) throw Error{RCG_ERR_INVALID, "rcg_basis_compress: no delivered solutions are kept"};
         const int nrhs = c->nrhs;
         const int m = (int)samp.size() * nrhs, m2 = m + (m & 1);
+        // the Gram eigensolver costs O(m^3) float64 operations per sweep (~4 s at m = 4096)
+        if (m > RCG_COMPRESS_MAX_COLS)
+            throw Error{RCG_ERR_INVALID, "rcg_basis_compress: more than RCG_COMPRESS_MAX_COLS snapshot columns kept"};
         if (r_cap <= 0 || r_cap > rmax) r_cap = rmax;
         cudaEvent_t e0, e1;
         RCG_CUDA_TRY(cudaEventCreate(&e0)); RCG_CUDA_TRY(cudaEventCreate(&e1));

@@ -39,6 +39,7 @@ EXPORTED = [
     "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load", "rcg_gemm_nn_f32",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
+RCG_COMPRESS_MAX_COLS = 4096
 
 
 class Grid(C.Structure):

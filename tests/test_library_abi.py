@@ -45,3 +45,15 @@ def test_host_only_entry_points(lib):
     bad = rcg.Grid(3, 10, -1.0)
     assert lib.rcg_create(C.byref(h), C.byref(bad), None, None) == rcg.RCG_ERR_INVALID
     assert lib.rcg_launch_count(None) == -1
+
+
+def test_header_constants_match_the_binding():
+    """Every RCG_* integer constant of include/rcg.h that the binding mirrors has the same value."""
+    from paper_1602_00138_gb300 import rcg
+    txt = open(os.path.join(ROOT, "include", "rcg.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(RCG_[A-Z_0-9]+)\s+(-?\d+)", txt)}
+    mirrored = [k for k in defs if hasattr(rcg, k)]
+    assert {"RCG_OK", "RCG_ERR_INVALID", "RCG_MIXED", "RCG_WAVE", "RCG_NOALLOC_MAX_COLS",
+            "RCG_COMPRESS_MAX_COLS"} <= set(mirrored)
+    for k in mirrored:
+        assert getattr(rcg, k) == defs[k], k
