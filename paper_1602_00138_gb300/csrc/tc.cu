@@ -154,15 +154,19 @@ __device__ __forceinline__ void prefetch_w(const double *wt, long long k0, long 
 // 32 float64 weights in shared memory) every value is first scaled by its
 // row's weight.  16-byte chunk o of the tile holds rows 4 c .. 4 c + 3 with
 // c = ((o / 16) mod 8) xor (m mod 8), m = o / 128 (the 128-byte swizzle).
-__device__ __forceinline__ void split_tile(char *hi, char *lo, const double *w = nullptr, double wscale = 1.0) {
+// WEIGHTED is a template argument so that the unweighted split carries no
+// weight arithmetic at all (not even predicated off); the scale multiplies in
+// float32 ((float)w * 1.0f == (float)w exactly).
+template <bool WEIGHTED>
+__device__ __forceinline__ void split_tile(char *hi, char *lo, const double *w = nullptr, float wscale = 1.f) {
 #pragma unroll
     for (int it = 0; it < TILE_BYTES / 16 / NTHR; ++it) {
         const int o = (threadIdx.x + it * NTHR) * 16;
         float4 v = *(const float4 *)(hi + o);
-        if (w) {
+        if constexpr (WEIGHTED) {
             const int m = o >> 7, c = ((o >> 4) & 7) ^ (m & 7);
-            v.x *= (float)(wscale * w[4 * c]); v.y *= (float)(wscale * w[4 * c + 1]);
-            v.z *= (float)(wscale * w[4 * c + 2]); v.w *= (float)(wscale * w[4 * c + 3]);
+            v.x *= (float)w[4 * c] * wscale; v.y *= (float)w[4 * c + 1] * wscale;
+            v.z *= (float)w[4 * c + 2] * wscale; v.w *= (float)w[4 * c + 3] * wscale;
         }
         float4 h, l;
         h.x = rn_tf32(v.x); h.y = rn_tf32(v.y); h.z = rn_tf32(v.z); h.w = rn_tf32(v.w);
@@ -293,9 +297,12 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
         asm volatile("cp.async.wait_group 1;" ::: "memory");      // step ks has landed (own copies)
         __syncthreads();                                           // ... everyone's; s_ok is uniform here
         if (!s_ok) { ok = false; break; }
-        split_tile(stg, stg + 2 * TILE_BYTES,                      // A hi | A lo (weighted rows)
-                   wt ? (const double *)(wsm + (int)(ks % NSTAGE) * WBYTES) : nullptr, wscale);
-        split_tile(stg + TILE_BYTES, stg + 3 * TILE_BYTES);        // B hi | B lo
+        if (wt)                                                    // A hi | A lo (weighted rows)
+            split_tile<true>(stg, stg + 2 * TILE_BYTES, (const double *)(wsm + (int)(ks % NSTAGE) * WBYTES),
+                             (float)wscale);
+        else
+            split_tile<false>(stg, stg + 2 * TILE_BYTES);
+        split_tile<false>(stg + TILE_BYTES, stg + 3 * TILE_BYTES); // B hi | B lo
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
