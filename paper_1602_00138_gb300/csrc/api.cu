@@ -2070,7 +2070,16 @@ int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, con
     return guarded(c, [&]() {
         if (nq < 0 || nparam < 0 || (nq > 0 && (!mu_dev || !Psi_dev)) || (J_dev && !dmu_dev))
             return fail(c, RCG_ERR_INVALID, "bad rom batch arguments");
-        c->eng->rom_eval_batch(nq, mu_dev, nparam, dmu_dev, Psi_dev, J_dev);
+        // chunks of points: bounded workspace (per point r x r matrices and n weights,
+        // per point and parameter a Gram) and grid dimensions
+        constexpr int CHUNK = 256;
+        const long long n = c->n, nd_ns = (long long)c->ndet * c->nsrc;
+        for (int q0 = 0; q0 < nq; q0 += CHUNK) {
+            const int m = std::min(CHUNK, nq - q0);
+            c->eng->rom_eval_batch(m, mu_dev + (long long)q0 * n, nparam,
+                                   dmu_dev ? dmu_dev + (long long)q0 * nparam * n : nullptr, Psi_dev + q0 * nd_ns,
+                                   J_dev ? J_dev + (long long)q0 * nparam * nd_ns : nullptr);
+        }
         return RCG_OK;
     });
 }

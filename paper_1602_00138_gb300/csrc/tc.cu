@@ -756,16 +756,22 @@ void tc_gram_w_batched(cudaStream_t st, long long n, const float *A, long long l
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     const unsigned tx = (unsigned)((ka + TM - 1) / TM);
-    dim3 grid(tx, tx, (unsigned)(zper * nbatch));
-    k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, A, lda, ka, 1, scratch, 1, err, wt, blist, bcount, zper, ldw,
-                                         ldl, wscale);
-    count_launch();
-    RCG_CHECK_LAUNCH();
-    const long long tot = (long long)ka * ka * nbatch;
-    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-    k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, zper, ka, ka, 1, C, ldc, accumulate ? 1 : 0, bcount, nbatch, ldcb);
-    count_launch();
-    RCG_CHECK_LAUNCH();
+    // grid z holds zper slices per batch and may not exceed 65535: chunks of batches
+    const int bmax = std::max(1, 65535 / zper);
+    for (int b0 = 0; b0 < nbatch; b0 += bmax) {
+        const int nb = std::min(bmax, nbatch - b0);
+        dim3 grid(tx, tx, (unsigned)(zper * nb));
+        k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, A, lda, ka, 1, scratch, 1, err, wt + b0 * ldw,
+                                             blist + b0 * ldl, bcount + b0, zper, ldw, ldl, wscale);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+        const long long tot = (long long)ka * ka * nb;
+        const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+        k_tc_reduce<<<blocks, 256, 0, st>>>(scratch, zper, ka, ka, 1, C + b0 * ldcb, ldc, accumulate ? 1 : 0,
+                                            bcount + b0, nb, ldcb);
+        count_launch();
+        RCG_CHECK_LAUNCH();
+    }
 }
 
 // Prepared-B float32 scratch of tc_gemm_nn: 2 m ldb floats, ldb = k rounded up to 32.
