@@ -290,8 +290,9 @@ int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const doub
  * or NULL, Psi_dev nq x ndet x nsrc (point q as in rcg_rom_eval at
  * Psi_dev + q ndet nsrc), J_dev nq x nparam x ndet x nsrc or NULL (needs
  * dmu_dev).  Each point's values equal rcg_rom_eval's at that point up to
- * rounding.  The caller owns every array; the call returns after the results
- * are written.  RCG_ERR_INVALID for nq < 0, missing arrays or an empty basis,
+ * rounding.  The points are processed in chunks of 256 (bounded workspace).
+ * The caller owns every array; the call returns after the results are
+ * written.  RCG_ERR_INVALID for nq < 0, missing arrays or an empty basis,
  * RCG_ERR_NOT_SPD if a reduced matrix is not positive definite. */
 int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, const double *dmu_dev,
                        double *Psi_dev, double *J_dev);
