@@ -136,6 +136,15 @@ def make_ctx(rcg, inp, opts, torch, device_inputs=True):
     return ctx
 
 
+def workload_config(name):
+    """The workload part of the JSON line's config, the same for both arms."""
+    from synthetic.phantom import WORKLOADS
+    wl = WORKLOADS[name]
+    return {"workload": name, "grid": f"{wl.dim}D {wl.N}^{wl.dim} ({wl.n} unknowns)",
+            "rhs": f"{wl.nsrc} sources + {wl.ndet} detectors", "samples": wl.K,
+            "solves_per_step": wl.K * wl.nrhs, "tol": wl.tol[0]}
+
+
 def replica_value(torch, ms_local, world, solves_per_step, steps, dev):
     """Whole-job throughput of N independent replicas (the path does not shard:
     every rank solves the whole workload): the slowest rank's time over the
@@ -559,11 +568,13 @@ def main():
         if rank != 0:
             return
         res = run_oracle_subprocess(args, steps=args.steps, warmup=args.warmup)
+        secs = res.get("seconds")
         line = {"impl": "reference", "metric": METRIC, "value": res.get("value"), "unit": "solves/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1e3 * secs / max(args.steps, 1), 3) if secs else None,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": args.workload, "order": "sequential",
-                                                "precision": "f64 (CPU oracle)"},
+                "data": "synthetic", "config": dict(workload_config(args.workload), order="sequential",
+                                                    precision="f64 (CPU oracle)"),
                 "cpu_baseline": {k: res.get(k) for k in ("value", "unit", "cores", "kind", "sample")},
                 "e2e": {"value": res.get("value"), "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -596,10 +607,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload,
-                       "grid": f"{wl.dim}D {wl.N}^{wl.dim} ({wl.n} unknowns)",
-                       "rhs": f"{wl.nsrc} sources + {wl.ndet} detectors", "samples": wl.K,
-                       "solves_per_step": res["solves_per_step"], "tol": wl.tol[0],
+            "config": {**workload_config(args.workload),
                        "precision": "f32 inner CG / stencil / basis, f64 refinement residuals, "
                                     "Galerkin matrices and decisions",
                        "order": "wave (all samples and RHS in one batch)", "tau_rank": CONTENDER["tau_rank"],
