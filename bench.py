@@ -553,6 +553,38 @@ def products_bench(torch, nshapes):
         del X
 
 
+def contender_line(args, world, res, cpu):
+    """The JSON line of this library's arm from the measured results `res`."""
+    from synthetic.phantom import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    return {
+        "metric": METRIC, "value": round(res["value"], 2), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {**workload_config(args.workload),
+                   "precision": "f32 inner CG / stencil / basis, f64 refinement residuals, "
+                                "Galerkin matrices and decisions",
+                   "order": "wave (all samples and RHS in one batch)", "tau_rank": CONTENDER["tau_rank"],
+                   "learned": True, "learning": res["learn"],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": f"working set > L2 ({res['solves_per_step']} lanes x {wl.n} nodes x 24 B = "
+                         f"{res['solves_per_step'] * wl.n * 24 / 1e9:.1f} GB)",
+                   "rank_V_after_step": res["rank_V"], "mean_cg_iters": res["mean_iters"],
+                   "phases_ms_last_step": {k: round(v, 2) for k, v in res["phases"].items()},
+                   "seed_s_untimed": round(res["seed_s"], 3)},
+        "roofline": res["roofline"],
+        "cpu_baseline": cpu,
+        "e2e": res["e2e"],
+        "clocks": res["clocks"],
+        "gpu_launches": res["launches"],
+        "baseline_fp64_sequential": res["base"],
+        "mixed_without_learning": res["nolearn"],
+        "rom_sweep": res.get("rom_sweep"),
+        "alg1_vs_alg2": res.get("alg1"),
+    }
+
+
 def main():
     args = parse_args()
     if args.products:
@@ -600,34 +632,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu and not args.ncu_region:
         cpu = run_oracle_subprocess(args)
     if rank == 0:
-        from synthetic.phantom import WORKLOADS
-        wl = WORKLOADS[args.workload]
-        line = {
-            "metric": METRIC, "value": round(res["value"], 2), "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {**workload_config(args.workload),
-                       "precision": "f32 inner CG / stencil / basis, f64 refinement residuals, "
-                                    "Galerkin matrices and decisions",
-                       "order": "wave (all samples and RHS in one batch)", "tau_rank": CONTENDER["tau_rank"],
-                       "learned": True, "learning": res["learn"],
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": f"working set > L2 ({res['solves_per_step']} lanes x {wl.n} nodes x 24 B = "
-                             f"{res['solves_per_step'] * wl.n * 24 / 1e9:.1f} GB)",
-                       "rank_V_after_step": res["rank_V"], "mean_cg_iters": res["mean_iters"],
-                       "phases_ms_last_step": {k: round(v, 2) for k, v in res["phases"].items()},
-                       "seed_s_untimed": round(res["seed_s"], 3)},
-            "roofline": res["roofline"],
-            "cpu_baseline": cpu,
-            "e2e": res["e2e"],
-            "clocks": res["clocks"],
-            "gpu_launches": res["launches"],
-            "baseline_fp64_sequential": res["base"],
-            "mixed_without_learning": res["nolearn"],
-            "rom_sweep": res.get("rom_sweep"),
-            "alg1_vs_alg2": res.get("alg1"),
-        }
+        line = contender_line(args, world, res, cpu)
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -24,3 +24,29 @@ def test_reference_line_has_the_contract_keys():
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_contender_line_has_the_contract_keys():
+    """The GPU arm's JSON line, built from a synthetic result record (no GPU needed)."""
+    import argparse
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    args = argparse.Namespace(workload="c2_3d64", steps=5, warmup=3)
+    res = dict(value=4000.0, ms=80.0, learn={}, solves_per_step=320, rank_V=117, mean_iters=39.0,
+               phases={"check": 6.0, "cg": 52.0}, seed_s=2.0,
+               roofline={"bound": "hbm", "achieved": 5900.0, "peak": 6800.0, "unit": "GB/s", "frac": 0.87,
+                         "traffic": None},
+               e2e={"value": 3990.0, "unit": "solves/s", "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1},
+               clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, launches=2490, base=None,
+               nolearn=None)
+    cpu = {"value": 5.0, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "s"}
+    line = bench.contender_line(args, 1, res, cpu)
+    json.dumps(line)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"):
+        assert k in line, k
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in line["roofline"], k
+    assert line["config"]["workload"] == "c2_3d64" and line["config"]["solves_per_step"] == 320
+    assert line["n_gpus"] == 1 and line["config"]["parallelism"] == "single GPU"
