@@ -55,7 +55,8 @@ extern "C" {
 #define RCG_ERR_CUDA          -2   /* a CUDA runtime call failed            */
 #define RCG_ERR_OOM           -3   /* device allocation failed or over cap  */
 #define RCG_ERR_NOT_SPD       -4   /* a small FP64 Cholesky found d <= 0    */
-#define RCG_ERR_NOT_CONVERGED -5   /* some RHS hit maxit; stats still filled */
+#define RCG_ERR_NOT_CONVERGED -5   /* some RHS hit maxit or the refinement-
+                                      restart cap; stats still filled        */
 #define RCG_ERR_BREAKDOWN     -6   /* p^T A p <= 0 or non-finite in CG      */
 #define RCG_ERR_TIMEOUT       -7   /* a bounded device wait ran out         */
 #define RCG_ERR_RANK_CAP      -8   /* basis V would exceed r_max            */
@@ -65,6 +66,7 @@ extern "C" {
 #define RCG_MIXED       1   /* float32 vectors / stencil / basis products, float64
                                refinement residuals, Galerkin matrices and
                                rank decisions                                  */
+#define RCG_MAX_PRIVATE 8   /* private columns of a recycle space U_j       */
 #define RCG_SEQUENTIAL  0   /* the paper's order: V grows between RHS          */
 #define RCG_WAVE        1   /* all RHS of `wave_samples` samples at once with V
                                frozen; ordered append afterwards               */
@@ -83,7 +85,11 @@ typedef struct {
     int    wave_samples;  /* samples per wave in RCG_WAVE (0 = all given)   */
     double tau_rank;      /* append iff ||new part|| / ||x|| > tau_rank     */
     int    k_u;           /* seed eigenvectors (Sec. 4.2.2: 10)             */
-    int    k_cap;         /* max columns of a recycle space U_j             */
+    int    k_cap;         /* max columns of a recycle space U_j = [U_0,
+                             private columns]; the private part holds at
+                             most RCG_MAX_PRIVATE columns, so values above
+                             k_u + RCG_MAX_PRIVATE act as that bound; when
+                             full, the oldest private column goes first     */
     int    r_max;         /* max columns of V (device memory is sized by it)*/
     int    max_samples;   /* sample slots (0..max_samples-1)                */
     int    maxit;         /* CG iterations per RHS before NOT_CONVERGED     */
@@ -290,12 +296,24 @@ int rcg_rom_eval_device(rcg_ctx *c, const double *mu_dev, int nparam, const doub
  * or NULL, Psi_dev nq x ndet x nsrc (point q as in rcg_rom_eval at
  * Psi_dev + q ndet nsrc), J_dev nq x nparam x ndet x nsrc or NULL (needs
  * dmu_dev).  Each point's values equal rcg_rom_eval's at that point up to
- * rounding.  The points are processed in chunks of 256 (bounded workspace).
- * The caller owns every array; the call returns after the results are
- * written.  RCG_ERR_INVALID for nq < 0, missing arrays or an empty basis,
+ * rounding.  The points are processed in chunks of
+ * rcg_rom_eval_batch_chunk() points, so the workspace stays within
+ * RCG_ROM_BATCH_WORKSPACE bytes (one point at a time if a single point needs
+ * more).  The caller owns every array; the call returns after the results
+ * are written.  RCG_ERR_INVALID for nq < 0, missing arrays or an empty basis,
  * RCG_ERR_NOT_SPD if a reduced matrix is not positive definite. */
 int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, const double *dmu_dev,
                        double *Psi_dev, double *J_dev);
+
+/* Points per chunk of rcg_rom_eval_batch for n unknowns, a basis of r
+ * columns, nsrc sources, ndet detectors and nparam parameters (0: no
+ * Jacobian): the largest count, at least 1 and at most 256, whose workspace
+ * (per point the reduced matrix, its weights, block lists and solves; per
+ * point and parameter a Gram, its block list and its tensor-core partial
+ * sums) fits in RCG_ROM_BATCH_WORKSPACE bytes.  Host arithmetic only:
+ * allocates nothing, needs no context; -1 for negative sizes. */
+#define RCG_ROM_BATCH_WORKSPACE (4LL << 30)
+int rcg_rom_eval_batch_chunk(long long n, int r, int nsrc, int ndet, int nparam);
 
 /* Elapsed device milliseconds of the named phase in the last call that ran
  * it ("check", "cg", "append", "seed_eig", "seed_x0", "rom", "rom_batch",

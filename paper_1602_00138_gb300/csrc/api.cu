@@ -155,6 +155,7 @@ struct Engine : EngineBase {
 
     // basis and caches
     T *V = nullptr;
+    int vcap = 0;                      // columns allocated for V (grows to rmax)
     int r = 0, r_seed = 0, s_star = -1, k_u = 0;
     double *Cstar = nullptr;           // V^T A~_* V, ld rmax
     T *X0 = nullptr;                   // seed solutions (nrhs columns)
@@ -190,7 +191,9 @@ struct Engine : EngineBase {
     T **p_xc = nullptr, **p_r = nullptr, **p_p = nullptr, **p_q = nullptr, **p_diag = nullptr;
     int *d_spec = nullptr, *d_si = nullptr, *d_kp = nullptr;
     double **d_sx = nullptr, **d_gsl = nullptr;
-    T *wpb = nullptr;                  // private deflation columns, [m][kp_max]
+    const void **d_wpp = nullptr;      // private deflation columns of each lane, [m][KPT] addresses
+    T *xhb = nullptr;                  // the network's columns of a wave
+    int xhb_cap = 0;
     float *mu_f = nullptr, *beta_f = nullptr;      // per-lane mu, beta of the float32 iteration
     int *d_alist = nullptr, *d_tlane = nullptr, *d_tsi = nullptr, *d_tcnt = nullptr;
     double *Yb = nullptr;
@@ -206,7 +209,7 @@ struct Engine : EngineBase {
     int ptr_cap = 0;
     // append workspace
     int acap = 0;
-    T *Wb = nullptr, *Qb = nullptr, *AQb = nullptr;
+    T *Wb = nullptr, *Qb = nullptr;
     double *Cb = nullptr, *M = nullptr, *S = nullptr, *R = nullptr, *RK = nullptr, *Ri = nullptr, *Rhat = nullptr;
     double *xn2 = nullptr, *ratio_d = nullptr;
     int *kept_d = nullptr, *d_K = nullptr, *d_cand = nullptr;
@@ -242,7 +245,8 @@ struct Engine : EngineBase {
     explicit Engine(rcg_ctx *ctx) : c(ctx), st(ctx->st), g(ctx->g), n(ctx->n), ld(ctx->ld), rmax(ctx->opt.r_max) {
         mixed = sizeof(T) == 4;
         D = mixed ? (const T *)ctx->D32 : (const T *)ctx->D64;
-        V = c->alloc<T>((size_t)rmax * ld);
+        vcap = std::min(rmax, 512);
+        V = c->alloc<T>((size_t)vcap * ld);
         Cstar = c->alloc<double>((size_t)rmax * rmax);
         Gs = c->alloc<double>((size_t)rmax * rmax);
         Ls = c->alloc<double>((size_t)rmax * rmax);
@@ -264,9 +268,10 @@ struct Engine : EngineBase {
         for (void *p : std::vector<void *>{x64, xc, rv, pv, qv, ls.rr, ls.pq, ls.wv, ls.gw, ls.kdef, ls.active, ls.flag,
                                            ls.iters, ls.thresh, ls.xa, ls.xt, d_mask, d_lnode, d_list, d_lw, d_rr,
                                            p_x64, p_diag64, p_xc, p_r, p_p, p_q, p_diag, d_spec, d_sx, d_gsl, Yb, d_si, d_kp,
-                                           mu_f, beta_f, d_alist, d_tlane, d_tsi, d_tcnt})
+                                           mu_f, beta_f, d_alist, d_tlane, d_tsi, d_tcnt, d_wpp})
             c->release(p);
         mcap = m;
+        d_wpp = c->alloc<const void *>((size_t)m * KPT);
         x64 = c->alloc<double>((size_t)m * ld);
         xc = c->alloc<T>((size_t)m * ld);
         rv = c->alloc<T>((size_t)m * ld);
@@ -340,6 +345,20 @@ struct Engine : EngineBase {
         c->sync();
     }
 
+    // room for `need` columns of V: grows by doubling up to r_max, keeping the
+    // first r columns (device memory follows the rank, not r_max)
+    void ensure_vcap(int need) {
+        if (need <= vcap) return;
+        if (need > rmax) throw Error{RCG_ERR_RANK_CAP, "basis V would exceed r_max columns"};
+        const int nc = std::min(rmax, std::max(need, 2 * vcap));
+        T *nv = c->alloc<T>((size_t)nc * ld);
+        if (r > 0) RCG_CUDA_TRY(cudaMemcpyAsync(nv, V, sizeof(T) * (size_t)r * ld, cudaMemcpyDeviceToDevice, st));
+        c->sync();
+        c->release(V);
+        V = nv;
+        vcap = nc;
+    }
+
     void ensure_ptr(int k) {
         if (k <= ptr_cap) return;
         c->release(d_ptrA); c->release(d_ptrB); c->release(d_ptrC);
@@ -351,12 +370,11 @@ struct Engine : EngineBase {
 
     void ensure_append(int a) {
         if (a <= acap) return;
-        for (void *p : std::vector<void *>{Wb, Qb, AQb, Cb, M, S, R, RK, Ri, Rhat, xn2, ratio_d, kept_d, d_K, d_cand})
+        for (void *p : std::vector<void *>{Wb, Qb, Cb, M, S, R, RK, Ri, Rhat, xn2, ratio_d, kept_d, d_K, d_cand})
             c->release(p);
         acap = std::max(a, 16);
         Wb = c->alloc<T>((size_t)acap * ld);
         Qb = c->alloc<T>((size_t)acap * ld);
-        AQb = c->alloc<T>((size_t)acap * ld);
         Cb = c->alloc<double>((size_t)(rmax + acap) * acap);
         M = c->alloc<double>((size_t)acap * acap);
         S = c->alloc<double>((size_t)acap * acap);
@@ -532,11 +550,21 @@ struct Engine : EngineBase {
         return {Gw[s], Lw[s]};
     }
 
-    // Cb = [V Q]^T (A~ Q) with A~ Q in float64 (the border of C_* or G_s):
-    // double-float products for the float32 basis, float64 otherwise.
-    void border_tn(const double *AQ, int ak) {
-        if constexpr (sizeof(T) == 4) gemm_tn_df(st, n, (const float *)V, ld, r + ak, AQ, ld, ak, Cb, r + ak, false);
-        else gemm_tn<T, double>(st, n, V, ld, r + ak, AQ, ld, ak, Cb, r + ak, false);
+    // Cb (r+ak x ak) = [V Q]^T (A~_s Q) for the ak new columns Q = V(:, r..r+ak)
+    // (the border of C_* or G_s), with A~_s Q in float64: double-float products
+    // for the float32 basis, float64 otherwise.  In chunks of AQ_CHUNK columns,
+    // so the float64 scratch stays small for a wave's large appends.
+    static constexpr int AQ_CHUNK = 32;
+    void border_cols(int ak, int s) {
+        ensure_aq64(std::min(ak, AQ_CHUNK));
+        for (int a0 = 0; a0 < ak; a0 += AQ_CHUNK) {
+            const int na = std::min(AQ_CHUNK, ak - a0);
+            convert_cols<T, double>(st, n, V + (long long)(r + a0) * ld, ld, Q64, ld, na);
+            apply_cols64(Q64, AQ64, na, s);
+            double *out = Cb + (long long)a0 * (r + ak);
+            if constexpr (sizeof(T) == 4) gemm_tn_df(st, n, (const float *)V, ld, r + ak, AQ64, ld, na, out, r + ak, false);
+            else gemm_tn<T, double>(st, n, V, ld, r + ak, AQ64, ld, na, out, r + ak, false);
+        }
     }
 
     // ------------------------------------------------------------ append
@@ -584,19 +612,16 @@ struct Engine : EngineBase {
         check_info("append second pass Q^T Q");
         lower_to_upper(st, M, ak, ak, RK);
         tri_upper_inverse(st, RK, ak, ak, Ri);
+        ensure_vcap(r + ak);
         prod_nn(Qb, ak, Ri, ak, ak, V + (long long)r * ld, 1.0, 0.0);
         // C_* bordered with [V Q]^T A~_* Q.  The stencil and the products are
         // float64 in both modes: for smooth columns A~ Q cancels to ~lambda_min
         // |Q|, so a float32 stencil would lose 3 digits of the Galerkin matrix
         // that the check, the deflation matrices and the reduced model solve with.
-        ensure_aq64(ak);
-        convert_cols<T, double>(st, n, V + (long long)r * ld, ld, Q64, ld, ak);
-        apply_cols64(Q64, AQ64, ak, s_star);
-        border_tn(AQ64, ak);
+        border_cols(ak, s_star);
         border_write(st, Cstar, rmax, r, ak, Cb, r + ak);
         if (border_sample >= 0 && gs_sample == border_sample && gs_r == r) {
-            if (border_sample != s_star) apply_cols64(Q64, AQ64, ak, border_sample);
-            border_tn(AQ64, ak);
+            border_cols(ak, border_sample);
             border_write(st, Gs, rmax, r, ak, Cb, r + ak);
             copy_new_rows(st, Gs, Ls, rmax, r, ak);
             RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
@@ -797,40 +822,38 @@ struct Engine : EngineBase {
             const long long npriv = (long long)m * kps;
             if (npriv > awp_cap) {
                 c->release(awp);
-                c->release(wpb);
                 awp_cap = npriv;
                 awp = c->alloc<T>((size_t)npriv * ld);
-                wpb = c->alloc<T>((size_t)npriv * ld);
             }
-            // private columns copied next to each other, then A~_s applied to them
-            std::vector<const T *> psrc;
-            std::vector<T *> pdst;
+            // private W columns by address (V, X_0, or the network's column),
+            // their images A~_s W next to each other per lane
+            std::vector<const void *> hwpp((size_t)m * KPT, (const void *)V);
             for (int l = 0; l < m; ++l)
                 for (int q = 0; q < kp[l]; ++q) {
                     const int e = spec[(size_t)l * KMAX + ku + q];
-                    psrc.push_back(e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld);
-                    T *w = wpb + ((long long)l * kps + q) * ld;
-                    pdst.push_back(w);
+                    const T *w = e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld;
+                    hwpp[(size_t)l * KPT + q] = w;
                     asrc.push_back(w);
                     adst.push_back(awp + ((long long)l * kps + q) * ld);
                     asamp.push_back(samp[l]);
                 }
-            if (!psrc.empty()) {            // one gather launch (stream-ordered before apply_cols reuses the scratch)
-                const int cnt = (int)psrc.size();
-                ensure_ptr(cnt);
-                c->h2d(d_ptrA, (const void **)psrc.data(), cnt);
-                c->h2d(d_ptrB, (const void **)pdst.data(), cnt);
-                copy_cols<T>(st, n, (const T *const *)d_ptrA, (T *const *)d_ptrB, cnt);
-            }
             // the network's column x_hat in slot kp[l] of the lane, then A~ x_hat with the others
             std::vector<int> aug_l;
             if (use_aug) {
                 std::vector<float *> hd;
                 std::vector<int> rows;
+                int naug = 0;
+                for (size_t a = 0; a < alanes.size(); ++a) naug += aug[alanes[a]];
+                if (naug > xhb_cap) {
+                    c->release(xhb);
+                    xhb_cap = naug;
+                    xhb = c->alloc<T>((size_t)naug * ld);
+                }
                 for (size_t a = 0; a < alanes.size(); ++a) {
                     const int l = alanes[a];
                     if (!aug[l]) continue;
-                    T *w = wpb + ((long long)l * kps + kp[l]) * ld;
+                    T *w = xhb + (long long)hd.size() * ld;
+                    hwpp[(size_t)l * KPT + kp[l]] = w;
                     hd.push_back((float *)w);
                     rows.push_back((int)a);
                     aug_l.push_back(l);
@@ -844,6 +867,7 @@ struct Engine : EngineBase {
                     net->upsample(st, net->outc, d_ldst, d_arow, (int)hd.size());
                 }
             }
+            c->h2d(d_wpp, hwpp.data(), hwpp.size());
             apply_cols(asrc, adst, asamp);
             c->h2d(d_spec, spec.data(), (size_t)m * KMAX);
             c->h2d(ls.kdef, kdef.data(), m);
@@ -856,7 +880,7 @@ struct Engine : EngineBase {
             gm.k_u = ku;
             gm.kp_max = std::max(kps, 1);
             gm.x = xc; gm.r = rv; gm.p = pv; gm.q = qv;
-            gm.wu = V; gm.awu = au0; gm.wp = wpb; gm.awp = awp;
+            gm.wu = V; gm.awu = au0; gm.awp = awp; gm.wpp = d_wpp;
             gm.si = d_si; gm.kp = d_kp;
             if (kmax_used > 0) {
                 lane_gw(st, (const double *const *)d_gsl, rmax, r, d_spec, (const double *const *)d_sx, ls.kdef, ls.gw, m);
@@ -868,7 +892,7 @@ struct Engine : EngineBase {
                 // Galerkin pivot of x_hat against U_j; kept columns border G_W^-1 on the device
                 const int nq = (int)aug_l.size();
                 c->h2d(d_aug_l, aug_l.data(), nq);
-                aug_dots(st, n, ld, (const float *)V, ku, (const float *)wpb, (const float *)awp, kps, d_kp, d_aug_l, nq,
+                aug_dots(st, n, ld, (const float *)V, ku, (const float *const *)d_wpp, (const float *)awp, kps, d_kp, d_aug_l, nq,
                          d_cd);
                 aug_border(st, ls.gw, ls.kdef, d_kp, d_aug_l, nq, d_cd, c->opt.tau_rank, d_kept);
                 std::vector<int> kh(nq);
@@ -981,7 +1005,7 @@ struct Engine : EngineBase {
                         relres[l] = std::sqrt(rr_h[l]) / std::fabs(lw[l]);
                         if (relres[l] <= ltol[l]) { done[l] = 1; }
                         else if (iters_h[l] >= c->opt.maxit) { done[l] = 1; status[l] = RCG_ERR_NOT_CONVERGED; }
-                        else if (restarts[l] > 200) { done[l] = 1; status[l] = RCG_ERR_BREAKDOWN; }
+                        else if (restarts[l] > 200) { done[l] = 1; status[l] = RCG_ERR_NOT_CONVERGED; }
                         else { Rl.push_back(l); ++restarts[l]; set_thresh(l, std::sqrt(rr_h[l])); }
                     }
                     if (!Rl.empty()) {
@@ -1389,6 +1413,8 @@ struct Engine : EngineBase {
         c->h2d(c->mu64 + (long long)ss * ld, mu.data(), (size_t)n);
         diag_sample(st, n, c->dstar, c->mu64 + (long long)ss * ld, c->h * c->h, c->diag64_of(ss), c->diag32_of(ss));
         c->sample_set[ss] = 1;
+        r = 0;
+        ensure_vcap(rr);
         for (int q = 0; q < rr; ++q) c->h2d(V + (long long)q * ld, hv.data() + (size_t)q * n, (size_t)n);
         RCG_CUDA_TRY(cudaMemcpy2DAsync(Cstar, sizeof(double) * rmax, hc.data(), sizeof(double) * rr, sizeof(double) * rr,
                                        rr, cudaMemcpyHostToDevice, st));
@@ -1687,7 +1713,7 @@ const char *rcg_strerror(int code) {
         case RCG_ERR_CUDA: return "CUDA runtime error";
         case RCG_ERR_OOM: return "out of device memory";
         case RCG_ERR_NOT_SPD: return "matrix not positive definite";
-        case RCG_ERR_NOT_CONVERGED: return "maximum iterations reached";
+        case RCG_ERR_NOT_CONVERGED: return "not converged (maximum iterations or refinement restarts reached)";
         case RCG_ERR_BREAKDOWN: return "Krylov breakdown";
         case RCG_ERR_TIMEOUT: return "device wait timed out";
         case RCG_ERR_RANK_CAP: return "basis rank cap reached";
@@ -2065,6 +2091,20 @@ int rcg_basis_compress(rcg_ctx *c, int r_max, double tau, double *sigma, int sig
     });
 }
 
+int rcg_rom_eval_batch_chunk(long long n, int r, int nsrc, int ndet, int nparam) {
+    if (n < 0 || r < 0 || nsrc < 0 || ndet < 0 || nparam < 0) return -1;
+    const long long ld = (n + 63) / 64 * 64, nbl = (n + 31) / 32, rr = (long long)r * r;
+    long long per = 8 * rr + 8 * ld + 4 * nbl + 4 + 8LL * r * (nsrc + ndet);
+    if (nparam > 0) per += (long long)nparam * (8 * rr + 4 * nbl + 4);
+    for (int k = 256; k > 1; --k) {
+        // the tensor-core partial sums of the chunk's weight vectors (k reduced
+        // matrices, then k nparam Jacobian Grams, in one scratch buffer)
+        const long long scr = rcg::tc_gram_w_batched_scratch(std::max(r, 1), k * std::max(nparam, 1), nullptr);
+        if (k * per + 4 * scr <= RCG_ROM_BATCH_WORKSPACE) return k;
+    }
+    return 1;
+}
+
 int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, const double *dmu_dev,
                        double *Psi_dev, double *J_dev) {
     return guarded(c, [&]() {
@@ -2072,7 +2112,8 @@ int rcg_rom_eval_batch(rcg_ctx *c, int nq, const double *mu_dev, int nparam, con
             return fail(c, RCG_ERR_INVALID, "bad rom batch arguments");
         // chunks of points: bounded workspace (per point r x r matrices and n weights,
         // per point and parameter a Gram) and grid dimensions
-        constexpr int CHUNK = 256;
+        const int CHUNK = std::max(1, rcg_rom_eval_batch_chunk(c->n, c->eng->rank(), c->nsrc, c->ndet,
+                                                               J_dev ? nparam : 0));
         const long long n = c->n, nd_ns = (long long)c->ndet * c->nsrc;
         for (int q0 = 0; q0 < nq; q0 += CHUNK) {
             const int m = std::min(CHUNK, nq - q0);

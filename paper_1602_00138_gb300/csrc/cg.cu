@@ -142,7 +142,12 @@ k_lane_dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask
     if (l >= ls.m || mask[l] == 0) return;
     const int ku = gm.k_u, kp = gm.kp[l], si = gm.si[l];
     const T *__restrict__ Ws = use_aw ? col<T>(gm.awu, (long long)si * ku, gm.ld) : (const T *)gm.wu;
-    const T *__restrict__ Wq = col<T>(use_aw ? gm.awp : gm.wp, (long long)l * gm.kp_max, gm.ld);
+    const T *Wq[KP_MAX];
+#pragma unroll
+    for (int c = 0; c < KP_MAX; ++c)
+        Wq[c] = c >= kp ? nullptr
+                        : use_aw ? col<T>(gm.awp, (long long)l * gm.kp_max + c, gm.ld)
+                                 : (const T *)gm.wpp[(long long)l * KPT + c];
     const T *__restrict__ R = (const T *)gm.r + (long long)l * gm.ld;
     T acc[NV];
 #pragma unroll
@@ -156,7 +161,7 @@ k_lane_dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask
             if (c < ku) acc[1 + c] += Ws[(long long)c * gm.ld + p] * v;
 #pragma unroll
         for (int c = 0; c < KP_MAX; ++c)
-            if (c < kp) acc[1 + KU_MAX + c] += Wq[(long long)c * gm.ld + p] * v;
+            if (c < kp) acc[1 + KU_MAX + c] += Wq[c][p] * v;
     }
     double accd[NV];
     __shared__ double out[NV];
@@ -203,7 +208,7 @@ k_restart_project(long long n, LaneGeom gm, LaneState ls, const int *__restrict_
         }
         for (int c = 0; c < kp; ++c) {
             const long long ci = (long long)l * gm.kp_max + c;
-            xs += col<T>(gm.wp, ci, gm.ld)[p] * mu[ku + c];
+            xs += ((const T *)gm.wpp[(long long)l * KPT + c])[p] * mu[ku + c];
             rs += col<T>(gm.awp, ci, gm.ld)[p] * mu[ku + c];
         }
         X[p] = xs;
@@ -252,7 +257,9 @@ k_direction(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask
     const T *__restrict__ R = (const T *)gm.r + o;
     T *__restrict__ P = (T *)gm.p + o;
     const T *__restrict__ WU = (const T *)gm.wu;
-    const T *__restrict__ WP = col<T>(gm.wp, (long long)l * gm.kp_max, gm.ld);
+    const T *WP[KP_MAX];
+#pragma unroll
+    for (int c = 0; c < KP_MAX; ++c) WP[c] = c < kp ? (const T *)gm.wpp[(long long)l * KPT + c] : nullptr;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         T v = R[p];
@@ -263,7 +270,7 @@ k_direction(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask
             if (c < ku) s += WU[(long long)c * gm.ld + p] * m_u[c];
 #pragma unroll
         for (int c = 0; c < KP_MAX; ++c)
-            if (c < kp) s += WP[(long long)c * gm.ld + p] * m_p[c];
+            if (c < kp) s += WP[c][p] * m_p[c];
         P[p] = v - s;
     }
 }

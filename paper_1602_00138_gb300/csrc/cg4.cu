@@ -580,6 +580,7 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
     __shared__ float smu[TILE][KU_MAX + KP_MAX];
     __shared__ float sbeta[TILE], salpha[TILE];
     __shared__ int slane[TILE], skp[TILE], sdir[TILE];
+    __shared__ const float *spw[TILE][KPM];
     const int t = blockIdx.y, cnt = tile_cnt[t], ku = gm.k_u;
     if (threadIdx.x < TILE) {
         int l = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
@@ -597,6 +598,11 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
         const int jj = e / (KU_MAX + KP_MAX), c = e % (KU_MAX + KP_MAX);
         const int l = slane[jj];
         smu[jj][c] = (l >= 0 && sdir[jj] && c < ku + skp[jj]) ? mu[(long long)l * KMAX + c] : 0.f;
+    }
+    for (int e = threadIdx.x; e < TILE * KPM; e += blockDim.x) {
+        const int jj = e / KPM, c = e % KPM;
+        const int l = slane[jj];
+        spw[jj][c] = (l >= 0 && sdir[jj] && c < skp[jj]) ? (const float *)gm.wpp[(long long)l * KPT + c] : nullptr;
     }
     const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
     const float *__restrict__ WU = (const float *)gm.wu;
@@ -649,11 +655,10 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
                     pv[g] = l >= 0 ? *(const float4 *)((const float *)gm.p + o) : z4;
                     xv[g] = (l >= 0 && salpha[jj] != 0.f) ? *(const float4 *)((const float *)gm.x + o) : z4;
                     rv[g] = dir ? *(const float4 *)((const float *)gm.r + o) : z4;
-                    const float *WP = (const float *)gm.wp + (long long)(l < 0 ? 0 : l) * gm.kp_max * gm.ld + p;
                     const int kp = skp[jj];
 #pragma unroll
                     for (int c = 0; c < KPM; ++c)
-                        wv[g][c] = (dir && c < kp) ? *(const float4 *)(WP + (long long)c * gm.ld) : z4;
+                        wv[g][c] = (dir && c < kp) ? *(const float4 *)(spw[jj][c] + p) : z4;
                 }
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
@@ -752,14 +757,19 @@ k_private_dots4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ 
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = 0.f;
     const float4 *__restrict__ R = (const float4 *)((const float *)gm.r + (long long)l * gm.ld);
-    const float *__restrict__ S = (const float *)(use_aw ? gm.awp : gm.wp) + (long long)l * gm.kp_max * gm.ld;
+    const float *S[KP_MAX];
+#pragma unroll
+    for (int c = 0; c < KP_MAX; ++c)
+        S[c] = c >= kp ? nullptr
+                       : use_aw ? (const float *)gm.awp + ((long long)l * gm.kp_max + c) * gm.ld
+                                : (const float *)gm.wpp[(long long)l * KPT + c];
     const int nv = (int)(n >> 2);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
         const float4 rv = R[v];
         acc[0] += dot4(rv, rv);
 #pragma unroll
         for (int c = 0; c < KP_MAX; ++c)
-            if (c < kp) acc[1 + c] += dot4(((const float4 *)(S + (long long)c * gm.ld))[v], rv);
+            if (c < kp) acc[1 + c] += dot4(((const float4 *)S[c])[v], rv);
     }
     __shared__ double out[NV];
     block_sum<NV>(acc, out);
@@ -834,11 +844,10 @@ k_project4(long long n, LaneGeom gm, const int *__restrict__ tile_lane, const in
                     rs.x += m * a.x; rs.y += m * a.y; rs.z += m * a.z; rs.w += m * a.w;
                 }
                 const int kp = skp[jj];
-                const float *WP = (const float *)gm.wp + (long long)l * gm.kp_max * gm.ld;
                 const float *AP = (const float *)gm.awp + (long long)l * gm.kp_max * gm.ld;
                 for (int c = 0; c < kp; ++c) {
                     const float m = smu[jj][ku + c];
-                    const float4 w = *(const float4 *)(WP + (long long)c * gm.ld + p);
+                    const float4 w = *(const float4 *)((const float *)gm.wpp[(long long)l * KPT + c] + p);
                     const float4 a = *(const float4 *)(AP + (long long)c * gm.ld + p);
                     xs.x += m * w.x; xs.y += m * w.y; xs.z += m * w.z; xs.w += m * w.w;
                     rs.x += m * a.x; rs.y += m * a.y; rs.z += m * a.z; rs.w += m * a.w;

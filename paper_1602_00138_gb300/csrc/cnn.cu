@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256) k_cnn_normalise(float *__restrict__ a, lo
 // l = alist[a]: w_q = U_0 column q (q < ku), private column q - ku (q < ku + kp),
 // and x_hat itself (q = ku + kp, the slot the network's column occupies).
 __global__ void __launch_bounds__(256)
-k_aug_dots(long long n, long long ld, const float *__restrict__ V, int ku, const float *__restrict__ wpb,
+k_aug_dots(long long n, long long ld, const float *__restrict__ V, int ku, const float *const *__restrict__ wpp,
            const float *__restrict__ awp, int kps, const int *__restrict__ kp, const int *__restrict__ alist,
            double *__restrict__ cd, long long chunk) {
     constexpr int NQ = KU_MAX + KP_MAX + 1;
@@ -386,7 +386,7 @@ k_aug_dots(long long n, long long ld, const float *__restrict__ V, int ku, const
     const int kpl = kp[l], nq = ku + kpl + 1;
     if (threadIdx.x < NQ) {
         const int q = threadIdx.x;
-        cols[q] = q < ku ? V + (long long)q * ld : wpb + ((long long)l * kps + (q - ku)) * ld;
+        cols[q] = q < ku ? V + (long long)q * ld : q < nq ? wpp[(long long)l * KPT + (q - ku)] : nullptr;
     }
     __syncthreads();
     const float *__restrict__ y = awp + ((long long)l * kps + kpl) * ld;
@@ -751,7 +751,7 @@ void Cnn::normalise(cudaStream_t st, float *a, int B) {
     RCG_CHECK_LAUNCH();
 }
 
-void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku, const float *wpb,
+void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku, const float *const *wpp,
               const float *awp, int kps, const int *kp, const int *alist, int na, double *cd) {
     if (na <= 0) return;
     RCG_CUDA_TRY(cudaMemsetAsync(cd, 0, sizeof(double) * (size_t)na * (KMAX + 1), st));
@@ -761,7 +761,7 @@ void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku
     chunk = (chunk + 3) / 4 * 4;
     z = (n + chunk - 1) / chunk;
     if (ld % 4 != 0) throw Error{RCG_ERR_INVALID, "aug_dots: leading dimension not a multiple of 4"};
-    k_aug_dots<<<dim3((unsigned)z, (unsigned)na), 256, 0, st>>>(n, ld, V, ku, wpb, awp, kps, kp, alist, cd, chunk);
+    k_aug_dots<<<dim3((unsigned)z, (unsigned)na), 256, 0, st>>>(n, ld, V, ku, wpp, awp, kps, kp, alist, cd, chunk);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include "../../include/rcg.h"
+
 namespace rcg {
 
 // ---------------------------------------------------------------- errors
@@ -55,7 +57,7 @@ template <typename T> struct Cols {
 
 constexpr int KMAX = 48;        // stride of the per-lane deflation arrays
 constexpr int KU_MAX = 16;      // shared (seed eigenvector) deflation columns
-constexpr int KP_MAX = 8;       // private deflation columns per lane
+constexpr int KP_MAX = RCG_MAX_PRIVATE;   // private deflation columns per lane
 
 // Per-lane CG state on the device (structure of arrays, m lanes).
 struct LaneState {
@@ -74,16 +76,23 @@ struct LaneState {
     int *xt;                // [m] iteration that set xa (-1: none); applied by that iteration's direction kernel
 };
 
-// Arithmetic addressing of the lanes of a wave (all columns ld apart):
+// Slots of a lane's private deflation columns in LaneGeom::wpp (the private
+// columns plus one for the learned column).
+constexpr int KPT = KP_MAX + 1;
+
+// Addressing of the lanes of a wave (all columns ld apart):
 //   x, r, p, q : lane l at base + l*ld (engine precision T)
 //   deflation columns of lane l: c < k_u shared: W = wu + c*ld (the first
 //   k_u basis columns), A W = awu + (si[l]*k_u + c)*ld (per sample slot);
-//   c >= k_u private: W = wp + (l*kp_max + c - k_u)*ld, A W likewise in awp.
+//   c >= k_u private: W = wpp[l*KPT + c - k_u] (a pointer table: the columns
+//   live in V, X_0 or the learned-column buffer, not copied per lane),
+//   A W = awp + (l*kp_max + c - k_u)*ld.
 struct LaneGeom {
     long long ld;
     int k_u, kp_max;
     void *x, *r, *p, *q;
-    const void *wu, *awu, *wp, *awp;
+    const void *wu, *awu, *awp;
+    const void *const *wpp;
     const int *si, *kp;
 };
 
@@ -210,7 +219,7 @@ class Cnn {
 // Augmentation of the private deflation spaces by the network's columns:
 // dots of A~ x_hat with every deflation column and x_hat, then the Galerkin
 // pivot test and the bordered inverse (see cnn.cu).
-void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku, const float *wpb,
+void aug_dots(cudaStream_t st, long long n, long long ld, const float *V, int ku, const float *const *wpp,
               const float *awp, int kps, const int *kp, const int *alist, int na, double *cd);
 void aug_border(cudaStream_t st, double *gw, int *kdef, int *kp, const int *alist, int na, const double *cd,
                 double tau, int *kept);

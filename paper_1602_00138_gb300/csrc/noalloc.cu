@@ -15,6 +15,8 @@
 #include "../../include/rcg.h"
 
 #include <mutex>
+#include <new>
+#include <string>
 #include <vector>
 
 namespace {
@@ -62,7 +64,8 @@ int ctx_operator(const rcg_ctx *c, int s, Grid *g, const double **D64, const flo
 void ctx_set_error(rcg_ctx *c, const std::string &msg);
 }  // namespace rcg
 
-extern "C" int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols) {
+namespace {
+int apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols) {
     using namespace rcg;
     if (!c) return RCG_ERR_INVALID;
     if (ncols < 0 || ncols > kMaxCols || !x_dev || !y_dev || (prec != RCG_FP64 && prec != RCG_MIXED)) {
@@ -86,30 +89,52 @@ extern "C" int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev,
         return rc;
     }
     const size_t es = prec == RCG_FP64 ? sizeof(double) : sizeof(float);
-    std::vector<const void *> h(3 * (size_t)kMaxCols, nullptr);
-    for (int j = 0; j < ncols; ++j) {
-        h[j] = (const char *)x_dev + (size_t)j * g.n * es;
-        h[kMaxCols + j] = (char *)y_dev + (size_t)j * g.n * es;
-        h[2 * kMaxCols + j] = prec == RCG_FP64 ? (const void *)diag64 : (const void *)diag32;
-    }
     long long *prev = g_launch_counter;
     g_launch_counter = launches;
     rc = RCG_OK;
     try {
-        RCG_CUDA_TRY(cudaMemcpyAsync(tab, h.data(), sizeof(void *) * h.size(), cudaMemcpyHostToDevice, st));
+        // the three tables of this call (ncols entries each) in one host buffer
+        std::vector<const void *> h(3 * (size_t)ncols, nullptr);
+        for (int j = 0; j < ncols; ++j) {
+            h[j] = (const char *)x_dev + (size_t)j * g.n * es;
+            h[(size_t)ncols + j] = (char *)y_dev + (size_t)j * g.n * es;
+            h[2 * (size_t)ncols + j] = prec == RCG_FP64 ? (const void *)diag64 : (const void *)diag32;
+        }
         const void **t = (const void **)tab;
+        for (int part = 0; part < 3; ++part)     // only the entries in use, into their table of the array
+            RCG_CUDA_TRY(cudaMemcpyAsync(t + (size_t)part * kMaxCols, h.data() + (size_t)part * ncols,
+                                         sizeof(void *) * (size_t)ncols, cudaMemcpyHostToDevice, st));
         if (prec == RCG_FP64)
             apply_op<double>(st, g, D64, (const double *const *)(t + 2 * kMaxCols), (const double *const *)t,
                              (double *const *)(t + kMaxCols), ncols, nullptr, nullptr);
         else
             apply_op<float>(st, g, D32, (const float *const *)(t + 2 * kMaxCols), (const float *const *)t,
                             (float *const *)(t + kMaxCols), ncols, nullptr, nullptr);
-        // the host table h is pageable and goes out of scope: wait for the copy and the kernel
+        // the host table h is pageable and goes out of scope: wait for the copies and the kernel
         RCG_CUDA_TRY(cudaStreamSynchronize(st));
     } catch (const Error &e) {
         ctx_set_error(c, e.msg);
         rc = e.code;
+    } catch (const std::bad_alloc &) {
+        ctx_set_error(c, "rcg_apply_noalloc: host allocation failed");
+        rc = RCG_ERR_OOM;
+    } catch (...) {
+        ctx_set_error(c, "rcg_apply_noalloc: unexpected exception");
+        rc = RCG_ERR_INVALID;
     }
     g_launch_counter = prev;
     return rc;
+}
+}  // namespace
+
+extern "C" int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols) {
+    // no C++ exception may cross the C boundary (the error messages are
+    // std::strings and can throw on the host)
+    try {
+        return apply_noalloc(c, s, prec, x_dev, y_dev, ncols);
+    } catch (const std::bad_alloc &) {
+        return RCG_ERR_OOM;
+    } catch (...) {
+        return RCG_ERR_INVALID;
+    }
 }

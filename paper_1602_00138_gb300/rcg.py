@@ -36,9 +36,10 @@ EXPORTED = [
     "rcg_phase_ms", "rcg_launch_count", "rcg_profile_enable", "rcg_profile_get", "rcg_apply_noalloc",
     "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
-    "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load", "rcg_gemm_nn_f32",
+    "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load", "rcg_gemm_nn_f32", "rcg_rom_eval_batch_chunk",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
+RCG_MAX_PRIVATE = 8
 RCG_COMPRESS_MAX_COLS = 4096
 
 
@@ -118,6 +119,7 @@ def load(path=LIB_PATH):
         "rcg_save": (I, [P, C.c_char_p]),
         "rcg_load": (I, [P, C.c_char_p]),
         "rcg_gemm_nn_f32": (I, [P, LL, I, P, I, I, LL, P, LL, D, D, I, P]),
+        "rcg_rom_eval_batch_chunk": (I, [LL, I, I, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -265,11 +267,29 @@ class Context:
         mu = np.ascontiguousarray(mu, dtype=np.float64)
         return self._check(self.L.rcg_set_sample(self.h, s, _ptr(mu)))
 
+    def _device_cols(self, x_dev, y_dev, ncols, prec):
+        """x and y must be contiguous CUDA tensors of the precision's dtype
+        (float64 for RCG_FP64, float32 for RCG_MIXED) holding ncols columns of
+        n values: anything else would hand the kernel a host or out-of-bounds
+        address."""
+        import torch
+        want = torch.float64 if prec == RCG_FP64 else torch.float32
+        for name, t in (("x", x_dev), ("y", y_dev)):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda:
+                raise ValueError(f"{name} must be a CUDA tensor")
+            if t.dtype != want or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous {want} tensor for prec {prec}")
+            if ncols < 0 or t.numel() < ncols * self.n:
+                raise ValueError(f"{name} holds {t.numel()} values, fewer than ncols * n = {ncols * self.n}")
+
     def apply(self, s, x_dev, y_dev, ncols, prec=RCG_FP64):
+        self._device_cols(x_dev, y_dev, ncols, prec)
         return self._check(self.L.rcg_apply(self.h, s, prec, _ptr(x_dev), _ptr(y_dev), ncols))
 
     def apply_noalloc(self, s, x_dev, y_dev, ncols, prec=RCG_FP64):
         """rcg_apply without device allocation (tables in a static device array)."""
+        if 0 <= ncols <= RCG_NOALLOC_MAX_COLS:
+            self._device_cols(x_dev, y_dev, ncols, prec)
         return self._check(self.L.rcg_apply_noalloc(self.h, s, prec, _ptr(x_dev), _ptr(y_dev), ncols))
 
     # ---- method

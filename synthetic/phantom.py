@@ -128,30 +128,74 @@ def node_coords(wl: Workload):
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
 
 
+def node_grid(wl: Workload):
+    """The `grid` argument of pals_mu / pals_dmu for node_coords(wl)."""
+    return (wl.N, wl.h, wl.dim)
+
+
 def _split(p, d):
     p = np.asarray(p, dtype=np.float64).reshape(-1, d + 2)
     return p[:, :d], p[:, d], p[:, d + 1]
 
 
-def pals_mu(p, X, mu_bg):
-    """Absorption at points X (n, d) for parameter vector p (n_anom*(d+2))."""
+def _support(X, c, w, grid=None):
+    """Indices (ascending) of the points where phi = exp(-|x - c|^2 / w^2) - 1/2
+    > -H_EPS, the only ones where an anomaly contributes (H and H' vanish
+    elsewhere): a ball of radius w sqrt(ln(1 / (1/2 - H_EPS))), found by a
+    per-axis box test.  grid = (N, h, d) says that X is the node grid of
+    node_coords (coordinate i h, i = 1..N, along each axis, x fastest); the
+    box test then runs only on the index box around the ball (one node wider
+    on every side), which gives the same set."""
+    R2 = w * w * np.log(1.0 / (0.5 - H_EPS))
+    R = np.sqrt(R2) * (1.0 + 1e-12)
+    if grid is None:
+        box = np.abs(X[:, 0] - c[0]) < R
+        for a in range(1, X.shape[1]):
+            box &= np.abs(X[:, a] - c[a]) < R
+        return np.nonzero(box)[0]
+    N, h, d = grid
+    rng = []
+    for a in range(d):
+        lo = max(1, int(np.floor((c[a] - R) / h)) - 1)
+        hi = min(N, int(np.ceil((c[a] + R) / h)) + 1)
+        if lo > hi:
+            return np.zeros(0, dtype=np.int64)
+        rng.append(np.arange(lo - 1, hi, dtype=np.int64))          # 0-based node index along the axis
+    if d == 2:
+        ix, iz = rng
+        cand = (ix[None, :] + N * iz[:, None]).ravel()
+    else:
+        ix, iy, iz = rng
+        cand = (ix[None, None, :] + N * (iy[None, :, None] + N * iz[:, None, None])).ravel()
+    Xc = X[cand]
+    box = np.abs(Xc[:, 0] - c[0]) < R
+    for a in range(1, d):
+        box &= np.abs(Xc[:, a] - c[a]) < R
+    return cand[box]
+
+
+def pals_mu(p, X, mu_bg, grid=None):
+    """Absorption at points X (n, d) for parameter vector p (n_anom*(d+2));
+    grid: see _support (a faster route on the node grid, same values)."""
     d = X.shape[1]
     c, w, m = _split(p, d)
     mu = np.full(X.shape[0], mu_bg, dtype=np.float64)
     for k in range(c.shape[0]):
-        r2 = np.sum((X - c[k]) ** 2, axis=1)
+        idx = _support(X, c[k], w[k], grid)
+        r2 = np.sum((X[idx] - c[k]) ** 2, axis=1)
         phi = np.exp(-r2 / w[k] ** 2) - 0.5
-        mu += (m[k] - mu_bg) * smooth_heaviside(phi)
+        mu[idx] += (m[k] - mu_bg) * smooth_heaviside(phi)
     return mu
 
 
-def pals_dmu(p, X, mu_bg):
-    """Analytic d mu / d p_k at points X: array (nparam, n)."""
+def pals_dmu(p, X, mu_bg, grid=None):
+    """Analytic d mu / d p_k at points X: array (nparam, n); grid as in pals_mu."""
     d = X.shape[1]
     c, w, m = _split(p, d)
     out = np.zeros((c.shape[0] * (d + 2), X.shape[0]), dtype=np.float64)
     for k in range(c.shape[0]):
-        diff = X - c[k]
+        idx = _support(X, c[k], w[k], grid)
+        diff = X[idx] - c[k]
         r2 = np.sum(diff ** 2, axis=1)
         E = np.exp(-r2 / w[k] ** 2)
         phi = E - 0.5
@@ -159,9 +203,9 @@ def pals_dmu(p, X, mu_bg):
         amp = m[k] - mu_bg
         base = k * (d + 2)
         for a in range(d):
-            out[base + a] = amp * Hp * E * 2.0 * diff[:, a] / w[k] ** 2
-        out[base + d] = amp * Hp * E * 2.0 * r2 / w[k] ** 3
-        out[base + d + 1] = smooth_heaviside(phi)
+            out[base + a, idx] = amp * Hp * E * 2.0 * diff[:, a] / w[k] ** 2
+        out[base + d, idx] = amp * Hp * E * 2.0 * r2 / w[k] ** 3
+        out[base + d + 1, idx] = smooth_heaviside(phi)
     return out
 
 
@@ -231,9 +275,10 @@ def make_workload(spec, K=None, seed=None, with_dmu=True):
     p0 = seed_params(wl, rng)
     ps = np.vstack([p0[None, :], sample_params(wl, p0, rng, wl.K)])
     X = node_coords(wl)
-    mu = np.stack([pals_mu(p, X, wl.mu_bg) for p in ps])
+    grid = node_grid(wl)
+    mu = np.stack([pals_mu(p, X, wl.mu_bg, grid) for p in ps])
     D = 1.0 / (3.0 * (mu[0] + wl.mu_s_prime))
-    dmu = np.stack([pals_dmu(p, X, wl.mu_bg) for p in ps]) if with_dmu else None
+    dmu = np.stack([pals_dmu(p, X, wl.mu_bg, grid) for p in ps]) if with_dmu else None
     src_nodes, src_ij = face_nodes(wl, wl.src_lattice, top=False)
     det_nodes, det_ij = face_nodes(wl, wl.det_lattice, top=True)
     return dict(wl=wl, dims=wl.dims, h=wl.h, n=wl.n, X=X, params=ps, mu=mu, D=D,

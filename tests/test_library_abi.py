@@ -54,6 +54,40 @@ def test_header_constants_match_the_binding():
     defs = {k: int(v) for k, v in re.findall(r"#define\s+(RCG_[A-Z_0-9]+)\s+(-?\d+)", txt)}
     mirrored = [k for k in defs if hasattr(rcg, k)]
     assert {"RCG_OK", "RCG_ERR_INVALID", "RCG_MIXED", "RCG_WAVE", "RCG_NOALLOC_MAX_COLS",
-            "RCG_COMPRESS_MAX_COLS"} <= set(mirrored)
+            "RCG_COMPRESS_MAX_COLS", "RCG_MAX_PRIVATE"} <= set(mirrored)
     for k in mirrored:
         assert getattr(rcg, k) == defs[k], k
+
+
+def test_rom_batch_chunk_bounds_the_workspace(lib):
+    """rcg_rom_eval_batch splits its points so that the workspace stays within
+    RCG_ROM_BATCH_WORKSPACE (4 GiB): at the 192^3 configuration (basis of
+    2048 columns, 128 + 128 right-hand sides, 40 parameters) a point needs
+    about 2 GB (40 Grams of 2048^2 float64 and their float32 partial sums), so
+    two points go together where 256 needed ~515 GB; small bases take the
+    full 256-point chunks.  Host arithmetic only (nothing allocated)."""
+    n = 192 ** 3
+    assert lib.rcg_rom_eval_batch_chunk(n, 2048, 128, 128, 40) == 2
+    assert lib.rcg_rom_eval_batch_chunk(n, 2048, 128, 128, 0) >= 1
+    assert lib.rcg_rom_eval_batch_chunk(64 ** 3, 120, 32, 32, 20) == 256
+    assert lib.rcg_rom_eval_batch_chunk(-1, 10, 1, 1, 1) == -1
+    # the bound itself: per point ~ nparam r^2 (8 B Gram + 4 B partial sums) at r = 512
+    k = lib.rcg_rom_eval_batch_chunk(128 ** 3, 512, 64, 64, 20)
+    per = 20 * 512 * 512 * 12 + 8 * 128 ** 3
+    assert (k - 1) * per <= 4 * 2 ** 30 and k >= 1
+
+
+def test_binding_refuses_host_or_short_operands(lib):
+    """apply / apply_noalloc check their operands before the library sees a
+    pointer: numpy arrays, CPU tensors and wrong dtypes are refused (no GPU
+    needed: the check runs before any call)."""
+    import numpy as np
+    import torch
+    from paper_1602_00138_gb300 import rcg
+    ctx = rcg.Context.__new__(rcg.Context)
+    ctx.n = 10
+    with pytest.raises(ValueError):
+        ctx._device_cols(np.zeros(20), np.zeros(20), 2, rcg.RCG_FP64)
+    with pytest.raises(ValueError):
+        ctx._device_cols(torch.zeros(20, dtype=torch.float64), torch.zeros(20, dtype=torch.float64), 2,
+                         rcg.RCG_FP64)

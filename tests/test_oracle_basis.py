@@ -125,6 +125,12 @@ def test_interpolation_theorem_at_sampled_points(order):
         bound = tol ** 2 * np.outer(np.linalg.norm(Ct, axis=0), np.linalg.norm(Bt, axis=0)) / lmin
         assert np.all(np.abs(P - Pr) <= 10 * bound + 1e-12 * np.abs(P).max())  # rounding floor ~ kappa * eps
         assert np.linalg.norm(J - Jr) <= 1e-6 * np.linalg.norm(J)
+        # the first-order Jacobian bound used by the GPU parity tests holds here
+        from tests.gpu_common import jacobian_galerkin_bound
+        lmin = np.linalg.eigvalsh(A.toarray())[0]
+        bJ, Jb = jacobian_galerkin_bound(A, Bt, Ct, inp["h"], inp["dmu"][i], inp["tol"], tau, lmin)
+        assert np.allclose(Jb, J, rtol=1e-12, atol=0)
+        assert np.linalg.norm(J - Jr) <= bJ * np.linalg.norm(J)
 
 
 def test_wave_order_appends_in_order_and_freezes_basis():
@@ -148,3 +154,22 @@ def test_wave_order_appends_in_order_and_freezes_basis():
             assert o["appended"] == (o["ratio"] > 1e-8)
     rat = [o["ratio"] for o in out if o["iters"] > 0]
     assert rat[-1] < 1e-2 * rat[0]
+
+
+def test_private_recycle_space_cap_evicts_the_oldest_column():
+    """U_j keeps at most k_cap columns: with k_cap = k_u + 2 and four
+    appended columns for one right-hand side, X_0(:, j) goes first, then the
+    older appended columns; U_0 is never evicted and the order is kept."""
+    rng = np.random.default_rng(11)
+    n, k_u = 30, 3
+    U0 = rng.standard_normal((n, k_u))
+    X0 = rng.standard_normal((n, 2))
+    st = basis.BasisState(V=np.zeros((n, 0)), U0=U0, X0=X0, priv=[[X0[:, 0].copy()], [X0[:, 1].copy()]],
+                          k_cap=k_u + 2)
+    q = [rng.standard_normal(n) for _ in range(4)]
+    st.push_private(0, q[0])
+    assert np.array_equal(st.U(0), np.column_stack([U0, X0[:, 0], q[0]]))
+    for c in q[1:]:
+        st.push_private(0, c)
+    assert np.array_equal(st.U(0), np.column_stack([U0, q[2], q[3]]))
+    assert np.array_equal(st.U(1), np.column_stack([U0, X0[:, 1]]))     # other RHS untouched

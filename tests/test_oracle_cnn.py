@@ -109,3 +109,43 @@ def test_features_are_normalised():
     assert abs(np.max(np.abs(x[0])) - 1.0) < 2 ** -8
     assert abs(np.mean(x[1])) < 2 ** -7           # block means average to the global mean
     assert cnn.n_params() == 29025
+
+
+def test_target_is_the_block_mean_over_its_largest_magnitude():
+    """Hand-computed: two coarse cells (f = 4 on a 4 x 4 x 8 grid) whose fine
+    values alternate 1, 3 (block mean 2) and -2, -6 (block mean -4); the
+    target divides the block means by the largest |block mean|, 4, and not by
+    the largest fine value (6) or a sum."""
+    dims = (4, 4, 8)
+    g = np.empty(4 * 4 * 8)
+    for z in range(8):
+        for y in range(4):
+            for x in range(4):
+                odd = (x + y + z) % 2
+                g[x + 4 * (y + 4 * z)] = (3.0 if odd else 1.0) if z < 4 else (-6.0 if odd else -2.0)
+    t = cnn.target(g, dims, cnn.pool_factor(dims))
+    assert t.shape == (2, 1, 1)
+    assert t[0, 0, 0] == 0.5 and t[1, 0, 0] == -1.0
+
+
+def test_loss_is_the_mean_over_pairs_and_coarse_nodes_with_master_weights():
+    """Hand-computed on a one-layer network (only the centre tap w and the
+    bias b set) and two 2 x 2 x 2 pairs: pair 1 has input 1 and target 1.5
+    everywhere, pair 2 input 0 and target 0 except 2.5 at one node.  With
+    w = 2 + 2^-10 (not a bfloat16 value: the loss must use it unrounded) and
+    b = 0.5 the squared errors sum to 8 (1 + 2^-10)^2 over pair 1 and
+    7 * 0.25 + 4 over pair 2; the loss is their total over 16 nodes (a sum,
+    or a mean per pair only, would differ)."""
+    channels = (1, 1)
+    theta = np.zeros(cnn.n_params(channels))
+    w = 2.0 + 2.0 ** -10
+    theta[13] = w
+    theta[27] = 0.5
+    inputs = [np.ones((1, 2, 2, 2)), np.zeros((1, 2, 2, 2))]
+    t2 = np.zeros((2, 2, 2))
+    t2[1, 0, 1] = 2.5
+    targets = [np.full((2, 2, 2), 1.5), t2]
+    expect = (8 * (1.0 + 2.0 ** -10) ** 2 + 7 * 0.25 + 4.0) / 16
+    assert abs(cnn.loss(theta, inputs, targets, channels) - expect) < 1e-15
+    # the rounded weights (inference) would give a different value
+    assert cnn.bf16(np.float32(w)) == 2.0

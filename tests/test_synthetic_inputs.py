@@ -35,3 +35,23 @@ def test_workload_shapes_and_seeding():
     assert np.all(a["D"] > 0) and np.all(a["mu"] >= 0.01 - 1e-15)
     assert WORKLOADS["c2_3d64"].n == 64 ** 3 and WORKLOADS["c3_3d128"].n == 2097152
     assert WORKLOADS["c5_3d192"].n == 7077888
+
+
+def test_grid_support_route_gives_the_same_fields():
+    """pals_mu / pals_dmu on the node grid: the index-box route (grid=...)
+    and the plain per-point route give identical arrays, also for anomalies
+    that touch the domain boundary."""
+    from synthetic.phantom import node_coords, node_grid
+    for name in ("t3d_21", "t2d_37"):
+        wl = WORKLOADS[name]
+        X = node_coords(wl)
+        rng = np.random.default_rng(12)
+        d = wl.dim
+        p = np.zeros((3, d + 2))
+        p[:, :d] = rng.uniform(0.0, 1.0, size=(3, d))
+        p[0, :d] = 0.02                                   # centre outside the node range
+        p[:, d] = rng.uniform(0.05, 0.2, size=3)
+        p[:, d + 1] = 0.03
+        p = p.ravel()
+        assert np.array_equal(pals_mu(p, X, 0.01), pals_mu(p, X, 0.01, node_grid(wl)))
+        assert np.array_equal(pals_dmu(p, X, 0.01), pals_dmu(p, X, 0.01, node_grid(wl)))
