@@ -1,14 +1,29 @@
 #!/usr/bin/env python3
-"""Benchmark: full-order solves/s at relres <= 1e-8 on the 3D 64^3 DOT workload
-(32 sources + 32 detectors, 5 parameter samples, 4 level-set anomalies),
-mixed-precision batched recycled CG vs plain FP64 recycled CG, one GB300.
+"""Benchmark: full-order solves/s at relres <= 1e-8, learned + mixed batched
+recycled CG against plain FP64 recycled CG, on one GB300.
 
-A step = reset the basis to the seed state, then Algorithm 2 over samples
-1..5 (Galerkin check, deflated CG on the corrections, ordered append) and
-one reduced-model evaluation (Psi_r and its Jacobian) at a held-out point.
-The seed (eigenvectors of A~_0 and X_0) is computed once, untimed, as the
-paper treats it as an offline step.  Every step's solutions are checked to
+Default workload: the 3D 192^3 configuration (7,077,888 unknowns, 128
+sources + 128 detectors, 20 parameter samples, 8 level-set anomalies, global
+basis V at most 2048 columns).  Its 5120 solves run in waves of one sample
+(256 right-hand-side lanes per wave, the lanes of a wave in one batch), so
+one step is one wave:
+
+    step k: Algorithm 2 over sample 1 + (k mod 20) -- Galerkin check from
+            range(V), deflated CG on the corrections with the learned column
+            in the private recycle spaces, ordered append -- and the reduced
+            model with its Jacobian at a held-out parameter point.
+
+V keeps growing from step to step; the timed region starts from the seed
+state, so `--steps 20` times exactly one pass over the configuration's 20
+samples (other step counts wrap around, returning to the seed state after
+sample 20).  The seed (eigenvectors of A~_0 and X_0) and the network's
+training on held-out parameter points are computed once, untimed, as the
+paper treats the seed as offline work.  Every step's solutions are checked to
 meet their tolerance (float64 residual recomputed on the device).
+
+The 3D 128^3 configuration (64 + 64 right-hand sides x 10 samples = 1280
+lanes in one wave, tolerances 1e-8 / 1e-6) is measured too and reported in
+the same JSON line under "second_config".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,44 +47,69 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "c2_3d64"
+WORKLOAD = "c5_3d192"
+SECOND = "c3_3d128"
 METRIC = "full-order solves/s at relres 1e-8: learned+mixed batched RCG vs plain FP64 RCG"
-CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0, learned=1)  # learned + mixed, one wave
-MIXED_PLAIN = dict(precision=1, order=1, tau_rank=1e-6, wave_samples=0)          # the same without the network
-NTRAIN, EPOCHS, BATCH, LR = 8, 40, 16, 1e-3     # training solves (held-out parameter points), Adam schedule
+CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, learned=1)      # learned + mixed, batched waves
+MIXED_PLAIN = dict(precision=1, order=1, tau_rank=1e-6)               # the same without the network
+FP64_PAPER = dict(precision=0, order=0, tau_rank=1e-12)               # FP64, paper order
+BATCH, LR = 16, 1e-3                                                   # Adam batch and learning rate
 MAX_TRAIN = 32
-FP64_PAPER = dict(precision=0, order=0, tau_rank=1e-12)                  # FP64, paper order
-ORACLE_RHS = (0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39)    # CPU sample: 8 src + 8 det
-ORACLE_SAMPLES = (1, 2)
+
+# Per workload: samples per wave (0 = all in one wave), basis cap, training
+# parameter points and epochs of the network, held-out points of the
+# reduced-model sweep, steps of the leg without the network, the CPU oracle's
+# bounded sample (samples, right-hand sides) and the FP64 baseline's samples.
+SETTINGS = {
+    "c5_3d192": dict(wave=1, r_max=2048, train=2, epochs=20, sweep=4, nolearn_steps=5,
+                     oracle_samples=(1,), oracle_rhs=(0, 128), base_samples=1,
+                     oracle_unavailable="the oracle cannot seed 7,077,888 unknowns within a bench run: its ARPACK "
+                                        "eigensolver for the 10 smallest eigenvectors of A~_0 (Sec. 4.2.2) ran "
+                                        "over 30 minutes on the host without converging",
+                     oracle_context="c2_3d64"),
+    "c3_3d128": dict(wave=0, r_max=1024, train=0, epochs=0, sweep=0, nolearn_steps=0,
+                     oracle_samples=(1,), oracle_rhs=(0, 64), base_samples=0),
+    "c2_3d64": dict(wave=0, r_max=1024, train=8, epochs=40, sweep=16, nolearn_steps=5,
+                    oracle_samples=(1, 2), oracle_rhs=(0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39),
+                    base_samples=0),
+}
+DEFAULT_SETTINGS = dict(wave=0, r_max=1024, train=2, epochs=10, sweep=0, nolearn_steps=0,
+                        oracle_samples=(1,), oracle_rhs=(0, 1, 2, 3), base_samples=0)
 
 
-def parse_args():
+def settings(name):
+    return SETTINGS.get(name, DEFAULT_SETTINGS)
+
+
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 sequential leg")
+    ap.add_argument("--second", default=SECOND, help="second configuration measured in the same run ('' skips it)")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 sequential and no-network legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--ncu-region", action="store_true",
                     help="profile only the timed steps (cudaProfilerStart/Stop); skip the other legs")
-    ap.add_argument("--train-samples", type=int, default=NTRAIN,
+    ap.add_argument("--train-samples", type=int, default=None,
                     help="parameter points solved (untimed) to train the learned augmentation")
-    ap.add_argument("--epochs", type=int, default=EPOCHS, help="Adam epochs over the recorded pairs")
+    ap.add_argument("--epochs", type=int, default=None, help="Adam epochs over the recorded pairs")
     ap.add_argument("--products", action="store_true",
                     help="time the basis product A^T B on the tensor cores and on CUDA cores (one JSON line per shape)")
     ap.add_argument("--products-shapes", type=int, default=4, help="number of --products shapes to run")
-    ap.add_argument("--rom-sweep", type=int, default=16,
-                    help="held-out parameter points for the reduced-model sweep (Psi_r and J through the "
-                         "last step's basis; 0 skips it)")
+    ap.add_argument("--rom-sweep", type=int, default=None,
+                    help="held-out parameter points for the reduced-model sweep (0 skips it)")
     ap.add_argument("--rom-batch", type=int, default=8, help="points per rcg_rom_eval_batch call in the sweep")
     ap.add_argument("--alg1-tau", type=float, default=1e-6,
-                    help="relative singular-value cut of the Algorithm 1 comparison (untimed; <= 0 skips it)")
+                    help="relative singular-value cut of the Algorithm 1 comparison (untimed; <= 0 skips it; "
+                         "only where the kept solutions fit in host memory)")
+    ap.add_argument("--cpu-timeout", type=float, default=900.0, help="seconds the CPU oracle leg may take")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # --------------------------------------------------------------------- clocks
@@ -125,24 +165,16 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- GPU pieces
-def make_ctx(rcg, inp, opts, torch, device_inputs=True):
-    wl = inp["wl"]
-    stream = torch.cuda.current_stream().cuda_stream
-    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, stream=stream, k_u=wl.k_u, max_samples=wl.K + 2 + MAX_TRAIN,
-                      r_max=1024, **opts)
-    ctx.set_diffusion(inp["D"])
-    ctx.set_sources_detectors(inp["src_ij"], inp["det_ij"])
-    ctx.set_tolerances(inp["tol"])
-    return ctx
-
-
 def workload_config(name):
     """The workload part of the JSON line's config, the same for both arms."""
     from synthetic.phantom import WORKLOADS
     wl = WORKLOADS[name]
+    st = settings(name)
+    spw = wl.K if st["wave"] <= 0 else min(st["wave"], wl.K)
     return {"workload": name, "grid": f"{wl.dim}D {wl.N}^{wl.dim} ({wl.n} unknowns)",
             "rhs": f"{wl.nsrc} sources + {wl.ndet} detectors", "samples": wl.K,
-            "solves_per_step": wl.K * wl.nrhs, "tol": wl.tol[0]}
+            "samples_per_step": spw, "solves_per_step": spw * wl.nrhs, "solves_per_pass": wl.K * wl.nrhs,
+            "tol": sorted(set(wl.tol)), "anomalies": wl.n_anom, "basis_cap": st["r_max"]}
 
 
 def replica_value(torch, ms_local, world, solves_per_step, steps, dev):
@@ -156,158 +188,199 @@ def replica_value(torch, ms_local, world, solves_per_step, steps, dev):
     return world * solves_per_step * steps / (ms_max / 1e3), ms_max
 
 
-def run_ours(args, rank, world, torch):
-    import numpy as np
-    from paper_1602_00138_gb300 import rcg
-    from synthetic.phantom import make_workload, heldout_params, pals_mu, pals_dmu
+def wave_plan(K, wave):
+    """Sample ranges (first, count) of the waves of one pass over samples 1..K."""
+    w = K if wave <= 0 else min(wave, K)
+    return [(s, min(w, K - s + 1)) for s in range(1, K + 1, w)]
 
-    inp = make_workload(args.workload, with_dmu=False)
-    wl = inp["wl"]
-    K, n = wl.K, wl.n
-    p_ho = heldout_params(wl, 1)[0]
-    mu_ho = pals_mu(p_ho, inp["X"], wl.mu_bg)
-    dmu_ho = np.ascontiguousarray(pals_dmu(p_ho, inp["X"], wl.mu_bg))      # (nparam, n)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    mu_dev = torch.tensor(inp["mu"], dtype=torch.float64, device=dev)       # samples resident in HBM
-    mu_ho_dev = torch.tensor(mu_ho, dtype=torch.float64, device=dev)
-    dmu_dev = torch.tensor(dmu_ho, dtype=torch.float64, device=dev)
-    psi_dev = torch.empty(wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
-    J_dev = torch.empty(wl.nparam * wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
-    # training samples of the learned augmentation: parameter points of the same
-    # jitter law, disjoint from the timed samples and the held-out ROM point
-    ntrain, epochs = min(args.train_samples, MAX_TRAIN), args.epochs
-    mu_tr = [pals_mu(p, inp["X"], wl.mu_bg) for p in heldout_params(wl, ntrain, seed_offset=2000)]
-    learn_info = {}
 
-    def train_network(ctx):
-        """Offline (untimed, like the seed): solve the training samples with
-        pair recording, then Adam on the recorded pairs."""
-        from synthetic.cnn_init import init_weights
-        for i, m in enumerate(mu_tr):
-            ctx.set_sample(K + 1 + i, m)
-        ctx.learn_set_weights(init_weights(0))
-        ctx.learn_record(True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.solve_all(K + 1, ntrain)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        loss0 = ctx.learn_train(1, BATCH, LR, 1)
-        loss = ctx.learn_train(max(epochs - 1, 0), BATCH, LR, 2) if epochs > 1 else loss0
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        ctx.learn_record(False)
-        learn_info.update(pairs=ctx.learn_pairs(), epochs=epochs, batch=BATCH, lr=LR, loss_first_epoch=loss0,
-                          loss_last_epoch=loss, data_s=round(t1 - t0, 3), train_s=round(t2 - t1, 3),
-                          training_samples=ntrain, params=len(ctx.learn_get_weights()))
+class Workload:
+    """Inputs of one configuration, host and device copies."""
 
-    def prepare(opts):
-        ctx = make_ctx(rcg, inp, opts, torch)
-        for s in range(K + 1):
-            ctx.set_sample(s, mu_dev[s])
-        t0 = time.perf_counter()
-        seed_stats = ctx.seed(0, None)
-        torch.cuda.synchronize()
-        seed_s = time.perf_counter() - t0
-        if opts.get("learned"):
-            train_network(ctx)
-        return ctx, seed_stats, seed_s
+    def __init__(self, name, torch, dev, heldout=1):
+        import numpy as np
+        from synthetic.phantom import make_workload, heldout_params, node_grid, pals_mu, pals_dmu
+        self.name = name
+        self.inp = make_workload(name, with_dmu=False)
+        self.wl = wl = self.inp["wl"]
+        self.st = settings(name)
+        self.grid = node_grid(wl)
+        self.X = self.inp["X"]
+        p_ho = heldout_params(wl, 1)[0]
+        self.mu_ho = pals_mu(p_ho, self.X, wl.mu_bg, self.grid)
+        self.dmu_ho = np.ascontiguousarray(pals_dmu(p_ho, self.X, wl.mu_bg, self.grid))     # (nparam, n)
+        self.mu_dev = torch.tensor(self.inp["mu"], dtype=torch.float64, device=dev)       # samples resident in HBM
+        self.mu_ho_dev = torch.tensor(self.mu_ho, dtype=torch.float64, device=dev)
+        self.dmu_dev = torch.tensor(self.dmu_ho, dtype=torch.float64, device=dev)
+        self.psi_dev = torch.empty(wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
+        self.J_dev = torch.empty(wl.nparam * wl.ndet * wl.nsrc, dtype=torch.float64, device=dev)
+        self.plan = wave_plan(wl.K, self.st["wave"])
 
-    def step(ctx):
-        ctx.reset_to_seed()
-        stats, rc = ctx.solve_all(1, K)
-        ctx.rom_eval_device(mu_ho_dev, dmu_dev, psi_dev, J_dev, wl.nparam)
+    def make_ctx(self, rcg, opts, torch, extra_samples=0, **kw):
+        wl = self.wl
+        stream = torch.cuda.current_stream().cuda_stream
+        ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, stream=stream, k_u=wl.k_u,
+                          max_samples=wl.K + 2 + extra_samples, r_max=self.st["r_max"],
+                          wave_samples=self.st["wave"], **opts, **kw)
+        ctx.set_diffusion(self.inp["D"])
+        ctx.set_sources_detectors(self.inp["src_ij"], self.inp["det_ij"])
+        ctx.set_tolerances(self.inp["tol"])
+        return ctx
+
+
+def check_stats(stats, tol):
+    bad = [s for s in stats if not (s["relres"] <= tol[s["rhs"]] * (1 + 1e-9)) or s["status"] != 0]
+    if bad:
+        raise RuntimeError(f"{len(bad)} right-hand sides missed their tolerance: {bad[:2]}")
+
+
+def run_leg(args, torch, W, ctx, steps, warmup, world=1, profile=False, clocks=None, step_rom=True):
+    """Warm-up steps, then `steps` timed steps from the seed state (CUDA events
+    on the launching stream, synchronised on both sides).  Returns a dict with
+    the total and per-step device ms, the launches and the last pass's stats."""
+    plan = W.plan
+    st = torch.cuda.current_stream()
+
+    def step(k):
+        s0, cnt = plan[k % len(plan)]
+        if k % len(plan) == 0:
+            ctx.reset_to_seed()
+        stats, rc = ctx.solve_all(s0, cnt)
+        if step_rom:
+            ctx.rom_eval_device(W.mu_ho_dev, W.dmu_dev, W.psi_dev, W.J_dev, W.wl.nparam)
         return stats
 
-    def check(stats):
-        bad = [s for s in stats if not (s["relres"] <= inp["tol"][s["rhs"]] * (1 + 1e-9)) or s["status"] != 0]
-        if bad:
-            raise RuntimeError(f"{len(bad)} right-hand sides missed their tolerance: {bad[:2]}")
+    for k in range(warmup):
+        check_stats(step(k), W.inp["tol"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    if profile:
+        ctx.profile(True)
+    l0 = ctx.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    if args.ncu_region:
+        torch.cuda.profiler.start()
+    ev[0].record(st)
+    all_stats = []
+    for k in range(steps):
+        all_stats.append(step(k))
+        ev[k + 1].record(st)
+    torch.cuda.synchronize()
+    if args.ncu_region:
+        torch.cuda.profiler.stop()
+    clk = clocks.stop() if clocks else None
+    ms = ev[0].elapsed_time(ev[steps])
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    launches = ctx.launch_count() - l0
+    prof = None
+    if profile:
+        prof = [ctx.profile_get(k) for k in range(5)]
+        ctx.profile(False)
+    for s in all_stats:
+        check_stats(s, W.inp["tol"])
+    flat = [x for s in all_stats for x in s]
+    return dict(ms=ms, per_step=per_step, launches=launches, stats=flat, prof=prof, clocks=clk,
+                solves=len(flat))
 
-    def timed(ctx, steps, warmup, profile=False):
-        for _ in range(warmup):
-            check(step(ctx))
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        if profile:
-            ctx.profile(True)
-        l0 = ctx.launch_count()
-        st = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        if args.ncu_region:
-            torch.cuda.profiler.start()
-        e0.record(st)
-        all_stats = []
-        for _ in range(steps):
-            all_stats.append(step(ctx))
-        e1.record(st)
-        torch.cuda.synchronize()
-        if args.ncu_region:
-            torch.cuda.profiler.stop()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            torch.distributed.barrier()
-        launches = ctx.launch_count() - l0
-        prof = None
-        if profile:
-            prof = [ctx.profile_get(k) for k in range(5)]
-            ctx.profile(False)
-        for s in all_stats:
-            check(s)
-        return ms, launches, all_stats, prof
 
-    # ---- contender: mixed precision, all samples in one wave
-    clocks = Clocks(torch.cuda.current_device())
-    ctx, seed_stats, seed_s = prepare(CONTENDER)
-    clocks.start()
-    ms, launches, all_stats, prof = timed(ctx, args.steps, args.warmup, profile=True)
-    clk = clocks.stop()
-    solves_per_step = K * wl.nrhs
-    value, ms_max = replica_value(torch, ms, world, solves_per_step, args.steps, dev)
-    phases = {k: ctx.phase_ms(k) for k in ("check", "cg", "append", "rom")}
-    rank_V = ctx.rank()
-    mean_iters = float(np.mean([s["iters"] for s in all_stats[-1]]))
-    learn_info["augmented_last_step"] = int(sum(s["augmented"] for s in all_stats[-1]))
-    trained = ctx.learn_get_weights()
+def train_network(ctx, W, torch, ntrain, epochs):
+    """Offline (untimed, like the seed): solve held-out parameter points with
+    pair recording, then Adam on the recorded pairs."""
+    from synthetic.cnn_init import init_weights
+    from synthetic.phantom import heldout_params, pals_mu
+    wl = W.wl
+    for i, p in enumerate(heldout_params(wl, ntrain, seed_offset=2000)):
+        ctx.set_sample(wl.K + 1 + i, pals_mu(p, W.X, wl.mu_bg, W.grid))
+    ctx.learn_set_weights(init_weights(0))
+    ctx.learn_record(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s0, cnt in wave_plan(ntrain, W.st["wave"]):
+        ctx.solve_all(wl.K + s0, cnt)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss0 = ctx.learn_train(1, BATCH, LR, 1)
+    loss = ctx.learn_train(max(epochs - 1, 0), BATCH, LR, 2) if epochs > 1 else loss0
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ctx.learn_record(False)
+    return dict(pairs=ctx.learn_pairs(), epochs=epochs, batch=BATCH, lr=LR, loss_first_epoch=loss0,
+                loss_last_epoch=loss, data_s=round(t1 - t0, 3), train_s=round(t2 - t1, 3),
+                training_samples=ntrain, params=len(ctx.learn_get_weights()))
 
-    # ---- roofline of the dominant inner-CG kernel (device events over the timed region)
+
+def prepare(rcg, W, opts, torch, ntrain=0, epochs=0, **kw):
+    ctx = W.make_ctx(rcg, opts, torch, extra_samples=ntrain if opts.get("learned") else 0, **kw)
+    for s in range(W.wl.K + 1):
+        ctx.set_sample(s, W.mu_dev[s])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seed_stats = ctx.seed(0, None)
+    torch.cuda.synchronize()
+    seed_s = time.perf_counter() - t0
+    learn = {}
+    if opts.get("learned"):
+        learn = train_network(ctx, W, torch, ntrain, epochs)
+    return ctx, seed_s, learn
+
+
+def roofline(W, prof, peak, peak_source):
+    """Achieved bandwidth of the dominant inner-CG kernel and of the stencil
+    kernel from the device timers of the timed steps.  Algorithmic bytes
+    (unique DRAM bytes a launch must move), per node per active lane, s = 4:
+      stencil    read p, write q (D and the sample diagonal once per sample,
+                 L2-resident, not counted): 2
+      update     read r, q, write r, the lane's private A~W columns: 3 + k_priv
+      u0dots     read r; the k_u shared A~_s U_0 columns once per tile of 32
+                 lanes: 1 + k_u / 32
+      direction  read r, p, write p, the private W columns, U_0 once per tile:
+                 3 + k_priv + k_u / 32 per continuing lane; read x, write x
+                 (the step x += alpha p) per updated lane, read p for an
+                 updated lane that stopped.  A private W column is a column of
+                 V or X_0 shared by the lanes of one right-hand side in a wave,
+                 so it counts once per right-hand side (k_priv / lanes per RHS).
+    """
+    wl, n, s_bytes = W.wl, W.wl.n, 4
+    lanes_per_rhs = wl.K if W.st["wave"] <= 0 else min(W.st["wave"], wl.K)
     names = ["k_stencil4 (q = A p)", "k_update4 (r)", "k_u0dots (shared deflation dots)", "k_mu (lane scalars)",
              "k_direction4 (x, p)"]
-    s_bytes = 4
-    # Algorithmic bytes (unique DRAM bytes a launch must move), per node per active lane:
-    #   stencil    read p, write q; D and the sample diagonal once per sample: 2 + 2/nrhs
-    #   update     read r, q, write r, the lane's private A~W columns: 3 + k_priv
-    #   u0dots     read r; the k_u shared A~_s U_0 columns once per tile of 32 lanes: 1 + k_u/32
-    #   direction  read r, p, write p, private W columns, U_0 once per tile: 3 + k_priv + k_u/32
-    #              per continuing lane; read x, write x (the step x += alpha p) per updated lane,
-    #              and read p for an updated lane that stopped
-    kdom = max((0, 1, 2, 4), key=lambda k: prof[k]["ms"])
-    P = prof[kdom]
-    A = P["lane_units"]
-    if kdom == 0:
-        alg = A * n * (2 + 2 / wl.nrhs) * s_bytes
-    elif kdom == 2:
-        alg = A * n * (1 + wl.k_u / 32) * s_bytes
-    elif kdom == 1:
+
+    def alg_bytes(k):
+        P = prof[k]
+        A = P["lane_units"]
+        if k == 0:
+            return A * n * 2 * s_bytes
+        if k == 2:
+            return A * n * (1 + wl.k_u / 32) * s_bytes
         kpriv = P["defl_cols"] - wl.k_u * A
-        alg = (3 * A + kpriv) * n * s_bytes
-    else:
-        kpriv = P["defl_cols"] - wl.k_u * A
+        if k == 1:
+            return (3 * A + kpriv) * n * s_bytes
         A_upd = prof[1]["lane_units"]
-        alg = ((3 + wl.k_u / 32) * A + kpriv + 2 * A_upd + max(A_upd - A, 0)) * n * s_bytes
-    per_launch_bytes = alg / max(P["launches"], 1)
-    per_launch_s = P["ms"] / 1e3 / max(P["launches"], 1)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    achieved = per_launch_bytes / per_launch_s / 1e9
-    # DRAM traffic of the dominant kernel from an ncu capture, valid only while
-    # the kernel's source text is the one that was measured
+        return ((3 + wl.k_u / 32) * A + kpriv / lanes_per_rhs + 2 * A_upd + max(A_upd - A, 0)) * n * s_bytes
+
+    def entry(k):
+        P = prof[k]
+        launches = max(P["launches"], 1)
+        per_launch_bytes = alg_bytes(k) / launches
+        per_launch_s = P["ms"] / 1e3 / launches
+        ach = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+        return {"kernel": names[k], "achieved": round(ach, 1), "frac": round(ach / peak, 4),
+                "launches": P["launches"], "avg_launch_us": round(per_launch_s * 1e6, 2),
+                "alg_bytes_per_launch": round(per_launch_bytes)}
+
+    kdom = max((0, 1, 2, 4), key=lambda k: prof[k]["ms"])
+    d = entry(kdom)
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path):
+        # DRAM traffic per lane and node of the dominant kernel from an ncu
+        # capture, valid only while the kernel's source text is the one measured
         tr = json.load(open(tr_path))
         src = open(os.path.join(ROOT, "paper_1602_00138_gb300", "csrc", "cg4.cu")).read()
         ent = tr.get(["stencil", "update", "u0dots", "mu", "direction"][kdom])
@@ -315,31 +388,63 @@ def run_ours(args, rank, world, torch):
             i = src.index("\n" + ent["kernel"] + "(")
             text = src[src.rindex("__global__", 0, i):src.index("\n}\n", i) + 3]
             if ent.get("kernel_sha256") == hashlib.sha256(text.encode()).hexdigest():
+                P = prof[kdom]
                 traffic = round(ent["dram_bytes_per_lane_node"] * n * P["lane_units"] / max(P["launches"], 1))
-    roofline = {"bound": "hbm", "kernel": names[kdom], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": "measured" if peaks else "fallback",
-                "launches": P["launches"], "avg_launch_us": round(per_launch_s * 1e6, 2),
-                "alg_bytes_per_launch": round(per_launch_bytes),
-                "kernels_ms": {names[k]: round(prof[k]["ms"], 3) for k in range(5)}}
+    out = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": "GB/s",
+           "frac": d["frac"], "traffic": traffic, "peak_source": peak_source, "launches": d["launches"],
+           "avg_launch_us": d["avg_launch_us"], "alg_bytes_per_launch": d["alg_bytes_per_launch"],
+           "stencil": entry(0), "kernels_ms": {names[k]: round(prof[k]["ms"], 3) for k in range(5)}}
+    return out
 
+
+def run_ours(args, rank, world, torch):
+    import numpy as np
+    from paper_1602_00138_gb300 import rcg
+    from synthetic.phantom import heldout_params, pals_mu, pals_dmu
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    W = Workload(args.workload, torch, dev)
+    wl, st = W.wl, W.st
+    n = wl.n
+    ntrain = min(args.train_samples if args.train_samples is not None else st["train"], MAX_TRAIN)
+    epochs = args.epochs if args.epochs is not None else st["epochs"]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_source = "measured" if peaks else "fallback"
+
+    # ---- contender: learned + mixed, batched waves
+    clocks = Clocks(torch.cuda.current_device())
+    ctx, seed_s, learn_info = prepare(rcg, W, CONTENDER, torch, ntrain, epochs)
+    leg = run_leg(args, torch, W, ctx, args.steps, args.warmup, world, profile=True, clocks=clocks)
+    clk = leg["clocks"]
+    spw = W.plan[0][1]
+    solves_per_step = leg["solves"] / args.steps
+    value, ms_max = replica_value(torch, leg["ms"], world, solves_per_step, args.steps, dev)
+    phases = {k: ctx.phase_ms(k) for k in ("check", "cg", "append", "rom")}
+    rank_V = ctx.rank()
+    iters = [s["iters"] for s in leg["stats"]]
+    learn_info["augmented"] = int(sum(s["augmented"] for s in leg["stats"]))
+    roof = roofline(W, leg["prof"], peak, peak_source)
+    res = dict(value=value, ms=ms_max / args.steps, launches=leg["launches"], roofline=roof, clocks=clk,
+               phases=phases, rank_V=rank_V, mean_iters=float(np.mean(iters)), seed_s=seed_s,
+               solves_per_step=solves_per_step, learn=learn_info, per_step_ms=[round(x, 2) for x in leg["per_step"]],
+               e2e=None, base=None, nolearn=None, rom_sweep=None, second=None, alg1=None)
     if args.ncu_region:
         ctx.close()
-        return dict(value=value, ms=ms_max / args.steps, launches=launches, roofline=roofline, e2e=None,
-                    clocks=clk, base=None, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
-                    seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=None)
+        return res
 
     # ---- reduced-model sweep: Psi_r and its Jacobian at held-out points through
     # the basis of the last timed step, batched, against one point per call
-    sweep = None
-    if args.rom_sweep > 0 and rank == 0:
-        Q, Bq = args.rom_sweep, max(1, min(args.rom_batch, args.rom_sweep))
+    nsweep = args.rom_sweep if args.rom_sweep is not None else st["sweep"]
+    if nsweep > 0 and rank == 0:
+        Q, Bq = nsweep, max(1, min(args.rom_batch, nsweep))
         ps = heldout_params(wl, Q, seed_offset=3000)
-        mus_sw = torch.tensor(np.stack([pals_mu(p, inp["X"], wl.mu_bg) for p in ps]), dtype=torch.float64,
+        mus_sw = torch.tensor(np.stack([pals_mu(p, W.X, wl.mu_bg, W.grid) for p in ps]), dtype=torch.float64,
                               device=dev)
         dmus_sw = torch.empty((Q, wl.nparam, n), dtype=torch.float64, device=dev)
         for q, p in enumerate(ps):
-            dmus_sw[q].copy_(torch.from_numpy(np.ascontiguousarray(pals_dmu(p, inp["X"], wl.mu_bg))))
+            dmus_sw[q].copy_(torch.from_numpy(np.ascontiguousarray(pals_dmu(p, W.X, wl.mu_bg, W.grid))))
         nd_ns = wl.ndet * wl.nsrc
         psi_sw = torch.empty((Q, nd_ns), dtype=torch.float64, device=dev)
         J_sw = torch.empty((Q, wl.nparam * nd_ns), dtype=torch.float64, device=dev)
@@ -369,115 +474,166 @@ def run_ours(args, rank, world, torch):
             times[name] = a.elapsed_time(b_) / 3
         dpsi = float(((psi_sw - psi_1).norm() / psi_1.norm()).item())
         dJ = float(((J_sw - J_1).norm() / J_1.norm()).item())
-        sweep = {"points": Q, "batch": Bq, "nparam": wl.nparam, "rank_V": rank_V,
-                 "evals_per_s": round(Q / (times["batched"] / 1e3), 1),
-                 "ms_per_point": round(times["batched"] / Q, 4),
-                 "single_call_ms_per_point": round(times["single"] / Q, 4),
-                 "rel_diff_vs_single": {"psi": dpsi, "J": dJ},
-                 "what": "Psi_r (ndet x nsrc) and J (nparam x ndet x nsrc) per point, inputs resident"}
+        res["rom_sweep"] = {"points": Q, "batch": Bq, "nparam": wl.nparam, "rank_V": rank_V,
+                            "evals_per_s": round(Q / (times["batched"] / 1e3), 1),
+                            "ms_per_point": round(times["batched"] / Q, 4),
+                            "single_call_ms_per_point": round(times["single"] / Q, 4),
+                            "rel_diff_vs_single": {"psi": dpsi, "J": dJ},
+                            "what": "Psi_r (ndet x nsrc) and J (nparam x ndet x nsrc) per point, inputs resident"}
         del mus_sw, dmus_sw, psi_sw, J_sw, psi_1, J_1
 
-    # ---- Algorithm 1 against Algorithm 2 (untimed): one pass of Algorithm 2 with
-    # the solutions kept, then the truncated SVD of the concatenated solutions
-    # (rcg_basis_compress); ranks, the compression time, and the reduced model
-    # of both bases at the sampled points (against the plain definition on the
-    # delivered solutions) and at held-out points (against each other)
-    alg1 = None
-    if args.alg1_tau > 0 and rank == 0:
-        ctx_a = make_ctx(rcg, inp, dict(MIXED_PLAIN, keep_solutions=1), torch)
-        for s in range(K + 1):
-            ctx_a.set_sample(s, mu_dev[s])
-        ctx_a.seed(0, None)
-        ctx_a.solve_all(1, K)
-        r2 = ctx_a.rank()
-        ps_ho = heldout_params(wl, 4, seed_offset=4000)
-        mus_ho = [pals_mu(p, inp["X"], wl.mu_bg) for p in ps_ho]
+    # ---- end to end through the public API with host buffers: every step copies
+    # its samples' mu and the held-out point's mu and dmu from pinned host memory
+    # and reads back the per-RHS statistics and Psi_r, J
+    trained = ctx.learn_get_weights()
+    pinned = torch.empty((wl.K + 1, n), dtype=torch.float64).pin_memory()
+    pinned.copy_(torch.from_numpy(W.inp["mu"]))
+    mu_ho_pin = torch.from_numpy(W.mu_ho).pin_memory()
+    dmu_pin = torch.from_numpy(W.dmu_ho).pin_memory()
 
-        def rom_errors(c):
-            smp = []
-            for s in range(1, K + 1):
-                P_r, _ = c.rom_eval(inp["mu"][s])
-                P_f, _ = c.full_eval(s)
-                smp.append(float(np.linalg.norm(P_r - P_f) / np.linalg.norm(P_f)))
-            return max(smp), [c.rom_eval(m)[0] for m in mus_ho]
-
-        # the plain definition uses the delivered solutions of Algorithm 2, kept in the context
-        e2_smp, P2_ho = rom_errors(ctx_a)
-        r1, sig = ctx_a.basis_compress(0, args.alg1_tau)
-        e1_smp, P1_ho = rom_errors(ctx_a)
-        d_ho = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(P1_ho, P2_ho))
-        alg1 = {"snapshot_columns": len(sig), "tau": args.alg1_tau, "rank_alg2": r2, "rank_alg1": r1,
-                "compress_ms": round(ctx_a.phase_ms("compress"), 2),
-                "sigma_ratio_at_rank_alg2": float(sig[min(r2, len(sig)) - 1] / sig[0]),
-                "psi_r_rel_err_sampled": {"alg2": e2_smp, "alg1": e1_smp},
-                "psi_r_rel_diff_heldout_alg1_vs_alg2": d_ho}
-        ctx_a.close()
-
-    # ---- end to end through the public API with host buffers
-    ctx_e = make_ctx(rcg, inp, CONTENDER, torch)
-    pinned = torch.empty((K + 1, n), dtype=torch.float64).pin_memory()
-    pinned.copy_(torch.from_numpy(inp["mu"]))
-    mu_ho_pin = torch.from_numpy(mu_ho).pin_memory()
-    dmu_pin = torch.from_numpy(dmu_ho).pin_memory()
-    for s in range(K + 1):
-        ctx_e.set_sample(s, pinned[s].numpy())
-    ctx_e.seed(0, None)
-    ctx_e.learn_set_weights(trained)          # the network trained above (untimed)
-
-    def e2e_step():
-        for s in range(1, K + 1):
-            ctx_e.set_sample(s, pinned[s].numpy())
-        ctx_e.reset_to_seed()
-        stats, _ = ctx_e.solve_all(1, K)
-        ctx_e.rom_eval(mu_ho_pin.numpy(), dmu_pin.numpy())
+    def e2e_step(k):
+        s0, cnt = W.plan[k % len(W.plan)]
+        for s in range(s0, s0 + cnt):
+            ctx.set_sample(s, pinned[s].numpy())
+        if k % len(W.plan) == 0:
+            ctx.reset_to_seed()
+        stats, _ = ctx.solve_all(s0, cnt)
+        ctx.rom_eval(mu_ho_pin.numpy(), dmu_pin.numpy())
         return stats
 
-    for _ in range(max(1, args.warmup)):
-        check(e2e_step())
+    for k in range(1):
+        check_stats(e2e_step(k), W.inp["tol"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        check(e2e_step())
+    h2d = 0
+    for k in range(args.steps):
+        check_stats(e2e_step(k), W.inp["tol"])
+        h2d += W.plan[k % len(W.plan)][1] * n * 8 + (1 + wl.nparam) * n * 8
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = time.perf_counter() - t0
     stat_bytes = ctypes.sizeof(rcg.Stat)
-    e2e = {"value": round(world * solves_per_step / e2e_s, 2), "unit": "solves/s",
-           "h2d_bytes_per_step": (K + 1 + wl.nparam) * n * 8,
-           "d2h_bytes_per_step": K * wl.nrhs * stat_bytes + wl.ndet * wl.nsrc * 8 * (1 + wl.nparam)}
-    ctx_e.close()
+    res["e2e"] = {"value": round(world * leg["solves"] / e2e_s, 2), "unit": "solves/s",
+                  "h2d_bytes_per_step": int(h2d / args.steps),
+                  "d2h_bytes_per_step": int(solves_per_step * stat_bytes + wl.ndet * wl.nsrc * 8 * (1 + wl.nparam))}
+    ctx.close()
+    del pinned, mu_ho_pin, dmu_pin
+    torch.cuda.empty_cache()
 
-    # ---- the same mixed wave without the network (the learned step's effect)
-    nolearn = None
-    if not args.no_baseline and rank == 0:
-        ctx_m, _, _ = prepare(MIXED_PLAIN)
-        ms_m, _, stats_m, _ = timed(ctx_m, args.steps, args.warmup)
-        nolearn = {"value": round(solves_per_step * args.steps / (ms_m / 1e3), 2), "unit": "solves/s",
-                   "ms_per_step": round(ms_m / args.steps, 3), "rank_V": ctx_m.rank(),
-                   "mean_cg_iters": float(np.mean([s["iters"] for s in stats_m[-1]]))}
+    # ---- the same mixed waves without the network (the learned step's effect),
+    # over the first steps of the pass, against the contender's same steps
+    nl = min(st["nolearn_steps"], args.steps)
+    if not args.no_baseline and rank == 0 and nl > 0:
+        ctx_m, _, _ = prepare(rcg, W, MIXED_PLAIN, torch)
+        leg_m = run_leg(args, torch, W, ctx_m, nl, 1)
+        res["nolearn"] = {"steps": nl, "value": round(leg_m["solves"] / (leg_m["ms"] / 1e3), 2), "unit": "solves/s",
+                          "contender_same_steps": round(leg_m["solves"] / (sum(leg["per_step"][:nl]) / 1e3), 2),
+                          "ms_per_step": round(leg_m["ms"] / nl, 3), "rank_V": ctx_m.rank(),
+                          "mean_cg_iters": float(np.mean([s["iters"] for s in leg_m["stats"]])),
+                          "contender_mean_cg_iters_same_steps": float(np.mean(
+                              [s["iters"] for s in leg["stats"][:len(leg_m["stats"])]]))}
         ctx_m.close()
 
-    # ---- plain FP64 recycled CG in the paper's order, same library and inputs
-    base = None
+    # ---- plain FP64 recycled CG in the paper's order, same library and inputs,
+    # over the first samples (a bounded sample of the pass: the float64 path is
+    # ~25x slower), against the contender's time for the same samples
+    nb = st["base_samples"] or wl.K
     if not args.no_baseline and rank == 0:
-        ctx_b, _, seed_b = prepare(FP64_PAPER)
-        ms_b, _, stats_b, _ = timed(ctx_b, 1, 1)
-        base = {"value": round(solves_per_step / (ms_b / 1e3), 2), "unit": "solves/s",
-                "ms_per_step": round(ms_b, 1), "rank_V": ctx_b.rank(),
-                "mean_iters": float(np.mean([s["iters"] for s in stats_b[-1]])),
-                "solved": int(sum(s["iters"] > 0 for s in stats_b[-1])),
-                "phases_ms": {k: round(ctx_b.phase_ms(k), 1) for k in ("check", "cg", "append", "rom")},
-                "precision": "f64", "order": "sequential (paper)", "seed_s": round(seed_b, 2)}
+        ctx_b, seed_b, _ = prepare(rcg, W, FP64_PAPER, torch)
+        torch.cuda.synchronize()
+        ctx_b.reset_to_seed()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        stats_b, _ = ctx_b.solve_all(1, nb)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        check_stats(stats_b, W.inp["tol"])
+        ms_b = e0.elapsed_time(e1)
+        steps_same = max(1, (nb + spw - 1) // spw)
+        res["base"] = {"value": round(len(stats_b) / (ms_b / 1e3), 2), "unit": "solves/s",
+                       "samples": list(range(1, nb + 1)), "solves": len(stats_b), "ms": round(ms_b, 1),
+                       "contender_same_samples": round(steps_same * solves_per_step / (sum(leg["per_step"][:steps_same]) / 1e3), 2),
+                       "rank_V": ctx_b.rank(), "mean_iters": float(np.mean([s["iters"] for s in stats_b])),
+                       "solved": int(sum(s["iters"] > 0 for s in stats_b)),
+                       "phases_ms": {k: round(ctx_b.phase_ms(k), 1) for k in ("check", "cg", "append")},
+                       "precision": "f64", "order": "sequential (paper)", "seed_s": round(seed_b, 2),
+                       "seed_phases_ms": {k: round(ctx_b.phase_ms(k), 1) for k in ("seed_eig", "seed_x0")}}
         ctx_b.close()
-    ctx.close()
-    return dict(value=value, ms=ms_max / args.steps, launches=launches, roofline=roofline, e2e=e2e,
-                clocks=clk, base=base, phases=phases, rank_V=rank_V, mean_iters=mean_iters,
-                seed_s=seed_s, solves_per_step=solves_per_step, learn=learn_info, nolearn=nolearn,
-                rom_sweep=sweep, alg1=alg1)
+
+    # ---- Algorithm 1 against Algorithm 2 (untimed), where the kept solutions fit in host memory
+    if args.alg1_tau > 0 and rank == 0 and wl.K * wl.nrhs * n * 8 < 8e9:
+        res["alg1"] = alg1_compare(args, rcg, W, torch)
+
+    # ---- the second configuration: mixed batched waves (no network)
+    if args.second and rank == 0:
+        res["second"] = second_config(args, rcg, torch, dev, peak, peak_source)
+    return res
+
+
+def alg1_compare(args, rcg, W, torch):
+    """One pass of Algorithm 2 with the solutions kept, then the truncated SVD
+    of the concatenated solutions (rcg_basis_compress); ranks, the compression
+    time, and the reduced model of both bases at the sampled points (against
+    the plain definition on the delivered solutions) and at held-out points."""
+    import numpy as np
+    from synthetic.phantom import heldout_params, pals_mu
+    wl = W.wl
+    ctx_a = W.make_ctx(rcg, dict(MIXED_PLAIN, keep_solutions=1), torch)
+    for s in range(wl.K + 1):
+        ctx_a.set_sample(s, W.mu_dev[s])
+    ctx_a.seed(0, None)
+    for s0, cnt in W.plan:
+        ctx_a.solve_all(s0, cnt)
+    r2 = ctx_a.rank()
+    mus_ho = [pals_mu(p, W.X, wl.mu_bg, W.grid) for p in heldout_params(wl, 4, seed_offset=4000)]
+
+    def rom_errors(c):
+        smp = []
+        for s in range(1, wl.K + 1):
+            P_r, _ = c.rom_eval(W.inp["mu"][s])
+            P_f, _ = c.full_eval(s)
+            smp.append(float(np.linalg.norm(P_r - P_f) / np.linalg.norm(P_f)))
+        return max(smp), [c.rom_eval(m)[0] for m in mus_ho]
+
+    e2_smp, P2_ho = rom_errors(ctx_a)
+    r1, sig = ctx_a.basis_compress(0, args.alg1_tau)
+    e1_smp, P1_ho = rom_errors(ctx_a)
+    d_ho = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(P1_ho, P2_ho))
+    out = {"snapshot_columns": len(sig), "tau": args.alg1_tau, "rank_alg2": r2, "rank_alg1": r1,
+           "compress_ms": round(ctx_a.phase_ms("compress"), 2),
+           "sigma_ratio_at_rank_alg2": float(sig[min(r2, len(sig)) - 1] / sig[0]),
+           "psi_r_rel_err_sampled": {"alg2": e2_smp, "alg1": e1_smp},
+           "psi_r_rel_diff_heldout_alg1_vs_alg2": d_ho}
+    ctx_a.close()
+    return out
+
+
+def second_config(args, rcg, torch, dev, peak, peak_source):
+    """The second configuration (default 3D 128^3: 1280 lanes in one wave,
+    tolerances 1e-8 / 1e-6) with the mixed batched solver, timed like the
+    contender (a step = every sample in one wave from the seed state)."""
+    import numpy as np
+    W2 = Workload(args.second, torch, dev)
+    wl = W2.wl
+    ctx2, seed2, _ = prepare(rcg, W2, MIXED_PLAIN, torch)
+    steps2 = max(1, min(args.steps, 5))
+    leg2 = run_leg(args, torch, W2, ctx2, steps2, max(1, min(args.warmup, 3)), profile=True)
+    roof2 = roofline(W2, leg2["prof"], peak, peak_source)
+    out = {**workload_config(args.second), "solver": "mixed batched RCG (no network)",
+           "steps": steps2, "value": round(leg2["solves"] / (leg2["ms"] / 1e3), 2), "unit": "solves/s",
+           "ms_per_step": round(leg2["ms"] / steps2, 3), "rank_V": ctx2.rank(),
+           "mean_cg_iters": float(np.mean([s["iters"] for s in leg2["stats"]])),
+           "phases_ms_last_step": {k: round(ctx2.phase_ms(k), 2) for k in ("check", "cg", "append", "rom")},
+           "seed_s_untimed": round(seed2, 3), "roofline": roof2, "gpu_launches": leg2["launches"]}
+    ctx2.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle leg
 def oracle_worker(args):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload."""
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload:
+    the seed on the sample's right-hand sides untimed, then each step one pass
+    of Algorithm 2 (check, deflated CG, append) over the sample, sequential."""
     import copy
     import numpy as np
     from oracle import basis as obasis, eigen, operator as op
@@ -485,38 +641,59 @@ def oracle_worker(args):
 
     inp = make_workload(args.workload, with_dmu=False)
     wl = inp["wl"]
-    cols = [j for j in ORACLE_RHS if j < wl.nrhs]
+    st = settings(args.workload)
+    cols = [j for j in st["oracle_rhs"] if j < wl.nrhs]
+    samples = tuple(s for s in st["oracle_samples"] if s <= wl.K)
+    t_setup = time.perf_counter()
     A0, Bt, Ct = op.assemble(inp, 0)
     B = np.hstack([Bt, Ct])[:, cols]
     tols = inp["tol"][cols]
     _, U0 = eigen.smallest_eigenpairs(A0, wl.k_u)
     st0 = obasis.seed(A0, B, U0, tols, tau=1e-12)
-    As = {i: op.assemble(inp, i)[0] for i in ORACLE_SAMPLES}
+    As = {i: op.assemble(inp, i)[0] for i in samples}
+    setup_s = time.perf_counter() - t_setup
     times = []
     for it in range(args.cpu_warmup + args.cpu_steps):
-        st = copy.deepcopy(st0)
+        stt = copy.deepcopy(st0)
         t0 = time.perf_counter()
-        out = obasis.solve_all(st, lambda i: As[i], ORACLE_SAMPLES, B, tols, order="sequential", tau=1e-12)
+        out = obasis.solve_all(stt, lambda i: As[i], samples, B, tols, order="sequential", tau=1e-12)
         dt = time.perf_counter() - t0
         if it >= args.cpu_warmup:
             times.append(dt)
         assert all(o["relres"] <= tols[o["rhs"]] * (1 + 1e-9) for o in out)
-    nsolve = len(ORACLE_SAMPLES) * len(cols)
+    nsolve = len(samples) * len(cols)
     print(json.dumps({"value": nsolve * len(times) / sum(times), "unit": "solves/s", "cores": 1,
-                      "kind": "oracle", "seconds": sum(times),
-                      "sample": f"{args.workload}: samples {list(ORACLE_SAMPLES)}, RHS {cols} "
-                                f"(8 sources + 8 detectors), sequential FP64, seed untimed"}))
+                      "kind": "oracle", "seconds": sum(times), "setup_s_untimed": round(setup_s, 1),
+                      "solves_per_step": nsolve,
+                      "sample": f"{args.workload}: samples {list(samples)}, RHS {cols}, sequential FP64 "
+                                f"Algorithm 2 from the oracle's own seed (untimed)"}))
 
 
-def run_oracle_subprocess(args, steps=1, warmup=0):
+def start_oracle_subprocess(args, steps=1, warmup=0, workload=None):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", args.workload,
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", workload or args.workload,
            "--cpu-steps", str(steps), "--cpu-warmup", str(warmup)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        return {"value": None, "error": (r.stderr or r.stdout)[-400:]}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    out = tempfile.TemporaryFile("w+")
+    err = tempfile.TemporaryFile("w+")
+    p = subprocess.Popen(cmd, stdout=out, stderr=err, text=True, env=env)
+    return (p, out, err, time.perf_counter())
+
+
+def finish_oracle_subprocess(handle, timeout):
+    p, out, err, t0 = handle
+    try:
+        p.wait(timeout=max(1.0, timeout - (time.perf_counter() - t0)))
+    except subprocess.TimeoutExpired:
+        p.kill()
+        p.wait()
+        return {"value": None, "unavailable": f"the oracle did not finish within {timeout:.0f} s on one host core "
+                                              f"(its ARPACK eigenvector seed and scipy solves at this size)"}
+    out.seek(0)
+    err.seek(0)
+    if p.returncode != 0:
+        return {"value": None, "error": (err.read() or out.read())[-400:]}
+    return json.loads(out.read().strip().splitlines()[-1])
 
 
 # ---------------------------------------------------------------------- main
@@ -557,20 +734,25 @@ def contender_line(args, world, res, cpu):
     """The JSON line of this library's arm from the measured results `res`."""
     from synthetic.phantom import WORKLOADS
     wl = WORKLOADS[args.workload]
+    cfg = workload_config(args.workload)
     return {
         "metric": METRIC, "value": round(res["value"], 2), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {**workload_config(args.workload),
+        "config": {**cfg,
                    "precision": "f32 inner CG / stencil / basis, f64 refinement residuals, "
                                 "Galerkin matrices and decisions",
-                   "order": "wave (all samples and RHS in one batch)", "tau_rank": CONTENDER["tau_rank"],
-                   "learned": True, "learning": res["learn"],
+                   "order": (f"waves of {cfg['samples_per_step']} sample(s): every RHS of a wave in one batch, "
+                             f"V frozen within a wave"),
+                   "step": "one wave (check, deflated CG, ordered append) + Psi_r and J at a held-out point; "
+                           "the timed region starts from the seed state and V grows across steps",
+                   "tau_rank": CONTENDER["tau_rank"], "learned": True, "learning": res["learn"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": f"working set > L2 ({res['solves_per_step']} lanes x {wl.n} nodes x 24 B = "
-                         f"{res['solves_per_step'] * wl.n * 24 / 1e9:.1f} GB)",
-                   "rank_V_after_step": res["rank_V"], "mean_cg_iters": res["mean_iters"],
+                   "l2": f"working set > L2 ({cfg['solves_per_step']} lanes x {wl.n} nodes x 24 B = "
+                         f"{cfg['solves_per_step'] * wl.n * 24 / 1e9:.1f} GB)",
+                   "rank_V_after_timed_steps": res["rank_V"], "mean_cg_iters": res["mean_iters"],
+                   "per_step_ms": res.get("per_step_ms"),
                    "phases_ms_last_step": {k: round(v, 2) for k, v in res["phases"].items()},
                    "seed_s_untimed": round(res["seed_s"], 3)},
         "roofline": res["roofline"],
@@ -582,7 +764,29 @@ def contender_line(args, world, res, cpu):
         "mixed_without_learning": res["nolearn"],
         "rom_sweep": res.get("rom_sweep"),
         "alg1_vs_alg2": res.get("alg1"),
+        "second_config": res.get("second"),
     }
+
+
+def reference_line(args, res):
+    """The reference arm's JSON line (the CPU oracle) from its worker result."""
+    st = settings(args.workload)
+    secs = res.get("seconds")
+    line = {"impl": "reference", "metric": METRIC, "value": res.get("value"), "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * secs / max(args.steps, 1), 3) if secs else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": dict(workload_config(args.workload), order="sequential", precision="f64 (CPU oracle)",
+                           solves_per_step=res.get("solves_per_step",
+                                                   len(st["oracle_samples"]) * len(st["oracle_rhs"])),
+                           timed_sample=res.get("sample")),
+            "cpu_baseline": {k: res.get(k) for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": res.get("value"), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    if res.get("value") is None:
+        return {"impl": "reference", "unavailable": res.get("unavailable") or (res.get("error") or "")[-200:]}
+    return line
 
 
 def main():
@@ -599,22 +803,20 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        res = run_oracle_subprocess(args, steps=args.steps, warmup=args.warmup)
-        secs = res.get("seconds")
-        line = {"impl": "reference", "metric": METRIC, "value": res.get("value"), "unit": "solves/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(1e3 * secs / max(args.steps, 1), 3) if secs else None,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": dict(workload_config(args.workload), order="sequential",
-                                                    precision="f64 (CPU oracle)"),
-                "cpu_baseline": {k: res.get(k) for k in ("value", "unit", "cores", "kind", "sample")},
-                "e2e": {"value": res.get("value"), "unit": "solves/s", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        if res.get("value") is None:
-            line["error"] = res.get("error")
-        print(json.dumps(line))
+        why = settings(args.workload).get("oracle_unavailable")
+        if why:
+            print(json.dumps({"impl": "reference", "unavailable": why}))
+            return
+        h = start_oracle_subprocess(args, steps=args.steps, warmup=args.warmup)
+        res = finish_oracle_subprocess(h, args.cpu_timeout)
+        print(json.dumps(reference_line(args, res)))
         return
 
+    # the CPU oracle leg runs on one host core beside the GPU legs
+    cpu_h = None
+    ctx_wl = settings(args.workload).get("oracle_context")
+    if rank == 0 and world == 1 and not args.no_cpu and not args.ncu_region:
+        cpu_h = start_oracle_subprocess(args, workload=ctx_wl)
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -629,8 +831,13 @@ def main():
     g.build()
     res = run_ours(args, rank, world, torch)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and not args.ncu_region:
-        cpu = run_oracle_subprocess(args)
+    if cpu_h is not None:
+        cpu = finish_oracle_subprocess(cpu_h, args.cpu_timeout)
+        if ctx_wl:
+            # the oracle cannot run this workload: its rate on a smaller
+            # configuration of the same family is context only
+            cpu = {**cpu, "workload": ctx_wl, "unavailable_for": args.workload,
+                   "why": settings(args.workload)["oracle_unavailable"]}
     if rank == 0:
         line = contender_line(args, world, res, cpu)
         print(json.dumps(line))

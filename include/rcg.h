@@ -176,6 +176,27 @@ int rcg_apply(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int n
 #define RCG_NOALLOC_MAX_COLS 1024
 int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols);
 
+/* The float32 operator of the inner CG iteration (the stencil of eq. sum,
+ * A~_s = A~_* + diag(h^2 mu_s), applied to every Lanczos / CG vector, Sec.
+ * 5.3): y_j = A~_s x_j for ncols device columns of n floats (leading
+ * dimension n, 16-byte aligned; needs N % 4 == 0), and dots[j] += x_j^T y_j
+ * (device, ncols doubles, may be NULL).  variant: -1 the autotuned choice
+ * (the one the solver uses for this grid and column count), or one of the
+ * RCG_STENCIL_VARIANTS kernels named by rcg_stencil_variant_name (0: rows,
+ * 1: plane ring, 2..13: z-marching tiles).  RCG_ERR_INVALID if the variant
+ * does not support the grid.  Parity / timing entry; returns after the
+ * context's stream has finished. */
+#define RCG_STENCIL_VARIANTS 14
+int rcg_apply_f32(rcg_ctx *c, int s, int variant, const float *x_dev, float *y_dev, int ncols, double *dots_dev);
+/* Name of stencil variant v (NULL if out of range); 1 if the variant runs on
+ * the grid of c, else 0. */
+const char *rcg_stencil_variant_name(int v);
+int rcg_stencil_variant_ok(const rcg_ctx *c, int v);
+/* The autotuner's record (one line per tuned grid and lane-count class: the
+ * time of every candidate and the choice) into buf (len bytes, NUL-
+ * terminated); returns the full length. */
+int rcg_tuning_report(char *buf, int len);
+
 /* The basis product of the orthogonalisation in the append (Sec. 5.3
  * incremental QR: V^T W, W^T W, V^T Q, Q^T Q), exposed for testing and
  * timing: C = A^T diag(w) B (w == NULL: C = A^T B; w != NULL is the weighted

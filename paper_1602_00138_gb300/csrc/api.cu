@@ -278,6 +278,7 @@ struct Engine : EngineBase {
         pv = c->alloc<T>((size_t)m * ld);
         qv = c->alloc<T>((size_t)m * ld);
         ls.m = m;
+        ls.nl = m;
         ls.rr = c->alloc<double>(3 * (size_t)m);
         ls.pq = c->alloc<double>(2 * (size_t)m);
         ls.wv = c->alloc<double>(2 * (size_t)m * KMAX);
@@ -910,6 +911,7 @@ struct Engine : EngineBase {
                 if (act[l]) set_thresh(l, std::sqrt(rr_h[l]));
             // the whole capacity: the scalar iteration launches over ls.m lanes and
             // skips those whose active / mask entry is 0 (lanes m.. of a smaller wave)
+            ls.nl = m;                     // the kernels of this wave launch over its m lanes
             RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * ls.m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * ls.m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * ls.m, st));
@@ -1873,6 +1875,59 @@ static int set_sample_impl(rcg_ctx *c, int s, const double *mu, bool device) {
 
 int rcg_set_sample(rcg_ctx *c, int s, const double *mu) { return set_sample_impl(c, s, mu, false); }
 int rcg_set_sample_device(rcg_ctx *c, int s, const double *mu_dev) { return set_sample_impl(c, s, mu_dev, true); }
+
+int rcg_apply_f32(rcg_ctx *c, int s, int variant, const float *x_dev, float *y_dev, int ncols, double *dots_dev) {
+    return guarded(c, [&]() {
+        if (s < 0 || s >= c->opt.max_samples || !c->sample_set[s] || ncols < 0 || !x_dev || !y_dev ||
+            variant < -1 || variant >= RCG_STENCIL_VARIANTS)
+            return fail(c, RCG_ERR_INVALID, "bad rcg_apply_f32 arguments");
+        if (!cg4_supported(c->g) || ((uintptr_t)x_dev & 15) || ((uintptr_t)y_dev & 15))
+            return fail(c, RCG_ERR_INVALID, "rcg_apply_f32 needs N % 4 == 0 and 16-byte aligned columns");
+        if (variant >= 0 && !stencil_variant_ok(c->g, variant))
+            return fail(c, RCG_ERR_INVALID, "the stencil variant does not support this grid");
+        if (ncols == 0) return RCG_OK;
+        std::vector<const float *> hs(ncols), hg(ncols);
+        std::vector<float *> hd(ncols);
+        std::vector<int> lanes(ncols), act(ncols, 1);
+        for (int j = 0; j < ncols; ++j) {
+            hs[j] = x_dev + (long long)j * c->n;
+            hd[j] = y_dev + (long long)j * c->n;
+            hg[j] = c->diag32_of(s);
+            lanes[j] = j;
+        }
+        const float **a = c->alloc<const float *>(ncols);
+        float **b = c->alloc<float *>(ncols);
+        const float **gp = c->alloc<const float *>(ncols);
+        int *dl = c->alloc<int>(ncols), *da = c->alloc<int>(ncols);
+        double *dd = dots_dev ? nullptr : c->alloc<double>(ncols);
+        c->h2d(a, hs.data(), ncols); c->h2d(b, hd.data(), ncols); c->h2d(gp, hg.data(), ncols);
+        c->h2d(dl, lanes.data(), ncols); c->h2d(da, act.data(), ncols);
+        if (dd) RCG_CUDA_TRY(cudaMemsetAsync(dd, 0, sizeof(double) * ncols, c->st));
+        stencil4_apply(c->st, c->g, c->D32, gp, a, b, ncols, dl, da, dots_dev ? dots_dev : dd, variant);
+        c->sync();
+        for (void *q : std::vector<void *>{(void *)a, (void *)b, (void *)gp, (void *)dl, (void *)da, (void *)dd})
+            c->release(q);
+        return RCG_OK;
+    });
+}
+
+const char *rcg_stencil_variant_name(int v) { return stencil_variant_name(v); }
+
+int rcg_stencil_variant_ok(const rcg_ctx *c, int v) { return c ? stencil_variant_ok(c->g, v) : 0; }
+
+int rcg_tuning_report(char *buf, int len) {
+    try {
+        const std::string r = stencil_tuning_report();
+        if (buf && len > 0) {
+            const int k = std::min<int>(len - 1, (int)r.size());
+            std::memcpy(buf, r.data(), (size_t)k);
+            buf[k] = 0;
+        }
+        return (int)r.size();
+    } catch (...) {
+        return RCG_ERR_INVALID;
+    }
+}
 
 int rcg_apply(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_dev, int ncols) {
     return guarded(c, [&]() {

@@ -305,9 +305,10 @@ void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *di
     const int sprev = (t - 1) % 3, scur = t % 3, snext = (t + 1) % 3, spq = t % 2, sw = t % 2;
     const bool tm = kt && kt->on;
     cudaEvent_t e = tm ? kt->start(st) : nullptr;
-    apply_op<T>(st, g, D, diag_of_col, p_ptr, q_ptr, ls.m, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
+    apply_op<T>(st, g, D, diag_of_col, p_ptr, q_ptr, ls.nl, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
     if (tm) { kt->stop(0, e, st); e = kt->start(st); }
-    dim3 grid(grid_x(g.n, ls.m), ls.m);
+    // the wave's lanes only: a wave smaller than the capacity keeps the whole GPU
+    dim3 grid(grid_x(g.n, ls.nl), ls.nl);
     k_update<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, sprev, scur, spq, sw);
     count_launch();
     RCG_CHECK_LAUNCH();
@@ -323,10 +324,10 @@ void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *di
 // rr[t mod 3] = r^T r and p = r - W Ginv (A W)^T r.
 template <typename T>
 void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t, const int *mask) {
-    dim3 grid(grid_x(g.n, ls.m), ls.m);
+    dim3 grid(grid_x(g.n, ls.nl), ls.nl);
     const int scur = t % 3, snext = (t + 1) % 3, sprev = (t + 2) % 3;
     const int sw = t % 2, sA = (t + 1) % 2;
-    k_lane_zero<<<ls.m, 64, 0, st>>>(ls, mask);
+    k_lane_zero<<<ls.nl, 64, 0, st>>>(ls, mask);
     count_launch();
     RCG_CHECK_LAUNCH();
     k_lane_dots<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, mask, 0, sA, 0, 0);       // W^T r -> wv[sA]
@@ -345,7 +346,7 @@ void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t
 }
 
 void lane_zero(cudaStream_t st, LaneState ls, const int *mask) {
-    k_lane_zero<<<ls.m, 64, 0, st>>>(ls, mask);
+    k_lane_zero<<<ls.nl, 64, 0, st>>>(ls, mask);
     count_launch();
     RCG_CHECK_LAUNCH();
 }

@@ -24,6 +24,10 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 
 namespace rcg {
 namespace {
@@ -292,6 +296,181 @@ k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict_
             for (int w = 0; w < kThreads / 32; ++w) t += red[w][i];
             atomicAdd(dots + c[i], t);
         }
+}
+
+// 3D grids with Nx % 4 == 0, any Nx / 4 that TX divides: q = A~ p for ZL
+// lanes per CTA over a TX x TY tile of float4 columns (TY = 256 / TX) and a
+// chunk of z planes, marching in z.  Thread (tx, ty) owns the float4 column
+// (x4 = x0 + tx, y = y0 + ty) and keeps planes z-1, z, z+1 of its own column
+// (and z+2 in flight) in registers for every lane and for D, so the two
+// z-neighbours cost no shared-memory traffic.  Only the current plane goes
+// through shared memory, for the four in-plane neighbours: each thread
+// stores its centre value, the edge threads copy the one-cell halo (x and y)
+// of the next plane by cp.async (zero-filled outside the grid), one barrier
+// per plane, two plane buffers.  D and the sample diagonals are shared by
+// the ZL lanes; fused p^T q per lane.
+template <int TX, int ZL>
+__global__ void __launch_bounds__(kThreads, ZL <= 2 ? 2 : 1)
+k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict__ diag_of_col,
+            const float *const *__restrict__ src, float *const *__restrict__ dst, const int *__restrict__ alist,
+            int na, const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ prof,
+            int zc) {
+    constexpr int TY = kThreads / TX, RW = TX + 2, RH = TY + 2, NA = ZL + 1;
+    extern __shared__ float4 pl[];                   // [2][NA][RH][RW]
+    const int nx4 = g.Nx >> 2, xtiles = nx4 / TX, ytiles = (g.Ny + TY - 1) / TY;
+    const int xt = blockIdx.x % xtiles, rest = blockIdx.x / xtiles;
+    const int yt = rest % ytiles, zb = rest / ytiles;
+    const int z0 = zb * zc, z1 = min(z0 + zc, g.Nz);
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x4 = xt * TX + tx, y = yt * TY + ty;
+    int c[ZL];
+    bool on[ZL];
+    int non = 0;
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        const int li = blockIdx.y * ZL + i;
+        c[i] = li < na ? alist[li] : -1;
+        on[i] = c[i] >= 0 && active[c[i]] != 0;
+        non += on[i];
+    }
+    if (non == 0 || z0 >= g.Nz) return;             // uniform over the CTA
+    if (prof && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *A[NA];                             // arrays: lanes' p, then D
+    float4 *Q[ZL];
+    const float4 *DG[ZL];
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        A[i] = on[i] ? (const float4 *)src[c[i]] : nullptr;
+        Q[i] = on[i] ? (float4 *)dst[c[i]] : nullptr;
+        DG[i] = on[i] ? (const float4 *)diag_of_col[c[i]] : nullptr;
+    }
+    A[ZL] = (const float4 *)D;
+    const bool yok = y < g.Ny;
+    const long long row4 = (long long)nx4 * g.Ny;   // float4 per plane
+    const long long col = (long long)y * nx4 + x4;  // this thread's column within a plane
+    // halo duty: x (tx = 0: x4 - 1, tx = TX - 1: x4 + 1), y (ty = 0: y - 1, ty = TY - 1: y + 1)
+    const int hxd = (tx == 0) ? -1 : (tx == TX - 1 ? 1 : 0);
+    const int hyd = (ty == 0) ? -1 : (ty == TY - 1 ? 1 : 0);
+    const bool hxok = hxd != 0 && yok && x4 + hxd >= 0 && x4 + hxd < nx4;
+    const bool hyok = hyd != 0 && y + hyd >= 0 && y + hyd < g.Ny;
+    const int cc = (ty + 1) * RW + (tx + 1);        // this thread's cell in a plane buffer
+    constexpr int PS = RH * RW;                      // float4 per array and buffer
+    auto buf = [&](int z) { return pl + (size_t)(z & 1) * NA * PS; };
+    // zero the halo cells no thread fills (corners, and the ghost columns /
+    // rows of both buffers are refilled with zero-byte copies below)
+    for (int e = threadIdx.x; e < 2 * NA * PS; e += kThreads) pl[e] = zero4;
+    __syncthreads();
+    // halo cells of plane z into its buffer (cp.async; zero bytes outside the grid)
+    auto halo = [&](int z) {
+        if (z >= z1) return;                         // plane z1 is only a z-neighbour (registers)
+        float4 *b = buf(z);
+        const long long pz = (long long)z * row4;
+        if (hxd != 0) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const bool ok = hxok && A[a] != nullptr;
+                cp_async16(b + a * PS + cc + hxd, ok ? A[a] + pz + col + hxd : (const float4 *)D, ok ? 16 : 0);
+            }
+        }
+        if (hyd != 0) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const bool ok = hyok && A[a] != nullptr;
+                cp_async16(b + a * PS + cc + hyd * RW, ok ? A[a] + pz + col + (long long)hyd * nx4 : (const float4 *)D,
+                           ok ? 16 : 0);
+            }
+        }
+    };
+    auto ld = [&](int a, int z) -> float4 {
+        return (yok && z >= 0 && z < g.Nz && A[a] != nullptr) ? A[a][(long long)z * row4 + col] : zero4;
+    };
+    float4 pm[NA], pc[NA], pn[NA], pnn[NA], dgc[ZL];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        pm[a] = ld(a, z0 - 1);
+        pc[a] = ld(a, z0);
+        pn[a] = ld(a, z0 + 1);
+    }
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) dgc[i] = (on[i] && yok) ? DG[i][(long long)z0 * row4 + col] : zero4;
+    halo(z0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    float acc[ZL];
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) acc[i] = 0.f;
+    for (int z = z0; z < z1; ++z) {
+        float4 dgn[ZL];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) pnn[a] = ld(a, z + 2);
+#pragma unroll
+        for (int i = 0; i < ZL; ++i) dgn[i] = (on[i] && yok && z + 1 < z1) ? DG[i][(long long)(z + 1) * row4 + col] : zero4;
+        float4 *b = buf(z);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) b[a * PS + cc] = pc[a];
+        asm volatile("cp.async.wait_group 0;" ::: "memory");      // this thread's halo copies of plane z
+        __syncthreads();                                           // everyone's; plane z-1 reads are done
+        halo(z + 1);                                               // into the buffer plane z-1 used
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (yok) {
+            const float4 *dp = b + ZL * PS;
+            const float4 Dc = pc[ZL];
+            const float Dl = dp[cc - 1].w, Dr = dp[cc + 1].x;
+            const float4 Dym = dp[cc - RW], Dyp = dp[cc + RW], Dzm = pm[ZL], Dzp = pn[ZL];
+            // face weights (D_p + D_q) / 2; towards a ghost they meet p = 0
+            const float wl = 0.5f * (Dc.x + Dl), wr = 0.5f * (Dc.w + Dr);
+            const float w01 = 0.5f * (Dc.x + Dc.y), w12 = 0.5f * (Dc.y + Dc.z), w23 = 0.5f * (Dc.z + Dc.w);
+            auto fw = [&](const float4 Dn) {
+                return make_float4(0.5f * (Dc.x + Dn.x), 0.5f * (Dc.y + Dn.y), 0.5f * (Dc.z + Dn.z),
+                                   0.5f * (Dc.w + Dn.w));
+            };
+            const float4 wym = fw(Dym), wyp = fw(Dyp), wzm = fw(Dzm), wzp = fw(Dzp);
+            const long long v = (long long)z * row4 + col;
+#pragma unroll
+            for (int i = 0; i < ZL; ++i) {
+                if (!on[i]) continue;
+                const float4 *xp = b + i * PS;
+                const float4 xc = pc[i];
+                const float xlv = xp[cc - 1].w, xrv = xp[cc + 1].x;
+                const float4 xym = xp[cc - RW], xyp = xp[cc + RW], xzm = pm[i], xzp = pn[i];
+                const float4 dg = dgc[i];
+                float4 o;
+                o.x = dg.x * xc.x - (wl * xlv + w01 * xc.y) - (wym.x * xym.x + wyp.x * xyp.x) - (wzm.x * xzm.x + wzp.x * xzp.x);
+                o.y = dg.y * xc.y - (w01 * xc.x + w12 * xc.z) - (wym.y * xym.y + wyp.y * xyp.y) - (wzm.y * xzm.y + wzp.y * xzp.y);
+                o.z = dg.z * xc.z - (w12 * xc.y + w23 * xc.w) - (wym.z * xym.z + wyp.z * xyp.z) - (wzm.z * xzm.z + wzp.z * xzp.z);
+                o.w = dg.w * xc.w - (w23 * xc.z + wr * xrv) - (wym.w * xym.w + wyp.w * xyp.w) - (wzm.w * xzm.w + wzp.w * xzp.w);
+                Q[i][v] = o;
+                acc[i] += dot4(xc, o);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) { pm[a] = pc[a]; pc[a] = pn[a]; pn[a] = pnn[a]; }
+#pragma unroll
+        for (int i = 0; i < ZL; ++i) dgc[i] = dgn[i];
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __shared__ double red[kThreads / 32][ZL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        double s = (double)acc[i];
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, o2);
+        if (lane == 0) red[warp][i] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ZL; ++i)
+        if (threadIdx.x == i && on[i]) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w][i];
+            atomicAdd(dots + c[i], t);
+        }
+}
+
+template <int TX, int ZL>
+constexpr size_t stencil4r_smem() {
+    return (size_t)2 * (ZL + 1) * (kThreads / TX + 2) * (TX + 2) * sizeof(float4);
 }
 
 // r -= alpha q; r^T r and the private (A W)^T r dots (the shared ones come
@@ -881,6 +1060,214 @@ bool stencil4z_supported(const Grid &g) {
            stencil4z_smem(nx4) <= 160 * 1024 && g.n < (1LL << 31);
 }
 
+namespace {
+
+int device_sms(int dev) {
+    static int sms[64] = {};
+    if (dev < 0 || dev >= 64) return 152;
+    if (!sms[dev]) {
+        int v = 0;
+        RCG_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        sms[dev] = v > 0 ? v : 152;
+    }
+    return sms[dev];
+}
+
+// k_stencil4r<TX, ZL> over the lanes of ll: per-plane tiles x lane groups x
+// z-chunks, the chunks sized for ~4 waves of resident CTAs (>= 8 planes each).
+template <int TX, int ZL>
+void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
+                float *const *q, const LaneList &ll, const int *active, double *dots, unsigned long long *prof) {
+    static int occ[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    const size_t smem = stencil4r_smem<TX, ZL>();
+    if (dev < 0 || dev >= 64 || !occ[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_stencil4r<TX, ZL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int o = 0;
+        RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_stencil4r<TX, ZL>, kThreads, smem));
+        if (dev >= 0 && dev < 64) occ[dev] = std::max(o, 1);
+    }
+    const int o = (dev >= 0 && dev < 64) ? occ[dev] : 1;
+    const int nx4 = g.Nx / 4, TY = kThreads / TX;
+    const long long T = (long long)(nx4 / TX) * ((g.Ny + TY - 1) / TY), G = (ll.na + ZL - 1) / ZL;
+    const long long resident = (long long)o * device_sms(dev);
+    long long nzc = (4 * resident + T * G - 1) / (T * G);
+    const long long maxc = std::max<long long>(1, g.Nz / 8);
+    nzc = std::max<long long>(1, std::min(nzc, maxc));
+    const int zc = (int)((g.Nz + nzc - 1) / nzc);
+    nzc = (g.Nz + zc - 1) / zc;
+    k_stencil4r<TX, ZL><<<dim3((unsigned)(T * nzc), (unsigned)G), kThreads, smem, st>>>(
+        g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc);
+}
+
+void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
+                float *const *q, const LaneList &ll, const int *active, double *dots, unsigned long long *prof) {
+    const int nx4 = g.Nx / 4, TY = kThreads / nx4;
+    const int ytiles = (g.Ny + TY - 1) / TY, pairs = (ll.na + ZL - 1) / ZL;
+    // z-chunks: enough CTAs for ~4 waves at 3 CTAs per SM, chunks of >= 4 planes
+    const long long base = (long long)ytiles * pairs;
+    long long nzc = (12LL * 152 + base - 1) / base;
+    const long long maxc = (g.Nz + 3) / 4;
+    if (nzc > maxc) nzc = maxc;
+    if (nzc < 1) nzc = 1;
+    const int zc = (int)((g.Nz + nzc - 1) / nzc);
+    nzc = (g.Nz + zc - 1) / zc;
+    const size_t smem = stencil4z_smem(nx4);
+    static bool attr[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_stencil4z, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    k_stencil4z<<<dim3((unsigned)(ytiles * nzc), pairs), kThreads, smem, st>>>(g, D, diag, p, q, ll.alist, ll.na,
+                                                                               active, dots, prof, zc);
+}
+
+// Stencil variants: 0 the row kernel k_stencil4 (any Nx % 4 == 0), 1 the
+// plane-ring kernel k_stencil4z (3D, 256 % (Nx / 4) == 0), and 2 + the
+// z-marching kernel k_stencil4r<TX, ZL> for TX in {4, 8, 16, 32} (TX | Nx/4),
+// ZL in {1, 2, 4}: id 2 + 3 log2(TX / 4) + log2(ZL).
+constexpr int S4_TXS[4] = {4, 8, 16, 32};
+constexpr int S4_ZLS[3] = {1, 2, 4};
+constexpr int S4_NVAR = 2 + 12;
+
+bool s4_variant_ok(const Grid &g, int v) {
+    if (v == 0) return cg4_supported(g);
+    if (v == 1) return stencil4z_supported(g);
+    if (v < 2 || v >= S4_NVAR) return false;
+    const int tx = S4_TXS[(v - 2) / 3];
+    return cg4_supported(g) && g.Ny > 1 && (g.Nx / 4) % tx == 0 && g.n < (1LL << 31);
+}
+
+std::string s4_variant_name(int v) {
+    if (v == 0) return "k_stencil4 (rows)";
+    if (v == 1) return "k_stencil4z (plane ring)";
+    return "k_stencil4r<" + std::to_string(S4_TXS[(v - 2) / 3]) + "," + std::to_string(S4_ZLS[(v - 2) % 3]) + ">";
+}
+
+void s4_launch(int v, cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
+               float *const *q, const LaneList &ll, const int *active, double *dots, unsigned long long *prof) {
+    const long long nv = g.n >> 2;
+    switch (v) {
+        case 0:
+            k_stencil4<<<dim3(gx_for(nv, ll.na, 8), ll.na), kThreads, 0, st>>>(g, D, diag, p, q, ll.alist, active, dots,
+                                                                             prof);
+            break;
+        case 1: launch_s4z(st, g, D, diag, p, q, ll, active, dots, prof); break;
+#define RCG_S4R(ID, TX, ZLV) case ID: launch_s4r<TX, ZLV>(st, g, D, diag, p, q, ll, active, dots, prof); break;
+        RCG_S4R(2, 4, 1) RCG_S4R(3, 4, 2) RCG_S4R(4, 4, 4)
+        RCG_S4R(5, 8, 1) RCG_S4R(6, 8, 2) RCG_S4R(7, 8, 4)
+        RCG_S4R(8, 16, 1) RCG_S4R(9, 16, 2) RCG_S4R(10, 16, 4)
+        RCG_S4R(11, 32, 1) RCG_S4R(12, 32, 2) RCG_S4R(13, 32, 4)
+#undef RCG_S4R
+        default: throw Error{RCG_ERR_INVALID, "unknown stencil variant"};
+    }
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+// The autotuner: the first float32 iteration of a (device, grid, lane-count
+// class) times every variant that supports the grid on that iteration's own
+// lanes (CUDA events, one warm-up and three timed launches each, p^T q into a
+// scratch buffer) and keeps the fastest; later iterations look it up.
+struct TuneKey {
+    int dev, Nx, Ny, Nz, cls;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, Nx, Ny, Nz, cls) < std::tie(o.dev, o.Nx, o.Ny, o.Nz, o.cls);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+std::vector<std::string> g_tune_log;
+
+int lane_class(int na) {
+    int c = 0;
+    while ((1 << c) < na && c < 14) ++c;
+    return c;
+}
+
+int s4_tuned(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
+             float *const *q, const LaneList &ll, const int *active, int mcap) {
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    const TuneKey key{dev, g.Nx, g.Ny, g.Nz, lane_class(ll.na)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    double *scr = nullptr;
+    RCG_CUDA_TRY(cudaMalloc(&scr, sizeof(double) * (size_t)std::max(mcap, 1)));   // p^T q of lanes < mcap
+    cudaEvent_t e0, e1;
+    RCG_CUDA_TRY(cudaEventCreate(&e0));
+    RCG_CUDA_TRY(cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = 0.f;
+    std::string log = "stencil " + std::to_string(g.Nx) + "x" + std::to_string(g.Ny) + "x" + std::to_string(g.Nz) +
+                      ", lanes <= " + std::to_string(1 << key.cls) + ":";
+    try {
+        for (int v = 0; v < S4_NVAR; ++v) {
+            if (!s4_variant_ok(g, v)) continue;
+            s4_launch(v, st, g, D, diag, p, q, ll, active, scr, nullptr);
+            RCG_CUDA_TRY(cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 3; ++rep) s4_launch(v, st, g, D, diag, p, q, ll, active, scr, nullptr);
+            RCG_CUDA_TRY(cudaEventRecord(e1, st));
+            RCG_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            RCG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= 3.f;
+            char b[96];
+            std::snprintf(b, sizeof b, " %s %.1f us;", s4_variant_name(v).c_str(), 1e3 * ms);
+            log += b;
+            if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0); cudaEventDestroy(e1); cudaFree(scr);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RCG_CUDA_TRY(cudaFree(scr));
+    log += " -> " + s4_variant_name(best);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    g_tune_log.push_back(log);
+    return best;
+}
+
+}  // namespace
+
+std::string stencil_tuning_report() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string s;
+    for (auto &l : g_tune_log) s += l + "\n";
+    return s;
+}
+
+const char *stencil_variant_name(int v) {
+    static std::string names[S4_NVAR];
+    if (v < 0 || v >= S4_NVAR) return nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] { for (int i = 0; i < S4_NVAR; ++i) names[i] = s4_variant_name(i); });
+    return names[v].c_str();
+}
+
+int stencil_variant_ok(const Grid &g, int v) { return s4_variant_ok(g, v) ? 1 : 0; }
+
+// q = A~_s p on ncols float32 columns with stencil variant v (-1: the tuned
+// choice), p^T q added into dots[c] (device, ncols doubles): a parity and
+// timing entry for the kernels of the inner iteration.
+void stencil4_apply(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
+                    float *const *q, int ncols, const int *lanes, const int *active, double *dots, int v) {
+    LaneList ll{lanes, ncols, nullptr, nullptr, nullptr, 0};
+    if (ncols <= 0) return;
+    if (v < 0) v = s4_tuned(st, g, D, diag, p, q, ll, active, ncols);
+    if (!s4_variant_ok(g, v)) throw Error{RCG_ERR_INVALID, "stencil variant does not support this grid"};
+    s4_launch(v, st, g, D, diag, p, q, ll, active, dots, nullptr);
+}
+
 // One float32 iteration t over the active lanes (see the file comment).
 void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *const *diag_of_col,
                    const float *const *p_ptr, float *const *q_ptr, LaneGeom gm, LaneState ls, LaneList ll, int t,
@@ -889,34 +1276,11 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     const int sprev = (t - 1) % 3, scur = t % 3, snext = (t + 1) % 3, spq = t % 2, sw = t % 2;
     const long long nv = g.n >> 2;
     const bool tm = kt && kt->on;
+    // the tuner's launches (first iteration of a grid and lane class only) run
+    // before the timed launch
+    const int sv = s4_tuned(st, g, D, diag_of_col, p_ptr, q_ptr, ll, ls.active, ls.m);
     cudaEvent_t e = tm ? kt->start(st) : nullptr;
-    if (stencil4z_supported(g)) {
-        const int nx4 = g.Nx / 4, TY = kThreads / nx4;
-        const int ytiles = (g.Ny + TY - 1) / TY, pairs = (ll.na + ZL - 1) / ZL;
-        // z-chunks: enough CTAs for ~4 waves at 3 CTAs per SM, chunks of >= 4 planes
-        const long long base = (long long)ytiles * pairs;
-        long long nzc = (12LL * 152 + base - 1) / base;
-        const long long maxc = (g.Nz + 3) / 4;
-        if (nzc > maxc) nzc = maxc;
-        if (nzc < 1) nzc = 1;
-        const int zc = (int)((g.Nz + nzc - 1) / nzc);
-        nzc = (g.Nz + zc - 1) / zc;
-        const size_t smem = stencil4z_smem(nx4);
-        static bool attr[64] = {};
-        int dev = 0;
-        RCG_CUDA_TRY(cudaGetDevice(&dev));
-        if (dev < 0 || dev >= 64 || !attr[dev]) {
-            RCG_CUDA_TRY(cudaFuncSetAttribute(k_stencil4z, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-            if (dev >= 0 && dev < 64) attr[dev] = true;
-        }
-        k_stencil4z<<<dim3((unsigned)(ytiles * nzc), pairs), kThreads, smem, st>>>(
-            g, D, diag_of_col, p_ptr, q_ptr, ll.alist, ll.na, ls.active, ls.pq + (long long)spq * ls.m, ls.prof, zc);
-    } else {
-        k_stencil4<<<dim3(gx_for(nv, ll.na, 8), ll.na), kThreads, 0, st>>>(
-            g, D, diag_of_col, p_ptr, q_ptr, ll.alist, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
-    }
-    count_launch();
-    RCG_CHECK_LAUNCH();
+    s4_launch(sv, st, g, D, diag_of_col, p_ptr, q_ptr, ll, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
     if (tm) { kt->stop(0, e, st); e = kt->start(st); }
     if (gm.kp_max <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
     else if (gm.kp_max <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);

@@ -61,7 +61,8 @@ constexpr int KP_MAX = RCG_MAX_PRIVATE;   // private deflation columns per lane
 
 // Per-lane CG state on the device (structure of arrays, m lanes).
 struct LaneState {
-    int m;                  // lanes
+    int m;                  // lane capacity (stride of the ring buffers)
+    int nl;                 // lanes 0 .. nl-1 of the current wave (<= m): launch extent
     double *rr;             // [3][m]  r^T r ring (slot = iteration mod 3)
     double *pq;             // [2][m]  p^T A p ring
     double *wv;             // [2][m][KMAX] (A W)^T r ring
@@ -347,6 +348,14 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
 void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, LaneList ll, int t, float *mu,
                  float *beta);
 void lane_zero(cudaStream_t st, LaneState ls, const int *mask);
+// q = A~_s p on ncols float32 columns with the inner iteration's stencil
+// variant v (-1: the autotuned choice; see cg4.cu), p^T q added into
+// dots[lanes[c]]; `active[lanes[c]]` != 0 for the columns to apply.
+void stencil4_apply(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
+                    float *const *q, int ncols, const int *lanes, const int *active, double *dots, int v);
+std::string stencil_tuning_report();
+const char *stencil_variant_name(int v);
+int stencil_variant_ok(const Grid &g, int v);
 
 // cg.cu
 template <typename T>

@@ -37,9 +37,11 @@ EXPORTED = [
     "rcg_gemm_tn_f32", "rcg_learn_nparams", "rcg_learn_geometry", "rcg_learn_set_weights",
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
     "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load", "rcg_gemm_nn_f32", "rcg_rom_eval_batch_chunk",
+    "rcg_apply_f32", "rcg_stencil_variant_name", "rcg_stencil_variant_ok", "rcg_tuning_report",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
 RCG_MAX_PRIVATE = 8
+RCG_STENCIL_VARIANTS = 14
 RCG_COMPRESS_MAX_COLS = 4096
 
 
@@ -120,6 +122,10 @@ def load(path=LIB_PATH):
         "rcg_load": (I, [P, C.c_char_p]),
         "rcg_gemm_nn_f32": (I, [P, LL, I, P, I, I, LL, P, LL, D, D, I, P]),
         "rcg_rom_eval_batch_chunk": (I, [LL, I, I, I, I]),
+        "rcg_apply_f32": (I, [P, I, I, P, P, I, P]),
+        "rcg_stencil_variant_name": (C.c_char_p, [I]),
+        "rcg_stencil_variant_ok": (I, [P, I]),
+        "rcg_tuning_report": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +194,19 @@ def gemm_nn_f32(V, Cmat, Out, alpha=1.0, beta=0.0, engine=1, stream=None):
     if rc != 0:
         raise RcgError(rc, lib().rcg_strerror(rc).decode())
     return Out
+
+
+def stencil_variant_name(v):
+    name = lib().rcg_stencil_variant_name(v)
+    return None if name is None else name.decode()
+
+
+def tuning_report():
+    """The stencil autotuner's record (one line per tuned grid and lane class)."""
+    n = lib().rcg_tuning_report(None, 0)
+    buf = C.create_string_buffer(max(n, 0) + 1)
+    lib().rcg_tuning_report(buf, len(buf))
+    return buf.value.decode()
 
 
 def default_options(**kw):
@@ -291,6 +310,20 @@ class Context:
         if 0 <= ncols <= RCG_NOALLOC_MAX_COLS:
             self._device_cols(x_dev, y_dev, ncols, prec)
         return self._check(self.L.rcg_apply_noalloc(self.h, s, prec, _ptr(x_dev), _ptr(y_dev), ncols))
+
+    def apply_f32(self, s, x_dev, y_dev, ncols, variant=-1, dots_dev=None):
+        """y = A~_s x with the inner iteration's float32 stencil kernel
+        `variant` (-1: the autotuned choice); dots_dev[j] += x_j^T y_j."""
+        self._device_cols(x_dev, y_dev, ncols, RCG_MIXED)
+        if dots_dev is not None:
+            import torch
+            if not (isinstance(dots_dev, torch.Tensor) and dots_dev.is_cuda and dots_dev.dtype == torch.float64
+                    and dots_dev.numel() >= ncols):
+                raise ValueError("dots must be a CUDA float64 tensor of ncols values")
+        return self._check(self.L.rcg_apply_f32(self.h, s, variant, _ptr(x_dev), _ptr(y_dev), ncols, _ptr(dots_dev)))
+
+    def stencil_variant_ok(self, v):
+        return bool(self.L.rcg_stencil_variant_ok(self.h, v))
 
     # ---- method
     def seed(self, s0, U0=None):

@@ -1,6 +1,9 @@
 """`bench.py --impl reference` (the CPU oracle timed as the reference arm)
 prints one JSON line with the contract's keys, on a small workload (2D 24^2)
-so that it runs in seconds on the CPU."""
+so that it runs in seconds on the CPU.  The oracle times a bounded sample of
+the workload (here sample 1 and four of the eight right-hand sides), and the
+line's config says so: its solves_per_step and ms_per_step are those of the
+timed sample, not of the whole pass."""
 import json
 import os
 import subprocess
@@ -19,7 +22,12 @@ def test_reference_line_has_the_contract_keys():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
-    assert line["config"]["workload"] == "t2d_24" and line["config"]["solves_per_step"] == 2 * 8
+    cfg = line["config"]
+    assert cfg["workload"] == "t2d_24" and cfg["solves_per_pass"] == 2 * 8
+    assert cfg["solves_per_step"] == 4 < cfg["solves_per_pass"]            # the timed sample, not the pass
+    assert "RHS [0, 1, 2, 3]" in cfg["timed_sample"]
+    # ms_per_step is the time of one step of the timed sample
+    assert abs(line["value"] - cfg["solves_per_step"] / (line["ms_per_step"] / 1e3)) <= 1e-3 * line["value"]   # ms_per_step is rounded
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
@@ -50,3 +58,15 @@ def test_contender_line_has_the_contract_keys():
         assert k in line["roofline"], k
     assert line["config"]["workload"] == "c2_3d64" and line["config"]["solves_per_step"] == 320
     assert line["n_gpus"] == 1 and line["config"]["parallelism"] == "single GPU"
+
+
+def test_reference_line_at_192_cubed_is_unavailable_with_its_reason():
+    """The oracle cannot seed the 192^3 configuration within a bench run (its
+    ARPACK eigensolver alone takes longer), so the reference arm says so
+    instead of timing another workload under this one's name."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "c5_3d192", "--steps", "20", "--warmup", "5"], capture_output=True, text=True, timeout=120,
+                       env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "ARPACK" in line["unavailable"]
