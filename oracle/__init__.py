@@ -14,7 +14,11 @@ Contents (each function cites the passage of the paper it restates):
                (Saad, Yeung, Erhel & Guyomarc'h 2000).
   eigen     -- smallest eigenvectors of A~_0 (Sec. 4.2.2).
   basis     -- Algorithm 2 (Sec. 4.3) in sequential and wave order, with the
-               ordered rank-revealing append.
+               ordered rank-revealing append; the per-RHS recycling of the
+               Sec. 6.3 comparison (Table 2).
+  minres    -- the paper's minimum-residual check (eq. initialz) and
+               recycled MINRES on the projected operator (Sec. 4.1, eqs.
+               eq01, SmallMin).
   rom       -- reduced transfer function and Jacobian (Sec. 3.3-3.4, eqs.
                newreduced, newjac) and the full-order plain definitions.
   cnn       -- the learned augmentation of the private recycle space (not

@@ -34,6 +34,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg as sla
 
+from . import minres
 from .solvers import deflated_cg
 
 
@@ -92,22 +93,29 @@ def galerkin_check(A, V, b):
     return x0, r0, np.linalg.norm(r0) / np.linalg.norm(b)
 
 
-def solve_lane(A, b, tol, V, W):
-    """Check, then (if needed) deflated CG on the correction equation."""
+def solve_lane(A, b, tol, V, W, check="galerkin", inner="cg"):
+    """Check, then (if needed) the inner solver on the correction equation:
+    check "galerkin" (the build's default) or "mr" (the paper's
+    minimum-residual guess, minres.mr_check); inner "cg" (deflated CG with
+    deflation space W) or "minres" (the paper's recycled MINRES with recycle
+    space W, minres.recycled_minres)."""
     bn = np.linalg.norm(b)
     if V.shape[1]:
-        x0, r0, rel0 = galerkin_check(A, V, b)
+        x0, r0, rel0 = galerkin_check(A, V, b) if check == "galerkin" else minres.mr_check(A, V, b)
     else:
         x0, r0, rel0 = np.zeros_like(b), b.copy(), 1.0
     if rel0 <= tol:
         return dict(x=x0, x0=x0, iters=0, relres0=rel0, relres=rel0, solved=False)
-    g, its, _ = deflated_cg(A, r0, W, tol, bn)
+    if inner == "minres":
+        g, its, _ = minres.recycled_minres(A, r0, W, tol, bn)
+    else:
+        g, its, _ = deflated_cg(A, r0, W, tol, bn)
     x = x0 + g
     rel = np.linalg.norm(b - A @ x) / bn
     return dict(x=x, x0=x0, iters=its, relres0=rel0, relres=rel, solved=True)
 
 
-def seed(A0, Bfull, U0, tols, tau=1e-12, k_cap=256):
+def seed(A0, Bfull, U0, tols, tau=1e-12, k_cap=256, inner="cg"):
     """Seed step of Algorithm 2: V = basis([U_0, X_0]), U_j = [U_0, X_0(:, j)].
     X_0(:, j) is computed with the Galerkin guess from range(U_0) and deflated
     CG with W = U_0, to relres tol_j."""
@@ -116,7 +124,7 @@ def seed(A0, Bfull, U0, tols, tau=1e-12, k_cap=256):
     X0 = np.zeros((n, nrhs))
     stats = []
     for j in range(nrhs):
-        res = solve_lane(A0, Bfull[:, j], tols[j], V, U0)
+        res = solve_lane(A0, Bfull[:, j], tols[j], V, U0, inner=inner)
         X0[:, j] = res["x"]
         stats.append(dict(sample=0, rhs=j, iters=res["iters"], relres0=res["relres0"],
                           relres=res["relres"], appended=True))
@@ -131,15 +139,17 @@ def seed(A0, Bfull, U0, tols, tau=1e-12, k_cap=256):
 
 
 def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", tau=1e-12,
-              keep_x=False):
-    """Outer loop of Algorithm 2 over `samples` (A_of(i) gives A~_i)."""
+              keep_x=False, check="galerkin", inner="cg"):
+    """Outer loop of Algorithm 2 over `samples` (A_of(i) gives A~_i); check
+    and inner as in solve_lane (check="mr", inner="minres" is the paper's
+    own form of Algorithm 2)."""
     nrhs = Bfull.shape[1]
     out = []
     if order == "sequential":
         for i in samples:
             A = A_of(i)
             for j in range(nrhs):
-                res = solve_lane(A, Bfull[:, j], tols[j], st.V, st.U(j))
+                res = solve_lane(A, Bfull[:, j], tols[j], st.V, st.U(j), check, inner)
                 rec = dict(sample=i, rhs=j, iters=res["iters"], relres0=res["relres0"],
                            relres=res["relres"], appended=False, ratio=0.0)
                 if res["solved"]:
@@ -159,7 +169,7 @@ def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", ta
         for i in samples:
             A = A_of(i)
             for j in range(nrhs):
-                res = solve_lane(A, Bfull[:, j], tols[j], V_wave, U_wave[j])
+                res = solve_lane(A, Bfull[:, j], tols[j], V_wave, U_wave[j], check, inner)
                 rec = dict(sample=i, rhs=j, iters=res["iters"], relres0=res["relres0"],
                            relres=res["relres"], appended=False, ratio=0.0)
                 if keep_x:
@@ -182,4 +192,37 @@ def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", ta
     else:
         raise ValueError(order)
     st.stats.extend(out)
+    return out
+
+
+def solve_all_per_rhs(st: BasisState, A_of, samples, Bfull, tols, tau=1e-12):
+    """The comparison method of Sec. 6.3 (Table 2; recycling as in Kilmer & de
+    Sturler 2006): no global basis.  For every sample i and RHS j the full
+    system A~_i x = b_j is solved by recycled MINRES with the recycle space
+    U_j of the state (U_0, X_0(:, j) and the earlier new directions of RHS j),
+    from the minimum-residual guess in range(U_j); the part of x_j outside
+    range(U_j) (normalised, if its relative size exceeds tau) joins U_j only.
+    st.V is not used or changed.  Returns the per-(sample, RHS) records."""
+    nrhs = Bfull.shape[1]
+    out = []
+    for i in samples:
+        A = A_of(i)
+        for j in range(nrhs):
+            b = Bfull[:, j]
+            bn = np.linalg.norm(b)
+            W = st.U(j)
+            z, r, rel0 = minres.mr_check(A, W, b)
+            rec = dict(sample=i, rhs=j, iters=0, relres0=rel0, relres=rel0, appended=False)
+            if rel0 > tols[j]:
+                g, its, _ = minres.recycled_minres(A, r, W, tols[j], bn)
+                x = z + g
+                rec["iters"] = its
+                rec["relres"] = np.linalg.norm(b - A @ x) / bn
+                Q, _ = np.linalg.qr(W)
+                w = x - Q @ (Q.T @ x)
+                w = w - Q @ (Q.T @ w)
+                if np.linalg.norm(w) > tau * np.linalg.norm(x):
+                    st.push_private(j, w / np.linalg.norm(w))
+                    rec["appended"] = True
+            out.append(rec)
     return out

@@ -98,6 +98,8 @@ WORKLOADS = {
     "t3d_33": Workload("t3d_33", 3, 33, 4, (4, 4), (4, 4), 3, (1e-8,), k_u=10),
     "t3d_32": Workload("t3d_32", 3, 32, 3, (4, 2), (3, 3), 3, (1e-8, 1e-6), k_u=10),
     "t2d_40": Workload("t2d_40", 2, 40, 2, (7, 1), (6, 1), 3, (1e-9,), k_u=10),
+    # 2D 48^2, 12 + 12, 2 samples: the iteration pattern of the paper's Table 2 at a small size
+    "t2d_48": Workload("t2d_48", 2, 48, 2, (12, 1), (12, 1), 2, (1e-10,), 0.03, k_u=10),
     # 16^3: the plane-streaming stencil with a ragged y-tile (64-row tile, 16 rows)
     "t3d_16": Workload("t3d_16", 3, 16, 2, (2, 2), (2, 2), 3, (1e-8,), k_u=10),
 }
