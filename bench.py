@@ -61,7 +61,7 @@ MAX_TRAIN = 32
 # reduced-model sweep, steps of the leg without the network, the CPU oracle's
 # bounded sample (samples, right-hand sides) and the FP64 baseline's samples.
 SETTINGS = {
-    "c5_3d192": dict(wave=1, r_max=2048, train=2, epochs=20, sweep=4, nolearn_steps=5,
+    "c5_3d192": dict(wave=1, r_max=2048, train=2, epochs=6, sweep=4, nolearn_steps=5,
                      oracle_samples=(1,), oracle_rhs=(0, 128), base_samples=1,
                      oracle_unavailable="the oracle cannot seed 7,077,888 unknowns within a bench run: its ARPACK "
                                         "eigensolver for the 10 smallest eigenvectors of A~_0 (Sec. 4.2.2) ran "
@@ -315,13 +315,19 @@ def train_network(ctx, W, torch, ntrain, epochs):
                 training_samples=ntrain, params=len(ctx.learn_get_weights()))
 
 
-def prepare(rcg, W, opts, torch, ntrain=0, epochs=0, **kw):
+def prepare(rcg, W, opts, torch, ntrain=0, epochs=0, seed_from=None, **kw):
+    """A context with the workload's samples set and the seed of Algorithm 2
+    computed (or copied from the seeded context `seed_from`: rcg_seed_copy,
+    the same seed state without recomputing it)."""
     ctx = W.make_ctx(rcg, opts, torch, extra_samples=ntrain if opts.get("learned") else 0, **kw)
     for s in range(W.wl.K + 1):
         ctx.set_sample(s, W.mu_dev[s])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    seed_stats = ctx.seed(0, None)
+    if seed_from is not None:
+        ctx.seed_copy(seed_from)
+    else:
+        ctx.seed(0, None)
     torch.cuda.synchronize()
     seed_s = time.perf_counter() - t0
     learn = {}
@@ -426,10 +432,11 @@ def run_ours(args, rank, world, torch):
     iters = [s["iters"] for s in leg["stats"]]
     learn_info["augmented"] = int(sum(s["augmented"] for s in leg["stats"]))
     roof = roofline(W, leg["prof"], peak, peak_source)
+    tuning = [l for l in rcg.tuning_report().splitlines() if l]
     res = dict(value=value, ms=ms_max / args.steps, launches=leg["launches"], roofline=roof, clocks=clk,
                phases=phases, rank_V=rank_V, mean_iters=float(np.mean(iters)), seed_s=seed_s,
                solves_per_step=solves_per_step, learn=learn_info, per_step_ms=[round(x, 2) for x in leg["per_step"]],
-               e2e=None, base=None, nolearn=None, rom_sweep=None, second=None, alg1=None)
+               e2e=None, base=None, nolearn=None, rom_sweep=None, second=None, alg1=None, tuning=tuning)
     if args.ncu_region:
         ctx.close()
         return res
@@ -515,30 +522,17 @@ def run_ours(args, rank, world, torch):
     res["e2e"] = {"value": round(world * leg["solves"] / e2e_s, 2), "unit": "solves/s",
                   "h2d_bytes_per_step": int(h2d / args.steps),
                   "d2h_bytes_per_step": int(solves_per_step * stat_bytes + wl.ndet * wl.nsrc * 8 * (1 + wl.nparam))}
-    ctx.close()
     del pinned, mu_ho_pin, dmu_pin
     torch.cuda.empty_cache()
 
-    # ---- the same mixed waves without the network (the learned step's effect),
-    # over the first steps of the pass, against the contender's same steps
-    nl = min(st["nolearn_steps"], args.steps)
-    if not args.no_baseline and rank == 0 and nl > 0:
-        ctx_m, _, _ = prepare(rcg, W, MIXED_PLAIN, torch)
-        leg_m = run_leg(args, torch, W, ctx_m, nl, 1)
-        res["nolearn"] = {"steps": nl, "value": round(leg_m["solves"] / (leg_m["ms"] / 1e3), 2), "unit": "solves/s",
-                          "contender_same_steps": round(leg_m["solves"] / (sum(leg["per_step"][:nl]) / 1e3), 2),
-                          "ms_per_step": round(leg_m["ms"] / nl, 3), "rank_V": ctx_m.rank(),
-                          "mean_cg_iters": float(np.mean([s["iters"] for s in leg_m["stats"]])),
-                          "contender_mean_cg_iters_same_steps": float(np.mean(
-                              [s["iters"] for s in leg["stats"][:len(leg_m["stats"])]]))}
-        ctx_m.close()
-
     # ---- plain FP64 recycled CG in the paper's order, same library and inputs,
     # over the first samples (a bounded sample of the pass: the float64 path is
-    # ~25x slower), against the contender's time for the same samples
+    # several times slower), against the contender's time for the same samples;
+    # it starts from the contender's seed state (float32 values, exact in
+    # float64), which the paper computes once offline
     nb = st["base_samples"] or wl.K
     if not args.no_baseline and rank == 0:
-        ctx_b, seed_b, _ = prepare(rcg, W, FP64_PAPER, torch)
+        ctx_b, seed_b, _ = prepare(rcg, W, FP64_PAPER, torch, seed_from=ctx)
         torch.cuda.synchronize()
         ctx_b.reset_to_seed()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -555,9 +549,25 @@ def run_ours(args, rank, world, torch):
                        "rank_V": ctx_b.rank(), "mean_iters": float(np.mean([s["iters"] for s in stats_b])),
                        "solved": int(sum(s["iters"] > 0 for s in stats_b)),
                        "phases_ms": {k: round(ctx_b.phase_ms(k), 1) for k in ("check", "cg", "append")},
-                       "precision": "f64", "order": "sequential (paper)", "seed_s": round(seed_b, 2),
-                       "seed_phases_ms": {k: round(ctx_b.phase_ms(k), 1) for k in ("seed_eig", "seed_x0")}}
+                       "precision": "f64", "order": "sequential (paper)",
+                       "seed": "the contender's seed state (rcg_seed_copy), untimed"}
         ctx_b.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    # ---- the same mixed waves without the network (the learned step's effect),
+    # over the first steps of the pass, against the contender's same steps
+    nl = min(st["nolearn_steps"], args.steps)
+    if not args.no_baseline and rank == 0 and nl > 0:
+        ctx_m, _, _ = prepare(rcg, W, MIXED_PLAIN, torch)
+        leg_m = run_leg(args, torch, W, ctx_m, nl, 1)
+        res["nolearn"] = {"steps": nl, "value": round(leg_m["solves"] / (leg_m["ms"] / 1e3), 2), "unit": "solves/s",
+                          "contender_same_steps": round(leg_m["solves"] / (sum(leg["per_step"][:nl]) / 1e3), 2),
+                          "ms_per_step": round(leg_m["ms"] / nl, 3), "rank_V": ctx_m.rank(),
+                          "mean_cg_iters": float(np.mean([s["iters"] for s in leg_m["stats"]])),
+                          "contender_mean_cg_iters_same_steps": float(np.mean(
+                              [s["iters"] for s in leg["stats"][:len(leg_m["stats"])]]))}
+        ctx_m.close()
 
     # ---- Algorithm 1 against Algorithm 2 (untimed), where the kept solutions fit in host memory
     if args.alg1_tau > 0 and rank == 0 and wl.K * wl.nrhs * n * 8 < 8e9:
@@ -754,7 +764,8 @@ def contender_line(args, world, res, cpu):
                    "rank_V_after_timed_steps": res["rank_V"], "mean_cg_iters": res["mean_iters"],
                    "per_step_ms": res.get("per_step_ms"),
                    "phases_ms_last_step": {k: round(v, 2) for k, v in res["phases"].items()},
-                   "seed_s_untimed": round(res["seed_s"], 3)},
+                   "seed_s_untimed": round(res["seed_s"], 3),
+                   "stencil_autotuner": res.get("tuning")},
         "roofline": res["roofline"],
         "cpu_baseline": cpu,
         "e2e": res["e2e"],

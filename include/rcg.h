@@ -67,6 +67,23 @@ extern "C" {
                                refinement residuals, Galerkin matrices and
                                rank decisions                                  */
 #define RCG_MAX_PRIVATE 8   /* private columns of a recycle space U_j       */
+/* check of Algorithm 2: the Galerkin guess x0 = V (V^T A~ V)^-1 V^T b (this
+ * library's default) or the paper's minimum-residual guess x0 = U K^T b with
+ * A~ V = K R, U = V R^-1 (Sec. 4.2.1, eq. initialz); both with an explicitly
+ * recomputed float64 residual */
+#define RCG_GALERKIN    0
+#define RCG_MR          1
+/* inner solver of the correction equation (eq. resi): CG deflated by U_j
+ * (Saad et al. 2000) or the paper's recycled MINRES with K_j = A~ U_j
+ * (Sec. 4.1, eqs. eq01 and SmallMin) */
+#define RCG_CG          0
+#define RCG_MINRES      1
+/* recycling: the paper's inner-outer method (global V and per-RHS U_j) or
+ * per-RHS recycle spaces only, the comparison method of Sec. 6.3 / Table 2
+ * (no V check: each system from the minimum-residual guess in range(U_j),
+ * new directions into U_j only) */
+#define RCG_INNER_OUTER 0
+#define RCG_PER_RHS     1
 #define RCG_SEQUENTIAL  0   /* the paper's order: V grows between RHS          */
 #define RCG_WAVE        1   /* all RHS of `wave_samples` samples at once with V
                                frozen; ordered append afterwards               */
@@ -102,6 +119,13 @@ typedef struct {
     int    learned;       /* RCG_MIXED: add the learned network's column to
                              the private U_j of every CG solve (needs
                              weights: rcg_learn_set_weights or _train)      */
+    int    wave_rhs;      /* RCG_WAVE: right-hand sides per wave (0 = all):
+                             a wave takes `wave_samples` samples x wave_rhs
+                             consecutive RHS, so V grows between the RHS
+                             blocks of a sample as in the paper's order      */
+    int    check;         /* RCG_GALERKIN (default) | RCG_MR                */
+    int    inner;         /* RCG_CG (default) | RCG_MINRES                  */
+    int    recycle;       /* RCG_INNER_OUTER (default) | RCG_PER_RHS        */
 } rcg_options;
 
 typedef struct {
@@ -117,9 +141,9 @@ typedef struct {
 } rcg_stat;
 
 /* Fill *o with defaults: FP64, sequential, tau_rank 1e-12, k_u 10,
- * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-5,
- * check_refine 0, keep_solutions 0,
- * seed_degree 0 (automatic), learned 0. */
+ * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-4,
+ * check_refine 0, keep_solutions 0, seed_degree 0 (automatic), learned 0,
+ * wave_rhs 0, check RCG_GALERKIN, inner RCG_CG, recycle RCG_INNER_OUTER. */
 void rcg_options_default(rcg_options *o);
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a
@@ -234,6 +258,17 @@ int rcg_seed(rcg_ctx *c, int s0, const double *U0, rcg_stat *stats);
 /* Return to the state right after rcg_seed (V, U_j, caches) without
  * recomputing it: O(1). */
 int rcg_reset_to_seed(rcg_ctx *c);
+
+/* The seed step's result of context src (Algorithm 2's first three lines:
+ * U_0, X_0, V = basis([U_0, X_0]), U_j = [U_0, X_0(:, j)], C_* = V^T A~_* V)
+ * copied into c, which then behaves as if rcg_seed had run on it (the paper
+ * computes the seed once, offline, and reuses it, Sec. 5.3).  Both contexts
+ * on the same device, with the same grid, D, sources / detectors and the
+ * seed sample's mu in the same slot (checked; RCG_ERR_INVALID otherwise).
+ * Precision: equal, or a float32 seed into a float64 context (the float32
+ * values are exact in float64; V^T X_0 is recomputed in float64); a float64
+ * seed into a float32 context is refused.  src is not changed. */
+int rcg_seed_copy(rcg_ctx *c, const rcg_ctx *src);
 
 /* Algorithm 2 outer loop over samples s_first .. s_first+s_count-1 (each
  * set by rcg_set_sample), in the order of options.order.  stats (host,

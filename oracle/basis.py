@@ -139,10 +139,11 @@ def seed(A0, Bfull, U0, tols, tau=1e-12, k_cap=256, inner="cg"):
 
 
 def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", tau=1e-12,
-              keep_x=False, check="galerkin", inner="cg"):
+              keep_x=False, check="galerkin", inner="cg", wave_samples=0, wave_rhs=0):
     """Outer loop of Algorithm 2 over `samples` (A_of(i) gives A~_i); check
     and inner as in solve_lane (check="mr", inner="minres" is the paper's
-    own form of Algorithm 2)."""
+    own form of Algorithm 2); wave order in waves of wave_samples samples x
+    wave_rhs right-hand sides (0: all)."""
     nrhs = Bfull.shape[1]
     out = []
     if order == "sequential":
@@ -163,32 +164,44 @@ def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", ta
                     rec["x"] = res["x"]
                 out.append(rec)
     elif order == "wave":
-        V_wave = st.V
-        U_wave = [st.U(j) for j in range(nrhs)]
-        cands, recs = [], []
-        for i in samples:
-            A = A_of(i)
-            for j in range(nrhs):
-                res = solve_lane(A, Bfull[:, j], tols[j], V_wave, U_wave[j], check, inner)
-                rec = dict(sample=i, rhs=j, iters=res["iters"], relres0=res["relres0"],
-                           relres=res["relres"], appended=False, ratio=0.0)
-                if keep_x:
-                    rec["x"] = res["x"]
-                recs.append(rec)
-                if res["solved"]:
-                    cands.append((len(recs) - 1, j, res["x"]))
-        if cands:
-            X = np.column_stack([c[2] for c in cands])
-            V, kept, ratios, Q = ordered_append(st.V, X, tau)
-            st.V = V
-            qi = 0
-            for (ri, j, _), k, rt in zip(cands, kept, ratios):
-                recs[ri]["ratio"] = float(rt)
-                if k:
-                    recs[ri]["appended"] = True
-                    st.push_private(j, Q[qi])
-                    qi += 1
-        out = recs
+        # waves of `wave_samples` samples x `wave_rhs` consecutive RHS (0 = all):
+        # V and every U_j are frozen within a wave; its candidates are appended
+        # afterwards in ascending (sample, RHS) order
+        samples = list(samples)
+        ws = wave_samples if wave_samples > 0 else len(samples)
+        wr = min(wave_rhs, nrhs) if wave_rhs > 0 else nrhs
+        out = []
+        for g0 in range(0, len(samples), ws):
+            group = samples[g0:g0 + ws]
+            for j0 in range(0, nrhs, wr):
+                rhs = range(j0, min(j0 + wr, nrhs))
+                V_wave = st.V
+                U_wave = {j: st.U(j) for j in rhs}
+                cands, recs = [], []
+                for i in group:
+                    A = A_of(i)
+                    for j in rhs:
+                        res = solve_lane(A, Bfull[:, j], tols[j], V_wave, U_wave[j], check, inner)
+                        rec = dict(sample=i, rhs=j, iters=res["iters"], relres0=res["relres0"],
+                                   relres=res["relres"], appended=False, ratio=0.0)
+                        if keep_x:
+                            rec["x"] = res["x"]
+                        recs.append(rec)
+                        if res["solved"]:
+                            cands.append((len(recs) - 1, j, res["x"]))
+                if cands:
+                    X = np.column_stack([c[2] for c in cands])
+                    V, kept, ratios, Q = ordered_append(st.V, X, tau)
+                    st.V = V
+                    qi = 0
+                    for (ri, j, _), k, rt in zip(cands, kept, ratios):
+                        recs[ri]["ratio"] = float(rt)
+                        if k:
+                            recs[ri]["appended"] = True
+                            st.push_private(j, Q[qi])
+                            qi += 1
+                out.extend(recs)
+        out.sort(key=lambda o: (o["sample"], o["rhs"]))
     else:
         raise ValueError(order)
     st.stats.extend(out)

@@ -40,8 +40,21 @@ struct Timer {
 
 }  // namespace
 
+// The state right after rcg_seed of an engine, for copying it into another
+// context (device pointers owned by the source).
+struct SeedView {
+    bool seeded = false;
+    int esize = 0;                     // bytes per element of V and X_0
+    int r_seed = 0, k_u = 0, s_star = -1, rmax = 0;
+    const void *V = nullptr, *X0 = nullptr;
+    const double *Cstar = nullptr;
+    std::vector<std::vector<int>> priv_seed;
+};
+
 struct EngineBase {
     virtual ~EngineBase() {}
+    virtual SeedView seed_view() const = 0;
+    virtual void seed_import(const SeedView &sv) = 0;
     virtual void seed(int s0, const double *U0, rcg_stat *stats) = 0;
     virtual void reset() = 0;
     virtual int compress(int r_cap, double tau, std::vector<double> &sigma) = 0;
@@ -1223,6 +1236,56 @@ struct Engine : EngineBase {
         if (stats) for (int j = 0; j < nrhs; ++j) stats[j] = out[j];
     }
 
+    SeedView seed_view() const override {
+        SeedView sv;
+        sv.seeded = seeded;
+        sv.esize = (int)sizeof(T);
+        sv.r_seed = r_seed;
+        sv.k_u = k_u;
+        sv.s_star = s_star;
+        sv.rmax = rmax;
+        sv.V = V;
+        sv.X0 = X0;
+        sv.Cstar = Cstar;
+        sv.priv_seed = priv_seed;
+        return sv;
+    }
+
+    // The seed state of another engine: V's first r_seed columns, the leading
+    // block of C_* (exact: float32 values are exact in float64), X_0 and the
+    // recycle lists; V^T X_0 recomputed in this engine's arithmetic.
+    void seed_import(const SeedView &sv) override {
+        if (!sv.seeded) throw Error{RCG_ERR_INVALID, "rcg_seed_copy: the source context is not seeded"};
+        if (sv.esize != (int)sizeof(T) && !(sv.esize == 4 && sizeof(T) == 8))
+            throw Error{RCG_ERR_INVALID, "rcg_seed_copy: a float64 seed cannot go into a float32 context"};
+        if (sv.r_seed > rmax) throw Error{RCG_ERR_RANK_CAP, "rcg_seed_copy: the seed basis exceeds r_max"};
+        const int nrhs = c->nrhs;
+        r = 0;
+        ensure_vcap(sv.r_seed);
+        if (!X0) { X0 = c->alloc<T>((size_t)nrhs * ld); sX0 = c->alloc<double>((size_t)rmax * nrhs); }
+        if (sv.esize == (int)sizeof(T)) {
+            RCG_CUDA_TRY(cudaMemcpyAsync(V, sv.V, sizeof(T) * (size_t)sv.r_seed * ld, cudaMemcpyDeviceToDevice, st));
+            RCG_CUDA_TRY(cudaMemcpyAsync(X0, sv.X0, sizeof(T) * (size_t)nrhs * ld, cudaMemcpyDeviceToDevice, st));
+        } else {
+            convert_cols<float, T>(st, n, (const float *)sv.V, ld, V, ld, sv.r_seed);
+            convert_cols<float, T>(st, n, (const float *)sv.X0, ld, X0, ld, nrhs);
+        }
+        RCG_CUDA_TRY(cudaMemcpy2DAsync(Cstar, sizeof(double) * rmax, sv.Cstar, sizeof(double) * sv.rmax,
+                                       sizeof(double) * sv.r_seed, sv.r_seed, cudaMemcpyDeviceToDevice, st));
+        r = sv.r_seed;
+        RCG_CUDA_TRY(cudaMemsetAsync(sX0, 0, sizeof(double) * rmax * nrhs, st));
+        prod_tn(V, r, X0, nrhs, sX0, rmax);
+        c->sync();
+        r_seed = r;
+        k_u = sv.k_u;
+        s_star = sv.s_star;
+        priv = priv_seed = sv.priv_seed;
+        gs_sample = -1;
+        au0_valid = false;
+        for (auto &d : dw_star) d = -1;
+        seeded = true;
+    }
+
     void reset() override {
         if (!seeded) throw Error{RCG_ERR_INVALID, "rcg_reset_to_seed before rcg_seed"};
         r = r_seed;
@@ -1342,14 +1405,20 @@ struct Engine : EngineBase {
                     record(out);
                 }
         } else {
+            // waves: `wave_samples` samples x `wave_rhs` consecutive RHS; the
+            // RHS blocks of a sample group run one after another, each seeing
+            // the columns the earlier blocks appended (the paper's inner-outer
+            // effect, kept in blocks of batched lanes)
             const int ws = c->opt.wave_samples > 0 ? c->opt.wave_samples : s_count;
-            for (int s0 = s_first; s0 < s_first + s_count; s0 += ws) {
-                std::vector<Lane> lanes;
-                for (int s = s0; s < std::min(s0 + ws, s_first + s_count); ++s)
-                    for (int j = 0; j < nrhs; ++j) lanes.push_back(Lane{s, j});
-                wave(lanes, false, false, out);
-                record(out);
-            }
+            const int wr = c->opt.wave_rhs > 0 ? std::min(c->opt.wave_rhs, nrhs) : nrhs;
+            for (int s0 = s_first; s0 < s_first + s_count; s0 += ws)
+                for (int j0 = 0; j0 < nrhs; j0 += wr) {
+                    std::vector<Lane> lanes;
+                    for (int s = s0; s < std::min(s0 + ws, s_first + s_count); ++s)
+                        for (int j = j0; j < std::min(j0 + wr, nrhs); ++j) lanes.push_back(Lane{s, j});
+                    wave(lanes, false, false, out);
+                    record(out);
+                }
         }
         return rc;
     }
@@ -1737,6 +1806,12 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
     if (o) c->opt = *o; else rcg_options_default(&c->opt);
     if (c->opt.precision != RCG_FP64 && c->opt.precision != RCG_MIXED) { delete c; return RCG_ERR_INVALID; }
     if (c->opt.order != RCG_SEQUENTIAL && c->opt.order != RCG_WAVE) { delete c; return RCG_ERR_INVALID; }
+    if (c->opt.wave_rhs < 0 || (c->opt.check != RCG_GALERKIN && c->opt.check != RCG_MR) ||
+        (c->opt.inner != RCG_CG && c->opt.inner != RCG_MINRES) ||
+        (c->opt.recycle != RCG_INNER_OUTER && c->opt.recycle != RCG_PER_RHS)) {
+        delete c;
+        return RCG_ERR_INVALID;
+    }
     if (c->opt.r_max < 1 || c->opt.max_samples < 1 || c->opt.k_u < 0 || c->opt.k_u > KU_MAX || c->opt.maxit < 1) {
         delete c;
         return RCG_ERR_INVALID;
@@ -1975,6 +2050,34 @@ int rcg_seed(rcg_ctx *c, int s0, const double *U0, rcg_stat *stats) {
         if (!c->have_rhs || s0 < 0 || s0 >= c->opt.max_samples || !c->sample_set[s0])
             return fail(c, RCG_ERR_INVALID, "rcg_seed needs D, sources/detectors and sample s0");
         c->eng->seed(s0, U0, stats);
+        return RCG_OK;
+    });
+}
+
+int rcg_seed_copy(rcg_ctx *c, const rcg_ctx *src) {
+    return guarded(c, [&]() {
+        if (!src || src == c || !src->eng || !c->eng) return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: bad contexts");
+        if (c->grid.dim != src->grid.dim || c->grid.N != src->grid.N || c->grid.robin_A != src->grid.robin_A ||
+            c->rhs_node != src->rhs_node || c->rhs_w != src->rhs_w || !c->have_D || !src->have_D)
+            return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: grid or sources / detectors differ");
+        const SeedView sv = src->eng->seed_view();
+        if (!sv.seeded) return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: the source context is not seeded");
+        if (sv.s_star < 0 || sv.s_star >= c->opt.max_samples || !c->sample_set[sv.s_star])
+            return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: set the seed sample slot first");
+        // D and the seed sample's mu must be the ones the seed was built for
+        const size_t n = (size_t)c->n;
+        std::vector<double> a(n), b(n);
+        c->d2h(a.data(), c->D64, n);
+        c->sync();
+        RCG_CUDA_TRY(cudaMemcpy(b.data(), src->D64, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        bool same = a == b;
+        c->d2h(a.data(), c->mu64 + (long long)sv.s_star * c->ld, n);
+        c->sync();
+        RCG_CUDA_TRY(cudaMemcpy(b.data(), src->mu64 + (long long)sv.s_star * src->ld, sizeof(double) * n,
+                                cudaMemcpyDeviceToHost));
+        same = same && a == b;
+        if (!same) return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: D or the seed sample's mu differ");
+        c->eng->seed_import(sv);
         return RCG_OK;
     });
 }

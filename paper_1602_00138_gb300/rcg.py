@@ -26,6 +26,9 @@ RCG_ERR_TIMEOUT = -7
 RCG_ERR_RANK_CAP = -8
 RCG_FP64, RCG_MIXED = 0, 1
 RCG_SEQUENTIAL, RCG_WAVE = 0, 1
+RCG_GALERKIN, RCG_MR = 0, 1
+RCG_CG, RCG_MINRES = 0, 1
+RCG_INNER_OUTER, RCG_PER_RHS = 0, 1
 
 EXPORTED = [
     "rcg_options_default", "rcg_create", "rcg_destroy", "rcg_last_error", "rcg_strerror",
@@ -38,6 +41,7 @@ EXPORTED = [
     "rcg_learn_get_weights", "rcg_learn_record", "rcg_learn_pairs", "rcg_learn_train", "rcg_learn_forward",
     "rcg_learn_gradient", "rcg_learn_predict", "rcg_full_eval", "rcg_save", "rcg_load", "rcg_gemm_nn_f32", "rcg_rom_eval_batch_chunk",
     "rcg_apply_f32", "rcg_stencil_variant_name", "rcg_stencil_variant_ok", "rcg_tuning_report",
+    "rcg_seed_copy",
 ]
 RCG_NOALLOC_MAX_COLS = 1024
 RCG_MAX_PRIVATE = 8
@@ -54,7 +58,8 @@ class Options(C.Structure):
                 ("tau_rank", C.c_double), ("k_u", C.c_int), ("k_cap", C.c_int), ("r_max", C.c_int),
                 ("max_samples", C.c_int), ("maxit", C.c_int), ("inner_eta", C.c_double),
                 ("check_refine", C.c_int), ("keep_solutions", C.c_int), ("seed_degree", C.c_int),
-                ("spin_budget", C.c_longlong), ("learned", C.c_int)]
+                ("spin_budget", C.c_longlong), ("learned", C.c_int), ("wave_rhs", C.c_int),
+                ("check", C.c_int), ("inner", C.c_int), ("recycle", C.c_int)]
 
 
 class Stat(C.Structure):
@@ -126,6 +131,7 @@ def load(path=LIB_PATH):
         "rcg_stencil_variant_name": (C.c_char_p, [I]),
         "rcg_stencil_variant_ok": (I, [P, I]),
         "rcg_tuning_report": (I, [P, I]),
+        "rcg_seed_copy": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -331,6 +337,10 @@ class Context:
         U = None if U0 is None else np.asfortranarray(U0, dtype=np.float64)
         self._check(self.L.rcg_seed(self.h, s0, _ptr(U), st))
         return stats_to_dicts(st)
+
+    def seed_copy(self, src):
+        """rcg_seed_copy: take the seed state of Context `src`."""
+        return self._check(self.L.rcg_seed_copy(self.h, src.h))
 
     def reset_to_seed(self):
         return self._check(self.L.rcg_reset_to_seed(self.h))

@@ -34,14 +34,15 @@ def effective_cap(k_u, k_cap):
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_run(name, order, tau, k_cap=256):
+def oracle_run(name, order, tau, k_cap=256, wave_samples=0, wave_rhs=0):
     inp = workload(name)
     wl = inp["wl"]
     U0, As, Bt, Ct = oracle_seed_inputs(name)
     B = np.hstack([Bt, Ct])
     st = obasis.seed(As[0], B, U0, inp["tol"], tau=tau, k_cap=effective_cap(wl.k_u, k_cap))
     seed_stats = list(st.stats)
-    out = obasis.solve_all(st, lambda i: As[i], range(1, wl.K + 1), B, inp["tol"], order=order, tau=tau)
+    out = obasis.solve_all(st, lambda i: As[i], range(1, wl.K + 1), B, inp["tol"], order=order, tau=tau,
+                           wave_samples=wave_samples, wave_rhs=wave_rhs)
     return st, seed_stats, out
 
 

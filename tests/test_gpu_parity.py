@@ -67,12 +67,14 @@ def test_stencil_matches_oracle_operator(torch_cuda, name):
     assert err32 <= 2e-6, err32
 
 
-def _check_run(name, precision, order, tau, psi_tol, wave_samples=0, k_cap=256):
+def _check_run(name, precision, order, tau, psi_tol, wave_samples=0, k_cap=256, wave_rhs=0):
     from paper_1602_00138_gb300 import rcg
     inp = workload(name)
     wl = inp["wl"]
-    st_o, seed_o, out_o = oracle_run(name, "sequential" if order == rcg.RCG_SEQUENTIAL else "wave", tau, k_cap)
-    ctx, seed_g, out_g, rc, r_seed = gpu_run(name, precision, order, tau, wave_samples=wave_samples, k_cap=k_cap)
+    st_o, seed_o, out_o = oracle_run(name, "sequential" if order == rcg.RCG_SEQUENTIAL else "wave", tau, k_cap,
+                                     wave_samples, wave_rhs)
+    ctx, seed_g, out_g, rc, r_seed = gpu_run(name, precision, order, tau, wave_samples=wave_samples, k_cap=k_cap,
+                                             wave_rhs=wave_rhs)
     try:
         assert rc == 0
         _, As, Bt, Ct = oracle_seed_inputs(name)
@@ -187,3 +189,17 @@ def test_recycle_space_cap_binds(torch_cuda, name):
     assert any(o["appended"] for o in out_o if o["sample"] == 1)     # the cap bound before sample 2
     diffs = [abs(a["iters"] - b["iters"]) for a, b in zip(out_g, out_o)]
     assert max(diffs) <= 2, diffs
+
+
+@pytest.mark.parametrize("name,ws,wr", [("t3d_32", 1, 5), ("t2d_37", 2, 4)])
+def test_wave_rhs_blocks_match_oracle(torch_cuda, name, ws, wr):
+    """Waves of ws samples x wr consecutive right-hand sides: V grows between
+    the blocks of a sample, as in the paper's order, with the lanes of a block
+    batched; decisions, ranks and the reduced model against the oracle run
+    with the same blocks (mixed precision on the float4 path, t3d_32; FP64 on
+    the scalar path, t2d_37)."""
+    from paper_1602_00138_gb300 import rcg
+    if name == "t3d_32":
+        _check_run(name, rcg.RCG_MIXED, rcg.RCG_WAVE, 1e-6, 1e-6, wave_samples=ws, wave_rhs=wr)
+    else:
+        _check_run(name, rcg.RCG_FP64, rcg.RCG_WAVE, 1e-9, 1e-8, wave_samples=ws, wave_rhs=wr)
