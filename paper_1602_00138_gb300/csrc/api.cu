@@ -38,6 +38,15 @@ struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
 };
 
+// dst = x / sqrt(nrm2[0]) (a recycle column of unit length)
+template <typename TD>
+__global__ void k_scaled_copy(long long n, const double *__restrict__ x, const double *__restrict__ nrm2,
+                              TD *__restrict__ dst) {
+    const double s = nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        dst[p] = (TD)(x[p] * s);
+}
+
 }  // namespace
 
 // The state right after rcg_seed of an engine, for copying it into another
@@ -447,6 +456,94 @@ struct Engine : EngineBase {
         // follow this kernel on the stream
     }
 
+    struct Lane { int s, j; };          // a (sample, RHS) lane of a wave
+
+    // ---- the paper's check and inner solver (float64 engine)
+    // A~_s V = K R with R = R2 R1 (CholQR2): K in Kmr (ld), L_i = R_i^T in Lmr1/2
+    double *Kmr = nullptr, *Kmr2 = nullptr, *Lmr1 = nullptr, *Lmr2 = nullptr, *Rmr = nullptr, *Rimr = nullptr;
+    int kmr_cap = 0, mr_s = -1, mr_r = -1;
+    void mr_factor(int s) {
+        if constexpr (sizeof(T) == 8) {
+            if (mr_s == s && mr_r == r) return;
+            if (r > kmr_cap) {
+                for (void *p : std::vector<void *>{Kmr, Kmr2, Lmr1, Lmr2, Rmr, Rimr}) c->release(p);
+                kmr_cap = std::max(r, std::min(rmax, 2 * kmr_cap));
+                Kmr = c->alloc<double>((size_t)kmr_cap * ld);
+                Kmr2 = c->alloc<double>((size_t)kmr_cap * ld);
+                for (double **p : {&Lmr1, &Lmr2, &Rmr, &Rimr}) *p = c->alloc<double>((size_t)kmr_cap * kmr_cap);
+            }
+            apply_cols64((const double *)V, Kmr, r, s);
+            double *Ls[2] = {Lmr1, Lmr2};
+            for (int pass = 0; pass < 2; ++pass) {
+                gemm_tn<double, double>(st, n, Kmr, ld, r, Kmr, ld, r, Ls[pass], r, false);
+                RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+                chol_inplace(st, Ls[pass], r, r, d_info);
+                check_info("minimum-residual check: Cholesky QR of A V");
+                lower_to_upper(st, Ls[pass], r, r, Rmr);
+                tri_upper_inverse(st, Rmr, r, r, Rimr);
+                gemm_nn<double, double>(st, n, Kmr, ld, r, Rimr, r, r, Kmr2, ld, 1.0, 0.0);
+                std::swap(Kmr, Kmr2);
+            }
+            mr_s = s;
+            mr_r = r;
+        } else {
+            (void)s;
+            throw Error{RCG_ERR_INVALID, "the minimum-residual check runs in the float64 engine"};
+        }
+    }
+    // recycled MINRES lanes: scalars [m][MR_NSC], dots, mu, alpha, step flags, 3 extra columns per lane
+    double *mr_sc = nullptr, *mr_hd = nullptr, *mr_mu = nullptr, *mr_alpha = nullptr, *mr_ext = nullptr;
+    int *mr_step = nullptr;
+    int mr_cap = 0;
+    void ensure_mres(int m) {
+        if (m <= mr_cap) return;
+        for (void *p : std::vector<void *>{mr_sc, mr_hd, mr_mu, mr_alpha, mr_ext, mr_step}) c->release(p);
+        mr_cap = m;
+        mr_sc = c->alloc<double>((size_t)m * MR_NSC);
+        mr_hd = c->alloc<double>((size_t)m * KMAX);
+        mr_mu = c->alloc<double>((size_t)m * KMAX);
+        mr_alpha = c->alloc<double>(m);
+        mr_step = c->alloc<int>(m);
+        mr_ext = c->alloc<double>((size_t)m * 3 * ld);
+    }
+    // per-RHS recycling (the Sec. 6.3 comparison): new directions of RHS j in
+    // a ring of KP_MAX columns, list entries -(2 + slot)
+    T *Ppr = nullptr;
+    std::vector<int> ppr_next;
+    void per_rhs_push(const std::vector<int> &cand, const std::vector<Lane> &lanes, std::vector<int> &kept,
+                      std::vector<double> &ratio) {
+        const int a = (int)cand.size();
+        kept.assign(a, 0);
+        ratio.assign(a, 0.0);
+        if (!a) return;
+        const int nrhs = c->nrhs;
+        if (!Ppr) {
+            Ppr = c->alloc<T>((size_t)nrhs * KP_MAX * ld);
+            ppr_next.assign(nrhs, 0);
+        }
+        ensure_append(a);
+        c->h2d(d_cand, cand.data(), a);
+        norm2_lanes(st, n, (const double *const *)p_x64, d_cand, a, xn2);
+        for (int i = 0; i < a; ++i) {
+            const int l = cand[i], j = lanes[l].j;
+            const int slot = ppr_next[j];
+            ppr_next[j] = (slot + 1) % KP_MAX;
+            auto &pl = priv[j];
+            // the slot's previous direction leaves the list first
+            pl.erase(std::remove(pl.begin(), pl.end(), -(2 + slot)), pl.end());
+            T *dst = Ppr + ((long long)j * KP_MAX + slot) * ld;
+            k_scaled_copy<T><<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(
+                n, x64 + (long long)l * ld, xn2 + i, dst);
+            ++c->launches;
+            RCG_CHECK_LAUNCH();
+            pl.push_back(-(2 + slot));
+            while (k_u + (int)pl.size() > std::min(c->opt.k_cap, k_u + KP_MAX) && !pl.empty()) pl.erase(pl.begin());
+            kept[i] = 1;
+            ratio[i] = 1.0;
+        }
+        c->sync();
+    }
+
     // float64 scratch for the new basis columns and their images
     double *Q64 = nullptr, *AQ64 = nullptr;
     int aq64_cap = 0;
@@ -647,12 +744,15 @@ struct Engine : EngineBase {
     }
 
     // -------------------------------------------------------------- wave
-    struct Lane { int s, j; };
 
     void wave(const std::vector<Lane> &lanes, bool seed_mode, bool seq, std::vector<rcg_stat> &out) {
         const int m = (int)lanes.size();
         ensure_lanes(m);
         const double tau = seed_mode ? c->opt.tau_rank : c->opt.tau_rank;
+        // the paper's own check and inner solver (float64 engine), and per-RHS recycling only
+        const bool use_mres = !mixed && c->opt.inner == RCG_MINRES;
+        const bool mr_check = !mixed && c->opt.check == RCG_MR && !seed_mode;
+        const bool per_rhs = c->opt.recycle == RCG_PER_RHS && !seed_mode;
         std::vector<int> lnode(m), samp(m);
         std::vector<double> lw(m), ltol(m);
         std::vector<double *> hdiag64(m);
@@ -682,7 +782,9 @@ struct Engine : EngineBase {
             if (l == 0 || samp[l] != samp[l - 1]) grp_begin.push_back(l);
         grp_begin.push_back(m);
         std::map<int, std::pair<double *, double *>> gal;
-        if (r > 0) {
+        const bool need_gal = !((c->opt.check == RCG_MR || c->opt.recycle == RCG_PER_RHS) && !seed_mode &&
+                                c->opt.inner == RCG_MINRES && !mixed);
+        if (r > 0 && need_gal) {
             // wave order: all samples' matrices and factors, then one status check
             if (!seq) RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
             for (size_t gi = 0; gi + 1 < grp_begin.size(); ++gi) {
@@ -713,11 +815,28 @@ struct Engine : EngineBase {
             c->d2h(rr_h.data(), d_rr, m);
             c->sync();
         };
-        if (r > 0) project(true);
-        else for (int l = 0; l < m; ++l) RCG_CUDA_TRY(cudaMemsetAsync(x64 + (long long)l * ld, 0, sizeof(double) * n, st));
+        // the minimum-residual guess from range(V): c = K^T b (a row of K), y = R^-1 c
+        // with A~_s V = K R2 R1 (CholQR, two passes), x0 = V y
+        auto mr_project = [&]() {
+            for (size_t gi = 0; gi + 1 < grp_begin.size(); ++gi) {
+                const int l0 = grp_begin[gi], l1 = grp_begin[gi + 1];
+                mr_factor(samp[l0]);
+                gather_rows<double>(st, (const double *)Kmr, ld, r, d_lnode + l0, d_lw + l0, l1 - l0,
+                                    Yb + (long long)l0 * rmax, rmax);
+                trsv_lower_batched(st, Lmr2, r, r, Yb + (long long)l0 * rmax, rmax, l1 - l0, true);
+                trsv_lower_batched(st, Lmr1, r, r, Yb + (long long)l0 * rmax, rmax, l1 - l0, true);
+            }
+            lift(V, r, Yb, rmax, m, x64, ld, 0.0);
+        };
+        if (r > 0 && !per_rhs) {
+            if (mr_check) mr_project();
+            else project(true);
+        } else {
+            for (int l = 0; l < m; ++l) RCG_CUDA_TRY(cudaMemsetAsync(x64 + (long long)l * ld, 0, sizeof(double) * n, st));
+        }
         std::vector<double> rr_h;
         residual(rr_h, nullptr);
-        if (r > 0 && !seed_mode) {
+        if (r > 0 && !seed_mode && !mr_check && !per_rhs) {
             for (int step = 0; step < c->opt.check_refine; ++step) {
                 project(false);
                 residual(rr_h, nullptr);
@@ -845,7 +964,9 @@ struct Engine : EngineBase {
             for (int l = 0; l < m; ++l)
                 for (int q = 0; q < kp[l]; ++q) {
                     const int e = spec[(size_t)l * KMAX + ku + q];
-                    const T *w = e >= 0 ? V + (long long)e * ld : X0 + (long long)lanes[l].j * ld;
+                    const T *w = e >= 0 ? V + (long long)e * ld
+                                 : e == -1 ? X0 + (long long)lanes[l].j * ld
+                                           : Ppr + ((long long)lanes[l].j * KP_MAX + (-e - 2)) * ld;
                     hwpp[(size_t)l * KPT + q] = w;
                     asrc.push_back(w);
                     adst.push_back(awp + ((long long)l * kps + q) * ld);
@@ -896,11 +1017,20 @@ struct Engine : EngineBase {
             gm.x = xc; gm.r = rv; gm.p = pv; gm.q = qv;
             gm.wu = V; gm.awu = au0; gm.awp = awp; gm.wpp = d_wpp;
             gm.si = d_si; gm.kp = d_kp;
+            ls.nl = m;                     // the kernels of this wave launch over its m lanes
             if (kmax_used > 0) {
-                lane_gw(st, (const double *const *)d_gsl, rmax, r, d_spec, (const double *const *)d_sx, ls.kdef, ls.gw, m);
+                if (use_mres) {
+                    // recycled MINRES: H = (A~ U_j)^T A~ U_j, whose inverse gives the
+                    // projector away from range(A~ U_j) = range(K_j)
+                    c->h2d(d_mask, act.data(), m);
+                    mres_gram(st, n, gm, ls, d_mask, ls.gw);
+                } else {
+                    lane_gw(st, (const double *const *)d_gsl, rmax, r, d_spec, (const double *const *)d_sx, ls.kdef,
+                            ls.gw, m);
+                }
                 RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
                 lane_inverse(st, ls.gw, ls.kdef, m, d_info);
-                check_info("deflation matrix U_j^T A U_j");
+                check_info(use_mres ? "recycle matrix (A U_j)^T A U_j" : "deflation matrix U_j^T A U_j");
             }
             if (!aug_l.empty()) {
                 // Galerkin pivot of x_hat against U_j; kept columns border G_W^-1 on the device
@@ -922,9 +1052,6 @@ struct Engine : EngineBase {
             };
             for (int l = 0; l < m; ++l)
                 if (act[l]) set_thresh(l, std::sqrt(rr_h[l]));
-            // the whole capacity: the scalar iteration launches over ls.m lanes and
-            // skips those whose active / mask entry is 0 (lanes m.. of a smaller wave)
-            ls.nl = m;                     // the kernels of this wave launch over its m lanes
             RCG_CUDA_TRY(cudaMemsetAsync(ls.iters, 0, sizeof(int) * ls.m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.active, 0, sizeof(int) * ls.m, st));
             RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * ls.m, st));
@@ -976,6 +1103,78 @@ struct Engine : EngineBase {
                     cg_restart<T>(st, g, gm, ls, t, d_mask);
                 }
             };
+            if (use_mres) {
+                // recycled MINRES cycles (minres.cu) until the float64 residual meets tol
+                ensure_mres(m);
+                ls.maxit = c->opt.maxit;
+                std::vector<double> sch((size_t)m * MR_NSC, 0.0);
+                for (int l = 0; l < m; ++l) sch[(size_t)l * MR_NSC + MR_THRESH] = thr[l];
+                c->h2d(mr_sc, sch.data(), sch.size());
+                LaneGeom gq = gm;
+                gq.r = gm.q;                               // (A~W)^T of A~ y at the end of a cycle
+                auto cycle_start = [&](const std::vector<int> &mask_h) {
+                    c->h2d(d_mask, mask_h.data(), m);
+                    mres_dots(st, n, gm, ls, d_mask, (const double *)gm.r, mr_hd);
+                    mres_mu(st, ls, d_mask, mr_hd, mr_mu, mr_sc);
+                    mres_cycle(st, n, gm, ls, d_mask, mr_mu, (double *const *)p_x64, mr_sc, false);
+                    mres_init(st, n, gm, ls, d_mask, mr_ext, mr_sc, ls.active);
+                };
+                cycle_start(act);
+                if (per_rhs) {
+                    // the guess from range(U_j) alone: its residual is the first cycle's xi
+                    std::vector<double> sc0((size_t)m * MR_NSC);
+                    c->d2h(sc0.data(), mr_sc, sc0.size());
+                    c->sync();
+                    for (int l = 0; l < m; ++l)
+                        if (act[l]) out[l].relres0 = relres0[l] = sc0[(size_t)l * MR_NSC + MR_XI] / std::fabs(lw[l]);
+                }
+                while (true) {
+                    for (int i = 0; i < chunk; ++i)
+                        mres_iteration(st, g, (const double *)D, (const double *const *)p_diag,
+                                       (const double *const *)p_p, (double *const *)p_q, gm, ls, ls.active, mr_step,
+                                       mr_alpha, mr_hd, mr_mu, mr_ext, mr_sc);
+                    c->d2h(flag_h.data(), ls.flag, m);
+                    c->d2h(active_h.data(), ls.active, m);
+                    c->d2h(iters_h.data(), ls.iters, m);
+                    c->sync();
+                    std::vector<int> F;
+                    for (int l = 0; l < m; ++l)
+                        if (act[l] && !done[l] && (flag_h[l] != 0 || !active_h[l])) F.push_back(l);
+                    if (!F.empty()) {
+                        // end of the cycle: x += y - W H^-1 (A~W)^T A~ y, then the float64 residual
+                        std::vector<int> fmask(m, 0);
+                        for (int l : F) fmask[l] = 1;
+                        c->h2d(d_mask, fmask.data(), m);
+                        apply_op<double>(st, g, c->D64, (const double *const *)p_diag64, (const double *const *)p_xc,
+                                         (double *const *)p_q, m, d_mask, nullptr, nullptr);
+                        mres_dots(st, n, gq, ls, d_mask, (const double *)gm.q, mr_hd);
+                        mres_mu(st, ls, d_mask, mr_hd, mr_mu, mr_sc);
+                        mres_cycle(st, n, gm, ls, d_mask, mr_mu, (double *const *)p_x64, mr_sc, true);
+                        residual(rr_h, d_mask);
+                        std::vector<int> Rl, rmask(m, 0);
+                        for (int l : F) {
+                            relres[l] = std::sqrt(rr_h[l]) / std::fabs(lw[l]);
+                            if (relres[l] <= ltol[l]) done[l] = 1;
+                            else if (iters_h[l] >= c->opt.maxit || restarts[l] > 200) {
+                                done[l] = 1;
+                                status[l] = RCG_ERR_NOT_CONVERGED;
+                            } else {
+                                Rl.push_back(l);
+                                rmask[l] = 1;
+                                ++restarts[l];
+                            }
+                        }
+                        if (!Rl.empty()) {
+                            RCG_CUDA_TRY(cudaMemsetAsync(ls.flag, 0, sizeof(int) * m, st));
+                            cycle_start(rmask);
+                        }
+                    }
+                    bool any = false;
+                    for (int l = 0; l < m; ++l)
+                        if (act[l] && !done[l]) any = true;
+                    if (!any) break;
+                }
+            } else {
             restart(act);
             if (vec) build_list();
             while (true) {
@@ -1037,6 +1236,7 @@ struct Engine : EngineBase {
                 if (!any) break;
                 if (vec) build_list();
             }
+            }
             c->d2h(iters_h.data(), ls.iters, m);
             c->sync();
             if (net && net->record && !alanes.empty()) {
@@ -1056,13 +1256,14 @@ struct Engine : EngineBase {
         std::vector<int> kept;
         std::vector<double> ratio;
         const int r_before = r;
-        append(cand, tau, (seq && !seed_mode) ? lanes[0].s : -1, kept, ratio);
+        if (per_rhs) per_rhs_push(cand, lanes, kept, ratio);
+        else append(cand, tau, (seq && !seed_mode) ? lanes[0].s : -1, kept, ratio);
         int qi = 0;
         for (size_t ci = 0; ci < cand.size(); ++ci) {
             const int l = cand[ci];
             out[l].ratio = ratio[ci];
             out[l].appended = kept[ci];
-            if (kept[ci] && !seed_mode) {
+            if (kept[ci] && !seed_mode && !per_rhs) {
                 auto &pl = priv[lanes[l].j];
                 pl.push_back(r_before + qi);
                 while (k_u + (int)pl.size() > std::min(c->opt.k_cap, k_u + KP_MAX) && !pl.empty()) pl.erase(pl.begin());
@@ -1808,7 +2009,11 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
     if (c->opt.order != RCG_SEQUENTIAL && c->opt.order != RCG_WAVE) { delete c; return RCG_ERR_INVALID; }
     if (c->opt.wave_rhs < 0 || (c->opt.check != RCG_GALERKIN && c->opt.check != RCG_MR) ||
         (c->opt.inner != RCG_CG && c->opt.inner != RCG_MINRES) ||
-        (c->opt.recycle != RCG_INNER_OUTER && c->opt.recycle != RCG_PER_RHS)) {
+        (c->opt.recycle != RCG_INNER_OUTER && c->opt.recycle != RCG_PER_RHS) ||
+        // the paper's check and solver run in the float64 engine; per-RHS recycle
+        // spaces hold columns outside V, which only the MINRES lanes address
+        ((c->opt.check == RCG_MR || c->opt.inner == RCG_MINRES) && c->opt.precision != RCG_FP64) ||
+        (c->opt.recycle == RCG_PER_RHS && c->opt.inner != RCG_MINRES)) {
         delete c;
         return RCG_ERR_INVALID;
     }

@@ -75,6 +75,13 @@ struct LaneState {
     unsigned long long *prof;  // optional work counters (see KTimer), or null
     float *xa;              // [m] alpha of the step x += alpha p still to apply (float32 iteration)
     int *xt;                // [m] iteration that set xa (-1: none); applied by that iteration's direction kernel
+    int maxit;              // iteration budget of a lane (recycled MINRES lanes)
+};
+
+// Per-lane scalars of the recycled MINRES lanes (minres.cu), [m][MR_NSC].
+enum {
+    MR_XI2, MR_XI, MR_PHI, MR_BETA, MR_C1, MR_S1, MR_C2, MR_S2, MR_WN2, MR_TAU, MR_GAMMA, MR_DELTA, MR_EPS,
+    MR_IBETA, MR_THRESH, MR_NSC = 16
 };
 
 // Slots of a lane's private deflation columns in LaneGeom::wpp (the private
@@ -356,6 +363,20 @@ void stencil4_apply(cudaStream_t st, const Grid &g, const float *D, const float 
 std::string stencil_tuning_report();
 const char *stencil_variant_name(int v);
 int stencil_variant_ok(const Grid &g, int v);
+
+// minres.cu (float64 lanes; LaneGeom as for CG with x = the MINRES iterate
+// y, p = v_k, q = A~ v_k / w; ext = [m][3] extra columns v_{k-1}, d_{k-1}, d_{k-2})
+void mres_gram(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask, double *H);
+void mres_dots(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
+               const double *src, double *hd);
+void mres_mu(cudaStream_t st, const LaneState &ls, const int *mask, const double *hd, double *mu, double *sc);
+void mres_cycle(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
+                const double *mu, double *const *x64, double *sc, bool finish);
+void mres_init(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask, double *ext,
+               double *sc, int *act);
+void mres_iteration(cudaStream_t st, const Grid &g, const double *D, const double *const *diag_of_col,
+                    const double *const *v_ptr, double *const *q_ptr, const LaneGeom &gm, const LaneState &ls,
+                    int *act, int *step, double *alpha, double *hd, double *mu, double *ext, double *sc);
 
 // cg.cu
 template <typename T>
