@@ -115,7 +115,10 @@ typedef struct {
     int    check_refine;  /* extra Galerkin refinement steps of the check   */
     int    keep_solutions;/* keep every delivered x (for rcg_solution_get)  */
     int    seed_degree;   /* Chebyshev filter degree of the eigen seed      */
-    long long spin_budget;/* reserved: bound of device-side waits           */
+    long long spin_budget;/* polls of a tensor-core kernel's main-loop waits
+                             for its MMAs (0 = 2^22); on running out the
+                             call returns RCG_ERR_TIMEOUT after the kernel
+                             has waited (full bound) for its last MMAs     */
     int    learned;       /* RCG_MIXED: add the learned network's column to
                              the private U_j of every CG solve (needs
                              weights: rcg_learn_set_weights or _train)      */

@@ -1916,7 +1916,9 @@ int fail(rcg_ctx *c, int code, const std::string &msg) {
 template <typename F> int guarded(rcg_ctx *c, F f) {
     if (!c) return RCG_ERR_INVALID;
     long long *prev = g_launch_counter;
+    const long long prev_spin = g_spin_budget;
     g_launch_counter = &c->launches;
+    g_spin_budget = c->opt.spin_budget;
     int rc;
     try {
         rc = f();
@@ -1928,6 +1930,7 @@ template <typename F> int guarded(rcg_ctx *c, F f) {
         rc = fail(c, RCG_ERR_INVALID, "unexpected exception");
     }
     g_launch_counter = prev;
+    g_spin_budget = prev_spin;
     return rc;
 }
 

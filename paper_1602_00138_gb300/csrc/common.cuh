@@ -37,6 +37,9 @@ struct Error {
 
 // Launch counter shared by all launchers of a context (set by the caller).
 extern thread_local long long *g_launch_counter;
+// Bound of the tensor-core kernels' main-loop waits for the calling context
+// (rcg_options.spin_budget; 0 = the built-in bound), set around each call.
+extern thread_local long long g_spin_budget;
 inline void count_launch() { if (g_launch_counter) ++*g_launch_counter; }
 
 // ------------------------------------------------------------ grid / operator

@@ -17,6 +17,7 @@
 namespace rcg {
 
 thread_local long long *g_launch_counter = nullptr;
+thread_local long long g_spin_budget = 0;
 
 namespace {
 

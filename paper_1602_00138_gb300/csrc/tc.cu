@@ -51,6 +51,11 @@ constexpr int WBYTES = TBK * 8;                          // the step's float64 r
 constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + NSTAGE * WBYTES + 1024;   // + 1024-byte alignment slack
 constexpr int LEVEL1 = 16;              // K-steps summed before the second level
 constexpr long long SPIN_LIMIT = 1LL << 22;
+
+// Polls of a main-loop mbarrier wait: the calling context's
+// rcg_options.spin_budget when positive, else SPIN_LIMIT.  The final wait
+// for the last committed step always has the full SPIN_LIMIT.
+long long spin_budget() { return g_spin_budget > 0 ? g_spin_budget : SPIN_LIMIT; }
 constexpr long long LIST_MIN_CHUNK = 8;  // fewest K-steps per slice when a block list sets the length
 constexpr int NUM_SMS = 152;
 
@@ -101,9 +106,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long i = 0; i < SPIN_LIMIT; ++i)
+// bounded wait (at most `limit` polls); returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
 }
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(NTHR, 1)
 k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const float *__restrict__ B, long long ldb,
         int kb, int symmetric, float *__restrict__ part, long long chunk, int *__restrict__ err,
         const double *__restrict__ wt, const int *__restrict__ blist, const int *__restrict__ bcount, int zper,
-        long long ldw_b, long long ldl_b, double wscale) {
+        long long ldw_b, long long ldl_b, double wscale, long long spin) {
     if (symmetric && blockIdx.x > blockIdx.y) return;        // lower tiles are mirrored by the reduction
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar[2];
@@ -276,6 +281,7 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
     for (int q = 0; q < 64; ++q) { acc1[q] = 0.f; acc2[q] = 0.f; }
     bool ok = true;
     long long drained = 0;                // steps whose partial is in acc1 / acc2
+    long long last = -1;                  // last step whose MMAs were committed (the same in every thread)
     auto drain = [&](long long q) {       // the MMAs of step q are complete
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t base = tmem + t_lane + (uint32_t)((q & 1) * TNc + col0);
@@ -320,11 +326,12 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
             }
             mma_commit(smem_u32(&mbar[ks & 1]));
         }
+        last = ks;
         // step ks-1: its MMAs free the stage that step ks+2 is copied into, and
         // its accumulator is drained while step ks runs on the tensor core
         if (ks >= 1) {
             const long long q = ks - 1;
-            if (mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1))) {
+            if (mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1), spin)) {
                 drain(q);
             } else {
                 s_ok = 0;
@@ -341,12 +348,13 @@ k_tc_tn(long long n, const float *__restrict__ A, long long lda, int ka, const f
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    // last step: wait for its MMAs (bounded, also after a timeout, so that
-    // nothing runs on the tensor memory when it is freed)
-    if (nk > 0 && drained < nk) {
-        const long long q = drained < nk - 1 ? (ok ? nk - 1 : drained) : nk - 1;
-        const bool done = mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1));
-        if (ok && done && q == nk - 1 && drained == nk - 1) drain(q);
+    // the last committed step: wait for its MMAs with the full bound, also
+    // after a main-loop timeout (the MMAs complete in issue order, so none
+    // runs on the tensor memory when it is freed); every earlier step was
+    // waited for in the loop, so the barrier's phase parity is unambiguous
+    if (last >= 0) {
+        const bool done = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), SPIN_LIMIT);
+        if (ok && done && last == nk - 1 && drained == nk - 1) drain(last);
         else ok = false;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");          // no copy in flight at exit
@@ -449,7 +457,7 @@ __global__ void k_nn_prep_b(const double *__restrict__ C, int ldc, int k, int m,
 __global__ void __launch_bounds__(NTHR, 1)
 k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const float *__restrict__ Bh,
         const float *__restrict__ Bl, int ldb, int m, float *__restrict__ Out, long long ldo, float alpha, float beta,
-        int *__restrict__ err) {
+        int *__restrict__ err, long long spin) {
     extern __shared__ __align__(1024) char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_slot;
@@ -517,6 +525,7 @@ k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const fl
     for (int q = 0; q < 64; ++q) { acc1[q] = 0.f; acc2[q] = 0.f; }
     bool ok = true;
     long long drained = 0;
+    long long last = -1;                  // last step whose MMAs were committed (the same in every thread)
     auto drain = [&](long long q) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t base = tmem + t_lane + (uint32_t)((q & 1) * TNc + col0);
@@ -570,9 +579,10 @@ k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const fl
             }
             mma_commit(smem_u32(&mbar[ks & 1]));
         }
+        last = ks;
         if (ks >= 1) {
             const long long q = ks - 1;
-            if (mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1))) {
+            if (mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1), spin)) {
                 drain(q);
             } else {
                 s_ok = 0;
@@ -585,10 +595,9 @@ k_tc_nn(long long n, const float *__restrict__ V, long long ldv, int k, const fl
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    if (nk > 0 && drained < nk) {
-        const long long q = drained < nk - 1 ? (ok ? nk - 1 : drained) : nk - 1;
-        const bool done = mbar_wait(smem_u32(&mbar[q & 1]), (uint32_t)((q >> 1) & 1));
-        if (ok && done && q == nk - 1 && drained == nk - 1) drain(q);
+    if (last >= 0) {                      // as in k_tc_tn: the last committed step, full bound
+        const bool done = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), SPIN_LIMIT);
+        if (ok && done && last == nk - 1 && drained == nk - 1) drain(last);
         else ok = false;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -714,7 +723,7 @@ void tc_gemm_tn(cudaStream_t st, long long n, const float *A, long long lda, int
     dim3 grid((ka + TM - 1) / TM, (kb + TNc - 1) / TNc, z);
     if ((blist != nullptr) != (bcount != nullptr) || (blist && !wt)) throw Error{RCG_ERR_INVALID, "tc_gemm_tn: block list"};
     k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, B, ldb, kb, symmetric ? 1 : 0, scratch, chunk, err, wt, blist,
-                                         bcount, z, 0, 0, 1.0);
+                                         bcount, z, 0, 0, 1.0, spin_budget());
     count_launch();
     RCG_CHECK_LAUNCH();
     const long long tot = (long long)ka * kb;
@@ -762,7 +771,7 @@ void tc_gram_w_batched(cudaStream_t st, long long n, const float *A, long long l
         const int nb = std::min(bmax, nbatch - b0);
         dim3 grid(tx, tx, (unsigned)(zper * nb));
         k_tc_tn<<<grid, NTHR, TC_SMEM, st>>>(n, A, lda, ka, A, lda, ka, 1, scratch, 1, err, wt + b0 * ldw,
-                                             blist + b0 * ldl, bcount + b0, zper, ldw, ldl, wscale);
+                                             blist + b0 * ldl, bcount + b0, zper, ldw, ldl, wscale, spin_budget());
         count_launch();
         RCG_CHECK_LAUNCH();
         const long long tot = (long long)ka * ka * nb;
@@ -797,7 +806,8 @@ void tc_gemm_nn(cudaStream_t st, long long n, const float *V, long long ldv, int
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)((m + TNc - 1) / TNc));
-    k_tc_nn<<<grid, NTHR, NN_SMEM, st>>>(n, V, ldv, k, Bh, Bl, ldb, m, Out, ldo, (float)alpha, (float)beta, err);
+    k_tc_nn<<<grid, NTHR, NN_SMEM, st>>>(n, V, ldv, k, Bh, Bl, ldb, m, Out, ldo, (float)alpha, (float)beta, err,
+                                         spin_budget());
     count_launch();
     RCG_CHECK_LAUNCH();
 }

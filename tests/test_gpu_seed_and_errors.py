@@ -118,3 +118,26 @@ def test_rank_cap_is_reported(rcg):
         assert e.value.code == rcg.RCG_ERR_RANK_CAP
     finally:
         ctx.close()
+
+
+def test_tiny_spin_budget_times_out_and_the_gpu_stays_usable(rcg):
+    """rcg_options.spin_budget bounds the tensor-core kernels' main-loop
+    waits for their MMAs.  With a budget of one poll the waits run out before
+    the tensor core finishes a step; the kernel then stops issuing, waits with
+    its full bound for the last MMAs it committed, frees its tensor memory and
+    reports RCG_ERR_TIMEOUT, which the call returns.  A context created
+    afterwards with the default budget runs the same seed normally."""
+    inp, ctx = _ctx(rcg, "t3d_32", precision=rcg.RCG_MIXED, order=rcg.RCG_WAVE, tau_rank=1e-6, spin_budget=1)
+    try:
+        with pytest.raises(rcg.RcgError) as e:
+            ctx.seed(0, None)
+        assert e.value.code == rcg.RCG_ERR_TIMEOUT
+    finally:
+        ctx.close()
+    inp, ctx = _ctx(rcg, "t3d_32", precision=rcg.RCG_MIXED, order=rcg.RCG_WAVE, tau_rank=1e-6)
+    try:
+        ctx.seed(0, None)
+        stats, rc = ctx.solve_all(1, 1)
+        assert rc == 0 and max(s["relres"] for s in stats) <= 1e-8 * 1.0001
+    finally:
+        ctx.close()
