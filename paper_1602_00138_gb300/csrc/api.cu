@@ -38,6 +38,63 @@ struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
 };
 
+// A chunk of CG iterations captured once as a CUDA graph and replayed on the
+// context's stream.  Capture needs a stream other than the legacy default
+// one, so the graph runs on a private stream ordered after / before the
+// context's stream by events.  Launches issued during the capture are counted
+// once per replay.
+class CgGraph {
+  public:
+    explicit CgGraph(cudaStream_t st) : st_(st) {}
+    CgGraph(const CgGraph &) = delete;
+    CgGraph &operator=(const CgGraph &) = delete;
+    ~CgGraph() {
+        if (exec_) cudaGraphExecDestroy(exec_);
+        if (graph_) cudaGraphDestroy(graph_);
+        if (ev0_) cudaEventDestroy(ev0_);
+        if (ev1_) cudaEventDestroy(ev1_);
+        if (gs_) cudaStreamDestroy(gs_);
+    }
+    bool ready() const { return exec_ != nullptr; }
+    template <typename F> void capture(F issue) {
+        RCG_CUDA_TRY(cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking));
+        RCG_CUDA_TRY(cudaEventCreateWithFlags(&ev0_, cudaEventDisableTiming));
+        RCG_CUDA_TRY(cudaEventCreateWithFlags(&ev1_, cudaEventDisableTiming));
+        long long *ctr = g_launch_counter;
+        long long counted = 0;
+        g_launch_counter = &counted;
+        RCG_CUDA_TRY(cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal));
+        try {
+            issue(gs_);
+        } catch (...) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(gs_, &dummy);
+            if (dummy) cudaGraphDestroy(dummy);
+            g_launch_counter = ctr;
+            throw;
+        }
+        g_launch_counter = ctr;
+        RCG_CUDA_TRY(cudaStreamEndCapture(gs_, &graph_));
+        RCG_CUDA_TRY(cudaGraphInstantiate(&exec_, graph_, 0));
+        per_launch_ = counted;
+    }
+    void launch() {
+        RCG_CUDA_TRY(cudaEventRecord(ev0_, st_));
+        RCG_CUDA_TRY(cudaStreamWaitEvent(gs_, ev0_, 0));
+        RCG_CUDA_TRY(cudaGraphLaunch(exec_, gs_));
+        RCG_CUDA_TRY(cudaEventRecord(ev1_, gs_));
+        RCG_CUDA_TRY(cudaStreamWaitEvent(st_, ev1_, 0));
+        if (g_launch_counter) *g_launch_counter += per_launch_;
+    }
+
+  private:
+    cudaStream_t st_, gs_ = nullptr;
+    cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
+    cudaGraph_t graph_ = nullptr;
+    cudaGraphExec_t exec_ = nullptr;
+    long long per_launch_ = 0;
+};
+
 // dst = x / sqrt(nrm2[0]) (a recycle column of unit length)
 template <typename TD>
 __global__ void k_scaled_copy(long long n, const double *__restrict__ x, const double *__restrict__ nrm2,
@@ -1061,10 +1118,16 @@ struct Engine : EngineBase {
             c->h2d(d_mask, act.data(), m);
             ls.prof = c->ktimer.on ? c->d_prof : nullptr;
             int t = 0;
-            const int chunk = m > 1 ? 8 : 12;
+
             std::vector<int> flag_h(m), active_h(m);
             // lanes selected by `sel` and tiles of <= 32 of them per sample slot
             const bool vec = mixed && cg4_supported(g);
+            // the scalar path replays a CUDA graph of a 6-iteration chunk: its ring
+            // slots (t mod 3, t mod 2) repeat every 6 iterations and restarts fall
+            // on chunk boundaries, so one capture per wave serves every chunk
+            const bool graph = !vec && !c->ktimer.on;
+            const int chunk = graph ? 6 : (m > 1 ? 8 : 12);
+            CgGraph cgg(st);
             LaneList ll{d_alist, 0, d_tlane, d_tsi, d_tcnt, 0};
             auto build_list_of = [&](const std::vector<int> &sel) {
                 std::vector<int> al, tl, tsi, tcnt;
@@ -1178,14 +1241,26 @@ struct Engine : EngineBase {
             restart(act);
             if (vec) build_list();
             while (true) {
-                for (int i = 0; i < chunk; ++i) {
-                    ++t;
-                    if (vec)
-                        cg_iteration4(st, g, (const float *)D, (const float *const *)p_diag, (const float *const *)p_p,
-                                      (float *const *)p_q, gm, ls, ll, t, mu_f, beta_f, &c->ktimer);
-                    else
-                        cg_iteration<T>(st, g, D, (const T *const *)p_diag, (const T *const *)p_p, p_q, gm, ls, t,
-                                        &c->ktimer);
+                if (graph) {
+                    if (!cgg.ready())
+                        cgg.capture([&](cudaStream_t cs) {
+                            for (int i = 1; i <= chunk; ++i)
+                                cg_iteration<T>(cs, g, D, (const T *const *)p_diag, (const T *const *)p_p, p_q, gm, ls,
+                                                t + i, nullptr);
+                        });
+                    cgg.launch();
+                    t += chunk;
+                } else {
+                    for (int i = 0; i < chunk; ++i) {
+                        ++t;
+                        if (vec)
+                            cg_iteration4(st, g, (const float *)D, (const float *const *)p_diag,
+                                          (const float *const *)p_p, (float *const *)p_q, gm, ls, ll, t, mu_f, beta_f,
+                                          &c->ktimer);
+                        else
+                            cg_iteration<T>(st, g, D, (const T *const *)p_diag, (const T *const *)p_p, p_q, gm, ls, t,
+                                            &c->ktimer);
+                    }
                 }
                 c->d2h(flag_h.data(), ls.flag, m);
                 c->d2h(active_h.data(), ls.active, m);
