@@ -567,38 +567,66 @@ struct Engine : EngineBase {
     // a ring of KP_MAX columns, list entries -(2 + slot)
     T *Ppr = nullptr;
     std::vector<int> ppr_next;
-    void per_rhs_push(const std::vector<int> &cand, const std::vector<Lane> &lanes, std::vector<int> &kept,
-                      std::vector<double> &ratio) {
-        const int a = (int)cand.size();
-        kept.assign(a, 0);
-        ratio.assign(a, 0.0);
-        if (!a) return;
-        const int nrhs = c->nrhs;
-        if (!Ppr) {
-            Ppr = c->alloc<T>((size_t)nrhs * KP_MAX * ld);
-            ppr_next.assign(nrhs, 0);
+    // The new direction of each listed lane, orthogonalised against its
+    // recycle space (two Gram-Schmidt passes with the Euclidean Gram W^T W of
+    // the lane's columns), normalised into the RHS's ring slot and appended to
+    // its list: the columns of U_j stay well conditioned, which the projector
+    // through H = (A~U_j)^T A~U_j needs.  kept[l] = 1 for the lanes stored.
+    void per_rhs_store(const std::vector<int> &sel, const std::vector<Lane> &lanes, const LaneGeom &gm,
+                       double tau, std::vector<int> &kept) {
+        const int m = (int)sel.size();
+        kept.assign(m, 0);
+        if (std::find(sel.begin(), sel.end(), 1) == sel.end()) return;
+        if constexpr (sizeof(T) == 8) {
+            const int nrhs = c->nrhs;
+            if (!Ppr) {
+                Ppr = c->alloc<T>((size_t)nrhs * KP_MAX * ld);
+                ppr_next.assign(nrhs, 0);
+            }
+            c->h2d(d_mask, sel.data(), m);
+            mres_gram(st, n, gm, ls, d_mask, ls.gw, true);
+            RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+            lane_inverse(st, ls.gw, ls.kdef, m, d_info);
+            check_info("per-RHS recycle space Gram W^T W");
+            double *w = (double *)qv;
+            for (int pass = 0; pass < 2; ++pass) {
+                const double *src = pass == 0 ? x64 : w;
+                mres_dots(st, n, gm, ls, d_mask, src, mr_hd, true);
+                mres_mu(st, ls, d_mask, mr_hd, mr_mu, mr_sc);
+                mres_sub(st, n, gm, ls, d_mask, src, mr_mu, w, mr_sc);
+            }
+            std::vector<int> lst;
+            for (int l = 0; l < m; ++l)
+                if (sel[l]) lst.push_back(l);
+            ensure_append((int)lst.size());
+            c->h2d(d_cand, lst.data(), lst.size());
+            norm2_lanes(st, n, (const double *const *)p_x64, d_cand, (int)lst.size(), xn2);
+            std::vector<double> sch((size_t)m * MR_NSC), xh(lst.size());
+            c->d2h(sch.data(), mr_sc, sch.size());
+            c->d2h(xh.data(), xn2, xh.size());
+            c->sync();
+            for (size_t i = 0; i < lst.size(); ++i) {
+                const int l = lst[i], j = lanes[l].j;
+                const double wn2 = sch[(size_t)l * MR_NSC + MR_XI2];
+                if (!(std::sqrt(wn2) > tau * std::sqrt(xh[i]))) continue;     // nothing new for U_j
+                const int slot = ppr_next[j];
+                ppr_next[j] = (slot + 1) % KP_MAX;
+                auto &pl = priv[j];
+                pl.erase(std::remove(pl.begin(), pl.end(), -(2 + slot)), pl.end());   // the slot's old direction
+                T *dst = Ppr + ((long long)j * KP_MAX + slot) * ld;
+                k_scaled_copy<T><<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(
+                    n, w + (long long)l * ld, mr_sc + (size_t)l * MR_NSC + MR_XI2, dst);
+                ++c->launches;
+                RCG_CHECK_LAUNCH();
+                pl.push_back(-(2 + slot));
+                while (k_u + (int)pl.size() > std::min(c->opt.k_cap, k_u + KP_MAX) && !pl.empty()) pl.erase(pl.begin());
+                kept[l] = 1;
+            }
+            c->sync();
+        } else {
+            (void)lanes; (void)gm; (void)tau;
+            throw Error{RCG_ERR_INVALID, "per-RHS recycling runs in the float64 engine"};
         }
-        ensure_append(a);
-        c->h2d(d_cand, cand.data(), a);
-        norm2_lanes(st, n, (const double *const *)p_x64, d_cand, a, xn2);
-        for (int i = 0; i < a; ++i) {
-            const int l = cand[i], j = lanes[l].j;
-            const int slot = ppr_next[j];
-            ppr_next[j] = (slot + 1) % KP_MAX;
-            auto &pl = priv[j];
-            // the slot's previous direction leaves the list first
-            pl.erase(std::remove(pl.begin(), pl.end(), -(2 + slot)), pl.end());
-            T *dst = Ppr + ((long long)j * KP_MAX + slot) * ld;
-            k_scaled_copy<T><<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(
-                n, x64 + (long long)l * ld, xn2 + i, dst);
-            ++c->launches;
-            RCG_CHECK_LAUNCH();
-            pl.push_back(-(2 + slot));
-            while (k_u + (int)pl.size() > std::min(c->opt.k_cap, k_u + KP_MAX) && !pl.empty()) pl.erase(pl.begin());
-            kept[i] = 1;
-            ratio[i] = 1.0;
-        }
-        c->sync();
     }
 
     // float64 scratch for the new basis columns and their images
@@ -914,6 +942,7 @@ struct Engine : EngineBase {
             }
         }
         std::vector<int> iters_h(m, 0);
+        std::vector<int> prh_kept;          // per-RHS recycling: lanes whose new direction joined U_j
         // learned augmentation (float32 engine): features of the check residuals,
         // the network's coarse prediction, coarse x0 when recording pairs
         Cnn *net = nullptr;
@@ -1168,7 +1197,7 @@ struct Engine : EngineBase {
             };
             if (use_mres) {
                 // recycled MINRES cycles (minres.cu) until the float64 residual meets tol
-                ensure_mres(m);
+                ensure_mres(ls.m);              // the kernels clear per-lane arrays over the capacity
                 ls.maxit = c->opt.maxit;
                 std::vector<double> sch((size_t)m * MR_NSC, 0.0);
                 for (int l = 0; l < m; ++l) sch[(size_t)l * MR_NSC + MR_THRESH] = thr[l];
@@ -1236,6 +1265,11 @@ struct Engine : EngineBase {
                     for (int l = 0; l < m; ++l)
                         if (act[l] && !done[l]) any = true;
                     if (!any) break;
+                }
+                if (per_rhs) {
+                    std::vector<int> sel(m, 0);
+                    for (int l = 0; l < m; ++l) sel[l] = act[l] && status[l] == RCG_OK;
+                    per_rhs_store(sel, lanes, gm, c->opt.tau_rank, prh_kept);
                 }
             } else {
             restart(act);
@@ -1331,8 +1365,13 @@ struct Engine : EngineBase {
         std::vector<int> kept;
         std::vector<double> ratio;
         const int r_before = r;
-        if (per_rhs) per_rhs_push(cand, lanes, kept, ratio);
-        else append(cand, tau, (seq && !seed_mode) ? lanes[0].s : -1, kept, ratio);
+        if (per_rhs) {
+            kept.assign(cand.size(), 0);
+            ratio.assign(cand.size(), 0.0);
+            for (size_t ci = 0; ci < cand.size(); ++ci) kept[ci] = prh_kept.empty() ? 0 : prh_kept[cand[ci]];
+        } else {
+            append(cand, tau, (seq && !seed_mode) ? lanes[0].s : -1, kept, ratio);
+        }
         int qi = 0;
         for (size_t ci = 0; ci < cand.size(); ++ci) {
             const int l = cand[ci];

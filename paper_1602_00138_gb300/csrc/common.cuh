@@ -24,8 +24,10 @@ struct Error {
 #define RCG_CUDA_TRY(expr)                                                          \
     do {                                                                            \
         cudaError_t e_ = (expr);                                                    \
-        if (e_ != cudaSuccess)                                                      \
+        if (e_ != cudaSuccess) {                                                    \
+            cudaGetLastError();  /* a returned error also sits in the last-error slot */ \
             throw ::rcg::Error{-2, std::string(#expr) + ": " + cudaGetErrorString(e_) + RCG_WHERE}; \
+        }                                                                           \
     } while (0)
 
 #define RCG_CHECK_LAUNCH()                                                          \
@@ -369,9 +371,14 @@ int stencil_variant_ok(const Grid &g, int v);
 
 // minres.cu (float64 lanes; LaneGeom as for CG with x = the MINRES iterate
 // y, p = v_k, q = A~ v_k / w; ext = [m][3] extra columns v_{k-1}, d_{k-1}, d_{k-2})
-void mres_gram(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask, double *H);
+// Gram / dots of the lane's recycle columns: A~W (use_w false) or W itself
+void mres_gram(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask, double *H,
+               bool use_w = false);
 void mres_dots(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
-               const double *src, double *hd);
+               const double *src, double *hd, bool use_w = false);
+// dst = src - W mu (lane blocks), ||dst||^2 added into sc[MR_XI2]
+void mres_sub(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
+              const double *src, const double *mu, double *dst, double *sc);
 void mres_mu(cudaStream_t st, const LaneState &ls, const int *mask, const double *hd, double *mu, double *sc);
 void mres_cycle(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
                 const double *mu, double *const *x64, double *sc, bool finish);

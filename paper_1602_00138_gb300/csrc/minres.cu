@@ -63,16 +63,16 @@ __device__ __forceinline__ const double *w_col(const LaneGeom &gm, int l, int c)
 // H[l] (KMAX stride, lower and upper) += (A~W)^T A~W over this CTA's nodes:
 // CTA (x, l, a) accumulates row a against columns b <= a.
 __global__ void __launch_bounds__(kThreads)
-k_mres_gram(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask, double *__restrict__ H) {
+k_mres_gram(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask, double *__restrict__ H, int use_w) {
     constexpr int NB = KU_MAX + KP_MAX;
     const int l = blockIdx.y, a = blockIdx.z;
     if (l >= ls.nl || mask[l] == 0) return;
     const int k = ls.kdef[l];
     if (a >= k) return;
-    const double *Aa = aw_col(gm, l, a);
+    const double *Aa = use_w ? w_col(gm, l, a) : aw_col(gm, l, a);
     const double *B[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) B[b] = b <= a ? aw_col(gm, l, b) : nullptr;
+    for (int b = 0; b < NB; ++b) B[b] = b <= a ? (use_w ? w_col(gm, l, b) : aw_col(gm, l, b)) : nullptr;
     double acc[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[b] = 0.0;
@@ -94,7 +94,7 @@ k_mres_gram(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask
 // hd[l][c] += (A~W_c)^T src_l for the lane's k columns (src = base + l ld).
 __global__ void __launch_bounds__(kThreads)
 k_mres_dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask, const double *__restrict__ src,
-            double *__restrict__ hd) {
+            double *__restrict__ hd, int use_w) {
     constexpr int NB = KU_MAX + KP_MAX;
     const int l = blockIdx.y;
     if (l >= ls.nl || mask[l] == 0) return;
@@ -102,7 +102,7 @@ k_mres_dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask
     const double *S = src + (long long)l * gm.ld;
     const double *C[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) C[c] = c < k ? aw_col(gm, l, c) : nullptr;
+    for (int c = 0; c < NB; ++c) C[c] = c < k ? (use_w ? w_col(gm, l, c) : aw_col(gm, l, c)) : nullptr;
     double acc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) acc[c] = 0.0;
@@ -182,6 +182,38 @@ k_mres_cycle(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mas
         block_sum_d<1>(a1, out);
         if (threadIdx.x == 0) atomicAdd(sc + (long long)l * MR_NSC + MR_XI2, out[0]);
     }
+}
+
+// dst = src - W mu for the masked lanes (lane blocks of stride ld), with
+// ||dst||^2 added into sc[XI2]: one Gram-Schmidt pass of src against W.
+__global__ void __launch_bounds__(kThreads)
+k_mres_sub(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ mask, const double *__restrict__ src,
+           const double *__restrict__ mu, double *__restrict__ dst, double *__restrict__ sc) {
+    constexpr int NB = KU_MAX + KP_MAX;
+    const int l = blockIdx.y;
+    if (l >= ls.nl || mask[l] == 0) return;
+    const int k = ls.kdef[l];
+    __shared__ double m[NB];
+    for (int c = threadIdx.x; c < NB; c += blockDim.x) m[c] = c < k ? mu[(long long)l * KMAX + c] : 0.0;
+    __syncthreads();
+    const double *W[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) W[c] = c < k ? w_col(gm, l, c) : nullptr;
+    const double *S = src + (long long)l * gm.ld;
+    double *Dd = dst + (long long)l * gm.ld;
+    double acc = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        double v = S[p];
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+            if (c < k) v -= W[c][p] * m[c];
+        Dd[p] = v;
+        acc += v * v;
+    }
+    double a1[1] = {acc};
+    __shared__ double out[1];
+    block_sum_d<1>(a1, out);
+    if (threadIdx.x == 0) atomicAdd(sc + (long long)l * MR_NSC + MR_XI2, out[0]);
 }
 
 // After the start: v /= xi; y = d_{k-1} = d_{k-2} = v_{k-1} = 0; CTA (0, l)
@@ -322,20 +354,29 @@ int gx_lanes(long long n, int lanes) {
 
 }  // namespace
 
-void mres_gram(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask, double *H) {
+void mres_gram(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask, double *H,
+               bool use_w) {
     if (ls.nl <= 0) return;
     RCG_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)ls.m * KMAX * KMAX, st));
     dim3 grid(gx_lanes(n, ls.nl * 4), ls.nl, KU_MAX + KP_MAX);
-    k_mres_gram<<<grid, kThreads, 0, st>>>(n, gm, ls, mask, H);
+    k_mres_gram<<<grid, kThreads, 0, st>>>(n, gm, ls, mask, H, use_w ? 1 : 0);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
 
 void mres_dots(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
-               const double *src, double *hd) {
+               const double *src, double *hd, bool use_w) {
     if (ls.nl <= 0) return;
     RCG_CUDA_TRY(cudaMemsetAsync(hd, 0, sizeof(double) * (size_t)ls.m * KMAX, st));
-    k_mres_dots<<<dim3(gx_lanes(n, ls.nl), ls.nl), kThreads, 0, st>>>(n, gm, ls, mask, src, hd);
+    k_mres_dots<<<dim3(gx_lanes(n, ls.nl), ls.nl), kThreads, 0, st>>>(n, gm, ls, mask, src, hd, use_w ? 1 : 0);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+void mres_sub(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const int *mask,
+              const double *src, const double *mu, double *dst, double *sc) {
+    if (ls.nl <= 0) return;
+    k_mres_sub<<<dim3(gx_lanes(n, ls.nl), ls.nl), kThreads, 0, st>>>(n, gm, ls, mask, src, mu, dst, sc);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
