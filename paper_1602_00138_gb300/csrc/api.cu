@@ -891,11 +891,12 @@ struct Engine : EngineBase {
             }
             lift(Vc, r, Yb, rmax, m, x64, ld, first ? 0.0 : 1.0);
         };
-        auto residual = [&](std::vector<double> &rr_h, const int *mask) {
+        // nact: how many lanes the mask selects (sizes the grid for them)
+        auto residual = [&](std::vector<double> &rr_h, const int *mask, int nact = -1) {
             RCG_CUDA_TRY(cudaMemsetAsync(d_rr, 0, sizeof(double) * m, st));
             residual64(st, g, c->W64, (const double *const *)p_diag64, (const double *const *)p_x64,
                        mixed ? nullptr : (double *const *)p_r, mixed ? (float *const *)p_r : nullptr, m, d_lnode, d_lw,
-                       d_rr, mask);
+                       d_rr, mask, nact < 0 ? m : nact);
             rr_h.resize(m);
             c->d2h(rr_h.data(), d_rr, m);
             c->sync();
@@ -1242,7 +1243,7 @@ struct Engine : EngineBase {
                         mres_dots(st, n, gq, ls, d_mask, (const double *)gm.q, mr_hd);
                         mres_mu(st, ls, d_mask, mr_hd, mr_mu, mr_sc);
                         mres_cycle(st, n, gm, ls, d_mask, mr_mu, (double *const *)p_x64, mr_sc, true);
-                        residual(rr_h, d_mask);
+                        residual(rr_h, d_mask, (int)F.size());
                         std::vector<int> Rl, rmask(m, 0);
                         for (int l : F) {
                             relres[l] = std::sqrt(rr_h[l]) / std::fabs(lw[l]);
@@ -1322,7 +1323,7 @@ struct Engine : EngineBase {
                     k_add_lanes<T><<<gr, 256, 0, st>>>(n, x64, ld, xc, ld, d_list);
                     ++c->launches;
                     RCG_CHECK_LAUNCH();
-                    residual(rr_h, d_mask);
+                    residual(rr_h, d_mask, (int)F.size());
                     std::vector<int> Rl;
                     for (int l : F) {
                         relres[l] = std::sqrt(rr_h[l]) / std::fabs(lw[l]);

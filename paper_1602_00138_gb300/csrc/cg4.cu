@@ -318,7 +318,10 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
     constexpr int TY = kThreads / TX, RW = TX + 2, RH = TY + 2, NA = ZL + 1;
     extern __shared__ float4 pl[];                   // [2][NA][RH][RW]
     const int nx4 = g.Nx >> 2, xtiles = nx4 / TX, ytiles = (g.Ny + TY - 1) / TY;
-    const int xt = blockIdx.x % xtiles, rest = blockIdx.x / xtiles;
+    // blockIdx.x: lane group (fastest, so that the CTAs resident together work
+    // on the same tile and share its D and diagonal planes in L2); blockIdx.y:
+    // (x tile, y tile, z chunk)
+    const int xt = blockIdx.y % xtiles, rest = blockIdx.y / xtiles;
     const int yt = rest % ytiles, zb = rest / ytiles;
     const int z0 = zb * zc, z1 = min(z0 + zc, g.Nz);
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -328,13 +331,13 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
     int non = 0;
 #pragma unroll
     for (int i = 0; i < ZL; ++i) {
-        const int li = blockIdx.y * ZL + i;
+        const int li = blockIdx.x * ZL + i;
         c[i] = li < na ? alist[li] : -1;
         on[i] = c[i] >= 0 && active[c[i]] != 0;
         non += on[i];
     }
     if (non == 0 || z0 >= g.Nz) return;             // uniform over the CTA
-    if (prof && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
+    if (prof && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 *A[NA];                             // arrays: lanes' p, then D
     float4 *Q[ZL];
@@ -346,6 +349,10 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
         DG[i] = on[i] ? (const float4 *)diag_of_col[c[i]] : nullptr;
     }
     A[ZL] = (const float4 *)D;
+    // lanes of one sample share the diagonal: load it once for the CTA
+    bool shared_dg = on[0];
+#pragma unroll
+    for (int i = 1; i < ZL; ++i) shared_dg = shared_dg && on[i] && DG[i] == DG[0];
     const bool yok = y < g.Ny;
     const long long row4 = (long long)nx4 * g.Ny;   // float4 per plane
     const long long col = (long long)y * nx4 + x4;  // this thread's column within a plane
@@ -393,7 +400,8 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
         pn[a] = ld(a, z0 + 1);
     }
 #pragma unroll
-    for (int i = 0; i < ZL; ++i) dgc[i] = (on[i] && yok) ? DG[i][(long long)z0 * row4 + col] : zero4;
+    for (int i = 0; i < ZL; ++i)
+        dgc[i] = (on[i] && yok && (i == 0 || !shared_dg)) ? DG[i][(long long)z0 * row4 + col] : zero4;
     halo(z0);
     asm volatile("cp.async.commit_group;" ::: "memory");
     float acc[ZL];
@@ -404,7 +412,9 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
 #pragma unroll
         for (int a = 0; a < NA; ++a) pnn[a] = ld(a, z + 2);
 #pragma unroll
-        for (int i = 0; i < ZL; ++i) dgn[i] = (on[i] && yok && z + 1 < z1) ? DG[i][(long long)(z + 1) * row4 + col] : zero4;
+        for (int i = 0; i < ZL; ++i)
+            dgn[i] = (on[i] && yok && z + 1 < z1 && (i == 0 || !shared_dg)) ? DG[i][(long long)(z + 1) * row4 + col]
+                                                                            : zero4;
         float4 *b = buf(z);
 #pragma unroll
         for (int a = 0; a < NA; ++a) b[a * PS + cc] = pc[a];
@@ -433,7 +443,7 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
                 const float4 xc = pc[i];
                 const float xlv = xp[cc - 1].w, xrv = xp[cc + 1].x;
                 const float4 xym = xp[cc - RW], xyp = xp[cc + RW], xzm = pm[i], xzp = pn[i];
-                const float4 dg = dgc[i];
+                const float4 dg = shared_dg ? dgc[0] : dgc[i];
                 float4 o;
                 o.x = dg.x * xc.x - (wl * xlv + w01 * xc.y) - (wym.x * xym.x + wyp.x * xyp.x) - (wzm.x * xzm.x + wzp.x * xzp.x);
                 o.y = dg.y * xc.y - (w01 * xc.x + w12 * xc.z) - (wym.y * xym.y + wyp.y * xyp.y) - (wzm.y * xzm.y + wzp.y * xzp.y);
@@ -1097,7 +1107,8 @@ void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *con
     nzc = std::max<long long>(1, std::min(nzc, maxc));
     const int zc = (int)((g.Nz + nzc - 1) / nzc);
     nzc = (g.Nz + zc - 1) / zc;
-    k_stencil4r<TX, ZL><<<dim3((unsigned)(T * nzc), (unsigned)G), kThreads, smem, st>>>(
+    if (T * nzc > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4r: more tiles than a grid's y extent"};
+    k_stencil4r<TX, ZL><<<dim3((unsigned)G, (unsigned)(T * nzc)), kThreads, smem, st>>>(
         g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc);
 }
 

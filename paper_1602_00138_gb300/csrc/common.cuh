@@ -246,7 +246,7 @@ void apply_op(cudaStream_t st, const Grid &g, const T *D, const T *const *diag_o
 void face_weights(cudaStream_t st, const Grid &g, const double *D, double *W);
 void residual64(cudaStream_t st, const Grid &g, const double *W, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,
-                const int *node, const double *bw, double *rr, const int *active);
+                const int *node, const double *bw, double *rr, const int *active, int nact = -1);
 
 // dense.cu
 template <typename TA, typename TB>

@@ -210,11 +210,14 @@ template void apply_op<float>(cudaStream_t, const Grid &, const float *, const f
 
 void residual64(cudaStream_t st, const Grid &g, const double *W, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,
-                const int *node, const double *bw, double *rr, const int *active) {
+                const int *node, const double *bw, double *rr, const int *active, int nact) {
     if (ncols <= 0) return;
     constexpr int NB = 8;
     const int groups = (ncols + NB - 1) / NB;
-    dim3 grid(grid_x_for(g.n, groups), groups);
+    // CTAs per group for the groups that hold selected columns (at most nact of
+    // them; the others exit at once): a restart of a few lanes keeps the GPU busy
+    const int busy = std::max(1, std::min(groups, nact < 0 ? ncols : nact));
+    dim3 grid(grid_x_for(g.n, busy), groups);
     k_residual64<NB><<<grid, kThreads, 0, st>>>(g, W, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
     count_launch();
     RCG_CHECK_LAUNCH();
