@@ -342,9 +342,10 @@ def roofline(W, prof, peak, peak_source):
     (unique DRAM bytes a launch must move), per node per active lane, s = 4:
       stencil    read p, write q (D and the sample diagonal once per sample,
                  L2-resident, not counted): 2
-      update     read r, q, write r, the lane's private A~W columns: 3 + k_priv
-      u0dots     read r; the k_u shared A~_s U_0 columns once per tile of 32
-                 lanes: 1 + k_u / 32
+      update     read r, q, write r, the lane's private A~W columns, and (fused
+                 shared dots) the k_u A~_s U_0 columns once per tile of 32
+                 lanes: 3 + k_priv + k_u / 32
+      u0dots     read r; A~_s U_0 once per tile of 32 lanes: 1 + k_u / 32
       direction  read r, p, write p, the private W columns, U_0 once per tile:
                  3 + k_priv + k_u / 32 per continuing lane; read x, write x
                  (the step x += alpha p) per updated lane, read p for an
@@ -354,8 +355,8 @@ def roofline(W, prof, peak, peak_source):
     """
     wl, n, s_bytes = W.wl, W.wl.n, 4
     lanes_per_rhs = wl.K if W.st["wave"] <= 0 else min(W.st["wave"], wl.K)
-    names = ["k_stencil4 (q = A p)", "k_update4 (r)", "k_u0dots (shared deflation dots)", "k_mu (lane scalars)",
-             "k_direction4 (x, p)"]
+    names = ["stencil (q = A p)", "update (r, with the shared deflation dots when k_u > 0)",
+             "k_u0dots (shared deflation dots, restarts only)", "k_mu (lane scalars)", "k_direction4 (x, p)"]
 
     def alg_bytes(k):
         P = prof[k]
@@ -366,7 +367,10 @@ def roofline(W, prof, peak, peak_source):
             return A * n * (1 + wl.k_u / 32) * s_bytes
         kpriv = P["defl_cols"] - wl.k_u * A
         if k == 1:
-            return (3 * A + kpriv) * n * s_bytes
+            # with k_u > 0 the update kernel also forms the shared deflation dots
+            # (A~_s U_0 once per tile of up to 32 lanes)
+            fused = prof[2]["launches"] == 0 and wl.k_u > 0
+            return (3 * A + kpriv + (A * wl.k_u / 32 if fused else 0)) * n * s_bytes
         A_upd = prof[1]["lane_units"]
         return ((3 + wl.k_u / 32) * A + kpriv / lanes_per_rhs + 2 * A_upd + max(A_upd - A, 0)) * n * s_bytes
 

@@ -709,6 +709,153 @@ k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_la
     }
 }
 
+// The update and the shared deflation dots in one pass over r, for the
+// lanes of tile blockIdx.y (<= 32 lanes of one sample slot) over this CTA's
+// node range: r -= alpha q; rr += r^T r; wv[c] += (A~_s U_0)_c^T r (c < k_u,
+// the U_0 images staged per stage of SN nodes in a cp.async ring and shared
+// by the tile's lanes); wv[k_u + c] += (A~ W_p)_c^T r (private columns).
+// It replaces k_update4 + k_u0dots inside an iteration: r is read once
+// instead of twice.  512 threads: thread (warp w, tl) serves lanes w + 16 q
+// (q < 2), float4 tl of every stage; the loads of both lanes go out before
+// their use (two lanes' accumulators per thread keep the registers below the
+// 128 of one 512-thread CTA per SM).  The CTA
+// with blockIdx.x == 0 records each lane's step (xa, xt) and clears the next
+// p^T q slot, as the owner CTA of k_update4 does.
+constexpr int kUU = 512;                // threads of k_update_u0
+template <int KUT, int KPM>
+__global__ void __launch_bounds__(kUU, 1)
+k_update_u0(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane, const int *__restrict__ tile_si,
+            const int *__restrict__ tile_cnt, int t, int sprev, int scur, int spq, int sw, long long chunk) {
+    constexpr int NV = 1 + KUT + KPM;
+    constexpr int NL = TILE / (kUU / 32);     // lanes per thread (2)
+    constexpr int G = KPM <= 4 ? 2 : 1;
+    __shared__ float4 Us[U0_NST][KUT][SN4];
+    __shared__ int slane[TILE], skp[TILE];
+    __shared__ float salpha[TILE];
+    const int tt = blockIdx.y, cnt = tile_cnt[tt], ku = gm.k_u;
+    if (threadIdx.x < TILE) {
+        int l = threadIdx.x < cnt ? tile_lane[tt * TILE + threadIdx.x] : -1;
+        float a = 0.f;
+        if (l >= 0 && ls.active[l] != 0) {
+            const double pq = ls.pq[spq * ls.m + l], rrp = ls.rr[sprev * ls.m + l];
+            if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rrp)) {
+                if (blockIdx.x == 0) ls.flag[l] = 2;          // breakdown: every CTA skips the lane
+                l = -1;
+            } else {
+                a = (float)(rrp / pq);
+                if (blockIdx.x == 0) {
+                    ls.xa[l] = a;
+                    ls.xt[l] = t;
+                    ls.pq[(1 - spq) * ls.m + l] = 0.0;
+                    if (ls.prof) {
+                        atomicAdd(ls.prof + 1, 1ULL);
+                        atomicAdd(ls.prof + 2, (unsigned long long)(ku + gm.kp[l]));
+                    }
+                }
+            }
+        } else {
+            l = -1;
+        }
+        slane[threadIdx.x] = l;
+        salpha[threadIdx.x] = a;
+        skp[threadIdx.x] = l >= 0 ? gm.kp[l] : 0;
+    }
+    const float *__restrict__ AU = (const float *)gm.awu + (long long)tile_si[tt] * ku * gm.ld;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
+    __syncthreads();
+    auto issue = [&](int st) {
+        if (st < nst) {
+            const long long base = r0 + (long long)st * SN;
+            for (int e = threadIdx.x; e < KUT * SN4; e += kUU) {
+                const int c = e / SN4, v4 = e % SN4;
+                const long long p = base + 4 * v4;
+                const bool ok = c < ku && p < r1;
+                const float *src = ok ? AU + (long long)c * gm.ld + p : AU;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(&Us[st % U0_NST][c][v4])),
+                             "l"(src), "r"(ok ? 16 : 0)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
+    float acc[NL][NV];
+#pragma unroll
+    for (int q = 0; q < NL; ++q)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[q][v] = 0.f;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    issue(0);
+    issue(1);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + 2);
+        asm volatile("cp.async.wait_group 2;" ::: "memory");     // stage st: this thread's copies
+        __syncthreads();                                          // ... and everyone's
+        const long long p = r0 + (long long)st * SN + 4 * tl;
+        if (p < r1) {
+#pragma unroll
+            for (int q0 = 0; q0 < NL; q0 += G) {
+                float4 qv[G], rv[G], av[G][KPM];
+#pragma unroll
+                for (int gq = 0; gq < G; ++gq) {
+                    const int l = slane[warp + (kUU / 32) * (q0 + gq)];
+                    const long long o = (long long)(l < 0 ? 0 : l) * gm.ld + p;
+                    qv[gq] = l >= 0 ? *(const float4 *)((const float *)gm.q + o) : z4;
+                    rv[gq] = l >= 0 ? *(const float4 *)((const float *)gm.r + o) : z4;
+                    const int kp = skp[warp + (kUU / 32) * (q0 + gq)];
+                    const float *AP = (const float *)gm.awp + (long long)(l < 0 ? 0 : l) * gm.kp_max * gm.ld + p;
+#pragma unroll
+                    for (int c = 0; c < KPM; ++c)
+                        av[gq][c] = (l >= 0 && c < kp) ? *(const float4 *)(AP + (long long)c * gm.ld) : z4;
+                }
+#pragma unroll
+                for (int gq = 0; gq < G; ++gq) {
+                    const int jj = warp + (kUU / 32) * (q0 + gq);
+                    const int l = slane[jj];
+                    if (l < 0) continue;
+                    const float a = salpha[jj];
+                    const float4 rn = make_float4(rv[gq].x - a * qv[gq].x, rv[gq].y - a * qv[gq].y,
+                                                  rv[gq].z - a * qv[gq].z, rv[gq].w - a * qv[gq].w);
+                    *(float4 *)((float *)gm.r + (long long)l * gm.ld + p) = rn;
+                    float *ac = acc[q0 + gq];
+                    ac[0] += dot4(rn, rn);
+#pragma unroll
+                    for (int c = 0; c < KUT; ++c) ac[1 + c] += dot4(Us[st % U0_NST][c][tl], rn);
+#pragma unroll
+                    for (int c = 0; c < KPM; ++c) ac[1 + KUT + c] += dot4(av[gq][c], rn);
+                }
+            }
+        }
+        __syncthreads();                                          // the ring slot of stage st is refilled next
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // warp sums per lane, one atomic per lane and column
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const int jj = warp + (kUU / 32) * q;
+        const int l = slane[jj];
+        if (l < 0) continue;                                      // uniform over the warp
+        const int kp = skp[jj];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            float x = acc[q][v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (tl == 0) {
+                if (v == 0) atomicAdd(ls.rr + scur * ls.m + l, (double)x);
+                else if (v <= KUT) {
+                    if (v - 1 < ku) atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + (v - 1), (double)x);
+                } else if (v - 1 - KUT < kp) {
+                    atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + ku + (v - 1 - KUT), (double)x);
+                }
+            }
+        }
+    }
+}
+
 template <int KUT>
 void u0dots_attr() {
     static bool attr[64] = {};
@@ -1293,13 +1440,6 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
     cudaEvent_t e = tm ? kt->start(st) : nullptr;
     s4_launch(sv, st, g, D, diag_of_col, p_ptr, q_ptr, ll, ls.active, ls.pq + (long long)spq * ls.m, ls.prof);
     if (tm) { kt->stop(0, e, st); e = kt->start(st); }
-    if (gm.kp_max <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
-    else if (gm.kp_max <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
-    else if (gm.kp_max <= 4) launch_update4<4>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
-    else launch_update4<KP_MAX>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
-    count_launch();
-    RCG_CHECK_LAUNCH();
-    if (tm) { kt->stop(1, e, st); e = kt->start(st); }
     // node range per CTA for the tile kernels: a multiple of SN, `slots` CTAs in total
     auto tile_chunk = [&](long long &z, long long slots = 6LL * 152) {
         z = std::max<long long>(1, slots / ll.ntiles);
@@ -1312,17 +1452,27 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         return chunk;
     };
     const int kut = gm.k_u <= 4 ? 4 : gm.k_u <= 8 ? 8 : gm.k_u <= 12 ? 12 : 16;
-    if (gm.k_u > 0) {
+    const bool fused = gm.k_u > 0;
+    if (fused) {
+        // the update with the shared deflation dots (one read of r)
         long long z;
-        const long long chunk = tile_chunk(z);
+        const long long chunk = tile_chunk(z, 4LL * 152);
         dim3 grid((unsigned)z, ll.ntiles);
-#define RCG_U0(K) u0dots_attr<K>(); \
-        k_u0dots<K><<<grid, kThreads, u0_smem<K>(), st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, sw, chunk, 0)
-        switch (kut) { case 4: RCG_U0(4); break; case 8: RCG_U0(8); break; case 12: RCG_U0(12); break; default: RCG_U0(16); }
-#undef RCG_U0
-        count_launch();
-        RCG_CHECK_LAUNCH();
-    }
+#define RCG_UU(K, P) k_update_u0<K, P><<<grid, kUU, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, \
+                                                                  t, sprev, scur, spq, sw, chunk)
+#define RCG_UUK(K) if (gm.kp_max <= 1) RCG_UU(K, 1); else if (gm.kp_max <= 2) RCG_UU(K, 2); \
+                   else if (gm.kp_max <= 4) RCG_UU(K, 4); else RCG_UU(K, KP_MAX)
+        switch (kut) { case 4: RCG_UUK(4); break; case 8: RCG_UUK(8); break; case 12: RCG_UUK(12); break;
+                       default: RCG_UUK(16); }
+#undef RCG_UUK
+#undef RCG_UU
+    } else if (gm.kp_max <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else if (gm.kp_max <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else if (gm.kp_max <= 4) launch_update4<4>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else launch_update4<KP_MAX>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+    if (tm) { kt->stop(1, e, st); e = kt->start(st); }
     if (tm) { kt->stop(2, e, st); e = kt->start(st); }
     k_mu<<<ll.na, 32, 0, st>>>(ls, ll.alist, sprev, scur, snext, sw, mu, beta, 0);
     count_launch();
