@@ -90,7 +90,7 @@ def test_reduced_model_matches_oracle_and_interpolates(run):
     Psi, J = ctx.rom_eval(inp["mu"][i], dmu)
     Psi_o, J_o = rom.rom_eval(V, At, Bt, Ct, wl.h, dmu)
     assert np.linalg.norm(Psi - Psi_o) <= 1e-6 * np.linalg.norm(Psi_o)
-    assert np.linalg.norm(J - J_o) <= 1e-5 * np.linalg.norm(J_o)
+    assert np.linalg.norm(J - J_o) <= 1e-6 * np.linalg.norm(J_o)     # the same basis: the mixed acceptance tolerance
     # interpolation at a sampled point: C~^T x of the delivered source solutions.
     # Those carry their own error (relres <= 1e-8, amplified by A~^-1 up to
     # ~kappa), so the bound is 1e-5 relative; a basis without the sampled

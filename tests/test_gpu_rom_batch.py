@@ -5,8 +5,9 @@ call, the evaluation the optimisation of Sec. 4.2.2 repeats through a fixed V.
 References: the oracle's reduced model built from the context's own basis
 (a float64 Galerkin projection with dense Cholesky), and rcg_rom_eval at
 each point.  Mixed precision forms the weighted Grams on the tensor cores
-(3xTF32 products, float64 slice sums), so the bounds are those of the
-single-point tests: 1e-6 relative for Psi_r, 1e-5 for J.  Held-out points
+(3xTF32 products, float64 slice sums); on the context's own basis the bounds
+are the acceptance tolerances: 1e-6 relative for Psi_r and J (mixed),
+1e-10 / 1e-9 (float64).  Held-out points
 (not used to build V) and the sampled points are both covered; a point
 count that is not a multiple of anything and nq = 0 are edge cases.
 """
@@ -59,7 +60,7 @@ def test_batch_matches_single_points_and_oracle(rcg, precision):
         Psi_b, J_b = ctx.rom_eval_batch(mus, dmus)
         assert Psi_b.shape == (len(mus), wl.ndet, wl.nsrc)
         assert J_b.shape == (len(mus), dmus.shape[1], wl.ndet, wl.nsrc)
-        psi_tol, j_tol = (1e-6, 1e-5) if prec else (1e-10, 1e-9)
+        psi_tol, j_tol = (1e-6, 1e-6) if prec else (1e-10, 1e-9)
         for q in range(len(mus)):
             Pq, Jq = ctx.rom_eval(mus[q], dmus[q])
             A = op.schur_for_mu(inp, mus[q])
@@ -96,6 +97,6 @@ def test_batch_edge_cases(rcg):
         # a single point equals rcg_rom_eval
         P1, J1 = ctx.rom_eval_batch(mus[:1], dmus[:1])
         Pq, Jq = ctx.rom_eval(mus[0], dmus[0])
-        assert rel(P1[0], Pq) <= 1e-6 and rel(J1[0], Jq) <= 1e-5
+        assert rel(P1[0], Pq) <= 1e-6 and rel(J1[0], Jq) <= 1e-6
     finally:
         ctx.close()
