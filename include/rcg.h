@@ -116,9 +116,11 @@ typedef struct {
     int    keep_solutions;/* keep every delivered x (for rcg_solution_get)  */
     int    seed_degree;   /* Chebyshev filter degree of the eigen seed      */
     long long spin_budget;/* polls of a tensor-core kernel's main-loop waits
-                             for its MMAs (0 = 2^22); on running out the
-                             call returns RCG_ERR_TIMEOUT after the kernel
-                             has waited (full bound) for its last MMAs     */
+                             for its MMAs (0 = 2^22; negative = none, so
+                             every such wait runs out: exercises the error
+                             path); on running out the call returns
+                             RCG_ERR_TIMEOUT after the kernel has waited
+                             (full bound) for its last MMAs               */
     int    learned;       /* RCG_MIXED: add the learned network's column to
                              the private U_j of every CG solve (needs
                              weights: rcg_learn_set_weights or _train)      */

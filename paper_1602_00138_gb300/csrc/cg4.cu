@@ -314,14 +314,16 @@ __global__ void __launch_bounds__(kThreads, ZL <= 2 ? 2 : 1)
 k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict__ diag_of_col,
             const float *const *__restrict__ src, float *const *__restrict__ dst, const int *__restrict__ alist,
             int na, const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ prof,
-            int zc) {
+            int zc, int lanes_fast) {
     constexpr int TY = kThreads / TX, RW = TX + 2, RH = TY + 2, NA = ZL + 1;
     extern __shared__ float4 pl[];                   // [2][NA][RH][RW]
     const int nx4 = g.Nx >> 2, xtiles = nx4 / TX, ytiles = (g.Ny + TY - 1) / TY;
-    // blockIdx.x: lane group (fastest, so that the CTAs resident together work
-    // on the same tile and share its D and diagonal planes in L2); blockIdx.y:
-    // (x tile, y tile, z chunk)
-    const int xt = blockIdx.y % xtiles, rest = blockIdx.y / xtiles;
+    // lanes_fast: blockIdx.x is the lane group and blockIdx.y the (x tile, y
+    // tile, z chunk), so that the CTAs resident together share a tile's D and
+    // diagonal planes in L2 (measured faster for few lane groups); otherwise
+    // the roles swap (faster for many)
+    const int lg = lanes_fast ? blockIdx.x : blockIdx.y, tz = lanes_fast ? blockIdx.y : blockIdx.x;
+    const int xt = tz % xtiles, rest = tz / xtiles;
     const int yt = rest % ytiles, zb = rest / ytiles;
     const int z0 = zb * zc, z1 = min(z0 + zc, g.Nz);
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -331,13 +333,13 @@ k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict_
     int non = 0;
 #pragma unroll
     for (int i = 0; i < ZL; ++i) {
-        const int li = blockIdx.x * ZL + i;
+        const int li = lg * ZL + i;
         c[i] = li < na ? alist[li] : -1;
         on[i] = c[i] >= 0 && active[c[i]] != 0;
         non += on[i];
     }
     if (non == 0 || z0 >= g.Nz) return;             // uniform over the CTA
-    if (prof && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
+    if (prof && tz == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 *A[NA];                             // arrays: lanes' p, then D
     float4 *Q[ZL];
@@ -1254,9 +1256,11 @@ void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *con
     nzc = std::max<long long>(1, std::min(nzc, maxc));
     const int zc = (int)((g.Nz + nzc - 1) / nzc);
     nzc = (g.Nz + zc - 1) / zc;
-    if (T * nzc > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4r: more tiles than a grid's y extent"};
-    k_stencil4r<TX, ZL><<<dim3((unsigned)G, (unsigned)(T * nzc)), kThreads, smem, st>>>(
-        g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc);
+    const bool lanes_fast = G <= 16;
+    if ((lanes_fast ? T * nzc : G) > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4r: grid y extent"};
+    const dim3 grid = lanes_fast ? dim3((unsigned)G, (unsigned)(T * nzc)) : dim3((unsigned)(T * nzc), (unsigned)G);
+    k_stencil4r<TX, ZL><<<grid, kThreads, smem, st>>>(g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc,
+                                                      lanes_fast ? 1 : 0);
 }
 
 void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,

@@ -53,9 +53,10 @@ constexpr int LEVEL1 = 16;              // K-steps summed before the second leve
 constexpr long long SPIN_LIMIT = 1LL << 22;
 
 // Polls of a main-loop mbarrier wait: the calling context's
-// rcg_options.spin_budget when positive, else SPIN_LIMIT.  The final wait
-// for the last committed step always has the full SPIN_LIMIT.
-long long spin_budget() { return g_spin_budget > 0 ? g_spin_budget : SPIN_LIMIT; }
+// rcg_options.spin_budget when positive, SPIN_LIMIT when 0, none when
+// negative (every main-loop wait runs out at once).  The final wait for the
+// last committed step always has the full SPIN_LIMIT.
+long long spin_budget() { return g_spin_budget > 0 ? g_spin_budget : g_spin_budget < 0 ? 0 : SPIN_LIMIT; }
 constexpr long long LIST_MIN_CHUNK = 8;  // fewest K-steps per slice when a block list sets the length
 constexpr int NUM_SMS = 152;
 

@@ -122,12 +122,13 @@ def test_rank_cap_is_reported(rcg):
 
 def test_tiny_spin_budget_times_out_and_the_gpu_stays_usable(rcg):
     """rcg_options.spin_budget bounds the tensor-core kernels' main-loop
-    waits for their MMAs.  With a budget of one poll the waits run out before
-    the tensor core finishes a step; the kernel then stops issuing, waits with
-    its full bound for the last MMAs it committed, frees its tensor memory and
-    reports RCG_ERR_TIMEOUT, which the call returns.  A context created
-    afterwards with the default budget runs the same seed normally."""
-    inp, ctx = _ctx(rcg, "t3d_32", precision=rcg.RCG_MIXED, order=rcg.RCG_WAVE, tau_rank=1e-6, spin_budget=1)
+    waits for their MMAs.  A negative budget allows no poll, so the first such
+    wait runs out (a step's MMAs usually complete within one poll, which would
+    not exercise the path); the kernel then stops issuing, waits with its full
+    bound for the last MMAs it committed, frees its tensor memory and reports
+    RCG_ERR_TIMEOUT, which the call returns.  A context created afterwards with
+    the default budget runs the same seed normally."""
+    inp, ctx = _ctx(rcg, "t3d_32", precision=rcg.RCG_MIXED, order=rcg.RCG_WAVE, tau_rank=1e-6, spin_budget=-1)
     try:
         with pytest.raises(rcg.RcgError) as e:
             ctx.seed(0, None)
