@@ -139,6 +139,8 @@ def test_tiny_spin_budget_times_out_and_the_gpu_stays_usable(rcg):
     try:
         ctx.seed(0, None)
         stats, rc = ctx.solve_all(1, 1)
-        assert rc == 0 and max(s["relres"] for s in stats) <= 1e-8 * 1.0001
+        assert rc == 0
+        for st in stats:                                   # tolerances alternate 1e-8 / 1e-6 over the RHS
+            assert st["relres"] <= inp["tol"][st["rhs"]] * 1.0001, st
     finally:
         ctx.close()
