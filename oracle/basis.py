@@ -143,14 +143,18 @@ def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", ta
     """Outer loop of Algorithm 2 over `samples` (A_of(i) gives A~_i); check
     and inner as in solve_lane (check="mr", inner="minres" is the paper's
     own form of Algorithm 2); wave order in waves of wave_samples samples x
-    wave_rhs right-hand sides (0: all)."""
-    nrhs = Bfull.shape[1]
+    wave_rhs right-hand sides (0: all).  Bfull is the n x nrhs matrix
+    [B~, C~], or a function of the sample giving it (B~ and C~ follow the
+    sample when D tracks mu)."""
+    samples = list(samples)
+    B_of = Bfull if callable(Bfull) else (lambda i: Bfull)
+    nrhs = B_of(samples[0]).shape[1]
     out = []
     if order == "sequential":
         for i in samples:
             A = A_of(i)
             for j in range(nrhs):
-                res = solve_lane(A, Bfull[:, j], tols[j], st.V, st.U(j), check, inner)
+                res = solve_lane(A, B_of(i)[:, j], tols[j], st.V, st.U(j), check, inner)
                 rec = dict(sample=i, rhs=j, iters=res["iters"], relres0=res["relres0"],
                            relres=res["relres"], appended=False, ratio=0.0)
                 if res["solved"]:
@@ -167,7 +171,6 @@ def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", ta
         # waves of `wave_samples` samples x `wave_rhs` consecutive RHS (0 = all):
         # V and every U_j are frozen within a wave; its candidates are appended
         # afterwards in ascending (sample, RHS) order
-        samples = list(samples)
         ws = wave_samples if wave_samples > 0 else len(samples)
         wr = min(wave_rhs, nrhs) if wave_rhs > 0 else nrhs
         out = []
@@ -181,7 +184,7 @@ def solve_all(st: BasisState, A_of, samples, Bfull, tols, order="sequential", ta
                 for i in group:
                     A = A_of(i)
                     for j in rhs:
-                        res = solve_lane(A, Bfull[:, j], tols[j], V_wave, U_wave[j], check, inner)
+                        res = solve_lane(A, B_of(i)[:, j], tols[j], V_wave, U_wave[j], check, inner)
                         rec = dict(sample=i, rhs=j, iters=res["iters"], relres0=res["relres0"],
                                    relres=res["relres"], appended=False, ratio=0.0)
                         if keep_x:

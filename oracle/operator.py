@@ -22,6 +22,24 @@ Robin rows on the boundary).  Readings of points the paper leaves open:
 Parity: pinned by the manufactured-solution convergence test, the
 full-versus-Schur transfer-function identity, structural checks of G, D1,
 D2 (Sec. 3 bullet list) and the constant-coefficient closed-form spectrum.
+
+Diffusion tracking the absorption (an extension; Sec. 2.1 takes D as known
+and fixed).  With the diffusion approximation's coefficient
+    D(x; p) = 1 / (3 (mu(x; p) + mu_s')),
+D changes with p wherever mu does, so A~, B~ and C~ all depend on p:
+    * A~: every face weight and the Robin term D_p / (1 + alpha_p) of the
+      Schur complement (eq. H and the block elimination of Sec. 3);
+    * B~ = b D_p / (1 + alpha_p) e_p and C~ = c alpha_p / (1 + alpha_p) e_p
+      at the face-adjacent node p of each source and detector (Sec. 3.1).
+schur_derivative gives dA~ along a direction (dD, dmu) analytically:
+    interior face (p, q):  w = (D_p + D_q)/2,      dw = (dD_p + dD_q)/2;
+    ghost face of p:       w = D_p,                dw = dD_p;
+    Robin face of p:       w = D_p/(1 + alpha_p),  dw = dD_p/(1 + alpha_p)^2;
+    (dA~)_pq = -dw on interior faces, (dA~)_pp = sum of the dw of p's faces
+    + h^2 dmu_p; rhs_derivative gives dB~ and dC~ (d/dD of D/(1+alpha) and of
+    alpha/(1+alpha) = (2A/h)/(1+alpha)^2).  With dD = -3 D^2 dmu the chain
+    rule through D(mu).  Pinned by central differences of the assembled
+    matrices and vectors (tests/test_oracle_tracking.py).
 """
 from __future__ import annotations
 
@@ -150,3 +168,77 @@ def assemble(inp, s):
 def schur_for_mu(inp, mu):
     fs = full_system(inp["dims"], inp["D"], mu, inp["h"], inp["robin_A"])
     return schur(fs)
+
+
+# ------------------------------------------------- diffusion tracking mu
+def diffusion_of_mu(mu, mu_s_prime):
+    """D = 1 / (3 (mu + mu_s')): the diffusion coefficient of the diffusion
+    approximation for absorption mu and reduced scattering mu_s'."""
+    return 1.0 / (3.0 * (np.asarray(mu, dtype=np.float64) + mu_s_prime))
+
+
+def assemble_tracking(inp, mu, mu_s_prime):
+    """A~, B~, C~ at absorption mu with D = D(mu) (every coefficient of the
+    full system of Sec. 2.1 follows the sample)."""
+    D = diffusion_of_mu(mu, mu_s_prime)
+    fs = full_system(inp["dims"], D, mu, inp["h"], inp["robin_A"])
+    At = schur(fs)
+    Bt, Ct, _, _ = effective_sources(fs, inp["src_ij"], inp["det_ij"])
+    return At, Bt, Ct
+
+
+def schur_derivative(dims, D, dD, dmu, h, robin_A):
+    """dA~ (sparse, n x n) when D changes by dD and mu by dmu (module
+    docstring): the face weights of A~ at D differentiated face by face."""
+    Nx, Ny, Nz = dims
+    n = Nx * Ny * Nz
+    D = np.asarray(D, dtype=np.float64)
+    dD = np.asarray(dD, dtype=np.float64)
+    i, j, k = _interior_index(dims)
+    p = i + Nx * (j + Ny * k)
+    rows, cols, vals = [], [], []
+    ddiag = h * h * np.asarray(dmu, dtype=np.float64)[p]
+    axes = [(i, Nx, 1)]
+    if Ny > 1:
+        axes.append((j, Ny, Nx))
+    for coord, extent, stride in axes:                 # Dirichlet axes: interior face or ghost face
+        for step in (-1, 1):
+            has = (coord + step >= 0) & (coord + step < extent)
+            q = np.where(has, p + step * stride, p)
+            dw = np.where(has, 0.5 * (dD[p] + dD[q]), dD[p])
+            ddiag = ddiag + dw
+            rows.append(p[has]); cols.append(q[has]); vals.append(-dw[has])
+    for step in (-1, 1):                               # Robin axis: interior face or eliminated Robin face
+        has = (k + step >= 0) & (k + step < Nz)
+        q = np.where(has, p + step * Nx * Ny, p)
+        alpha = 2.0 * robin_A * D[p] / h
+        dw = np.where(has, 0.5 * (dD[p] + dD[q]), dD[p] / (1.0 + alpha) ** 2)
+        ddiag = ddiag + dw
+        rows.append(p[has]); cols.append(q[has]); vals.append(-dw[has])
+    rows.append(p); cols.append(p); vals.append(ddiag)
+    M = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    M.sum_duplicates()
+    return M
+
+
+def rhs_derivative(inp, D, dD):
+    """(dB~, dC~) when D changes by dD: the Robin elimination's source weight
+    D_p/(1 + alpha_p) and detector weight alpha_p/(1 + alpha_p) at each
+    face-adjacent node, differentiated in D_p (unit source / detector
+    strengths, as in effective_sources)."""
+    Nx, Ny, Nz = inp["dims"]
+    n = Nx * Ny * Nz
+    h, A = inp["h"], inp["robin_A"]
+    D = np.asarray(D, dtype=np.float64)
+    dD = np.asarray(dD, dtype=np.float64)
+
+    def cols(face_ij, top):
+        out = np.zeros((n, len(face_ij)))
+        for c, (ii, jj) in enumerate(face_ij):
+            node = (ii - 1) + Nx * ((jj - 1) + Ny * ((Nz - 1) if top else 0))
+            alpha = 2.0 * A * D[node] / h
+            dwt = (2.0 * A / h) / (1.0 + alpha) ** 2 if top else 1.0 / (1.0 + alpha) ** 2
+            out[node, c] = dwt * dD[node]
+        return out
+
+    return cols(inp["src_ij"], False), cols(inp["det_ij"], True)
