@@ -84,6 +84,21 @@ extern "C" {
  * new directions into U_j only) */
 #define RCG_INNER_OUTER 0
 #define RCG_PER_RHS     1
+/* diffusion coefficient: fixed (Sec. 2.1: D known, set by rcg_set_diffusion)
+ * or tracking the absorption at every sample and parameter point,
+ * D = 1 / (3 (mu + mu_s')) (the diffusion approximation's coefficient; an
+ * extension).  Tracking makes A~ change off the diagonal (every face weight
+ * and the Robin term D/(1 + alpha) of the Schur complement, Sec. 3), moves
+ * the effective source / detector weights of Sec. 3.1 with the sample, and
+ * gives the Jacobian of eq. newjac the stencil term and the weights'
+ * derivatives.  With tracking, the D of rcg_set_diffusion is only the
+ * reference for the solver's right-hand sides: the systems are solved with
+ * those weights and the solutions scaled to the sample's own (relative
+ * tolerances and Algorithm 2's decisions do not change under that scaling);
+ * rcg_solution_get, rcg_full_eval and the reduced model use the sample's
+ * weights.  Runs the scalar CG path (the float4 stencils share one D). */
+#define RCG_D_FIXED       0
+#define RCG_D_TRACKS_MU   1
 #define RCG_SEQUENTIAL  0   /* the paper's order: V grows between RHS          */
 #define RCG_WAVE        1   /* all RHS of `wave_samples` samples at once with V
                                frozen; ordered append afterwards               */
@@ -131,6 +146,9 @@ typedef struct {
     int    check;         /* RCG_GALERKIN (default) | RCG_MR                */
     int    inner;         /* RCG_CG (default) | RCG_MINRES                  */
     int    recycle;       /* RCG_INNER_OUTER (default) | RCG_PER_RHS        */
+    int    d_model;       /* RCG_D_FIXED (default) | RCG_D_TRACKS_MU        */
+    double mu_s_prime;    /* reduced scattering mu_s' of RCG_D_TRACKS_MU
+                             (> 0; default 1)                                */
 } rcg_options;
 
 typedef struct {
@@ -148,7 +166,8 @@ typedef struct {
 /* Fill *o with defaults: FP64, sequential, tau_rank 1e-12, k_u 10,
  * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-4,
  * check_refine 0, keep_solutions 0, seed_degree 0 (automatic), learned 0,
- * wave_rhs 0, check RCG_GALERKIN, inner RCG_CG, recycle RCG_INNER_OUTER. */
+ * wave_rhs 0, check RCG_GALERKIN, inner RCG_CG, recycle RCG_INNER_OUTER,
+ * d_model RCG_D_FIXED, mu_s_prime 1. */
 void rcg_options_default(rcg_options *o);
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a

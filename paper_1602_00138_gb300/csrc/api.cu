@@ -137,7 +137,7 @@ struct EngineBase {
 // ---------------------------------------------------------- state file I/O
 // Binary layout of rcg_save: magic, a header of int64 fields, then arrays
 // (each: int64 count, raw elements).  Little-endian host order.
-constexpr char kMagic[8] = {'R', 'C', 'G', 'S', 'T', 'A', 'T', '1'};
+constexpr char kMagic[8] = {'R', 'C', 'G', 'S', 'T', 'A', 'T', '2'};
 inline void wr(std::FILE *f, const void *p, size_t bytes) {
     if (bytes && std::fwrite(p, 1, bytes, f) != bytes) throw Error{RCG_ERR_INVALID, "rcg_save: write failed"};
 }
@@ -173,14 +173,20 @@ struct rcg_ctx {
     bool have_D = false, have_rhs = false;
     int nsrc = 0, ndet = 0, nrhs = 0;
     std::vector<int> rhs_node;
-    std::vector<double> rhs_w, tol;
+    std::vector<double> rhs_w, rhs_wt, tol;   // effective weights at the reference D; source / detector strengths
     std::vector<char> sample_set;
     // device coefficient fields
     double *D64 = nullptr, *dstar = nullptr, *mu64 = nullptr, *diag64 = nullptr;
+    // diffusion tracking the absorption: per-sample D, face weights (3 columns)
+    double *Ds64 = nullptr, *Ws64 = nullptr;
+    float *Ds32 = nullptr;
+    bool track() const { return opt.d_model == RCG_D_TRACKS_MU; }
+    double *Ds64_of(int s) { return Ds64 + (long long)s * ld; }
+    double *Ws64_of(int s) { return Ws64 + 3LL * s * ld; }
     double *W64 = nullptr;             // face weights (D_p + D_q)/2 towards +x, +y, +z (3 columns)
     float *D32 = nullptr, *diag32 = nullptr;
     int *d_rhs_node = nullptr;
-    double *d_rhs_w = nullptr;
+    double *d_rhs_w = nullptr, *d_rhs_wt = nullptr, *d_ones = nullptr;
     std::unique_ptr<EngineBase> eng;
     std::map<std::string, double> phase;
     std::vector<std::vector<double>> solutions;   // per sample, host copies (keep_solutions)
@@ -714,11 +720,70 @@ struct Engine : EngineBase {
         gemm_tn_acc<T, T, double>(st, n, A, ld, ka, A, ld, ka, C, ldc, true, w);
     }
 
-    // G = C_* + V^T diag(h^2 (mu_s - mu_*)) V (r x r) and its Cholesky factor L.
+    // ---- diffusion tracking the absorption: operator differences and derivatives
+    // (dg diagonal, dw face weights towards +x, +y, +z) and products over their rows
+    double *tk_dg = nullptr, *tk_dw = nullptr, *tk_touch = nullptr;
+    int *tk_bl = nullptr, *tk_bc = nullptr;
+    T *tk_Xc = nullptr;
+    double *tk_Yc = nullptr;
+    long long tk_cap = 0;
+    // the point of a reduced-model evaluation: D, face weights, diagonal, weights
+    double *tp_D = nullptr, *tp_W = nullptr, *tp_diag = nullptr, *tp_w = nullptr, *tp_G = nullptr, *tp_P = nullptr;
+    double *tp_dwt = nullptr;
+    int tp_dwt_cap = 0;
+    void ensure_track() {
+        if (tk_dg) return;
+        tk_dg = c->alloc<double>(ld);
+        tk_dw = c->alloc<double>((size_t)3 * ld);
+        tk_touch = c->alloc<double>(ld);
+        tk_bl = c->alloc<int>((size_t)(n + 31) / 32);
+        tk_bc = c->alloc<int>(1);
+    }
+    // G (ka x ka, ld ldg) += X^T dA X with dA the operator difference or
+    // derivative in (tk_dg, tk_dw): Y = dA X in float64 on the 32-row blocks
+    // where dA has a nonzero row, next to those rows of X, then one product
+    // per chunk of blocks (double-float for a float32 X, float64 otherwise).
+    void delta_gram(const T *X, int ka, double *G, int ldg) {
+        if (ka <= 0) return;
+        track_touch(st, g, tk_dg, tk_dw, tk_touch);
+        tc_block_list(st, n, tk_touch, tk_bl, tk_bc);
+        int nb = 0;
+        c->d2h(&nb, tk_bc, 1);
+        c->sync();
+        if (nb <= 0) return;
+        const long long max_blocks = std::max<long long>(1, (1LL << 27) / ((long long)ka * 32));   // ~1 GiB of Y
+        const int bchunk = (int)std::min<long long>(nb, max_blocks);
+        const long long need = (long long)bchunk * 32 * ka;
+        if (need > tk_cap) {
+            c->release(tk_Xc);
+            c->release(tk_Yc);
+            tk_cap = need;
+            tk_Xc = c->alloc<T>((size_t)need);
+            tk_Yc = c->alloc<double>((size_t)need);
+        }
+        for (int b0 = 0; b0 < nb; b0 += bchunk) {
+            const int nbc = std::min(bchunk, nb - b0);
+            const long long rows = (long long)nbc * 32;
+            delta_rows<T>(st, g, tk_bl, b0, nbc, tk_dg, tk_dw, X, ld, ka, tk_Xc, tk_Yc, rows);
+            if constexpr (sizeof(T) == 4)
+                gemm_tn_df(st, rows, (const float *)tk_Xc, rows, ka, tk_Yc, rows, ka, G, ldg, true);
+            else
+                gemm_tn<double, double>(st, rows, (const double *)tk_Xc, rows, ka, tk_Yc, rows, ka, G, ldg, true);
+        }
+    }
+
+    // G = C_* + V^T (A~_s - A~_*) V (r x r) and its Cholesky factor L: with a fixed
+    // D the difference is diag(h^2 (mu_s - mu_*)); with D tracking mu it also
+    // changes every face weight on and around the support of mu_s - mu_*.
     void galerkin(int s, double *G, double *L, bool reset_info = true) {
         RCG_CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * rmax, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        if (s != s_star) {
+        if (s != s_star && c->track()) {
+            ensure_track();
+            scaled_diff(st, n, c->diag64_of(s), c->diag64_of(s_star), 1.0, tk_dg);
+            scaled_diff(st, 3 * ld, c->Ws64_of(s), c->Ws64_of(s_star), 1.0, tk_dw);
+            delta_gram(V, r, G, rmax);
+        } else if (s != s_star) {
             const double *w = delta_weights(s);
             gram_w_acc(V, r, G, rmax, w, mixed ? dwl[s] : nullptr, mixed ? dwc + s : nullptr);
         }
@@ -1151,7 +1216,7 @@ struct Engine : EngineBase {
 
             std::vector<int> flag_h(m), active_h(m);
             // lanes selected by `sel` and tiles of <= 32 of them per sample slot
-            const bool vec = mixed && cg4_supported(g);
+            const bool vec = mixed && cg4_supported(g) && !c->track();     // the float4 stencils take one fixed D
             // the scalar path replays a CUDA graph of a 6-iteration chunk: its ring
             // slots (t mod 3, t mod 2) repeat every 6 iterations and restarts fall
             // on chunk boundaries, so one capture per wave serves every chunk
@@ -1399,13 +1464,32 @@ struct Engine : EngineBase {
             out[l].status = status[l];
         }
         if (c->opt.keep_solutions) {
-            std::vector<double> hx(n);
+            // with D tracking mu the lanes solved with the reference weights: scale each
+            // solution by the ratio of its sample's weight to the reference one
+            double *ws = nullptr, *xs = nullptr;
+            if (c->track()) {
+                ws = c->alloc<double>((size_t)c->nrhs);
+                xs = c->alloc<double>(ld);
+            }
+            int ws_sample = -1;
             for (int l = 0; l < m; ++l) {
                 auto &sol = c->solutions[lanes[l].s];
                 if (sol.empty()) sol.assign((size_t)n * c->nrhs, 0.0);
-                c->d2h(sol.data() + (size_t)lanes[l].j * n, x64 + (long long)l * ld, n);
+                const double *src = x64 + (long long)l * ld;
+                if (c->track()) {
+                    if (ws_sample != lanes[l].s) {
+                        rhs_weights(st, c->Ds64_of(lanes[l].s), c->d_rhs_node, c->d_rhs_wt, c->nsrc, c->nrhs,
+                                    c->grid.robin_A, c->h, ws);
+                        ws_sample = lanes[l].s;
+                    }
+                    ratio_scale(st, n, src, ld, ws + lanes[l].j, c->d_rhs_w + lanes[l].j, xs, ld, 1);
+                    src = xs;
+                }
+                c->d2h(sol.data() + (size_t)lanes[l].j * n, src, n);
             }
             c->sync();
+            c->release(ws);
+            c->release(xs);
         }
     }
 
@@ -1452,7 +1536,7 @@ struct Engine : EngineBase {
         ensure_append(b);
         T *X = xc, *AX = rv, *Y1 = pv, *Y2 = qv;
         unsigned long long *gb = (unsigned long long *)d_rr;
-        gershgorin(st, g, c->D64, c->diag64_of(s0), gb);
+        gershgorin(st, g, sample_D(g, c->diag64_of(s0), c->D64), c->diag64_of(s0), gb);
         unsigned long long bits = 0;
         c->d2h(&bits, gb, 1);
         c->sync();
@@ -1798,7 +1882,13 @@ struct Engine : EngineBase {
         // the seed sample slot gets mu_* back (its diagonal too)
         const int ss = (int)hdr[3];
         c->h2d(c->mu64 + (long long)ss * ld, mu.data(), (size_t)n);
-        diag_sample(st, n, c->dstar, c->mu64 + (long long)ss * ld, c->h * c->h, c->diag64_of(ss), c->diag32_of(ss));
+        if (c->track())
+            track_coefficients(st, g, c->mu64 + (long long)ss * ld, c->opt.mu_s_prime, c->h, c->grid.robin_A,
+                               c->Ds64_of(ss), c->Ds32 + (long long)ss * ld, c->Ws64_of(ss), c->diag64_of(ss),
+                               c->diag32_of(ss));
+        else
+            diag_sample(st, n, c->dstar, c->mu64 + (long long)ss * ld, c->h * c->h, c->diag64_of(ss),
+                        c->diag32_of(ss));
         c->sample_set[ss] = 1;
         r = 0;
         ensure_vcap(rr);
@@ -1857,21 +1947,41 @@ struct Engine : EngineBase {
             Zr = c->alloc<double>((size_t)rmax * nd);
             wtmp = c->alloc<double>(ld);
         }
-        // A~_r = C_* + V^T diag(h^2 (mu - mu_*)) V
-        scaled_diff(st, n, mu, c->mu64 + (long long)s_star * ld, c->h * c->h, wtmp);
+        // A~_r = C_* + V^T (A~(p) - A~_*) V
         RCG_CUDA_TRY(cudaMemcpy2DAsync(Ar, sizeof(double) * r, Cstar, sizeof(double) * rmax, sizeof(double) * r, r,
                                        cudaMemcpyDeviceToDevice, st));
-        if (mixed) {
-            if (!rom_bl) { rom_bl = c->alloc<int>((size_t)(n + 31) / 32); rom_bc = c->alloc<int>(1); }
-            tc_block_list(st, n, wtmp, rom_bl, rom_bc);
+        const double *wsrc = c->d_rhs_w;                   // effective source / detector weights at p
+        if (c->track()) {
+            ensure_track();
+            if (!tp_D) {
+                tp_D = c->alloc<double>(ld);
+                tp_W = c->alloc<double>((size_t)3 * ld);
+                tp_diag = c->alloc<double>(ld);
+                tp_w = c->alloc<double>(c->nrhs);
+                tp_G = c->alloc<double>((size_t)rmax * c->nrhs);
+                tp_P = c->alloc<double>((size_t)2 * ns * nd);
+            }
+            track_coefficients(st, g, mu, c->opt.mu_s_prime, c->h, c->grid.robin_A, tp_D, nullptr, tp_W, tp_diag,
+                               nullptr);
+            scaled_diff(st, n, tp_diag, c->diag64_of(s_star), 1.0, tk_dg);
+            scaled_diff(st, 3 * ld, tp_W, c->Ws64_of(s_star), 1.0, tk_dw);
+            delta_gram(V, r, Ar, r);
+            rhs_weights(st, tp_D, c->d_rhs_node, c->d_rhs_wt, ns, c->nrhs, c->grid.robin_A, c->h, tp_w);
+            wsrc = tp_w;
+        } else {
+            scaled_diff(st, n, mu, c->mu64 + (long long)s_star * ld, c->h * c->h, wtmp);
+            if (mixed) {
+                if (!rom_bl) { rom_bl = c->alloc<int>((size_t)(n + 31) / 32); rom_bc = c->alloc<int>(1); }
+                tc_block_list(st, n, wtmp, rom_bl, rom_bc);
+            }
+            gram_w_acc(V, r, Ar, r, wtmp, mixed ? rom_bl : nullptr, mixed ? rom_bc : nullptr);
         }
-        gram_w_acc(V, r, Ar, r, wtmp, mixed ? rom_bl : nullptr, mixed ? rom_bc : nullptr);
         RCG_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), st));
         chol_inplace(st, Ar, r, r, d_info);
         check_info("reduced matrix V^T A(p) V");
         // B~_r, C~_r: row gathers of V (point sources / receivers)
-        gather_rows<T>(st, V, ld, r, c->d_rhs_node, c->d_rhs_w, ns, Br, r);
-        gather_rows<T>(st, V, ld, r, c->d_rhs_node + ns, c->d_rhs_w + ns, nd, Crm, r);
+        gather_rows<T>(st, V, ld, r, c->d_rhs_node, wsrc, ns, Br, r);
+        gather_rows<T>(st, V, ld, r, c->d_rhs_node + ns, wsrc + ns, nd, Crm, r);
         RCG_CUDA_TRY(cudaMemcpyAsync(Xr, Br, sizeof(double) * r * ns, cudaMemcpyDeviceToDevice, st));
         RCG_CUDA_TRY(cudaMemcpyAsync(Zr, Crm, sizeof(double) * r * nd, cudaMemcpyDeviceToDevice, st));
         trsv_lower_batched(st, Ar, r, r, Xr, r, ns, false);
@@ -1880,7 +1990,36 @@ struct Engine : EngineBase {
         trsv_lower_batched(st, Ar, r, r, Zr, r, nd, true);
         // Psi_r = C~_r^T X_r  (ndet x nsrc)
         gemm_tn<double, double>(st, r, Crm, r, nd, Xr, r, ns, Psi, nd, false);
-        if (J && dmu && mixed && r >= 16 && tc_gemm_tn_ok(ld, ld, V, V)) {
+        if (J && dmu && c->track()) {
+            // J_k = -Z_r^T (V^T dA~_k V) X_r + (V^T dC~_k)^T X_r + Z_r^T (V^T dB~_k): the
+            // Grams of the operator derivatives (stencil and Robin terms with
+            // dD = -3 D^2 dmu_k) over their rows, all J_k in one launch, then the
+            // terms of the weights' derivatives from (V X_r) and (V Z_r) at the nodes
+            const long long gsz = (long long)nparam * r * r;
+            if (gsz > jk_gcap) {
+                c->release(jk_G);
+                jk_gcap = std::max(gsz, 2 * jk_gcap);
+                jk_G = c->alloc<double>((size_t)jk_gcap);
+            }
+            RCG_CUDA_TRY(cudaMemsetAsync(jk_G, 0, sizeof(double) * (size_t)gsz, st));
+            for (int k = 0; k < nparam; ++k) {
+                track_deriv(st, g, tp_D, dmu + (long long)k * n, c->h, c->grid.robin_A, -1.0, tk_dg, tk_dw);
+                delta_gram(V, r, jk_G + (long long)k * r * r, r);
+            }
+            rom_jac(st, r, nparam, jk_G, Xr, ns, Zr, nd, J);
+            if (nparam > tp_dwt_cap) {
+                c->release(tp_dwt);
+                tp_dwt_cap = nparam;
+                tp_dwt = c->alloc<double>((size_t)nparam * c->nrhs);
+            }
+            gather_rows<T>(st, V, ld, r, c->d_rhs_node, c->d_ones, c->nrhs, tp_G, r);   // V rows at all nodes
+            double *Pd = tp_P, *Ps = tp_P + (long long)ns * nd;
+            gemm_tn<double, double>(st, r, tp_G + (long long)ns * r, r, nd, Xr, r, ns, Pd, nd, false);
+            gemm_tn<double, double>(st, r, tp_G, r, ns, Zr, r, nd, Ps, ns, false);
+            rhs_weights(st, tp_D, c->d_rhs_node, c->d_rhs_wt, ns, c->nrhs, c->grid.robin_A, c->h, nullptr, dmu, n,
+                        nparam, tp_dwt);
+            jac_rhs_terms(st, nparam, nd, ns, tp_dwt, Pd, Ps, J);
+        } else if (J && dmu && mixed && r >= 16 && tc_gemm_tn_ok(ld, ld, V, V)) {
             // J_k = Z_r^T G_k X_r with G_k = V^T diag(-h^2 dmu_k) V: the weighted Grams on the
             // tensor cores over the support of dmu_k (one launch for all k), then all J_k in one float64 launch
             const long long nbl = (n + 31) / 32;
@@ -1939,7 +2078,7 @@ struct Engine : EngineBase {
         if (nq <= 0) return;
         const int ns = c->nsrc, nd = c->ndet;
         const bool jac = J && dmu && nparam > 0;
-        const bool batched = mixed && r >= 16 && tc_gemm_tn_ok(ld, ld, V, V) &&
+        const bool batched = mixed && !c->track() && r >= 16 && tc_gemm_tn_ok(ld, ld, V, V) &&
                              (!jac || ((((uintptr_t)dmu) & 15) == 0 && (n & 1) == 0));
         if (!batched) {
             for (int q = 0; q < nq; ++q)
@@ -2094,6 +2233,8 @@ void rcg_options_default(rcg_options *o) {
     o->keep_solutions = 0;
     o->seed_degree = 0;
     o->spin_budget = 0;
+    o->d_model = RCG_D_FIXED;
+    o->mu_s_prime = 1.0;
 }
 
 const char *rcg_strerror(int code) {
@@ -2131,7 +2272,9 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
         // the paper's check and solver run in the float64 engine; per-RHS recycle
         // spaces hold columns outside V, which only the MINRES lanes address
         ((c->opt.check == RCG_MR || c->opt.inner == RCG_MINRES) && c->opt.precision != RCG_FP64) ||
-        (c->opt.recycle == RCG_PER_RHS && c->opt.inner != RCG_MINRES)) {
+        (c->opt.recycle == RCG_PER_RHS && c->opt.inner != RCG_MINRES) ||
+        (c->opt.d_model != RCG_D_FIXED && c->opt.d_model != RCG_D_TRACKS_MU) ||
+        (c->opt.d_model == RCG_D_TRACKS_MU && !(c->opt.mu_s_prime > 0 && std::isfinite(c->opt.mu_s_prime)))) {
         delete c;
         return RCG_ERR_INVALID;
     }
@@ -2160,6 +2303,18 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
         c->mu64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
         c->diag64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
         c->diag32 = c->alloc<float>((size_t)c->opt.max_samples * c->ld);
+        if (c->track()) {
+            // per-sample D and face weights, addressed from a sample's diagonal (Grid)
+            c->Ds64 = c->alloc<double>((size_t)c->opt.max_samples * c->ld);
+            c->Ds32 = c->alloc<float>((size_t)c->opt.max_samples * c->ld);
+            c->Ws64 = c->alloc<double>((size_t)3 * c->opt.max_samples * c->ld);
+            c->g.dbase64 = c->diag64;
+            c->g.dbase32 = c->diag32;
+            c->g.Ds64 = c->Ds64;
+            c->g.Ds32 = c->Ds32;
+            c->g.Ws64 = c->Ws64;
+            c->g.dspan = (long long)c->opt.max_samples * c->ld;
+        }
         c->d_prof = c->alloc<unsigned long long>(8);
         RCG_CUDA_TRY(cudaMemsetAsync(c->d_prof, 0, sizeof(unsigned long long) * 8, c->st));
         if (c->opt.precision == RCG_MIXED) c->eng.reset(new Engine<float>(c));
@@ -2213,6 +2368,7 @@ int rcg_set_sources_detectors(rcg_ctx *c, int nsrc, const int *src_ij, const dou
         c->nrhs = nsrc + ndet;
         c->rhs_node.assign(c->nrhs, 0);
         c->rhs_w.assign(c->nrhs, 0.0);
+        c->rhs_wt.assign(c->nrhs, 0.0);
         for (int q = 0; q < c->nrhs; ++q) {
             const bool is_src = q < nsrc;
             const int *ij = is_src ? src_ij + 2 * q : det_ij + 2 * (q - nsrc);
@@ -2225,15 +2381,22 @@ int rcg_set_sources_detectors(rcg_ctx *c, int nsrc, const int *src_ij, const dou
             const double wt = is_src ? (src_w ? src_w[q] : 1.0) : (det_w ? det_w[q - nsrc] : 1.0);
             // b~ = s D_p / (1 + alpha_p) e_p,  c~ = c alpha_p / (1 + alpha_p) e_p  (Sec. 3.1)
             c->rhs_node[q] = (int)p;
+            c->rhs_wt[q] = wt;
             c->rhs_w[q] = wt * (is_src ? Dp / (1.0 + alpha) : alpha / (1.0 + alpha));
             if (!(c->rhs_w[q] != 0.0) || !std::isfinite(c->rhs_w[q])) return fail(c, RCG_ERR_INVALID, "zero weight");
         }
-        c->release(c->d_rhs_node);
-        c->release(c->d_rhs_w);
+        for (void *p : std::vector<void *>{c->d_rhs_node, c->d_rhs_w, c->d_rhs_wt, c->d_ones}) c->release(p);
         c->d_rhs_node = c->alloc<int>(c->nrhs);
         c->d_rhs_w = c->alloc<double>(c->nrhs);
+        c->d_rhs_wt = c->alloc<double>(c->nrhs);
+        c->d_ones = c->alloc<double>(c->nrhs);
         c->h2d(c->d_rhs_node, c->rhs_node.data(), c->nrhs);
         c->h2d(c->d_rhs_w, c->rhs_w.data(), c->nrhs);
+        c->h2d(c->d_rhs_wt, c->rhs_wt.data(), c->nrhs);
+        {
+            const std::vector<double> ones((size_t)c->nrhs, 1.0);
+            c->h2d(c->d_ones, ones.data(), c->nrhs);
+        }
         c->tol.assign(c->nrhs, 1e-8);
         c->sync();
         c->have_rhs = true;
@@ -2263,7 +2426,11 @@ static int set_sample_impl(rcg_ctx *c, int s, const double *mu, bool device) {
                 if (!(mu[p] >= 0) || !std::isfinite(mu[p])) return fail(c, RCG_ERR_INVALID, "mu must be >= 0 and finite");
             c->h2d(dst, mu, c->n);
         }
-        diag_sample(c->st, c->n, c->dstar, dst, c->h * c->h, c->diag64_of(s), c->diag32_of(s));
+        if (c->track())
+            track_coefficients(c->st, c->g, dst, c->opt.mu_s_prime, c->h, c->grid.robin_A, c->Ds64_of(s),
+                               c->Ds32 + (long long)s * c->ld, c->Ws64_of(s), c->diag64_of(s), c->diag32_of(s));
+        else
+            diag_sample(c->st, c->n, c->dstar, dst, c->h * c->h, c->diag64_of(s), c->diag32_of(s));
         c->sync();
         c->sample_set[s] = 1;
         if (c->eng) c->eng->sample_changed(s);
@@ -2281,6 +2448,7 @@ int rcg_apply_f32(rcg_ctx *c, int s, int variant, const float *x_dev, float *y_d
             return fail(c, RCG_ERR_INVALID, "bad rcg_apply_f32 arguments");
         if (!cg4_supported(c->g) || ((uintptr_t)x_dev & 15) || ((uintptr_t)y_dev & 15))
             return fail(c, RCG_ERR_INVALID, "rcg_apply_f32 needs N % 4 == 0 and 16-byte aligned columns");
+        if (c->track()) return fail(c, RCG_ERR_INVALID, "rcg_apply_f32: the float4 stencils take one fixed D");
         if (variant >= 0 && !stencil_variant_ok(c->g, variant))
             return fail(c, RCG_ERR_INVALID, "the stencil variant does not support this grid");
         if (ncols == 0) return RCG_OK;
@@ -2381,8 +2549,9 @@ int rcg_seed_copy(rcg_ctx *c, const rcg_ctx *src) {
     return guarded(c, [&]() {
         if (!src || src == c || !src->eng || !c->eng) return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: bad contexts");
         if (c->grid.dim != src->grid.dim || c->grid.N != src->grid.N || c->grid.robin_A != src->grid.robin_A ||
-            c->rhs_node != src->rhs_node || c->rhs_w != src->rhs_w || !c->have_D || !src->have_D)
-            return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: grid or sources / detectors differ");
+            c->rhs_node != src->rhs_node || c->rhs_w != src->rhs_w || !c->have_D || !src->have_D ||
+            c->opt.d_model != src->opt.d_model || (c->track() && c->opt.mu_s_prime != src->opt.mu_s_prime))
+            return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: grid, sources / detectors or D model differ");
         const SeedView sv = src->eng->seed_view();
         if (!sv.seeded) return fail(c, RCG_ERR_INVALID, "rcg_seed_copy: the source context is not seeded");
         if (sv.s_star < 0 || sv.s_star >= c->opt.max_samples || !c->sample_set[sv.s_star])
@@ -2444,6 +2613,66 @@ int rcg_solution_get(rcg_ctx *c, int s, double *X) {
     });
 }
 
+// rcg_full_eval with D tracking mu at sample s: the weights at D_s and
+//   J_k = -Z^T dA~_k X + dC~_k^T X + Z^T dB~_k
+// (dA~_k: the operator derivative with dD = -3 D_s^2 dmu_k, applied on its
+// rows; dB~_k, dC~_k: the weights' derivatives at the source / detector nodes).
+static int full_eval_tracking(rcg_ctx *c, int s, int nparam, const double *dmu, double *Psi, double *J) {
+    const int ns = c->nsrc, nd = c->ndet, nrhs = c->nrhs;
+    const long long n = c->n, ld = c->ld;
+    const std::vector<double> &X = c->solutions[s];
+    std::vector<double> ws(nrhs);
+    double *d_ws = c->alloc<double>(nrhs);
+    rhs_weights(c->st, c->Ds64_of(s), c->d_rhs_node, c->d_rhs_wt, ns, nrhs, c->grid.robin_A, c->h, d_ws);
+    c->d2h(ws.data(), d_ws, nrhs);
+    c->sync();
+    c->release(d_ws);
+    for (int j = 0; j < ns; ++j)
+        for (int d = 0; d < nd; ++d)
+            Psi[d + (long long)nd * j] = ws[ns + d] * X[(size_t)j * n + c->rhs_node[ns + d]];
+    if (!dmu) return RCG_OK;
+    const long long nbl = (n + 31) / 32;
+    double *dX = c->alloc<double>((size_t)nrhs * ld), *dm = c->alloc<double>((size_t)nparam * n);
+    double *dg = c->alloc<double>(ld), *dw = c->alloc<double>((size_t)3 * ld), *touch = c->alloc<double>(ld);
+    double *dJ = c->alloc<double>((size_t)nparam * nd * ns), *dwt = c->alloc<double>((size_t)nparam * nrhs);
+    int *bl = c->alloc<int>((size_t)nbl), *bc = c->alloc<int>(1);
+    double *Xc = c->alloc<double>((size_t)nbl * 32 * nrhs), *Yc = c->alloc<double>((size_t)nbl * 32 * nrhs);
+    for (int j = 0; j < nrhs; ++j) c->h2d(dX + (long long)j * ld, X.data() + (size_t)j * n, (size_t)n);
+    c->h2d(dm, dmu, (size_t)nparam * n);
+    for (int k = 0; k < nparam; ++k) {
+        double *Jk = dJ + (long long)k * nd * ns;
+        track_deriv(c->st, c->g, c->Ds64_of(s), dm + (long long)k * n, c->h, c->grid.robin_A, -1.0, dg, dw);
+        track_touch(c->st, c->g, dg, dw, touch);
+        tc_block_list(c->st, n, touch, bl, bc);
+        int nb = 0;
+        c->d2h(&nb, bc, 1);
+        c->sync();
+        if (nb <= 0) {
+            RCG_CUDA_TRY(cudaMemsetAsync(Jk, 0, sizeof(double) * (size_t)nd * ns, c->st));
+            continue;
+        }
+        const long long rows = (long long)nb * 32;
+        // -Z^T dA_k X over the rows of dA_k: Z rows (detector columns of Xc) against dA_k X
+        delta_rows<double>(c->st, c->g, bl, 0, nb, dg, dw, dX, ld, nrhs, Xc, Yc, rows);
+        gemm_tn<double, double>(c->st, rows, Xc + (long long)ns * rows, rows, nd, Yc, rows, ns, Jk, nd, false);
+    }
+    rhs_weights(c->st, c->Ds64_of(s), c->d_rhs_node, c->d_rhs_wt, ns, nrhs, c->grid.robin_A, c->h, nullptr, dm, n,
+                nparam, dwt);
+    std::vector<double> hdwt((size_t)nparam * nrhs);
+    c->d2h(J, dJ, (size_t)nparam * nd * ns);
+    c->d2h(hdwt.data(), dwt, hdwt.size());
+    c->sync();
+    for (void *p : std::vector<void *>{dX, dm, dg, dw, touch, dJ, dwt, bl, bc, Xc, Yc}) c->release(p);
+    // the weights' terms: dC~_k^T x_j = dc_{k,d} x_j(node_d), z_d^T dB~_k = db_{k,j} z_d(node_j)
+    for (int k = 0; k < nparam; ++k)
+        for (int j = 0; j < ns; ++j)
+            for (int d = 0; d < nd; ++d)
+                J[(long long)k * nd * ns + d + (long long)nd * j] +=
+                    hdwt[(size_t)k * nrhs + ns + d] * X[(size_t)j * n + c->rhs_node[ns + d]] +
+                    hdwt[(size_t)k * nrhs + j] * X[(size_t)(ns + d) * n + c->rhs_node[j]];
+    return RCG_OK;
+}
+
 int rcg_full_eval(rcg_ctx *c, int s, int nparam, const double *dmu, double *Psi, double *J) {
     return guarded(c, [&]() {
         if (!c->opt.keep_solutions || s < 0 || s >= c->opt.max_samples || !Psi || c->solutions[s].empty())
@@ -2452,6 +2681,7 @@ int rcg_full_eval(rcg_ctx *c, int s, int nparam, const double *dmu, double *Psi,
         const int ns = c->nsrc, nd = c->ndet;
         const long long n = c->n, ld = c->ld;
         const std::vector<double> &X = c->solutions[s];       // n x nrhs, sources then detectors
+        if (c->track()) return full_eval_tracking(c, s, nparam, dmu, Psi, J);
         // Psi[d, j] = c~_d^T x_j: the receivers are point functionals w_d e_{node_d}
         for (int j = 0; j < ns; ++j)
             for (int d = 0; d < nd; ++d)
@@ -2481,7 +2711,10 @@ int rcg_save(rcg_ctx *c, const char *path) {
         if (!f) return fail(c, RCG_ERR_INVALID, std::string("rcg_save: cannot open ") + path);
         try {
             wr(f, kMagic, sizeof(kMagic));
-            const long long g[6] = {c->grid.dim, c->grid.N, c->n, c->opt.precision, c->nsrc, c->ndet};
+            long long mus_bits = 0;
+            std::memcpy(&mus_bits, &c->opt.mu_s_prime, sizeof(mus_bits));
+            const long long g[8] = {c->grid.dim, c->grid.N, c->n, c->opt.precision, c->nsrc, c->ndet,
+                                    c->opt.d_model, c->track() ? mus_bits : 0};
             wr(f, g, sizeof(g));
             std::vector<double> D((size_t)c->n);
             c->d2h(D.data(), c->D64, (size_t)c->n);
@@ -2518,11 +2751,13 @@ int rcg_load(rcg_ctx *c, const char *path) {
             char m[8];
             rd(f, m, sizeof(m));
             if (std::memcmp(m, kMagic, sizeof(m)) != 0) throw Error{RCG_ERR_INVALID, "rcg_load: not an rcg state file"};
-            long long g[6];
+            long long g[8];
             rd(f, g, sizeof(g));
+            long long mus_bits = 0;
+            std::memcpy(&mus_bits, &c->opt.mu_s_prime, sizeof(mus_bits));
             if (g[0] != c->grid.dim || g[1] != c->grid.N || g[2] != c->n || g[3] != c->opt.precision ||
-                g[4] != c->nsrc || g[5] != c->ndet)
-                throw Error{RCG_ERR_INVALID, "rcg_load: grid, precision or source/detector counts differ"};
+                g[4] != c->nsrc || g[5] != c->ndet || g[6] != c->opt.d_model || g[7] != (c->track() ? mus_bits : 0))
+                throw Error{RCG_ERR_INVALID, "rcg_load: grid, precision, source/detector counts or D model differ"};
             auto D = rd_vec<double>(f, c->n);
             auto node = rd_vec<int>(f, c->nrhs);
             auto w = rd_vec<double>(f, c->nrhs);

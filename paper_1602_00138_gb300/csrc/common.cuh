@@ -51,7 +51,33 @@ struct Grid {
     int Nx, Ny, Nz;
     long long n;       // Nx*Ny*Nz
     long long ld;      // padded column stride of every n-vector (elements)
+    // Diffusion tracking the absorption (rcg_options.d_model): the per-sample
+    // D (float64 / float32) and face weights (3 columns) of sample slot s sit
+    // at s ld (D) and 3 s ld (W) from these bases.  A kernel handed the
+    // diagonal of slot s (dbase + s ld, the only diagonals the library passes)
+    // finds that slot's coefficients at the same offset.  Null: fixed D.
+    const double *dbase64 = nullptr, *Ds64 = nullptr, *Ws64 = nullptr;
+    const float *dbase32 = nullptr, *Ds32 = nullptr;
+    long long dspan = 0;                 // slots x ld: offsets past it are not a sample's
 };
+
+// The D of the sample whose diagonal is dg (tracking), else the shared D.
+__host__ __device__ inline const double *sample_D(const Grid &g, const double *dg, const double *D) {
+    if (!g.Ds64) return D;
+    const long long o = dg - g.dbase64;
+    return (o >= 0 && o < g.dspan) ? g.Ds64 + o : D;
+}
+__host__ __device__ inline const float *sample_D(const Grid &g, const float *dg, const float *D) {
+    if (!g.Ds32) return D;
+    const long long o = dg - g.dbase32;
+    return (o >= 0 && o < g.dspan) ? g.Ds32 + o : D;
+}
+// The face weights (3 columns, stride ld) of the sample whose float64 diagonal is dg.
+__host__ __device__ inline const double *sample_W(const Grid &g, const double *dg, const double *W) {
+    if (!g.Ws64) return W;
+    const long long o = dg - g.dbase64;
+    return (o >= 0 && o < g.dspan) ? g.Ws64 + 3 * o : W;
+}
 
 // Columns addressed as base + j*ld.
 template <typename T> struct Cols {
@@ -247,6 +273,23 @@ void face_weights(cudaStream_t st, const Grid &g, const double *D, double *W);
 void residual64(cudaStream_t st, const Grid &g, const double *W, const double *const *diag_of_col,
                 const double *const *x, double *const *r, float *const *r32, int ncols,
                 const int *node, const double *bw, double *rr, const int *active, int nact = -1);
+
+// track.cu (diffusion tracking the absorption)
+void track_coefficients(cudaStream_t st, const Grid &g, const double *mu, double mus, double h, double robin_A,
+                        double *D64, float *D32, double *W64, double *diag64, float *diag32);
+void track_deriv(cudaStream_t st, const Grid &g, const double *D, const double *dmu, double h, double robin_A,
+                 double scale, double *dg, double *dw);
+void track_touch(cudaStream_t st, const Grid &g, const double *dg, const double *dw, double *touch);
+template <typename T>
+void delta_rows(cudaStream_t st, const Grid &g, const int *blist, int b0, int nb, const double *dg, const double *dw,
+                const T *X, long long ldx, int ncols, T *Xc, double *Yc, long long ldc);
+void rhs_weights(cudaStream_t st, const double *D, const int *node, const double *wt, int nsrc, int nrhs,
+                 double robin_A, double h, double *w, const double *dmu = nullptr, long long lddmu = 0,
+                 int nparam = 0, double *dwt = nullptr);
+void jac_rhs_terms(cudaStream_t st, int nparam, int nd, int ns, const double *dwt, const double *Pd, const double *Ps,
+                   double *J);
+void ratio_scale(cudaStream_t st, long long n, const double *x, long long ldx, const double *w1, const double *w0,
+                 double *dst, long long ldd, int ncols);
 
 // dense.cu
 template <typename TA, typename TB>

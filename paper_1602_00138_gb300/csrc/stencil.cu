@@ -62,6 +62,7 @@ k_apply(Grid g, const T *__restrict__ D, const T *const *__restrict__ diag_of_co
     const T *__restrict__ x = src[c];
     T *__restrict__ y = dst[c];
     const T *__restrict__ dg = diag_of_col[c];
+    D = sample_D(g, dg, D);
     const int sxy = g.Nx * g.Ny;          // grids here are < 2^31 nodes (checked at rcg_create)
     const int nn = (int)g.n;
     const bool has_y = g.Ny > 1;
@@ -99,7 +100,9 @@ k_apply(Grid g, const T *__restrict__ D, const T *const *__restrict__ diag_of_co
 }
 
 // r_c = b_c - A~_{s(c)} x_c in float64, b_c = bw_c e_{node_c}; optional float32 copy; rr_c += r^T r.
-template <int NB>
+// TRACK: every column reads the face weights of its own sample (diffusion
+// tracking the absorption); otherwise W is shared and read once per node.
+template <int NB, bool TRACK>
 __global__ void __launch_bounds__(kThreads)
 k_residual64(Grid g, const double *__restrict__ W, const double *const *__restrict__ diag_of_col,
              const double *const *__restrict__ xsrc, double *const *__restrict__ rdst,
@@ -125,21 +128,36 @@ k_residual64(Grid g, const double *__restrict__ W, const double *const *__restri
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const int i = p % g.Nx, rest = p / g.Nx;
         const int j = rest % g.Ny, k = rest / g.Ny;
-        const double wxm = i > 0 ? Wx[p - 1] : 0.0, wxp = Wx[p];
-        const double wym = j > 0 ? Wy[p - g.Nx] : 0.0, wyp = Wy[p];
-        const double wzm = k > 0 ? Wz[p - sxy] : 0.0, wzp = Wz[p];
+        double wxm = 0.0, wxp = 0.0, wym = 0.0, wyp = 0.0, wzm = 0.0, wzp = 0.0;
+        if constexpr (!TRACK) {
+            wxm = i > 0 ? Wx[p - 1] : 0.0; wxp = Wx[p];
+            wym = j > 0 ? Wy[p - g.Nx] : 0.0; wyp = Wy[p];
+            wzm = k > 0 ? Wz[p - sxy] : 0.0; wzp = Wz[p];
+        }
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
             if (!act[t]) continue;
             const int c = c0 + t;
             const double *x = xsrc[c];
-            double v = diag_of_col[c][p] * x[p];
-            if (i > 0) v -= wxm * x[p - 1];
-            if (i < g.Nx - 1) v -= wxp * x[p + 1];
-            if (j > 0) v -= wym * x[p - g.Nx];
-            if (j < g.Ny - 1) v -= wyp * x[p + g.Nx];
-            if (k > 0) v -= wzm * x[p - sxy];
-            if (k < g.Nz - 1) v -= wzp * x[p + sxy];
+            const double *dgc = diag_of_col[c];
+            double v = dgc[p] * x[p];
+            if constexpr (TRACK) {
+                const double *Wc = sample_W(g, dgc, W);
+                const double *Wcx = Wc, *Wcy = Wc + g.ld, *Wcz = Wc + 2 * g.ld;
+                if (i > 0) v -= Wcx[p - 1] * x[p - 1];
+                if (i < g.Nx - 1) v -= Wcx[p] * x[p + 1];
+                if (j > 0) v -= Wcy[p - g.Nx] * x[p - g.Nx];
+                if (j < g.Ny - 1) v -= Wcy[p] * x[p + g.Nx];
+                if (k > 0) v -= Wcz[p - sxy] * x[p - sxy];
+                if (k < g.Nz - 1) v -= Wcz[p] * x[p + sxy];
+            } else {
+                if (i > 0) v -= wxm * x[p - 1];
+                if (i < g.Nx - 1) v -= wxp * x[p + 1];
+                if (j > 0) v -= wym * x[p - g.Nx];
+                if (j < g.Ny - 1) v -= wyp * x[p + g.Nx];
+                if (k > 0) v -= wzm * x[p - sxy];
+                if (k < g.Nz - 1) v -= wzp * x[p + sxy];
+            }
             const double b = (p == node[c]) ? bw[c] : 0.0;
             const double res = b - v;
             if (rdst) rdst[c][p] = res;
@@ -218,7 +236,10 @@ void residual64(cudaStream_t st, const Grid &g, const double *W, const double *c
     // them; the others exit at once): a restart of a few lanes keeps the GPU busy
     const int busy = std::max(1, std::min(groups, nact < 0 ? ncols : nact));
     dim3 grid(grid_x_for(g.n, busy), groups);
-    k_residual64<NB><<<grid, kThreads, 0, st>>>(g, W, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
+    if (g.Ws64)
+        k_residual64<NB, true><<<grid, kThreads, 0, st>>>(g, W, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
+    else
+        k_residual64<NB, false><<<grid, kThreads, 0, st>>>(g, W, diag_of_col, x, r, r32, ncols, node, bw, rr, active);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
