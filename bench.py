@@ -337,8 +337,8 @@ def prepare(rcg, W, opts, torch, ntrain=0, epochs=0, seed_from=None, **kw):
 
 
 def roofline(W, prof, peak, peak_source):
-    """Achieved bandwidth of the dominant inner-CG kernel and of the stencil
-    kernel from the device timers of the timed steps.  Algorithmic bytes
+    """Achieved bandwidth of the dominant inner-CG kernel, of the stencil
+    kernel and of the update kernel from the device timers of the timed steps.  Algorithmic bytes
     (unique DRAM bytes a launch must move), per node per active lane, s = 4:
       stencil    read p, write q (D and the sample diagonal once per sample,
                  L2-resident, not counted): 2
@@ -403,7 +403,8 @@ def roofline(W, prof, peak, peak_source):
     out = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": "GB/s",
            "frac": d["frac"], "traffic": traffic, "peak_source": peak_source, "launches": d["launches"],
            "avg_launch_us": d["avg_launch_us"], "alg_bytes_per_launch": d["alg_bytes_per_launch"],
-           "stencil": entry(0), "kernels_ms": {names[k]: round(prof[k]["ms"], 3) for k in range(5)}}
+           "stencil": entry(0), "update": entry(1),
+           "kernels_ms": {names[k]: round(prof[k]["ms"], 3) for k in range(5)}}
     return out
 
 
