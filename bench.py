@@ -99,6 +99,9 @@ def parse_args(argv=None):
     ap.add_argument("--products", action="store_true",
                     help="time the basis product A^T B on the tensor cores and on CUDA cores (one JSON line per shape)")
     ap.add_argument("--products-shapes", type=int, default=4, help="number of --products shapes to run")
+    ap.add_argument("--stencil", type=int, default=0, metavar="LANES",
+                    help="time the inner iteration's float32 stencil kernels alone on LANES columns of the "
+                         "workload's grid (every variant the grid supports; one JSON line)")
     ap.add_argument("--rom-sweep", type=int, default=None,
                     help="held-out parameter points for the reduced-model sweep (0 skips it)")
     ap.add_argument("--rom-batch", type=int, default=8, help="points per rcg_rom_eval_batch call in the sweep")
@@ -805,11 +808,55 @@ def reference_line(args, res):
     return line
 
 
+def stencil_bench(args, torch):
+    """q = A~_s p on `args.stencil` float32 columns of the workload's grid with
+    every stencil variant the grid supports and with the autotuned choice:
+    CUDA events on the launching stream around 10 launches after 3 warm-up
+    launches; GB/s counts the algorithmic bytes (read p, write q)."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_1602_00138_gb300 import rcg
+    from synthetic.phantom import make_workload
+    inp = make_workload(args.workload, K=1, with_dmu=False)
+    wl = inp["wl"]
+    L, n = args.stencil, wl.n
+    st = torch.cuda.current_stream()
+    with rcg.Context(wl.dim, wl.N, wl.robin_A, stream=st.cuda_stream, max_samples=2) as ctx:
+        ctx.set_diffusion(inp["D"])
+        ctx.set_sample(1, inp["mu"][1])
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn((L, n), dtype=torch.float32, device="cuda", generator=gen)
+        y = torch.empty_like(x)
+        d = torch.zeros(L, dtype=torch.float64, device="cuda")
+        out = {}
+        for v in [-1] + list(range(rcg.RCG_STENCIL_VARIANTS)):
+            if v >= 0 and not ctx.stencil_variant_ok(v):
+                continue
+            for _ in range(3):
+                ctx.apply_f32(1, x, y, L, variant=v, dots_dev=d)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(10):
+                ctx.apply_f32(1, x, y, L, variant=v, dots_dev=d)
+            e1.record(st)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / 10
+            name = "autotuned" if v < 0 else rcg.stencil_variant_name(v)
+            out[name] = {"us": round(us, 1), "GB_per_s": round(L * n * 8 / us / 1e3, 1)}
+        print(json.dumps({"stencil": f"{wl.dim}D {wl.N}^{wl.dim}", "lanes": L, "variants": out,
+                          "tuner": rcg.tuning_report()}))
+
+
 def main():
     args = parse_args()
     if args.products:
         import torch
         products_bench(torch, args.products_shapes)
+        return
+    if args.stencil > 0:
+        import torch
+        stencil_bench(args, torch)
         return
     if args.cpu_worker:
         oracle_worker(args)
