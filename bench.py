@@ -64,8 +64,8 @@ SETTINGS = {
     "c5_3d192": dict(wave=1, r_max=2048, train=2, epochs=6, sweep=4, nolearn_steps=5,
                      oracle_samples=(1,), oracle_rhs=(0, 128), base_samples=1,
                      oracle_unavailable="the oracle cannot seed 7,077,888 unknowns within a bench run: its ARPACK "
-                                        "eigensolver for the 10 smallest eigenvectors of A~_0 (Sec. 4.2.2) ran "
-                                        "over 30 minutes on the host without converging",
+                                        "eigensolver for the 10 smallest eigenvectors of A~_0 (Sec. 4.2.2) took "
+                                        "45 minutes on one host core, before any solve",
                      oracle_context="c2_3d64"),
     "c3_3d128": dict(wave=0, r_max=1024, train=0, epochs=0, sweep=0, nolearn_steps=0,
                      oracle_samples=(1,), oracle_rhs=(0, 64), base_samples=0),

@@ -314,15 +314,19 @@ __global__ void __launch_bounds__(kThreads, ZL <= 2 ? 2 : 1)
 k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict__ diag_of_col,
             const float *const *__restrict__ src, float *const *__restrict__ dst, const int *__restrict__ alist,
             int na, const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ prof,
-            int zc, int lanes_fast) {
+            int zc, int gc) {
     constexpr int TY = kThreads / TX, RW = TX + 2, RH = TY + 2, NA = ZL + 1;
     extern __shared__ float4 pl[];                   // [2][NA][RH][RW]
     const int nx4 = g.Nx >> 2, xtiles = nx4 / TX, ytiles = (g.Ny + TY - 1) / TY;
-    // lanes_fast: blockIdx.x is the lane group and blockIdx.y the (x tile, y
-    // tile, z chunk), so that the CTAs resident together share a tile's D and
-    // diagonal planes in L2 (measured faster for few lane groups); otherwise
-    // the roles swap (faster for many)
-    const int lg = lanes_fast ? blockIdx.x : blockIdx.y, tz = lanes_fast ? blockIdx.y : blockIdx.x;
+    // Grid order.  gc > 0: lane groups in chunks of gc, the group within its
+    // chunk fastest (blockIdx.x), then the (x tile, y tile, z chunk)
+    // (blockIdx.y), then the chunk (blockIdx.z): the CTAs resident together
+    // are gc lane groups on a run of tiles, so each tile's D and diagonal
+    // planes come from DRAM once per chunk and serve its groups from L2.
+    // gc == 0: the tile fastest, then the lane group (each group streams
+    // whole planes; D and the diagonal are read again for every group).
+    const int lg = gc > 0 ? (int)blockIdx.z * gc + (int)blockIdx.x : (int)blockIdx.y;
+    const int tz = gc > 0 ? (int)blockIdx.y : (int)blockIdx.x;
     const int xt = tz % xtiles, rest = tz / xtiles;
     const int yt = rest % ytiles, zb = rest / ytiles;
     const int z0 = zb * zc, z1 = min(z0 + zc, g.Nz);
@@ -1234,9 +1238,12 @@ int device_sms(int dev) {
 
 // k_stencil4r<TX, ZL> over the lanes of ll: per-plane tiles x lane groups x
 // z-chunks, the chunks sized for ~4 waves of resident CTAs (>= 8 planes each).
+// gc: lane groups per chunk of the grid order (see k_stencil4r); -1 picks
+// all groups in one chunk for up to 16 groups and the tile-first order above.
 template <int TX, int ZL>
 void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
-                float *const *q, const LaneList &ll, const int *active, double *dots, unsigned long long *prof) {
+                float *const *q, const LaneList &ll, const int *active, double *dots, unsigned long long *prof,
+                int gc = -1) {
     static int occ[64] = {};
     int dev = 0;
     RCG_CUDA_TRY(cudaGetDevice(&dev));
@@ -1256,11 +1263,13 @@ void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *con
     nzc = std::max<long long>(1, std::min(nzc, maxc));
     const int zc = (int)((g.Nz + nzc - 1) / nzc);
     nzc = (g.Nz + zc - 1) / zc;
-    const bool lanes_fast = G <= 16;
-    if ((lanes_fast ? T * nzc : G) > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4r: grid y extent"};
-    const dim3 grid = lanes_fast ? dim3((unsigned)G, (unsigned)(T * nzc)) : dim3((unsigned)(T * nzc), (unsigned)G);
-    k_stencil4r<TX, ZL><<<grid, kThreads, smem, st>>>(g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc,
-                                                      lanes_fast ? 1 : 0);
+    if (gc < 0) gc = G <= 16 ? (int)G : 0;
+    if (gc > G) gc = (int)G;
+    const long long nchunk = gc > 0 ? (G + gc - 1) / gc : 0;
+    if ((gc > 0 ? std::max(T * nzc, nchunk) : G) > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4r: grid extent"};
+    const dim3 grid = gc > 0 ? dim3((unsigned)gc, (unsigned)(T * nzc), (unsigned)nchunk)
+                             : dim3((unsigned)(T * nzc), (unsigned)G);
+    k_stencil4r<TX, ZL><<<grid, kThreads, smem, st>>>(g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc, gc);
 }
 
 void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
@@ -1288,24 +1297,30 @@ void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *con
 }
 
 // Stencil variants: 0 the row kernel k_stencil4 (any Nx % 4 == 0), 1 the
-// plane-ring kernel k_stencil4z (3D, 256 % (Nx / 4) == 0), and 2 + the
+// plane-ring kernel k_stencil4z (3D, 256 % (Nx / 4) == 0), 2 + the
 // z-marching kernel k_stencil4r<TX, ZL> for TX in {4, 8, 16, 32} (TX | Nx/4),
-// ZL in {1, 2, 4}: id 2 + 3 log2(TX / 4) + log2(ZL).
+// ZL in {1, 2, 4}: id 2 + 3 log2(TX / 4) + log2(ZL), in the default grid
+// order; and 14 + the same kernel for (TX, ZL) in {(8, 2), (16, 2)} with the
+// lane groups in chunks of 4, 8 or 16: id 14 + 3 (TX == 16) + log2(chunk / 4).
 constexpr int S4_TXS[4] = {4, 8, 16, 32};
 constexpr int S4_ZLS[3] = {1, 2, 4};
-constexpr int S4_NVAR = 2 + 12;
+constexpr int S4_NVAR = 2 + 12 + 6;
+static_assert(S4_NVAR == RCG_STENCIL_VARIANTS, "variant count");
 
 bool s4_variant_ok(const Grid &g, int v) {
     if (v == 0) return cg4_supported(g);
     if (v == 1) return stencil4z_supported(g);
     if (v < 2 || v >= S4_NVAR) return false;
-    const int tx = S4_TXS[(v - 2) / 3];
+    const int tx = v >= 14 ? (v >= 17 ? 16 : 8) : S4_TXS[(v - 2) / 3];
     return cg4_supported(g) && g.Ny > 1 && (g.Nx / 4) % tx == 0 && g.n < (1LL << 31);
 }
 
 std::string s4_variant_name(int v) {
     if (v == 0) return "k_stencil4 (rows)";
     if (v == 1) return "k_stencil4z (plane ring)";
+    if (v >= 14)
+        return std::string(v >= 17 ? "k_stencil4r<16,2>" : "k_stencil4r<8,2>") + " chunks of " +
+               std::to_string(4 << ((v - 14) % 3)) + " groups";
     return "k_stencil4r<" + std::to_string(S4_TXS[(v - 2) / 3]) + "," + std::to_string(S4_ZLS[(v - 2) % 3]) + ">";
 }
 
@@ -1324,6 +1339,12 @@ void s4_launch(int v, cudaStream_t st, const Grid &g, const float *D, const floa
         RCG_S4R(8, 16, 1) RCG_S4R(9, 16, 2) RCG_S4R(10, 16, 4)
         RCG_S4R(11, 32, 1) RCG_S4R(12, 32, 2) RCG_S4R(13, 32, 4)
 #undef RCG_S4R
+        case 14: case 15: case 16:
+            launch_s4r<8, 2>(st, g, D, diag, p, q, ll, active, dots, prof, 4 << (v - 14));
+            break;
+        case 17: case 18: case 19:
+            launch_s4r<16, 2>(st, g, D, diag, p, q, ll, active, dots, prof, 4 << (v - 17));
+            break;
         default: throw Error{RCG_ERR_INVALID, "unknown stencil variant"};
     }
     count_launch();

@@ -100,3 +100,26 @@ def test_batch_edge_cases(rcg):
         assert rel(P1[0], Pq) <= 1e-6 and rel(J1[0], Jq) <= 1e-6
     finally:
         ctx.close()
+
+
+def test_batch_of_more_points_than_one_chunk(rcg):
+    """257 points: more than one chunk of rcg_rom_eval_batch (at most 256
+    points per chunk), so the second chunk's offsets into mu, dmu, Psi and J
+    are exercised; every point equals rcg_rom_eval at that point."""
+    name = "t3d_32"
+    inp = workload(name)
+    wl = inp["wl"]
+    ps = heldout_params(wl, 257, seed_offset=3000)
+    mus = np.stack([pals_mu(p, inp["X"], wl.mu_bg) for p in ps])
+    dmus = np.stack([pals_dmu(p, inp["X"], wl.mu_bg) for p in ps])
+    ctx, _, _, rc, _ = gpu_run(name, rcg.RCG_MIXED, rcg.RCG_WAVE, 1e-6)
+    try:
+        assert rc == 0
+        Psi_b, J_b = ctx.rom_eval_batch(mus, dmus)
+        for q in (0, 1, 128, 255, 256):
+            Pq, Jq = ctx.rom_eval(mus[q], dmus[q])
+            assert rel(Psi_b[q], Pq) <= 1e-6 and rel(J_b[q], Jq) <= 1e-6, q
+        # the chunks do not bleed: the last point differs from its neighbour where their parameters do
+        assert rel(Psi_b[256], Psi_b[255]) > 1e-9
+    finally:
+        ctx.close()

@@ -1,6 +1,7 @@
 """Every float32 stencil kernel of the inner CG iteration (rcg_apply_f32,
 variants 0..RCG_STENCIL_VARIANTS-1: the row kernel, the plane ring and the
-z-marching tiles with 1, 2 or 4 lanes per CTA) against the oracle's operator
+z-marching tiles with 1, 2 or 4 lanes per CTA, in both grid orders and with
+lane groups in chunks) against the oracle's operator
 A~_s (the numerically formed Schur complement of the full finite-difference
 system, Sec. 3) on grids with one and several x-tiles, a ragged y-tile
 (80 rows in tiles of 64) and a z-chunk boundary, plus the fused p^T q.
@@ -64,3 +65,30 @@ def test_every_stencil_variant_matches_the_oracle_operator(rcg, N):
     if (N // 4) % 4 == 0:
         assert any(v >= 2 for v in ran)
     assert "stencil" in rcg.tuning_report()
+
+
+def test_chunked_grid_orders_with_many_lanes(rcg):
+    """37 columns (19 lane groups of two): the tile-first order (more than 16
+    groups) and chunks of 4, 8 and 16 groups, each with a ragged last chunk,
+    against the oracle's operator."""
+    import torch
+    wl = replace(WORKLOADS["t3d_16"], name="t3d_32c", N=32)
+    inp = make_workload(wl, with_dmu=False)
+    A, _, _ = op.assemble(inp, 1)
+    rng = np.random.default_rng(37)
+    ncols = 37
+    X = rng.standard_normal((ncols, wl.n)).astype(np.float32)
+    Y_ref = (A @ X.astype(np.float64).T).T
+    scale = abs(A).sum(axis=1).max() * np.abs(X).max()
+    with rcg.Context(wl.dim, wl.N, wl.robin_A) as ctx:
+        ctx.set_diffusion(inp["D"])
+        ctx.set_sample(1, inp["mu"][1])
+        x = torch.tensor(X, device="cuda")
+        for v in range(2, rcg.RCG_STENCIL_VARIANTS):
+            if not ctx.stencil_variant_ok(v):
+                continue
+            y = torch.full_like(x, float("nan"))
+            ctx.apply_f32(1, x, y, ncols, variant=v)
+            torch.cuda.synchronize()
+            err = np.abs(y.double().cpu().numpy() - Y_ref).max() / scale
+            assert err <= 2e-6, (v, rcg.stencil_variant_name(v), err)
