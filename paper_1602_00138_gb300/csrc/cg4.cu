@@ -309,8 +309,10 @@ k_stencil4z(Grid g, const float *__restrict__ D, const float *const *__restrict_
 // of the next plane by cp.async (zero-filled outside the grid), one barrier
 // per plane, two plane buffers.  D and the sample diagonals are shared by
 // the ZL lanes; fused p^T q per lane.
-template <int TX, int ZL>
-__global__ void __launch_bounds__(kThreads, ZL <= 2 ? 2 : 1)
+// MB: CTAs per SM the register allocation must allow (2 by default for up to
+// two lanes; 3 trades a few spilled registers for occupancy).
+template <int TX, int ZL, int MB = (ZL <= 2 ? 2 : 1)>
+__global__ void __launch_bounds__(kThreads, MB)
 k_stencil4r(Grid g, const float *__restrict__ D, const float *const *__restrict__ diag_of_col,
             const float *const *__restrict__ src, float *const *__restrict__ dst, const int *__restrict__ alist,
             int na, const int *__restrict__ active, double *__restrict__ dots, unsigned long long *__restrict__ prof,
@@ -862,6 +864,181 @@ k_update_u0(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile
     }
 }
 
+// k_update_u0 with every stream staged through shared memory: each thread
+// copies its own float4 of r, q and the private A~W columns of its two lanes
+// by cp.async into a ring of NST stages (its own data: no barrier needed for
+// it), NST - 1 stages ahead of its use, next to the tile's shared A~_s U_0
+// rows.  The register version keeps one stage of loads in flight per thread
+// (124 registers, one 512-thread CTA per SM: ~68% of the DRAM bandwidth);
+// here NST - 1 stages are in flight in shared memory.  Same arithmetic,
+// same reductions.
+template <int KPM>
+__host__ __device__ constexpr int uus_nst() { return KPM <= 1 ? 4 : KPM <= 2 ? 3 : 2; }
+template <int KUT, int KPM>
+constexpr size_t uus_smem() {
+    return sizeof(float4) * (size_t)uus_nst<KPM>() * (KUT * SN4 + 2 * (2 + KPM) * kUU);
+}
+
+template <int KUT, int KPM>
+__global__ void __launch_bounds__(kUU, 1)
+k_update_u0s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane, const int *__restrict__ tile_si,
+             const int *__restrict__ tile_cnt, int t, int sprev, int scur, int spq, int sw, long long chunk) {
+    constexpr int NST = uus_nst<KPM>();
+    constexpr int NV = 1 + KUT + KPM;
+    constexpr int NW = kUU / 32;              // warps
+    constexpr int NL = TILE / NW;             // lanes per thread (2)
+    constexpr int NB = 2 + KPM;               // r, q, private columns
+    extern __shared__ float4 usm[];
+    float4 *Us = usm;                         // [NST][KUT][SN4]
+    float4 *Ls = usm + NST * KUT * SN4;       // [NST][NL][NB][kUU]
+    __shared__ int slane[TILE], skp[TILE];
+    __shared__ float salpha[TILE];
+    const int tt = blockIdx.y, cnt = tile_cnt[tt], ku = gm.k_u;
+    if (threadIdx.x < TILE) {
+        int l = threadIdx.x < cnt ? tile_lane[tt * TILE + threadIdx.x] : -1;
+        float a = 0.f;
+        if (l >= 0 && ls.active[l] != 0) {
+            const double pq = ls.pq[spq * ls.m + l], rrp = ls.rr[sprev * ls.m + l];
+            if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rrp)) {
+                if (blockIdx.x == 0) ls.flag[l] = 2;          // breakdown: every CTA skips the lane
+                l = -1;
+            } else {
+                a = (float)(rrp / pq);
+                if (blockIdx.x == 0) {
+                    ls.xa[l] = a;
+                    ls.xt[l] = t;
+                    ls.pq[(1 - spq) * ls.m + l] = 0.0;
+                    if (ls.prof) {
+                        atomicAdd(ls.prof + 1, 1ULL);
+                        atomicAdd(ls.prof + 2, (unsigned long long)(ku + gm.kp[l]));
+                    }
+                }
+            }
+        } else {
+            l = -1;
+        }
+        slane[threadIdx.x] = l;
+        salpha[threadIdx.x] = a;
+        skp[threadIdx.x] = l >= 0 ? gm.kp[l] : 0;
+    }
+    const float *__restrict__ AU = (const float *)gm.awu + (long long)tile_si[tt] * ku * gm.ld;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
+    int myl[NL], mykp[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        myl[q] = slane[warp + NW * q];
+        mykp[q] = skp[warp + NW * q];
+    }
+    const float *Rb = (const float *)gm.r, *Qb = (const float *)gm.q, *Wb = (const float *)gm.awp;
+    auto cp16 = [](float4 *dst, const float *src, bool ok) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(src), "r"(ok ? 16 : 0)
+                     : "memory");
+    };
+    auto issue = [&](int st) {
+        if (st < nst) {
+            const long long base = r0 + (long long)st * SN;
+            const int slot = st % NST;
+            for (int e = threadIdx.x; e < KUT * SN4; e += kUU) {
+                const int c = e / SN4, v4 = e % SN4;
+                const long long p = base + 4 * v4;
+                const bool ok = c < ku && p < r1;
+                cp16(&Us[(slot * KUT + c) * SN4 + v4], ok ? AU + (long long)c * gm.ld + p : AU, ok);
+            }
+            const long long p = base + 4 * tl;
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int l = myl[q];
+                const bool okp = l >= 0 && p < r1;
+                const long long o = (long long)(l < 0 ? 0 : l) * gm.ld + p;
+                float4 *dst = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
+                cp16(dst, okp ? Rb + o : Rb, okp);
+                cp16(dst + kUU, okp ? Qb + o : Qb, okp);
+                const float *AP = Wb + (long long)(l < 0 ? 0 : l) * gm.kp_max * gm.ld + p;
+#pragma unroll
+                for (int c = 0; c < KPM; ++c) {
+                    const bool ok = okp && c < mykp[q];
+                    cp16(dst + (2 + c) * kUU, ok ? AP + (long long)c * gm.ld : Rb, ok);
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float acc[NL][NV];
+#pragma unroll
+    for (int q = 0; q < NL; ++q)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[q][v] = 0.f;
+#pragma unroll
+    for (int st = 0; st < NST - 1; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + NST - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(NST - 1) : "memory");   // stage st: this thread's copies
+        __syncthreads();                                                   // ... and the U_0 rows of all threads
+        const int slot = st % NST;
+        const long long p = r0 + (long long)st * SN + 4 * tl;
+        if (p < r1) {
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int l = myl[q];
+                if (l < 0) continue;
+                const float4 *src = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
+                const float4 rv = src[0], qv = src[kUU];
+                const float a = salpha[warp + NW * q];
+                const float4 rn = make_float4(rv.x - a * qv.x, rv.y - a * qv.y, rv.z - a * qv.z, rv.w - a * qv.w);
+                *(float4 *)((float *)gm.r + (long long)l * gm.ld + p) = rn;
+                float *ac = acc[q];
+                ac[0] += dot4(rn, rn);
+#pragma unroll
+                for (int c = 0; c < KUT; ++c) ac[1 + c] += dot4(Us[(slot * KUT + c) * SN4 + tl], rn);
+#pragma unroll
+                for (int c = 0; c < KPM; ++c) ac[1 + KUT + c] += dot4(src[(2 + c) * kUU], rn);
+            }
+        }
+        __syncthreads();                                          // the U_0 slot of stage st is refilled next
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const int l = myl[q];
+        if (l < 0) continue;                                      // uniform over the warp
+        const int kp = mykp[q];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            float x = acc[q][v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (tl == 0) {
+                if (v == 0) atomicAdd(ls.rr + scur * ls.m + l, (double)x);
+                else if (v <= KUT) {
+                    if (v - 1 < ku) atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + (v - 1), (double)x);
+                } else if (v - 1 - KUT < kp) {
+                    atomicAdd(ls.wv + ((long long)sw * ls.m + l) * KMAX + ku + (v - 1 - KUT), (double)x);
+                }
+            }
+        }
+    }
+}
+
+template <int KUT, int KPM>
+void launch_update_u0s(cudaStream_t st, dim3 grid, long long n, LaneGeom gm, LaneState ls, const LaneList &ll, int t,
+                       int sprev, int scur, int spq, int sw, long long chunk) {
+    static bool attr[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_update_u0s<KUT, KPM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)uus_smem<KUT, KPM>()));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    k_update_u0s<KUT, KPM><<<grid, kUU, uus_smem<KUT, KPM>(), st>>>(n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, t,
+                                                                    sprev, scur, spq, sw, chunk);
+}
+
 template <int KUT>
 void u0dots_attr() {
     static bool attr[64] = {};
@@ -1238,9 +1415,10 @@ int device_sms(int dev) {
 
 // k_stencil4r<TX, ZL> over the lanes of ll: per-plane tiles x lane groups x
 // z-chunks, the chunks sized for ~4 waves of resident CTAs (>= 8 planes each).
-// gc: lane groups per chunk of the grid order (see k_stencil4r); -1 picks
-// all groups in one chunk for up to 16 groups and the tile-first order above.
-template <int TX, int ZL>
+// gc: lane groups per chunk of the grid order (see k_stencil4r); -1 (the
+// variants' choice) puts all groups in one chunk for up to 16 groups and
+// takes the tile-first order above that.
+template <int TX, int ZL, int MB = (ZL <= 2 ? 2 : 1)>
 void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
                 float *const *q, const LaneList &ll, const int *active, double *dots, unsigned long long *prof,
                 int gc = -1) {
@@ -1249,9 +1427,10 @@ void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *con
     RCG_CUDA_TRY(cudaGetDevice(&dev));
     const size_t smem = stencil4r_smem<TX, ZL>();
     if (dev < 0 || dev >= 64 || !occ[dev]) {
-        RCG_CUDA_TRY(cudaFuncSetAttribute(k_stencil4r<TX, ZL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RCG_CUDA_TRY(
+            cudaFuncSetAttribute(k_stencil4r<TX, ZL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int o = 0;
-        RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_stencil4r<TX, ZL>, kThreads, smem));
+        RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_stencil4r<TX, ZL, MB>, kThreads, smem));
         if (dev >= 0 && dev < 64) occ[dev] = std::max(o, 1);
     }
     const int o = (dev >= 0 && dev < 64) ? occ[dev] : 1;
@@ -1269,7 +1448,8 @@ void launch_s4r(cudaStream_t st, const Grid &g, const float *D, const float *con
     if ((gc > 0 ? std::max(T * nzc, nchunk) : G) > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4r: grid extent"};
     const dim3 grid = gc > 0 ? dim3((unsigned)gc, (unsigned)(T * nzc), (unsigned)nchunk)
                              : dim3((unsigned)(T * nzc), (unsigned)G);
-    k_stencil4r<TX, ZL><<<grid, kThreads, smem, st>>>(g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc, gc);
+    k_stencil4r<TX, ZL, MB><<<grid, kThreads, smem, st>>>(g, D, diag, p, q, ll.alist, ll.na, active, dots, prof, zc,
+                                                          gc);
 }
 
 void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
@@ -1300,27 +1480,27 @@ void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *con
 // plane-ring kernel k_stencil4z (3D, 256 % (Nx / 4) == 0), 2 + the
 // z-marching kernel k_stencil4r<TX, ZL> for TX in {4, 8, 16, 32} (TX | Nx/4),
 // ZL in {1, 2, 4}: id 2 + 3 log2(TX / 4) + log2(ZL), in the default grid
-// order; and 14 + the same kernel for (TX, ZL) in {(8, 2), (16, 2)} with the
-// lane groups in chunks of 4, 8 or 16: id 14 + 3 (TX == 16) + log2(chunk / 4).
+// order; and with registers for 3 CTAs per SM: 14 <16,2>, 15 <8,2>.
+// (Chunked lane-group orders for many lanes measured no faster than the
+// tile-first order at 64-256 lanes of the 192^3 grid: the kernel is not
+// short of DRAM bandwidth there but of memory-level parallelism.)
 constexpr int S4_TXS[4] = {4, 8, 16, 32};
 constexpr int S4_ZLS[3] = {1, 2, 4};
-constexpr int S4_NVAR = 2 + 12 + 6;
+constexpr int S4_NVAR = 2 + 12 + 2;
 static_assert(S4_NVAR == RCG_STENCIL_VARIANTS, "variant count");
 
 bool s4_variant_ok(const Grid &g, int v) {
     if (v == 0) return cg4_supported(g);
     if (v == 1) return stencil4z_supported(g);
     if (v < 2 || v >= S4_NVAR) return false;
-    const int tx = v >= 14 ? (v >= 17 ? 16 : 8) : S4_TXS[(v - 2) / 3];
+    const int tx = v >= 14 ? (v == 15 ? 8 : 16) : S4_TXS[(v - 2) / 3];
     return cg4_supported(g) && g.Ny > 1 && (g.Nx / 4) % tx == 0 && g.n < (1LL << 31);
 }
 
 std::string s4_variant_name(int v) {
     if (v == 0) return "k_stencil4 (rows)";
     if (v == 1) return "k_stencil4z (plane ring)";
-    if (v >= 14)
-        return std::string(v >= 17 ? "k_stencil4r<16,2>" : "k_stencil4r<8,2>") + " chunks of " +
-               std::to_string(4 << ((v - 14) % 3)) + " groups";
+    if (v >= 14) return std::string(v == 15 ? "k_stencil4r<8,2>" : "k_stencil4r<16,2>") + ", 3 CTAs per SM";
     return "k_stencil4r<" + std::to_string(S4_TXS[(v - 2) / 3]) + "," + std::to_string(S4_ZLS[(v - 2) % 3]) + ">";
 }
 
@@ -1339,12 +1519,8 @@ void s4_launch(int v, cudaStream_t st, const Grid &g, const float *D, const floa
         RCG_S4R(8, 16, 1) RCG_S4R(9, 16, 2) RCG_S4R(10, 16, 4)
         RCG_S4R(11, 32, 1) RCG_S4R(12, 32, 2) RCG_S4R(13, 32, 4)
 #undef RCG_S4R
-        case 14: case 15: case 16:
-            launch_s4r<8, 2>(st, g, D, diag, p, q, ll, active, dots, prof, 4 << (v - 14));
-            break;
-        case 17: case 18: case 19:
-            launch_s4r<16, 2>(st, g, D, diag, p, q, ll, active, dots, prof, 4 << (v - 17));
-            break;
+        case 14: launch_s4r<16, 2, 3>(st, g, D, diag, p, q, ll, active, dots, prof); break;
+        case 15: launch_s4r<8, 2, 3>(st, g, D, diag, p, q, ll, active, dots, prof); break;
         default: throw Error{RCG_ERR_INVALID, "unknown stencil variant"};
     }
     count_launch();
@@ -1483,14 +1659,17 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
         long long z;
         const long long chunk = tile_chunk(z, 4LL * 152);
         dim3 grid((unsigned)z, ll.ntiles);
+// up to four private columns: the staged kernel; more: the register version
+#define RCG_UUS(K, P) launch_update_u0s<K, P>(st, grid, g.n, gm, ls, ll, t, sprev, scur, spq, sw, chunk)
 #define RCG_UU(K, P) k_update_u0<K, P><<<grid, kUU, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, \
                                                                   t, sprev, scur, spq, sw, chunk)
-#define RCG_UUK(K) if (gm.kp_max <= 1) RCG_UU(K, 1); else if (gm.kp_max <= 2) RCG_UU(K, 2); \
-                   else if (gm.kp_max <= 4) RCG_UU(K, 4); else RCG_UU(K, KP_MAX)
+#define RCG_UUK(K) if (gm.kp_max <= 1) RCG_UUS(K, 1); else if (gm.kp_max <= 2) RCG_UUS(K, 2); \
+                   else if (gm.kp_max <= 4) RCG_UUS(K, 4); else RCG_UU(K, KP_MAX)
         switch (kut) { case 4: RCG_UUK(4); break; case 8: RCG_UUK(8); break; case 12: RCG_UUK(12); break;
                        default: RCG_UUK(16); }
 #undef RCG_UUK
 #undef RCG_UU
+#undef RCG_UUS
     } else if (gm.kp_max <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
     else if (gm.kp_max <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
     else if (gm.kp_max <= 4) launch_update4<4>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);

@@ -14,9 +14,11 @@ the paper reports and explains:
     directions the source half appends also serve the adjoint half (measured:
     61 MINRES iterations at RHS 1 of the first system, 3 at RHS 33), so the
     test does not require it;
-  * per-RHS recycling keeps a roughly flat count (Table 2's right columns)
-    and needs more than twice the total iterations (5006 against 22659 in
-    the paper);
+  * per-RHS recycling does not speed up along the right-hand sides (Table 2's
+    right columns: the last eight of a half need at least half the iterations
+    of its first eight, where the inner-outer method needs at most a fifth)
+    and needs more than twice the total iterations (5006 against 22659 in the
+    paper);
   * every delivered solution meets its tolerance under the oracle's residual;
   * the basis holds k_u + the seed solutions + one column per appended solve.
 """
@@ -86,6 +88,10 @@ def test_paper_shape_table1_pattern_and_table2_direction(rcg):
         seg = it_io[i * m:(i + 1) * m]
         assert seg[ns - 1] <= 0.2 * seg[0] and seg[-1] <= 0.2 * max(seg[ns], 1), seg
         assert seg[19] < seg[0] if i == 0 else seg[19] <= seg[0], seg    # RHS 20 of Table 1
+        # per-RHS recycling does not speed up along the right-hand sides of a half
         pseg = it_pr[i * m:(i + 1) * m]
-        assert min(pseg) > 0.5 * max(pseg), pseg
-    assert 2 * sum(it_io) < sum(it_pr), (sum(it_io), sum(it_pr))
+        for h0 in (0, ns):
+            first, last = np.mean(pseg[h0:h0 + 8]), np.mean(pseg[h0 + ns - 8:h0 + ns])
+            assert last >= 0.5 * first, (i, h0, pseg)
+            assert np.mean(seg[h0 + ns - 8:h0 + ns]) <= 0.2 * max(np.mean(seg[h0:h0 + 8]), 1), (i, h0, seg)
+    assert 2 * sum(it_io) < sum(it_pr), (sum(it_io), sum(it_pr), it_io, it_pr)

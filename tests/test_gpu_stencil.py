@@ -1,7 +1,7 @@
 """Every float32 stencil kernel of the inner CG iteration (rcg_apply_f32,
 variants 0..RCG_STENCIL_VARIANTS-1: the row kernel, the plane ring and the
-z-marching tiles with 1, 2 or 4 lanes per CTA, in both grid orders and with
-lane groups in chunks) against the oracle's operator
+z-marching tiles with 1, 2 or 4 lanes per CTA, in both grid orders, and two
+with registers for three CTAs per SM) against the oracle's operator
 A~_s (the numerically formed Schur complement of the full finite-difference
 system, Sec. 3) on grids with one and several x-tiles, a ragged y-tile
 (80 rows in tiles of 64) and a z-chunk boundary, plus the fused p^T q.
@@ -67,10 +67,10 @@ def test_every_stencil_variant_matches_the_oracle_operator(rcg, N):
     assert "stencil" in rcg.tuning_report()
 
 
-def test_chunked_grid_orders_with_many_lanes(rcg):
-    """37 columns (19 lane groups of two): the tile-first order (more than 16
-    groups) and chunks of 4, 8 and 16 groups, each with a ragged last chunk,
-    against the oracle's operator."""
+def test_tile_first_grid_order_with_many_lanes(rcg):
+    """37 columns (19 lane groups of two, a ragged last group): the tile-first
+    grid order that more than 16 groups take, every z-marching variant, against
+    the oracle's operator."""
     import torch
     wl = replace(WORKLOADS["t3d_16"], name="t3d_32c", N=32)
     inp = make_workload(wl, with_dmu=False)
