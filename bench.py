@@ -69,6 +69,10 @@ SETTINGS = {
                      oracle_context="c2_3d64"),
     "c3_3d128": dict(wave=0, r_max=1024, train=0, epochs=0, sweep=0, nolearn_steps=0,
                      oracle_samples=(1,), oracle_rhs=(0, 64), base_samples=0),
+    # 16 training phantoms of 2-6 random anomalies x 128 right-hand sides =
+    # 2048 plain-method solves (waves of 10 phantoms), then Adam
+    "c4_3d128": dict(wave=0, r_max=1024, train=16, train_law="random", train_wave=10, epochs=20, sweep=0,
+                     nolearn_steps=1, oracle_samples=(1,), oracle_rhs=(0, 64), base_samples=0),
     "c2_3d64": dict(wave=0, r_max=1024, train=8, epochs=40, sweep=16, nolearn_steps=5,
                     oracle_samples=(1, 2), oracle_rhs=(0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39),
                     base_samples=0),
@@ -293,18 +297,24 @@ def run_leg(args, torch, W, ctx, steps, warmup, world=1, profile=False, clocks=N
 
 
 def train_network(ctx, W, torch, ntrain, epochs):
-    """Offline (untimed, like the seed): solve held-out parameter points with
-    pair recording, then Adam on the recorded pairs."""
+    """Offline (untimed, like the seed): solve the training phantoms with pair
+    recording, then Adam on the recorded pairs.  The phantoms are held-out
+    jitters of the workload's parameter point, or (train_law "random") fresh
+    phantoms of 2-6 random anomalies."""
     from synthetic.cnn_init import init_weights
-    from synthetic.phantom import heldout_params, pals_mu
+    from synthetic.phantom import heldout_params, pals_mu, training_params
     wl = W.wl
-    for i, p in enumerate(heldout_params(wl, ntrain, seed_offset=2000)):
+    if W.st.get("train_law") == "random":
+        ps = training_params(wl, ntrain)
+    else:
+        ps = heldout_params(wl, ntrain, seed_offset=2000)
+    for i, p in enumerate(ps):
         ctx.set_sample(wl.K + 1 + i, pals_mu(p, W.X, wl.mu_bg, W.grid))
     ctx.learn_set_weights(init_weights(0))
     ctx.learn_record(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for s0, cnt in wave_plan(ntrain, W.st["wave"]):
+    for s0, cnt in wave_plan(ntrain, W.st.get("train_wave", W.st["wave"])):
         ctx.solve_all(wl.K + s0, cnt)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -315,7 +325,8 @@ def train_network(ctx, W, torch, ntrain, epochs):
     ctx.learn_record(False)
     return dict(pairs=ctx.learn_pairs(), epochs=epochs, batch=BATCH, lr=LR, loss_first_epoch=loss0,
                 loss_last_epoch=loss, data_s=round(t1 - t0, 3), train_s=round(t2 - t1, 3),
-                training_samples=ntrain, params=len(ctx.learn_get_weights()))
+                training_samples=ntrain, params=len(ctx.learn_get_weights()),
+                training_phantoms=W.st.get("train_law", "heldout jitters of the workload's parameter point"))
 
 
 def prepare(rcg, W, opts, torch, ntrain=0, epochs=0, seed_from=None, **kw):

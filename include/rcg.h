@@ -435,13 +435,19 @@ int rcg_profile_get(rcg_ctx *c, int kernel, rcg_kprof *out);
  * A~^-1 r0; the trilinear upsampling x_hat joins that solve's private U_j
  * (never V) iff its Galerkin pivot sqrt(s/d) > tau_rank, where d = x_hat^T
  * A~ x_hat and s = d - c^T (U_j^T A~ U_j)^-1 c, c = U_j^T A~ x_hat.  Network:
- * channels 2-16-16-16-16-16-1, 3x3x3 zero-padded convolutions with bias, ReLU
- * between layers, rcg_learn_nparams() parameters laid out per layer as
- * W [Cout][Cin][27] (offset (dz+1)*9+(dy+1)*3+(dx+1)) then b [Cout].
- * Inference rounds the weights to bfloat16 (float32 sums); training keeps
- * float32 master weights (Adam, mean squared error against
- * coarse(x - x0) / max|coarse(x - x0)| of recorded solves).  All arrays
- * below are host memory owned by the caller; coarse arrays are
+ * a 3-level U-Net on the coarse grid (levels halved by 2x2x2 block means,
+ * dims ceil(G/2); nearest-cell doubling on the way up), ten 3x3x3
+ * zero-padded convolutions with bias, (Cin, Cout) = (2,16) (16,16) | (16,32)
+ * (32,32) | (32,64) | (96,32) (32,32) | (48,16) (16,16) (16,1), where layers
+ * 5 and 7 read [up(deeper level), skip of their level]; ReLU after every
+ * layer but the last.  rcg_learn_nparams() = 243,473 parameters laid out per
+ * layer as W [Cout][Cin][27] (offset (dz+1)*9+(dy+1)*3+(dx+1)) then
+ * b [Cout].  The convolutions run on the tensor cores with bfloat16 weights
+ * and activations (every ReLU and halving output rounded to bfloat16) and
+ * float32 accumulation; training keeps float32 master weights (Adam, mean
+ * squared error against coarse(x - x0) / max|coarse(x - x0)| of recorded
+ * solves) and forms the gradient from bfloat16 operands.  All arrays below
+ * are host memory owned by the caller; coarse arrays are
  * [batch][channel][Gz][Gy][Gx], x fastest. */
 int rcg_learn_nparams(void);
 /* dims[0..3] = Gx, Gy, Gz, f of the context's grid. */
@@ -456,11 +462,13 @@ int rcg_learn_pairs(rcg_ctx *c, int *npairs);
  * shuffled batches of `batch` (shuffles seeded by `seed`); *loss (may be NULL)
  * = mean loss of the last epoch.  RCG_ERR_INVALID if nothing was recorded. */
 int rcg_learn_train(rcg_ctx *c, int epochs, int batch, double lr, unsigned long long seed, double *loss);
-/* The network on B inputs in[B][2][V] -> out[B][V]; rounded != 0: bfloat16
- * weights (inference), else the float32 master weights. */
-int rcg_learn_forward(rcg_ctx *c, const float *in, int B, int rounded, float *out);
+/* The network (inference: bfloat16 weights and activations) on B inputs
+ * in[B][2][V] -> out[B][V]. */
+int rcg_learn_forward(rcg_ctx *c, const float *in, int B, float *out);
 /* Loss and its gradient grad[nparam] with respect to the master weights for
- * one batch in[B][2][V], targets tg[B][V]. */
+ * one batch in[B][2][V], targets tg[B][V] (the training pass: bfloat16
+ * operands, so both approximate those of the exact network to bfloat16
+ * precision). */
 int rcg_learn_gradient(rcg_ctx *c, const float *in, const float *tg, int B, float *grad, double *loss);
 /* Features feat[2][V] (may be NULL) and x_hat[n] (may be NULL) of one
  * residual r0[n] (float32) at sample slot s, with the bfloat16 weights. */

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "librcg.so")
-SOURCES = ["stencil.cu", "dense.cu", "small.cu", "misc.cu", "cg.cu", "cg4.cu", "api.cu", "noalloc.cu", "tc.cu", "cnn.cu", "minres.cu", "track.cu"]
+SOURCES = ["stencil.cu", "dense.cu", "small.cu", "misc.cu", "cg.cu", "cg4.cu", "api.cu", "noalloc.cu", "tc.cu", "cnn.cu", "unet.cu", "minres.cu", "track.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1042,7 +1042,7 @@ struct Engine : EngineBase {
             }
             if (use_aug) {
                 net->ensure(net->outc, net->outc_cap, (long long)na * Vc);
-                net->forward(st, net->feat, na, net->outc, true);
+                net->forward(st, net->feat, na, net->outc);
             }
         }
         if (nact) {
@@ -2930,7 +2930,7 @@ int rcg_learn_train(rcg_ctx *c, int epochs, int batch, double lr, unsigned long 
     });
 }
 
-int rcg_learn_forward(rcg_ctx *c, const float *in, int B, int rounded, float *out) {
+int rcg_learn_forward(rcg_ctx *c, const float *in, int B, float *out) {
     return guarded(c, [&]() {
         if (!in || !out || B < 1) throw Error{RCG_ERR_INVALID, "rcg_learn_forward: bad arguments"};
         Cnn &net = c->net();
@@ -2938,7 +2938,7 @@ int rcg_learn_forward(rcg_ctx *c, const float *in, int B, int rounded, float *ou
         const long long V = net.geom.V;
         float *din = c->alloc<float>((size_t)B * 2 * V), *dout = c->alloc<float>((size_t)B * V);
         c->h2d(din, in, (size_t)B * 2 * V);
-        net.forward(c->st, din, B, dout, rounded != 0);
+        net.forward(c->st, din, B, dout);
         c->d2h(out, dout, (size_t)B * V);
         c->sync();
         c->release(din);
@@ -2986,7 +2986,7 @@ int rcg_learn_predict(rcg_ctx *c, int s, const float *r0, float *feat, float *xh
         c->h2d(pm, &hm, 1);
         c->h2d(px, &hx, 1);
         net.features(c->st, pr, pm, 1, df);
-        net.forward(c->st, df, 1, dout, true);
+        net.forward(c->st, df, 1, dout);
         net.upsample(c->st, dout, px, nullptr, 1);
         if (feat) c->d2h(feat, df, (size_t)2 * V);
         if (xhat) c->d2h(xhat, dx, (size_t)c->n);

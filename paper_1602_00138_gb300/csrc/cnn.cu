@@ -6,11 +6,12 @@
 //
 //   features   block means over f^3 fine nodes: [coarse(r0) / max|coarse(r0)|,
 //              coarse(mu) / mean(mu) - 1], rounded to bfloat16
-//   network    channels 2 -> 16 -> 16 -> 16 -> 16 -> 16 -> 1, 3x3x3 zero-padded
-//              convolutions with bias, ReLU between layers; inference uses the
-//              bfloat16-rounded weights (products of bfloat16 values, float32
-//              sums), training the float32 master weights (Adam, mean squared
-//              error against coarse(g) / max|coarse(g)|)
+//   network    a 3-level U-Net (16-32-64 channels, ten 3x3x3 convolutions,
+//              skip connections) on the coarse grid, bfloat16 activations and
+//              weights on the tensor cores with float32 accumulation
+//              (unet.cu); training keeps float32 master weights (Adam, mean
+//              squared error against coarse(g) / max|coarse(g)|) and computes
+//              the gradient with bfloat16 operands
 //   upsample   trilinear interpolation from coarse cell centres to fine nodes
 //
 // Parameter layout: per layer W [Cout][Cin][27] (offset (dz+1)*9+(dy+1)*3+(dx+1))
@@ -26,12 +27,7 @@
 
 namespace rcg {
 
-const int CNN_CH[CNN_LAYERS + 1] = {2, 16, 16, 16, 16, 16, 1};
-
 namespace {
-
-constexpr int CT = 128;          // threads of the convolution kernels
-constexpr int CMAX = 16;         // widest layer
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -93,167 +89,6 @@ k_cnn_features(CnnGeom cg, const float *const *__restrict__ r0, const double *co
     for (long long v = threadIdx.x; v < cg.V; v += blockDim.x) {
         o0[v] = bf16_round(o0[v] * ia);
         o1[v] = bf16_round(o1[v] / mean - 1.0f);
-    }
-}
-
-// out[b][co][p] = bias[co] + sum_ci sum_d W[co][ci][d] in[b][ci][p + d]  (zero
-// padding), optional ReLU.  One thread per VX consecutive x nodes (Gx % VX ==
-// 0), all COUT outputs; the weights sit in shared memory as [ci][27][COUT] so
-// that a (ci, d) step reads them as float4 broadcasts and uses each for VX nodes.
-template <int COUT, int VX>
-__global__ void __launch_bounds__(CT)
-k_conv3_fwd(const float *__restrict__ in, int Cin, float *__restrict__ out, const float *__restrict__ W,
-            const float *__restrict__ bias, int relu, int Gx, int Gy, int Gz, long long V) {
-    extern __shared__ float4 wsm4[];
-    float *wsm = (float *)wsm4;
-    for (int e = threadIdx.x; e < COUT * Cin * 27; e += CT) {
-        const int co = e / (Cin * 27), rem = e % (Cin * 27);       // rem = ci*27 + d
-        wsm[rem * COUT + co] = W[e];
-    }
-    __syncthreads();
-    const long long v0 = ((long long)blockIdx.x * CT + threadIdx.x) * VX;
-    if (v0 >= V) return;
-    const int b = blockIdx.y;
-    int x, y, z;
-    coords(v0, Gx, Gy, x, y, z);
-    float acc[VX][COUT];
-#pragma unroll
-    for (int j = 0; j < VX; ++j)
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[j][co] = bias[co];
-    for (int ci = 0; ci < Cin; ++ci) {
-        const float *__restrict__ src = in + ((long long)b * Cin + ci) * V;
-        for (int dzy = 0; dzy < 9; ++dzy) {
-            const int yy = y + dzy % 3 - 1, zz = z + dzy / 3 - 1;
-            if (yy < 0 || yy >= Gy || zz < 0 || zz >= Gz) continue;
-            const float *row = src + ((long long)zz * Gy + yy) * Gx;
-            // x - 1 .. x + VX: the row segment every tap of this (dz, dy) needs
-            float seg[VX + 2];
-#pragma unroll
-            for (int j = 0; j < VX + 2; ++j) {
-                const int xx = x + j - 1;
-                seg[j] = (xx >= 0 && xx < Gx) ? row[xx] : 0.f;
-            }
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const float *w = wsm + (ci * 27 + dzy * 3 + dx) * COUT;
-                if constexpr (COUT % 4 == 0) {
-#pragma unroll
-                    for (int q = 0; q < COUT / 4; ++q) {
-                        const float4 w4 = ((const float4 *)w)[q];
-#pragma unroll
-                        for (int j = 0; j < VX; ++j) {
-                            const float val = seg[j + dx];
-                            acc[j][4 * q] += w4.x * val;
-                            acc[j][4 * q + 1] += w4.y * val;
-                            acc[j][4 * q + 2] += w4.z * val;
-                            acc[j][4 * q + 3] += w4.w * val;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int co = 0; co < COUT; ++co)
-#pragma unroll
-                        for (int j = 0; j < VX; ++j) acc[j][co] += w[co] * seg[j + dx];
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int co = 0; co < COUT; ++co)
-#pragma unroll
-        for (int j = 0; j < VX; ++j) {
-            float a = acc[j][co];
-            if (relu) a = fmaxf(a, 0.f);
-            out[((long long)b * COUT + co) * V + v0 + j] = a;
-        }
-}
-
-// din[b][ci][q] = (sum_co sum_d W[co][ci][d] dout[b][co][q - d]) * (act[b][ci][q] > 0):
-// the gradient with respect to the input of a layer whose input is a ReLU output.
-template <int CIN>
-__global__ void __launch_bounds__(CT)
-k_conv3_bwd_data(const float *__restrict__ dout, int Cout, const float *__restrict__ W,
-                 const float *__restrict__ act, float *__restrict__ din, int Gx, int Gy, int Gz, long long V) {
-    extern __shared__ float4 wsm4[];
-    float *wsm = (float *)wsm4;
-    for (int e = threadIdx.x; e < Cout * CIN * 27; e += CT) {
-        const int co = e / (CIN * 27), rem = e % (CIN * 27), ci = rem / 27, d = rem % 27;
-        wsm[(co * 27 + d) * CIN + ci] = W[e];
-    }
-    __syncthreads();
-    const long long v = (long long)blockIdx.x * CT + threadIdx.x;
-    if (v >= V) return;
-    const int b = blockIdx.y;
-    int x, y, z;
-    coords(v, Gx, Gy, x, y, z);
-    float acc[CIN];
-#pragma unroll
-    for (int ci = 0; ci < CIN; ++ci) acc[ci] = 0.f;
-    for (int co = 0; co < Cout; ++co) {
-        const float *__restrict__ src = dout + ((long long)b * Cout + co) * V;
-        for (int d = 0; d < 27; ++d) {
-            // input node v feeds output node v - d
-            const int xx = x - (d % 3 - 1), yy = y - ((d / 3) % 3 - 1), zz = z - (d / 9 - 1);
-            if (xx < 0 || xx >= Gx || yy < 0 || yy >= Gy || zz < 0 || zz >= Gz) continue;
-            const float g = src[((long long)zz * Gy + yy) * Gx + xx];
-            const float4 *w4 = (const float4 *)(wsm + (co * 27 + d) * CIN);
-#pragma unroll
-            for (int q = 0; q < CIN / 4; ++q) {
-                const float4 w = w4[q];
-                acc[4 * q] += w.x * g;
-                acc[4 * q + 1] += w.y * g;
-                acc[4 * q + 2] += w.z * g;
-                acc[4 * q + 3] += w.w * g;
-            }
-        }
-    }
-#pragma unroll
-    for (int ci = 0; ci < CIN; ++ci) {
-        const long long o = ((long long)b * CIN + ci) * V + v;
-        din[o] = act[o] > 0.f ? acc[ci] : 0.f;
-    }
-}
-
-// dW[co][ci][d] = sum_b sum_p dout[b][co][p] in[b][ci][p + d]; db[co] = sum dout.
-// One CTA per (co, ci) pair; 27 sums per thread, reduced in shared memory.
-__global__ void __launch_bounds__(256)
-k_conv3_bwd_w(const float *__restrict__ dout, int Cout, const float *__restrict__ in, int Cin,
-              float *__restrict__ dW, float *__restrict__ db, int B, int Gx, int Gy, int Gz, long long V) {
-    const int co = blockIdx.x / Cin, ci = blockIdx.x % Cin;
-    float acc[27], ab = 0.f;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) acc[d] = 0.f;
-    const long long tot = (long long)B * V;
-    for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int b = (int)(e / V);
-        const long long v = e % V;
-        int x, y, z;
-        coords(v, Gx, Gy, x, y, z);
-        const float g = dout[((long long)b * Cout + co) * V + v];
-        ab += g;
-        const float *__restrict__ src = in + ((long long)b * Cin + ci) * V;
-#pragma unroll
-        for (int d = 0; d < 27; ++d) {
-            const int xx = x + d % 3 - 1, yy = y + (d / 3) % 3 - 1, zz = z + d / 9 - 1;
-            if (xx >= 0 && xx < Gx && yy >= 0 && yy < Gy && zz >= 0 && zz < Gz)
-                acc[d] += g * src[((long long)zz * Gy + yy) * Gx + xx];
-        }
-    }
-    __shared__ float red[8][28];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 0; d < 28; ++d) {
-        float s = d < 27 ? acc[d] : ab;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp][d] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < 28) {
-        float s = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        if (threadIdx.x < 27) dW[((long long)co * Cin + ci) * 27 + threadIdx.x] = s;
-        else if (ci == 0) db[co] = s;
     }
 }
 
@@ -498,30 +333,24 @@ CnnGeom cnn_geom(const Grid &g) {
 
 int cnn_nparams() {
     int P = 0;
-    for (int l = 0; l < CNN_LAYERS; ++l) P += CNN_CH[l + 1] * CNN_CH[l] * 27 + CNN_CH[l + 1];
+    for (int l = 0; l < UNET_LAYERS; ++l) P += UNET_COUT[l] * UNET_CIN[l] * 27 + UNET_COUT[l];
     return P;
 }
 
 // ------------------------------------------------------------------ network
-Cnn::Cnn(const Grid &g) : geom(cnn_geom(g)), P(cnn_nparams()) {
+Cnn::Cnn(const Grid &g) : geom(cnn_geom(g)), P(cnn_nparams()), net(geom.Gx, geom.Gy, geom.Gz) {
+    if (net.P != P) throw Error{RCG_ERR_INVALID, "learned network: parameter layouts disagree"};
     RCG_CUDA_TRY(cudaMalloc(&theta, sizeof(float) * P));
     RCG_CUDA_TRY(cudaMalloc(&theta16, sizeof(float) * P));
     RCG_CUDA_TRY(cudaMalloc(&grad, sizeof(float) * P));
     RCG_CUDA_TRY(cudaMalloc(&adam_m, sizeof(float) * P));
     RCG_CUDA_TRY(cudaMalloc(&adam_v, sizeof(float) * P));
     RCG_CUDA_TRY(cudaMalloc(&d_loss, sizeof(double)));
-    int o = 0;
-    for (int l = 0; l < CNN_LAYERS; ++l) {
-        woff[l] = o;
-        o += CNN_CH[l + 1] * CNN_CH[l] * 27;
-        boff[l] = o;
-        o += CNN_CH[l + 1];
-    }
 }
 
 Cnn::~Cnn() {
-    for (void *p : std::vector<void *>{theta, theta16, grad, adam_m, adam_v, d_loss, act, dact0, dact1, pin, ptg,
-                                       bin, btg, d_idx, feat, outc, x0c})
+    for (void *p : std::vector<void *>{theta, theta16, grad, adam_m, adam_v, d_loss, act, pin, ptg, bin, btg, d_idx,
+                                       feat, outc, x0c})
         if (p) cudaFree(p);
 }
 
@@ -543,10 +372,13 @@ void Cnn::set_weights(cudaStream_t st, const float *host) {
     have = true;
 }
 
+// bfloat16 copy of the master weights (inference biases) and the packed
+// bfloat16 weights of the tensor-core convolutions
 void Cnn::refresh_bf16(cudaStream_t st) {
     k_round_bf16<<<(P + 255) / 256, 256, 0, st>>>(theta, theta16, P);
     count_launch();
     RCG_CHECK_LAUNCH();
+    net.pack(st, theta, false);
 }
 
 void Cnn::features(cudaStream_t st, const float *const *r0, const double *const *mu, int nl, float *out) {
@@ -556,88 +388,31 @@ void Cnn::features(cudaStream_t st, const float *const *r0, const double *const 
     RCG_CHECK_LAUNCH();
 }
 
-void Cnn::conv(cudaStream_t st, int l, const float *in, float *out, int B, bool relu, bool rounded) {
-    const int Cin = CNN_CH[l], Cout = CNN_CH[l + 1];
-    const float *Wt = (rounded ? theta16 : theta) + woff[l];
-    const float *bt = (rounded ? theta16 : theta) + boff[l];
-    const size_t sm = sizeof(float) * (size_t)Cout * Cin * 27;
-    const int vx = geom.Gx % 4 == 0 ? 4 : 1;
-    const long long thr = (geom.V + vx - 1) / vx;
-    dim3 grid((unsigned)((thr + CT - 1) / CT), (unsigned)B);
-#define RCG_CONV(CO, VXT) k_conv3_fwd<CO, VXT><<<grid, CT, sm, st>>>(in, Cin, out, Wt, bt, relu ? 1 : 0, geom.Gx, \
-                                                                     geom.Gy, geom.Gz, geom.V)
-    if (Cout == 16) {
-        if (vx == 4) RCG_CONV(16, 4);
-        else RCG_CONV(16, 1);
-    } else {
-        if (vx == 4) RCG_CONV(1, 4);
-        else RCG_CONV(1, 1);
-    }
-#undef RCG_CONV
-    count_launch();
-    RCG_CHECK_LAUNCH();
-}
-
-// Inference on B inputs [B][2][V] -> out [B][V], bfloat16 weights, in chunks
-// of lanes so that the two ping-pong activation buffers stay small.
-void Cnn::forward(cudaStream_t st, const float *in, int B, float *out, bool rounded) {
+// Inference on B inputs [B][2][V] -> out [B][V] with the bfloat16 weights,
+// in chunks of items whose activations fit in about 2 GB.
+void Cnn::forward(cudaStream_t st, const float *in, int B, float *out) {
     const long long V = geom.V;
-    const int chunk = (int)std::max<long long>(1, std::min<long long>(B, (64LL << 20) / (V * CMAX)));
-    ensure(dact0, dact0_cap, (long long)chunk * CMAX * V);
-    ensure(dact1, dact1_cap, (long long)chunk * CMAX * V);
+    const int chunk = (int)std::max<long long>(1, std::min<long long>(B, (2LL << 30) / net.bytes_per_item()));
     for (int b0 = 0; b0 < B; b0 += chunk) {
         const int nb = std::min(chunk, B - b0);
-        const float *cur = in + (long long)b0 * CNN_CH[0] * V;
-        for (int l = 0; l < CNN_LAYERS; ++l) {
-            float *dst = l == CNN_LAYERS - 1 ? out + (long long)b0 * V : (l % 2 == 0 ? dact0 : dact1);
-            conv(st, l, cur, dst, nb, l < CNN_LAYERS - 1, rounded);
-            cur = dst;
-        }
+        net.forward(st, theta16, in + (long long)b0 * 2 * V, nb, out + (long long)b0 * V);
     }
+    if (net.error(st)) throw Error{RCG_ERR_TIMEOUT, "learned network: a tensor-core wait ran out"};
 }
 
-// One training batch: forward with the master weights keeping every layer's
-// output, mean squared error, backward into `grad`.  Returns nothing; the loss
-// is accumulated into d_loss.
+// One training batch: the forward pass with the master weights rounded to
+// bfloat16 (master biases), the mean squared error and its gradient, the
+// backward pass into `grad`; the loss is accumulated into d_loss.
 void Cnn::forward_backward(cudaStream_t st, const float *in, const float *tg, int B) {
     const long long V = geom.V;
-    long long tot = 0;
-    long long aoff[CNN_LAYERS + 1];
-    aoff[0] = 0;
-    for (int l = 0; l < CNN_LAYERS; ++l) aoff[l + 1] = aoff[l] + (long long)B * CNN_CH[l + 1] * V;
-    tot = aoff[CNN_LAYERS];
-    ensure(act, act_cap, tot);
-    ensure(dact0, dact0_cap, (long long)B * CMAX * V);
-    ensure(dact1, dact1_cap, (long long)B * CMAX * V);
-    const float *cur = in;
-    for (int l = 0; l < CNN_LAYERS; ++l) {
-        conv(st, l, cur, act + aoff[l], B, l < CNN_LAYERS - 1, false);
-        cur = act + aoff[l];
-    }
-    // d(out) from the loss
-    const float *outp = act + aoff[CNN_LAYERS - 1];
-    k_mse<<<(int)std::min<long long>((B * V + 255) / 256, 1024), 256, 0, st>>>(outp, tg, dact0, (long long)B * V, d_loss);
+    ensure(act, act_cap, 2LL * B * V);
+    float *outp = act, *dout = act + (long long)B * V;
+    net.pack(st, theta, true);
+    net.forward(st, theta, in, B, outp);
+    k_mse<<<(int)std::min<long long>((B * V + 255) / 256, 1024), 256, 0, st>>>(outp, tg, dout, (long long)B * V, d_loss);
     count_launch();
     RCG_CHECK_LAUNCH();
-    float *g = dact0, *gnext = dact1;
-    for (int l = CNN_LAYERS - 1; l >= 0; --l) {
-        const int Cin = CNN_CH[l], Cout = CNN_CH[l + 1];
-        const float *lin = l == 0 ? in : act + aoff[l - 1];
-        k_conv3_bwd_w<<<Cout * Cin, 256, 0, st>>>(g, Cout, lin, Cin, grad + woff[l], grad + boff[l], B, geom.Gx,
-                                                   geom.Gy, geom.Gz, V);
-        count_launch();
-        RCG_CHECK_LAUNCH();
-        if (l > 0) {
-            const size_t sm = sizeof(float) * (size_t)Cout * Cin * 27;
-            dim3 grid((unsigned)((V + CT - 1) / CT), (unsigned)B);
-            set_smem(k_conv3_bwd_data<16>, sm);
-            k_conv3_bwd_data<16><<<grid, CT, sm, st>>>(g, Cout, theta + woff[l], act + aoff[l - 1], gnext, geom.Gx,
-                                                         geom.Gy, geom.Gz, V);
-            count_launch();
-            RCG_CHECK_LAUNCH();
-            std::swap(g, gnext);
-        }
-    }
+    net.backward(st, dout, B, grad);
 }
 
 double Cnn::gradient(cudaStream_t st, const float *in, const float *tg, int B) {
@@ -646,6 +421,7 @@ double Cnn::gradient(cudaStream_t st, const float *in, const float *tg, int B) {
     double h = 0.0;
     RCG_CUDA_TRY(cudaMemcpyAsync(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     RCG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (net.error(st)) throw Error{RCG_ERR_TIMEOUT, "learned network: a tensor-core wait ran out"};
     return h;
 }
 
@@ -721,6 +497,7 @@ double Cnn::train(cudaStream_t st, int epochs, int B, double lr, unsigned long l
         RCG_CUDA_TRY(cudaStreamSynchronize(st));
         last = nb ? h / nb : 0.0;
     }
+    if (net.error(st)) throw Error{RCG_ERR_TIMEOUT, "learned network: a tensor-core wait ran out"};
     refresh_bf16(st);
     have = true;
     return last;

@@ -2,6 +2,7 @@
 // kernels' host-side launchers.  See include/rcg.h for the public ABI.
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -203,10 +204,64 @@ struct CnnGeom {
     int Gx, Gy, Gz;      // coarse grid
     long long V;         // coarse nodes
 };
-constexpr int CNN_LAYERS = 6;
-extern const int CNN_CH[CNN_LAYERS + 1];
 CnnGeom cnn_geom(const Grid &g);
 int cnn_nparams();
+
+// The network itself: a 3-level U-Net (16-32-64 channels, ten 3x3x3
+// convolutions) on the coarse grid, bfloat16 activations on the tensor
+// cores (unet.cu).  Layer l reads UNET_CIN[l] channels (stacked
+// [up(deeper), skip] for layers 5 and 7) and writes UNET_COUT[l].
+constexpr int UNET_LAYERS = 10;
+extern const int UNET_CIN[UNET_LAYERS];
+extern const int UNET_COUT[UNET_LAYERS];
+
+class UNet {
+  public:
+    UNet(int Gx, int Gy, int Gz);
+    ~UNet();
+    UNet(const UNet &) = delete;
+    UNet &operator=(const UNet &) = delete;
+    // bfloat16 copies of the weights in the kernels' layouts (forward, and the
+    // transposed layout of the backward pass when `backward`)
+    void pack(cudaStream_t st, const float *theta, bool backward);
+    // in[B][2][V0] -> out[B][V0] (float32); biases read from theta
+    void forward(cudaStream_t st, const float *theta, const float *in, int B, float *out);
+    // grad[P] (zeroed here) from d loss / d out [B][V0], after forward() on the same batch
+    void backward(cudaStream_t st, const float *dout, int B, float *grad);
+    // RCG_ERR_TIMEOUT if a tensor-core wait ran out since the last call (synchronises)
+    int error(cudaStream_t st);
+    // device bytes of the activations of one item
+    long long bytes_per_item() const { return 2LL * (80 * V[0] + 144 * V[1] + 96 * V[2]) + 12 * 128; }
+
+    int P = 0;
+    int woff[UNET_LAYERS], boff[UNET_LAYERS];
+
+  private:
+    enum { A_IN, A_A0, A_S0, A_P0, A_A1, A_S1, A_P1, A_A2, A_A3, A_A4, A_A5, A_A6, A_N };
+    struct Layer {
+        int lvl, Cin, Cout, NP, NPb, Cg, nsrc;
+        int sC[2] = {0, 0}, sreal[2] = {0, 0}, sup[2] = {0, 0}, sk0[2] = {0, 0}, sci0[2] = {0, 0};
+        int nchunk, nchunk_b;
+        long long pack_f, pack_b;
+    };
+    void layout(int B);
+    void grow(void *&p, long long &cap, long long bytes);
+    void conv(cudaStream_t st, int l, const __nv_bfloat16 *s0, const __nv_bfloat16 *s1, const float *bias, bool relu,
+              __nv_bfloat16 *y, float *yf, const __nv_bfloat16 *mask, int B, bool backward = false,
+              const __nv_bfloat16 *wp_override = nullptr);
+    void down(cudaStream_t st, const __nv_bfloat16 *x, int C, int lvl, int B, __nv_bfloat16 *y);
+    const __nv_bfloat16 *act(int id) const;
+    __nv_bfloat16 *actw(int id);
+
+    int G[3][3];
+    long long V[3];
+    Layer lay[UNET_LAYERS];
+    long long aoff[A_N];
+    int cur_B = 0;
+    void *wpf = nullptr, *wpb = nullptr, *abuf = nullptr, *gbuf = nullptr, *fbuf = nullptr;
+    long long abuf_cap = 0, gbuf_cap = 0, fbuf_cap = 0;
+    int *d_err = nullptr;
+};
 
 // The network, its Adam state, the recorded training pairs and work buffers
 // (device memory owned here).
@@ -220,7 +275,7 @@ class Cnn {
     void set_weights(cudaStream_t st, const float *host);
     void refresh_bf16(cudaStream_t st);
     void features(cudaStream_t st, const float *const *r0, const double *const *mu, int nl, float *out);
-    void forward(cudaStream_t st, const float *in, int B, float *out, bool rounded);
+    void forward(cudaStream_t st, const float *in, int B, float *out);
     double gradient(cudaStream_t st, const float *in, const float *tg, int B);
     void add_pairs(cudaStream_t st, const float *feat, const float *tgt, int cnt);
     double train(cudaStream_t st, int epochs, int B, double lr, unsigned long long seed);
@@ -237,16 +292,15 @@ class Cnn {
     float *theta = nullptr, *theta16 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     double *d_loss = nullptr;
     long long t_adam = 0;
-    int woff[CNN_LAYERS], boff[CNN_LAYERS];
+    UNet net;
     // work buffers of the solver integration (grown on demand)
     float *feat = nullptr, *outc = nullptr, *x0c = nullptr;
     long long feat_cap = 0, outc_cap = 0, x0c_cap = 0;
 
   private:
-    void conv(cudaStream_t st, int l, const float *in, float *out, int B, bool relu, bool rounded);
     void forward_backward(cudaStream_t st, const float *in, const float *tg, int B);
-    float *act = nullptr, *dact0 = nullptr, *dact1 = nullptr;
-    long long act_cap = 0, dact0_cap = 0, dact1_cap = 0;
+    float *act = nullptr;
+    long long act_cap = 0;
     float *pin = nullptr, *ptg = nullptr;
     long long pair_cap = 0;
     float *bin = nullptr, *btg = nullptr;

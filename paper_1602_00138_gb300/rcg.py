@@ -121,7 +121,7 @@ def load(path=LIB_PATH):
         "rcg_learn_record": (I, [P, I]),
         "rcg_learn_pairs": (I, [P, C.POINTER(I)]),
         "rcg_learn_train": (I, [P, I, I, D, C.c_ulonglong, C.POINTER(D)]),
-        "rcg_learn_forward": (I, [P, P, I, I, P]),
+        "rcg_learn_forward": (I, [P, P, I, P]),
         "rcg_learn_gradient": (I, [P, P, P, I, P, C.POINTER(D)]),
         "rcg_learn_predict": (I, [P, I, P, P, P]),
         "rcg_full_eval": (I, [P, I, I, P, P, P]),
@@ -479,11 +479,11 @@ class Context:
         self._check(self.L.rcg_learn_train(self.h, epochs, batch, lr, seed, C.byref(loss)))
         return loss.value
 
-    def learn_forward(self, inp, rounded=True):
+    def learn_forward(self, inp):
         x = np.ascontiguousarray(inp, dtype=np.float32)
         B = x.shape[0]
         out = np.zeros((B,) + x.shape[2:], dtype=np.float32)
-        self._check(self.L.rcg_learn_forward(self.h, _ptr(x), B, 1 if rounded else 0, _ptr(out)))
+        self._check(self.L.rcg_learn_forward(self.h, _ptr(x), B, _ptr(out)))
         return out
 
     def learn_gradient(self, inp, tg):

@@ -86,6 +86,9 @@ WORKLOADS = {
     "c2_3d64": Workload("c2_3d64", 3, 64, 4, (8, 4), (8, 4), 5, (1e-8,)),
     # 3D 128^3, 64 + 64, 10 samples, tolerances alternating 1e-8 / 1e-6
     "c3_3d128": Workload("c3_3d128", 3, 128, 4, (8, 8), (8, 8), 10, (1e-8, 1e-6)),
+    # 3D 128^3 learned augmentation: 64 + 64, 10 samples, tol 1e-8; the
+    # network trains on plain-method solves at training_params phantoms
+    "c4_3d128": Workload("c4_3d128", 3, 128, 4, (8, 8), (8, 8), 10, (1e-8,)),
     # 3D 192^3, 128 + 128, 20 samples, 8 anomalies
     "c5_3d192": Workload("c5_3d192", 3, 192, 8, (16, 8), (16, 8), 20, (1e-8,)),
     # the paper's experiment shape: 2D 201^2, 32 + 32, K* = 3, tol 1e-7 (Sec. 6)
@@ -295,3 +298,17 @@ def heldout_params(wl: Workload, count=1, seed_offset=1000):
     p0 = seed_params(wl, rng)
     rng2 = np.random.default_rng(wl.seed + seed_offset)
     return sample_params(wl, p0, rng2, count)
+
+
+def training_params(wl: Workload, count, seed_offset=5000, n_min=2, n_max=6):
+    """Phantoms of the learned augmentation's training set: each draws its
+    own number of anomalies (uniform in n_min..n_max) and fresh centres,
+    widths and absorptions from the seed point's law (seed_params), so they
+    are not jitters of the workload's phantom.  Returns a list of parameter
+    vectors (lengths differ)."""
+    rng = np.random.default_rng(wl.seed + seed_offset)
+    out = []
+    for _ in range(count):
+        na = int(rng.integers(n_min, n_max + 1))
+        out.append(seed_params(replace(wl, n_anom=na), rng))
+    return out

@@ -1,13 +1,22 @@
-"""GPU tests of the learned augmentation (rcg_learn_*), against the oracle's
-network (oracle/cnn.py) on the same seeded weights and inputs.
+"""GPU tests of the learned augmentation (rcg_learn_*): the U-Net on the
+tensor cores against the oracle's network (oracle/cnn.py) on the same seeded
+weights and inputs.
 
-* forward pass: bfloat16 (inference) and float32 (training) weights, outputs
-  within float32 rounding of the float64 oracle;
+* forward pass (inference: bfloat16 weights and activations, float32 sums on
+  the tensor cores) against the oracle's inference network (the same
+  bfloat16 roundings, float64 sums): the sums differ in rounding only, which
+  can flip an activation's bfloat16 rounding by one ulp (2^-8 relative) on
+  isolated nodes, and the later layers spread each flip over their receptive
+  field (measured: at most 7e-3 of the largest output magnitude, 9e-4 in the
+  mean on a 21^3 coarse grid); the outputs must agree to 2e-2 and 3e-3 (an
+  indexing or layout fault gives errors of order one), on grids with whole
+  and ragged tiles, odd level dims and a 2D grid;
 * gradient: the loss and its gradient with respect to the master weights
-  against the oracle's loss and central finite differences of it;
+  (the training pass, bfloat16 operands) against the oracle's exact loss and
+  central finite differences of it, to bfloat16 precision;
 * features and x_hat: coarse features equal the oracle's up to isolated
   one-ulp bfloat16 rounding flips (float32 vs float64 block means), x_hat the
-  oracle's upsampling of the network output;
+  oracle's upsampling of the oracle network's output on those features;
 * the solver with the augmentation: pairs are recorded, training lowers the
   loss, and every solve still meets its tolerance by the oracle's residual,
   with the learned column accepted into U_j.
@@ -38,7 +47,7 @@ def _weights(seed):
     rng = np.random.default_rng(50 + seed)
     # non-zero biases so that they are exercised
     o = 0
-    for ci, co in zip(cnn.CHANNELS[:-1], cnn.CHANNELS[1:]):
+    for ci, co in cnn.LAYERS:
         o += co * ci * 27
         th[o:o + co] = 0.05 * rng.standard_normal(co)
         o += co
@@ -58,24 +67,41 @@ def _ctx(rcg, name, **opts):
     return inp, ctx
 
 
-def test_forward_matches_oracle(rcg):
-    inp, ctx = _ctx(rcg, "t3d_32")
+def _forward_errors(out, ref):
+    """Largest and mean absolute difference relative to max|ref|."""
+    sc = np.max(np.abs(ref))
+    d = np.abs(out - ref)
+    return np.max(d) / sc, np.mean(d) / sc
+
+
+@pytest.mark.parametrize("name,geom", [("t3d_32", (8, 8, 8, 4)), ("t3d_21", (21, 21, 21, 1)),
+                                       ("t2d_37", (37, 1, 37, 1))])
+def test_forward_matches_oracle(rcg, name, geom):
+    inp, ctx = _ctx(rcg, name)
     try:
         Gx, Gy, Gz, f = ctx.learn_geometry()
-        assert (Gx, Gy, Gz, f) == (8, 8, 8, 4)
+        assert (Gx, Gy, Gz, f) == geom
         theta = _weights(1)
         ctx.learn_set_weights(theta)
         rng = np.random.default_rng(11)
         x = cnn.bf16(rng.standard_normal((3, 2, Gz, Gy, Gx)))
-        for rounded in (True, False):
-            out = ctx.learn_forward(x, rounded=rounded)
-            for b in range(3):
-                ref = cnn.forward(theta, x[b], round_weights=rounded)
-                err = np.max(np.abs(out[b] - ref)) / np.max(np.abs(ref))
-                assert err < 2e-5, (rounded, b, err)
+        out = ctx.learn_forward(x)
+        for b in range(3):
+            ref = cnn.forward(theta, x[b])
+            emax, emean = _forward_errors(out[b], ref)
+            print(name, b, emax, emean)
+            assert emax < 2e-2 and emean < 3e-3, (name, b, emax, emean)
         assert np.array_equal(ctx.learn_get_weights(), theta)
     finally:
         ctx.close()
+
+
+def _layer_offsets():
+    o, out = 0, []
+    for ci, co in cnn.LAYERS:
+        out.append((o, o + co * ci * 27))      # weights, biases
+        o += co * ci * 27 + co
+    return out
 
 
 def test_gradient_matches_finite_differences_of_the_oracle_loss(rcg):
@@ -90,17 +116,34 @@ def test_gradient_matches_finite_differences_of_the_oracle_loss(rcg):
         loss, g = ctx.learn_gradient(x, t)
         th64 = theta.astype(np.float64)
         ref_loss = cnn.loss(th64, list(x), list(t))
-        assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+        # the training pass computes with bfloat16 operands: its loss is the
+        # exact network's to bfloat16 precision
+        assert abs(loss - ref_loss) <= 2e-2 * ref_loss, (loss, ref_loss)
         P = cnn.n_params()
-        idx = np.unique(np.concatenate([rng.integers(0, P, 40), [P - 1, P - 2, 864, 880]]))
+        # random entries plus, per layer, a weight and a bias; the skip parts
+        # of the stacked inputs of layers 5 and 7; the two real input channels of layer 0
+        offs = _layer_offsets()
+        picks = [rng.integers(0, P, 24)]
+        for l, (wo, bo) in enumerate(offs):
+            picks.append([wo + rng.integers(0, bo - wo), bo])
+        ci5, ci7 = cnn.LAYERS[5][0], cnn.LAYERS[7][0]
+        picks.append([offs[5][0] + (3 * ci5 + 70) * 27 + 13, offs[7][0] + (2 * ci7 + 40) * 27 + 4])
+        picks.append([offs[0][0] + (5 * 2 + 1) * 27 + 22, P - 1])
+        idx = np.unique(np.concatenate(picks))
         gmax = np.max(np.abs(g))
+        fds = []
         for i in idx:
             h = 1e-4 * max(1.0, abs(th64[i]))
             tp, tm = th64.copy(), th64.copy()
             tp[i] += h
             tm[i] -= h
-            fd = (cnn.loss(tp, list(x), list(t)) - cnn.loss(tm, list(x), list(t))) / (2 * h)
-            assert abs(g[i] - fd) <= 2e-3 * gmax + 1e-3 * abs(fd), (i, g[i], fd)
+            fds.append((cnn.loss(tp, list(x), list(t)) - cnn.loss(tm, list(x), list(t))) / (2 * h))
+        fds = np.array(fds)
+        gi = g[idx].astype(np.float64)
+        err = np.abs(gi - fds)
+        print("gradient: max err / gmax", np.max(err) / gmax, "cos", gi @ fds / np.linalg.norm(gi) / np.linalg.norm(fds))
+        assert np.all(err <= 3e-2 * gmax + 3e-2 * np.abs(fds)), list(zip(idx, gi, fds))
+        assert gi @ fds >= 0.995 * np.linalg.norm(gi) * np.linalg.norm(fds)
     finally:
         ctx.close()
 
@@ -124,7 +167,8 @@ def test_features_and_prediction_match_oracle(rcg):
         assert np.count_nonzero(diff) <= max(2, feat.size // 500)
         out = cnn.forward(theta, feat.astype(np.float64))
         ref_x = cnn.upsample(out, dims, f)
-        assert np.max(np.abs(xhat - ref_x)) <= 2e-5 * np.max(np.abs(ref_x))
+        emax, emean = _forward_errors(xhat, ref_x)
+        assert emax < 2e-2 and emean < 3e-3, (emax, emean)
     finally:
         ctx.close()
 

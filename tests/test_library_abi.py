@@ -31,6 +31,23 @@ def test_every_declared_symbol_is_exported(lib):
     assert sorted(rcg.EXPORTED) == names
 
 
+def test_binding_argument_counts_match_the_header(lib):
+    """Every binding signature takes as many arguments as the header's
+    prototype declares (a mismatch would pass garbage through ctypes)."""
+    txt = open(os.path.join(ROOT, "include", "rcg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = dict(re.findall(r"\b(rcg_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S))
+    checked = 0
+    for name in _declared():
+        if name not in protos:
+            continue
+        params = protos[name].strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, (name, params)
+        checked += 1
+    assert checked >= 40
+
+
 def test_host_only_entry_points(lib):
     from paper_1602_00138_gb300 import rcg
     o = rcg.default_options()
