@@ -49,6 +49,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "c5_3d192"
 SECOND = "c3_3d128"
+LEARNED = "c4_3d128"
 METRIC = "full-order solves/s at relres 1e-8: learned+mixed batched RCG vs plain FP64 RCG"
 CONTENDER = dict(precision=1, order=1, tau_rank=1e-6, learned=1)      # learned + mixed, batched waves
 MIXED_PLAIN = dict(precision=1, order=1, tau_rank=1e-6)               # the same without the network
@@ -61,7 +62,8 @@ MAX_TRAIN = 32
 # reduced-model sweep, steps of the leg without the network, the CPU oracle's
 # bounded sample (samples, right-hand sides) and the FP64 baseline's samples.
 SETTINGS = {
-    "c5_3d192": dict(wave=1, r_max=2048, train=2, epochs=6, sweep=4, nolearn_steps=5,
+    "c5_3d192": dict(wave=1, r_max=2048, train=8, train_law="random", train_wave=1, epochs=10, sweep=4,
+                     nolearn_steps=5,
                      oracle_samples=(1,), oracle_rhs=(0, 128), base_samples=1,
                      oracle_unavailable="the oracle cannot seed 7,077,888 unknowns within a bench run: its ARPACK "
                                         "eigensolver for the 10 smallest eigenvectors of A~_0 (Sec. 4.2.2) took "
@@ -72,7 +74,7 @@ SETTINGS = {
     # 16 training phantoms of 2-6 random anomalies x 128 right-hand sides =
     # 2048 plain-method solves (waves of 10 phantoms), then Adam
     "c4_3d128": dict(wave=0, r_max=1024, train=16, train_law="random", train_wave=10, epochs=20, sweep=0,
-                     nolearn_steps=1, oracle_samples=(1,), oracle_rhs=(0, 64), base_samples=0),
+                     nolearn_steps=1, oracle_samples=(1,), oracle_rhs=(0, 64), base_samples=1),
     "c2_3d64": dict(wave=0, r_max=1024, train=8, epochs=40, sweep=16, nolearn_steps=5,
                     oracle_samples=(1, 2), oracle_rhs=(0, 1, 2, 3, 4, 5, 6, 7, 32, 33, 34, 35, 36, 37, 38, 39),
                     base_samples=0),
@@ -93,6 +95,11 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--second", default=SECOND, help="second configuration measured in the same run ('' skips it)")
+    ap.add_argument("--learned-mode", default="start", choices=["deflate", "start"],
+                    help="the learned column deflates every CG iteration (deflate) or enters the first Galerkin "
+                         "projection only (start)")
+    ap.add_argument("--learned-config", default=LEARNED,
+                    help="configuration of the learned-augmentation comparison measured in the same run ('' skips it)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 sequential and no-network legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--ncu-region", action="store_true",
@@ -116,7 +123,9 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
-    return ap.parse_args(argv)
+    a = ap.parse_args(argv)
+    CONTENDER["learned_mode"] = 1 if a.learned_mode == "start" else 0
+    return a
 
 
 # --------------------------------------------------------------------- clocks
@@ -595,7 +604,41 @@ def run_ours(args, rank, world, torch):
     # ---- the second configuration: mixed batched waves (no network)
     if args.second and rank == 0:
         res["second"] = second_config(args, rcg, torch, dev, peak, peak_source)
+    # ---- the learned-augmentation configuration: learned + mixed against mixed alone
+    if args.learned_config and rank == 0 and args.learned_config != args.workload:
+        res["learned_cfg"] = learned_config(args, rcg, torch, dev)
     return res
+
+
+def learned_config(args, rcg, torch, dev):
+    """The learned-augmentation configuration (default 3D 128^3, 64 + 64
+    right-hand sides x 10 samples in one wave, tol 1e-8): the network trained
+    (untimed) on 2048 plain-method solves at 16 random 2-6-anomaly phantoms,
+    then learned + mixed against mixed batched RCG alone from the same seed,
+    each timed over the same steps (a step = every sample in one wave)."""
+    import numpy as np
+    W4 = Workload(args.learned_config, torch, dev)
+    st = W4.st
+    ctx4, seed4, learn4 = prepare(rcg, W4, CONTENDER, torch, st["train"], st["epochs"])
+    steps4 = max(1, min(args.steps, 2))
+    leg4 = run_leg(args, torch, W4, ctx4, steps4, 1)
+    ctx_p, _, _ = prepare(rcg, W4, MIXED_PLAIN, torch, seed_from=ctx4)
+    legp = run_leg(args, torch, W4, ctx_p, steps4, 1)
+    v4 = leg4["solves"] / (leg4["ms"] / 1e3)
+    vp = legp["solves"] / (legp["ms"] / 1e3)
+    out = {**workload_config(args.learned_config), "steps": steps4,
+           "learned_mixed": {"value": round(v4, 2), "unit": "solves/s", "ms_per_step": round(leg4["ms"] / steps4, 3),
+                             "mean_cg_iters": float(np.mean([s["iters"] for s in leg4["stats"]])),
+                             "augmented": int(sum(s["augmented"] for s in leg4["stats"])), "rank_V": ctx4.rank()},
+           "mixed_without_learning": {"value": round(vp, 2), "unit": "solves/s",
+                                      "ms_per_step": round(legp["ms"] / steps4, 3),
+                                      "mean_cg_iters": float(np.mean([s["iters"] for s in legp["stats"]])),
+                                      "rank_V": ctx_p.rank()},
+           "learned_over_plain": round(v4 / vp, 4), "learning": learn4, "seed_s_untimed": round(seed4, 3)}
+    ctx_p.close()
+    ctx4.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def alg1_compare(args, rcg, W, torch):
@@ -776,7 +819,9 @@ def contender_line(args, world, res, cpu):
                              f"V frozen within a wave"),
                    "step": "one wave (check, deflated CG, ordered append) + Psi_r and J at a held-out point; "
                            "the timed region starts from the seed state and V grows across steps",
-                   "tau_rank": CONTENDER["tau_rank"], "learned": True, "learning": res["learn"],
+                   "tau_rank": CONTENDER["tau_rank"], "learned": True,
+                   "learned_mode": "first projection only" if CONTENDER.get("learned_mode") else "deflates every iteration",
+                   "learning": res["learn"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"working set > L2 ({cfg['solves_per_step']} lanes x {wl.n} nodes x 24 B = "
                          f"{cfg['solves_per_step'] * wl.n * 24 / 1e9:.1f} GB)",
@@ -795,6 +840,7 @@ def contender_line(args, world, res, cpu):
         "rom_sweep": res.get("rom_sweep"),
         "alg1_vs_alg2": res.get("alg1"),
         "second_config": res.get("second"),
+        "learned_config": res.get("learned_cfg"),
     }
 
 

@@ -97,6 +97,8 @@ extern "C" {
  * tolerances and Algorithm 2's decisions do not change under that scaling);
  * rcg_solution_get, rcg_full_eval and the reduced model use the sample's
  * weights.  Runs the scalar CG path (the float4 stencils share one D). */
+#define RCG_LEARN_DEFLATE 0
+#define RCG_LEARN_START   1
 #define RCG_D_FIXED       0
 #define RCG_D_TRACKS_MU   1
 #define RCG_SEQUENTIAL  0   /* the paper's order: V grows between RHS          */
@@ -149,6 +151,13 @@ typedef struct {
     int    d_model;       /* RCG_D_FIXED (default) | RCG_D_TRACKS_MU        */
     double mu_s_prime;    /* reduced scattering mu_s' of RCG_D_TRACKS_MU
                              (> 0; default 1)                                */
+    int    learned_mode;  /* with `learned`: RCG_LEARN_DEFLATE (default) keeps
+                             the network's column in U_j for every CG
+                             iteration of the solve (augmented CG);
+                             RCG_LEARN_START uses it in the first Galerkin
+                             projection x0 += W (W^T A~ W)^-1 W^T r only and
+                             then iterates deflated by U_j alone (no
+                             per-iteration cost)                             */
 } rcg_options;
 
 typedef struct {
@@ -167,7 +176,7 @@ typedef struct {
  * k_cap 256, r_max 2048, max_samples 32, maxit 20000, inner_eta 1e-4,
  * check_refine 0, keep_solutions 0, seed_degree 0 (automatic), learned 0,
  * wave_rhs 0, check RCG_GALERKIN, inner RCG_CG, recycle RCG_INNER_OUTER,
- * d_model RCG_D_FIXED, mu_s_prime 1. */
+ * d_model RCG_D_FIXED, mu_s_prime 1, learned_mode RCG_LEARN_DEFLATE. */
 void rcg_options_default(rcg_options *o);
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a

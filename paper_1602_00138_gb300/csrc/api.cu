@@ -305,13 +305,13 @@ struct Engine : EngineBase {
     const float **d_lr = nullptr;
     const double **d_lm = nullptr, **d_lx = nullptr;
     float **d_ldst = nullptr;
-    int *d_arow = nullptr, *d_aug_l = nullptr, *d_kept = nullptr;
+    int *d_arow = nullptr, *d_aug_l = nullptr, *d_kept = nullptr, *d_drop = nullptr;
     double *d_cd = nullptr;
     int lp_cap = 0;
     void ensure_learn(int m) {
         if (m <= lp_cap) return;
         for (void *p : std::vector<void *>{(void *)d_lr, (void *)d_lm, (void *)d_lx, (void *)d_ldst, (void *)d_arow,
-                                           (void *)d_aug_l, (void *)d_kept, (void *)d_cd})
+                                           (void *)d_aug_l, (void *)d_kept, (void *)d_drop, (void *)d_cd})
             c->release(p);
         lp_cap = m;
         d_lr = c->alloc<const float *>(m);
@@ -321,6 +321,7 @@ struct Engine : EngineBase {
         d_arow = c->alloc<int>(m);
         d_aug_l = c->alloc<int>(m);
         d_kept = c->alloc<int>(m);
+        d_drop = c->alloc<int>(m);
         d_cd = c->alloc<double>((size_t)m * (KMAX + 1));
     }
     // rom workspace
@@ -1016,6 +1017,7 @@ struct Engine : EngineBase {
             if (!seed_mode && c->cnn && (c->cnn->record || (c->opt.learned && c->cnn->have))) net = c->cnn.get();
         }
         const bool use_aug = net && c->opt.learned && net->have;
+        bool drop_first = false;       // RCG_LEARN_START: the first start drops the learned columns
         std::vector<int> alanes;
         if (net && nact) {
             for (int l = 0; l < m; ++l)
@@ -1195,6 +1197,13 @@ struct Engine : EngineBase {
                 c->d2h(kh.data(), d_kept, nq);
                 c->sync();
                 for (int i = 0; i < nq; ++i) out[aug_l[i]].augmented = kh[i];
+                if (c->opt.learned_mode == RCG_LEARN_START) {
+                    // the kept columns serve the first projection only
+                    std::vector<int> dm(m, 0);
+                    for (int i = 0; i < nq; ++i) dm[aug_l[i]] = kh[i];
+                    c->h2d(d_drop, dm.data(), m);
+                    drop_first = true;
+                }
             }
             // thresholds and the first (re)start
             std::vector<double> thr(m, 0.0);
@@ -1251,14 +1260,18 @@ struct Engine : EngineBase {
                 for (int l = 0; l < m; ++l) sel[l] = act[l] && !done[l];
                 build_list_of(sel);
             };
-            // (re)start the lanes flagged in `mask_h` (also uploaded to d_mask)
+            // (re)start the lanes flagged in `mask_h` (also uploaded to d_mask);
+            // the first start drops the learned columns after its projection
+            // under RCG_LEARN_START
             auto restart = [&](const std::vector<int> &mask_h) {
+                int *drop = drop_first ? d_drop : nullptr;
+                drop_first = false;
                 if (vec) {
                     lane_zero(st, ls, d_mask);
                     build_list_of(mask_h);
-                    cg_restart4(st, g, gm, ls, ll, t, mu_f, beta_f);
+                    cg_restart4(st, g, gm, ls, ll, t, mu_f, beta_f, drop);
                 } else {
-                    cg_restart<T>(st, g, gm, ls, t, d_mask);
+                    cg_restart<T>(st, g, gm, ls, t, d_mask, drop);
                 }
             };
             if (use_mres) {
@@ -2274,6 +2287,7 @@ int rcg_create(rcg_ctx **out, const rcg_grid *gr, const rcg_options *o, void *st
         ((c->opt.check == RCG_MR || c->opt.inner == RCG_MINRES) && c->opt.precision != RCG_FP64) ||
         (c->opt.recycle == RCG_PER_RHS && c->opt.inner != RCG_MINRES) ||
         (c->opt.d_model != RCG_D_FIXED && c->opt.d_model != RCG_D_TRACKS_MU) ||
+        (c->opt.learned_mode != RCG_LEARN_DEFLATE && c->opt.learned_mode != RCG_LEARN_START) ||
         (c->opt.d_model == RCG_D_TRACKS_MU && !(c->opt.mu_s_prime > 0 && std::isfinite(c->opt.mu_s_prime)))) {
         delete c;
         return RCG_ERR_INVALID;

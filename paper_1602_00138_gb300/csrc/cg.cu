@@ -323,7 +323,7 @@ void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *di
 // the current iterate), set x = W mu0, r -= A W mu0 (mu0 = Ginv W^T r),
 // rr[t mod 3] = r^T r and p = r - W Ginv (A W)^T r.
 template <typename T>
-void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t, const int *mask) {
+void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t, const int *mask, int *drop) {
     dim3 grid(grid_x(g.n, ls.nl), ls.nl);
     const int scur = t % 3, snext = (t + 1) % 3, sprev = (t + 2) % 3;
     const int sw = t % 2, sA = (t + 1) % 2;
@@ -336,11 +336,50 @@ void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t
     k_restart_project<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, mask, sA);
     count_launch();
     RCG_CHECK_LAUNCH();
+    // the learned column served the projection only (RCG_LEARN_START)
+    drop_last_private(st, ls, const_cast<int *>(gm.kp), drop, ls.nl);
     k_lane_dots<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, mask, 1, sw, 1, scur);    // rr, (A W)^T r -> wv[sw]
     count_launch();
     RCG_CHECK_LAUNCH();
     // the direction kernel zeroes wv[1 - sw] == wv[sA] (the scratch above) and rr[snext]
     k_direction<T><<<grid, kThreads, 0, st>>>(g.n, gm, ls, mask, sprev, scur, snext, sw, 1);
+    count_launch();
+    RCG_CHECK_LAUNCH();
+}
+
+// Lanes with drop[l] != 0 give up their last private deflation column (the
+// learned column, which the augmentation bordered last): kdef and kp fall
+// by one, and the lane's inverse H = (W^T A~ W)^-1 loses that column: with
+// k the new count, the inverse of the leading k x k block of W^T A~ W is
+// H11 - h12 h21 / h22 (the bordering step undone).  drop[l] is cleared.
+// One CTA per lane.
+__global__ void k_drop_last_private(LaneState ls, int *kp, int *drop) {
+    const int l = blockIdx.x;
+    if (!drop[l]) return;
+    const int k1 = ls.kdef[l];
+    if (k1 > 0 && kp[l] > 0) {
+        double *H = ls.gw + (long long)l * KMAX * KMAX;
+        const int k = k1 - 1;
+        const double hkk = H[k + (long long)k * KMAX];
+        // entries (i, j < k) read column k and row k, which no thread writes
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            const int i = e % k, j = e / k;
+            H[i + (long long)j * KMAX] -= H[i + (long long)k * KMAX] * H[k + (long long)j * KMAX] / hkk;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (k1 > 0 && kp[l] > 0) {
+            --ls.kdef[l];
+            --kp[l];
+        }
+        drop[l] = 0;
+    }
+}
+
+void drop_last_private(cudaStream_t st, LaneState ls, int *kp, int *drop, int m) {
+    if (!drop || m <= 0) return;
+    k_drop_last_private<<<m, 128, 0, st>>>(ls, kp, drop);
     count_launch();
     RCG_CHECK_LAUNCH();
 }
@@ -355,7 +394,7 @@ template void cg_iteration<double>(cudaStream_t, const Grid &, const double *, c
                                    const double *const *, double *const *, LaneGeom, LaneState, int, KTimer *);
 template void cg_iteration<float>(cudaStream_t, const Grid &, const float *, const float *const *,
                                   const float *const *, float *const *, LaneGeom, LaneState, int, KTimer *);
-template void cg_restart<double>(cudaStream_t, const Grid &, LaneGeom, LaneState, int, const int *);
-template void cg_restart<float>(cudaStream_t, const Grid &, LaneGeom, LaneState, int, const int *);
+template void cg_restart<double>(cudaStream_t, const Grid &, LaneGeom, LaneState, int, const int *, int *);
+template void cg_restart<float>(cudaStream_t, const Grid &, LaneGeom, LaneState, int, const int *, int *);
 
 }  // namespace rcg

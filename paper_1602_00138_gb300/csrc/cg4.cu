@@ -1693,7 +1693,7 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
 // (Re)start of the lanes of ll (float32, Nx % 4 == 0) at iteration number t;
 // the same steps as cg_restart in cg.cu.  k_lane_zero has run for these lanes.
 void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, LaneList ll, int t, float *mu,
-                 float *beta) {
+                 float *beta, int *drop) {
     if (ll.na <= 0) return;
     const int scur = t % 3, snext = (t + 1) % 3, sprev = (t + 2) % 3;
     const int sw = t % 2, sA = (t + 1) % 2;
@@ -1725,6 +1725,8 @@ void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, Lane
 #undef RCG_PJ
     count_launch();
     RCG_CHECK_LAUNCH();
+    // the learned column served the projection only (RCG_LEARN_START)
+    drop_last_private(st, ls, const_cast<int *>(gm.kp), drop, ls.nl);
     // rr and (A W)^T r -> rr[scur], wv[sw]
     if (gm.k_u > 0) { RCG_U0S(0, sw); count_launch(); RCG_CHECK_LAUNCH(); }
 #undef RCG_U0S

@@ -455,7 +455,7 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
                    const float *const *p_ptr, float *const *q_ptr, LaneGeom gm, LaneState ls, LaneList ll, int t,
                    float *mu, float *beta, KTimer *kt);
 void cg_restart4(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, LaneList ll, int t, float *mu,
-                 float *beta);
+                 float *beta, int *drop = nullptr);
 void lane_zero(cudaStream_t st, LaneState ls, const int *mask);
 // q = A~_s p on ncols float32 columns with the inner iteration's stencil
 // variant v (-1: the autotuned choice; see cg4.cu), p^T q added into
@@ -491,7 +491,10 @@ void cg_iteration(cudaStream_t st, const Grid &g, const T *D, const T *const *di
                   const T *const *p_ptr, T *const *q_ptr, LaneGeom gm, LaneState ls, int t,
                   KTimer *kt = nullptr);
 template <typename T>
-void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t, const int *mask);
+void cg_restart(cudaStream_t st, const Grid &g, LaneGeom gm, LaneState ls, int t, const int *mask,
+                int *drop = nullptr);
+// Lanes with drop[l] != 0 lose their last private deflation column (kdef, kp - 1); drop is cleared.
+void drop_last_private(cudaStream_t st, LaneState ls, int *kp, int *drop, int m);
 template <typename T>
 void gather_cols(cudaStream_t st, long long n, const T *const *src, T *dst, long long ld, int count);
 

@@ -30,6 +30,7 @@ RCG_GALERKIN, RCG_MR = 0, 1
 RCG_CG, RCG_MINRES = 0, 1
 RCG_INNER_OUTER, RCG_PER_RHS = 0, 1
 RCG_D_FIXED, RCG_D_TRACKS_MU = 0, 1
+RCG_LEARN_DEFLATE, RCG_LEARN_START = 0, 1
 
 EXPORTED = [
     "rcg_options_default", "rcg_create", "rcg_destroy", "rcg_last_error", "rcg_strerror",
@@ -61,7 +62,7 @@ class Options(C.Structure):
                 ("check_refine", C.c_int), ("keep_solutions", C.c_int), ("seed_degree", C.c_int),
                 ("spin_budget", C.c_longlong), ("learned", C.c_int), ("wave_rhs", C.c_int),
                 ("check", C.c_int), ("inner", C.c_int), ("recycle", C.c_int),
-                ("d_model", C.c_int), ("mu_s_prime", C.c_double)]
+                ("d_model", C.c_int), ("mu_s_prime", C.c_double), ("learned_mode", C.c_int)]
 
 
 class Stat(C.Structure):

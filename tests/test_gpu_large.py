@@ -14,6 +14,15 @@ alternating; mixed precision, all 1280 lanes in one wave, V <= 1024):
     hold those samples' solutions to their tolerance, and the reduced transfer
     function's error is second order in it (Sec. 3.4).
 
+3D 128^3 learned augmentation (64 + 64 right-hand sides, samples 1-2, tol
+1e-8, learned + mixed in one wave; the U-Net trained on 512 plain-method
+solves at four random 2-6-anomaly phantoms):
+  * every solve delivered, sampled solutions within tolerance by the
+    oracle's residual, the learned column accepted into U_j;
+  * fewer mean CG iterations than mixed batched RCG without the network from
+    the same seed;
+  * Psi_r at samples 1 and 2 equals that run's to 1e-6.
+
 3D 192^3 (128 + 128, samples 1-2 of 20, waves of one sample, V <= 2048):
   * every solve delivered; seed rank k_u + 256;
   * Psi_r at samples 1 and 2 equals the plain float64 run's to 1e-6 (the
@@ -23,7 +32,8 @@ import numpy as np
 import pytest
 
 from oracle import operator as op, rom
-from synthetic.phantom import make_workload
+from synthetic.cnn_init import init_weights
+from synthetic.phantom import make_workload, pals_mu, training_params
 
 pytestmark = pytest.mark.gpu
 
@@ -106,6 +116,65 @@ def test_128_cubed_batched_wave(rcg):
             assert _rel(Pm, P) <= 1e-6, (smp, _rel(Pm, P))
     finally:
         ctx.close()
+
+
+def test_128_cubed_learned_augmentation(rcg):
+    inp = make_workload("c4_3d128", K=2, with_dmu=False)
+    wl = inp["wl"]
+    ntrain = 4
+    ctx = rcg.Context(wl.dim, wl.N, wl.robin_A, k_u=wl.k_u, max_samples=3 + ntrain, precision=rcg.RCG_MIXED,
+                      order=rcg.RCG_WAVE, tau_rank=1e-6, r_max=1024, keep_solutions=1, learned=1)
+    ctx.set_diffusion(inp["D"])
+    ctx.set_sources_detectors(inp["src_ij"], inp["det_ij"])
+    ctx.set_tolerances(inp["tol"])
+    for s in range(3):
+        ctx.set_sample(s, inp["mu"][s])
+    plain = None
+    try:
+        X = np.asarray(inp["X"])
+        grid = (wl.N, wl.h, wl.dim)
+        for i, p in enumerate(training_params(wl, ntrain)):
+            ctx.set_sample(3 + i, pals_mu(p, X, wl.mu_bg, grid))
+        ctx.seed(0, None)
+        ctx.learn_set_weights(init_weights(0))
+        ctx.learn_record(True)
+        stats, rc = ctx.solve_all(3, ntrain)
+        assert rc == 0
+        assert ctx.learn_pairs() == ntrain * wl.nrhs
+        first = ctx.learn_train(1, batch=16, lr=1e-3, seed=1)
+        last = ctx.learn_train(7, batch=16, lr=1e-3, seed=2)
+        assert last < first
+        ctx.learn_record(False)
+        ctx.reset_to_seed()
+        stats, rc = ctx.solve_all(1, 2)
+        assert rc == 0 and len(stats) == 2 * wl.nrhs
+        for st in stats:
+            assert st["relres"] <= inp["tol"][st["rhs"]] * 1.0001, st
+        assert sum(st["augmented"] for st in stats) > wl.nrhs
+        for smp in (1, 2):
+            A, Bt, Ct = op.assemble(inp, smp)
+            B = np.hstack([Bt, Ct])
+            Xs = ctx.solutions(smp)
+            for j in (0, wl.nsrc - 1, wl.nsrc, wl.nrhs - 1):
+                rr = np.linalg.norm(B[:, j] - A @ Xs[:, j]) / np.linalg.norm(B[:, j])
+                assert rr <= inp["tol"][j] * 1.05, (smp, j, rr)
+            del Xs, A
+        plain = _ctx(rcg, inp, 2, precision=rcg.RCG_MIXED, order=rcg.RCG_WAVE, tau_rank=1e-6, r_max=1024)
+        plain.seed_copy(ctx)
+        stats_p, rc = plain.solve_all(1, 2)
+        assert rc == 0
+        it_l = np.mean([st["iters"] for st in stats])
+        it_p = np.mean([st["iters"] for st in stats_p])
+        print("mean CG iterations: learned", it_l, "plain", it_p)
+        assert it_l < it_p, (it_l, it_p)
+        for smp in (1, 2):
+            P_l = ctx.rom_eval(inp["mu"][smp])[0]
+            P_p = plain.rom_eval(inp["mu"][smp])[0]
+            assert _rel(P_l, P_p) <= 1e-6, (smp, _rel(P_l, P_p))
+    finally:
+        ctx.close()
+        if plain is not None:
+            plain.close()
 
 
 def test_192_cubed_waves_of_one_sample(rcg):

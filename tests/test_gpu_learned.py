@@ -173,8 +173,10 @@ def test_features_and_prediction_match_oracle(rcg):
         ctx.close()
 
 
-def test_learned_solves_meet_tolerance_and_training_lowers_the_loss(rcg):
-    inp, ctx = _ctx(rcg, "t3d_32", learned=1, tau_rank=1e-6)
+@pytest.mark.parametrize("mode", ["deflate", "start"])
+def test_learned_solves_meet_tolerance_and_training_lowers_the_loss(rcg, mode):
+    lm = rcg.RCG_LEARN_START if mode == "start" else rcg.RCG_LEARN_DEFLATE
+    inp, ctx = _ctx(rcg, "t3d_32", learned=1, tau_rank=1e-6, learned_mode=lm)
     try:
         wl = inp["wl"]
         U0, As, Bt, Ct = oracle_seed_inputs("t3d_32")
