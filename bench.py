@@ -113,6 +113,9 @@ def parse_args(argv=None):
     ap.add_argument("--stencil", type=int, default=0, metavar="LANES",
                     help="time the inner iteration's float32 stencil kernels alone on LANES columns of the "
                          "workload's grid (every variant the grid supports; one JSON line)")
+    ap.add_argument("--unet", type=int, default=0, metavar="ITEMS",
+                    help="time the learned network alone on ITEMS inputs of the workload's coarse grid: inference "
+                         "and one training gradient of 16 items (tensor-core convolutions; one JSON line)")
     ap.add_argument("--rom-sweep", type=int, default=None,
                     help="held-out parameter points for the reduced-model sweep (0 skips it)")
     ap.add_argument("--rom-batch", type=int, default=8, help="points per rcg_rom_eval_batch call in the sweep")
@@ -405,7 +408,7 @@ def roofline(W, prof, peak, peak_source):
         ach = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
         return {"kernel": names[k], "achieved": round(ach, 1), "frac": round(ach / peak, 4),
                 "launches": P["launches"], "avg_launch_us": round(per_launch_s * 1e6, 2),
-                "alg_bytes_per_launch": round(per_launch_bytes)}
+                "alg_bytes_per_launch": round(per_launch_bytes), "lane_units": P["lane_units"]}
 
     kdom = max((0, 1, 2, 4), key=lambda k: prof[k]["ms"])
     d = entry(kdom)
@@ -421,8 +424,10 @@ def roofline(W, prof, peak, peak_source):
             i = src.index("\n" + ent["kernel"] + "(")
             text = src[src.rindex("__global__", 0, i):src.index("\n}\n", i) + 3]
             if ent.get("kernel_sha256") == hashlib.sha256(text.encode()).hexdigest():
-                P = prof[kdom]
-                traffic = round(ent["dram_bytes_per_lane_node"] * n * P["lane_units"] / max(P["launches"], 1))
+                # the capture's DRAM bytes over its algorithmic bytes (both
+                # proportional to the lane-node units a launch processes),
+                # scaled to this run's launches
+                traffic = round(ent["dram_over_alg"] * d["alg_bytes_per_launch"])
     out = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": "GB/s",
            "frac": d["frac"], "traffic": traffic, "peak_source": peak_source, "launches": d["launches"],
            "avg_launch_us": d["avg_launch_us"], "alg_bytes_per_launch": d["alg_bytes_per_launch"],
@@ -905,8 +910,53 @@ def stencil_bench(args, torch):
                           "tuner": rcg.tuning_report()}))
 
 
+def unet_bench(args, torch):
+    """The learned network on `args.unet` random inputs of the workload's
+    coarse grid: inference (rcg_learn_forward) and one training gradient of
+    16 items (rcg_learn_gradient), wall time around each call after a warm-up
+    call (the calls copy their host inputs and outputs); flops count the ten
+    convolutions' multiply-adds."""
+    import numpy as np
+    import __graft_entry__ as g
+    g.build()
+    from paper_1602_00138_gb300 import rcg
+    from oracle.cnn import LAYERS, half_dims
+    from synthetic.cnn_init import init_weights
+    from synthetic.phantom import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    B = args.unet
+    with rcg.Context(wl.dim, wl.N, wl.robin_A) as ctx:
+        Gx, Gy, Gz, f = ctx.learn_geometry()
+        ctx.learn_set_weights(init_weights(0))
+        rng = np.random.default_rng(0)
+        x = rng.standard_normal((B, 2, Gz, Gy, Gx)).astype(np.float32)
+        t = rng.standard_normal((16, Gz, Gy, Gx)).astype(np.float32)
+        ctx.learn_forward(x[:1])
+        ctx.learn_gradient(x[:1], t[:1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.learn_forward(x)
+        t1 = time.perf_counter()
+        ctx.learn_gradient(x[:16], t[:16])
+        t2 = time.perf_counter()
+    G0 = (Gz, Gy, Gx)
+    G1 = half_dims(G0)
+    G2 = half_dims(G1)
+    V = [int(np.prod(G0)), int(np.prod(G1)), int(np.prod(G2))]
+    lvl = (0, 0, 1, 1, 2, 1, 1, 0, 0, 0)
+    flops = sum(2 * 27 * ci * co * V[lvl[l]] for l, (ci, co) in enumerate(LAYERS))
+    print(json.dumps({"unet": f"coarse {Gx}x{Gy}x{Gz} (f = {f})", "items": B,
+                      "forward_ms": round((t1 - t0) * 1e3, 2), "gradient16_ms": round((t2 - t1) * 1e3, 2),
+                      "forward_tflops_incl_copies": round(B * flops / (t1 - t0) / 1e12, 2),
+                      "gflop_per_item": round(flops / 1e9, 3)}))
+
+
 def main():
     args = parse_args()
+    if args.unet > 0:
+        import torch
+        unet_bench(args, torch)
+        return
     if args.products:
         import torch
         products_bench(torch, args.products_shapes)

@@ -1168,6 +1168,7 @@ struct Engine : EngineBase {
             gm.ld = ld;
             gm.k_u = ku;
             gm.kp_max = std::max(kps, 1);
+            gm.kp_sel = gm.kp_max;
             gm.x = xc; gm.r = rv; gm.p = pv; gm.q = qv;
             gm.wu = V; gm.awu = au0; gm.awp = awp; gm.wpp = d_wpp;
             gm.si = d_si; gm.kp = d_kp;
@@ -1352,6 +1353,9 @@ struct Engine : EngineBase {
                 }
             } else {
             restart(act);
+            // RCG_LEARN_START: the learned columns are gone after the first
+            // start, so the iterations take the templates of the other columns
+            if (c->opt.learned_mode == RCG_LEARN_START) gm.kp_sel = std::max(kp_max, 1);
             if (vec) build_list();
             while (true) {
                 if (graph) {

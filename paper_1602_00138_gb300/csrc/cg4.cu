@@ -1247,9 +1247,9 @@ void dir_launch(cudaStream_t st, long long n, const LaneGeom &gm, const LaneStat
 template <int KUT>
 void dir_launch_kp(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const LaneList &ll,
                    const float *mu, const float *beta, int it) {
-    if (gm.kp_max <= 1) dir_launch<KUT, 1>(st, n, gm, ls, ll, mu, beta, it);
-    else if (gm.kp_max <= 2) dir_launch<KUT, 2>(st, n, gm, ls, ll, mu, beta, it);
-    else if (gm.kp_max <= 4) dir_launch<KUT, 4>(st, n, gm, ls, ll, mu, beta, it);
+    if (gm.kp_sel <= 1) dir_launch<KUT, 1>(st, n, gm, ls, ll, mu, beta, it);
+    else if (gm.kp_sel <= 2) dir_launch<KUT, 2>(st, n, gm, ls, ll, mu, beta, it);
+    else if (gm.kp_sel <= 4) dir_launch<KUT, 4>(st, n, gm, ls, ll, mu, beta, it);
     else dir_launch<KUT, KP_MAX>(st, n, gm, ls, ll, mu, beta, it);
 }
 
@@ -1663,16 +1663,16 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
 #define RCG_UUS(K, P) launch_update_u0s<K, P>(st, grid, g.n, gm, ls, ll, t, sprev, scur, spq, sw, chunk)
 #define RCG_UU(K, P) k_update_u0<K, P><<<grid, kUU, 0, st>>>(g.n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, \
                                                                   t, sprev, scur, spq, sw, chunk)
-#define RCG_UUK(K) if (gm.kp_max <= 1) RCG_UUS(K, 1); else if (gm.kp_max <= 2) RCG_UUS(K, 2); \
-                   else if (gm.kp_max <= 4) RCG_UUS(K, 4); else RCG_UU(K, KP_MAX)
+#define RCG_UUK(K) if (gm.kp_sel <= 1) RCG_UUS(K, 1); else if (gm.kp_sel <= 2) RCG_UUS(K, 2); \
+                   else if (gm.kp_sel <= 4) RCG_UUS(K, 4); else RCG_UU(K, KP_MAX)
         switch (kut) { case 4: RCG_UUK(4); break; case 8: RCG_UUK(8); break; case 12: RCG_UUK(12); break;
                        default: RCG_UUK(16); }
 #undef RCG_UUK
 #undef RCG_UU
 #undef RCG_UUS
-    } else if (gm.kp_max <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
-    else if (gm.kp_max <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
-    else if (gm.kp_max <= 4) launch_update4<4>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    } else if (gm.kp_sel <= 1) launch_update4<1>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else if (gm.kp_sel <= 2) launch_update4<2>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
+    else if (gm.kp_sel <= 4) launch_update4<4>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
     else launch_update4<KP_MAX>(st, g.n, gm, ls, ll, t, sprev, scur, spq, sw);
     count_launch();
     RCG_CHECK_LAUNCH();

@@ -130,6 +130,7 @@ constexpr int KPT = KP_MAX + 1;
 struct LaneGeom {
     long long ld;
     int k_u, kp_max;
+    int kp_sel;             // bound on every lane's current private count (<= kp_max): picks the kernels' templates
     void *x, *r, *p, *q;
     const void *wu, *awu, *awp;
     const void *const *wpp;
