@@ -241,10 +241,12 @@ int rcg_apply_noalloc(rcg_ctx *c, int s, int prec, const void *x_dev, void *y_de
  * (the one the solver uses for this grid and column count), or one of the
  * RCG_STENCIL_VARIANTS kernels named by rcg_stencil_variant_name (0: rows,
  * 1: plane ring, 2..13: z-marching tiles, 14..15: z-marching tiles with
- * registers for three CTAs per SM).  RCG_ERR_INVALID if the variant
- * does not support the grid.  Parity / timing entry; returns after the
- * context's stream has finished. */
-#define RCG_STENCIL_VARIANTS 16
+ * registers for three CTAs per SM, 16..18: planes of 64 x 16 or 64 x 8
+ * tiles copied by TMA into a shared-memory ring, Nx % 64 == 0).
+ * RCG_ERR_INVALID if the variant does not support the grid;
+ * RCG_ERR_TIMEOUT if a TMA copy's wait ran out.  Parity / timing entry;
+ * returns after the context's stream has finished. */
+#define RCG_STENCIL_VARIANTS 19
 int rcg_apply_f32(rcg_ctx *c, int s, int variant, const float *x_dev, float *y_dev, int ncols, double *dots_dev);
 /* Name of stencil variant v (NULL if out of range); 1 if the variant runs on
  * the grid of c, else 0. */

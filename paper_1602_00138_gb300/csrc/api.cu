@@ -1234,6 +1234,13 @@ struct Engine : EngineBase {
             const int chunk = graph ? 6 : (m > 1 ? 8 : 12);
             CgGraph cgg(st);
             LaneList ll{d_alist, 0, d_tlane, d_tsi, d_tcnt, 0};
+            if (mixed) {                   // the lanes' p columns and the sample diagonals (TMA stencil)
+                ll.pbase = (const float *)pv;
+                ll.pld = ld;
+                ll.pcols = m;
+                ll.gbase = c->diag32;
+                ll.gslots = c->opt.max_samples;
+            }
             auto build_list_of = [&](const std::vector<int> &sel) {
                 std::vector<int> al, tl, tsi, tcnt;
                 for (int l = 0; l < m; ++l)
@@ -1384,6 +1391,8 @@ struct Engine : EngineBase {
                 c->d2h(iters_h.data(), ls.iters, m);
                 c->sync();
                 c->ktimer.harvest();
+                if (vec && stencil_take_error(st))
+                    throw Error{RCG_ERR_TIMEOUT, "stencil: a TMA copy's wait ran out"};
                 std::vector<int> F;
                 bool force = false;
                 for (int l = 0; l < m; ++l) {
@@ -2487,8 +2496,10 @@ int rcg_apply_f32(rcg_ctx *c, int s, int variant, const float *x_dev, float *y_d
         c->h2d(a, hs.data(), ncols); c->h2d(b, hd.data(), ncols); c->h2d(gp, hg.data(), ncols);
         c->h2d(dl, lanes.data(), ncols); c->h2d(da, act.data(), ncols);
         if (dd) RCG_CUDA_TRY(cudaMemsetAsync(dd, 0, sizeof(double) * ncols, c->st));
-        stencil4_apply(c->st, c->g, c->D32, gp, a, b, ncols, dl, da, dots_dev ? dots_dev : dd, variant);
+        stencil4_apply(c->st, c->g, c->D32, gp, a, b, ncols, dl, da, dots_dev ? dots_dev : dd, variant, x_dev, c->n,
+                       c->diag32, c->opt.max_samples);
         c->sync();
+        if (stencil_take_error(c->st)) throw Error{RCG_ERR_TIMEOUT, "rcg_apply_f32: a TMA copy's wait ran out"};
         for (void *q : std::vector<void *>{(void *)a, (void *)b, (void *)gp, (void *)dl, (void *)da, (void *)dd})
             c->release(q);
         return RCG_OK;

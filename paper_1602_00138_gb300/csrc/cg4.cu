@@ -23,6 +23,8 @@
 // to 32 active lanes of one sample slot.
 #include "common.cuh"
 
+#include <cuda.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -1476,6 +1478,307 @@ void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *con
                                                                                active, dots, prof, zc);
 }
 
+// ---------------------------------------------------------------- TMA stencil
+// k_stencil4t<ZL, TY>: q = A~ p for ZL lanes per CTA over a tile of 64 x TY
+// nodes (x, y), marching in z over a chunk of planes.  Every plane of the
+// tile (with a one-node halo in y, four floats in x so that the copy starts
+// on a 16-byte boundary) arrives in shared memory by one TMA tensor copy per
+// array (the lanes' p, D, and the lanes' sample diagonals without halo) on a
+// ring of US4 stages with an mbarrier each; the copy of plane z + 3 is issued
+// as soon as plane z - 1's stage is free, so two planes per CTA are in
+// flight without holding registers.  Out-of-grid planes and rows arrive as
+// zeros (the Dirichlet ghosts; the Robin faces are in the diagonal).  Thread
+// (tx, ty) computes the float4 column x = 4 tx of row ty for every lane from
+// shared memory, stores q and adds p^T q.  Every mbarrier wait is bounded:
+// on timeout the CTA records the error in g_s4t_err, waits (bounded) for the
+// copies it issued and returns.
+constexpr int US4 = 4;                  // stages of the plane ring
+constexpr int T4X = 64;                 // tile width in nodes (16 float4 columns)
+constexpr int T4W = T4X + 8;            // copied row width: x0 - 4 .. x0 + 67
+constexpr long long S4T_SPIN = 1LL << 22;
+__device__ int g_s4t_err;
+
+__host__ __device__ constexpr int s4t_align(int b) { return (b + 127) / 128 * 128; }
+template <int TY> __host__ __device__ constexpr int s4t_pbox() { return s4t_align(T4W * (TY + 2) * 4); }
+template <int TY> __host__ __device__ constexpr int s4t_gbox() { return s4t_align(T4X * TY * 4); }
+template <int ZL, int TY> __host__ __device__ constexpr int s4t_stage() {
+    return (ZL + 1) * s4t_pbox<TY>() + ZL * s4t_gbox<TY>();
+}
+template <int ZL, int TY> constexpr size_t s4t_smem() { return (size_t)US4 * s4t_stage<ZL, TY>() + 1024; }
+
+__device__ __forceinline__ uint32_t s4_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool s4_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma4(uint32_t dst, const CUtensorMap *tm, int x, int y, int z, int w, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(z), "r"(w), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap *tm, int x, int y, int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+
+template <int ZL, int TY>
+__global__ void __launch_bounds__(16 * TY)
+k_stencil4t(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_d,
+            const __grid_constant__ CUtensorMap tm_g, Grid g, const float *gbase,
+            const float *const *__restrict__ diag_of_col, float *const *__restrict__ dst,
+            const int *__restrict__ alist, int na, const int *__restrict__ active, double *__restrict__ dots,
+            unsigned long long *__restrict__ prof, int zc) {
+    constexpr int NT = 16 * TY, PB = s4t_pbox<TY>(), GB = s4t_gbox<TY>(), SB = s4t_stage<ZL, TY>();
+    extern __shared__ __align__(1024) char s4t_raw[];
+    __shared__ __align__(8) unsigned long long mbar[US4];
+    __shared__ int s_ok;
+    char *sm = (char *)(((uintptr_t)s4t_raw + 1023) & ~(uintptr_t)1023);
+    const int xtiles = g.Nx / T4X, ytiles = (g.Ny + TY - 1) / TY;
+    const int tz = blockIdx.x, lg = blockIdx.y;
+    const int xt = tz % xtiles, rest = tz / xtiles, yt = rest % ytiles, zb = rest / ytiles;
+    const int z0 = zb * zc, z1 = min(z0 + zc, g.Nz);
+    int c[ZL], slot[ZL];
+    bool on[ZL];
+    int non = 0;
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        const int li = lg * ZL + i;
+        c[i] = li < na ? alist[li] : -1;
+        on[i] = c[i] >= 0 && active[c[i]] != 0;
+        slot[i] = on[i] ? (int)((diag_of_col[c[i]] - gbase) / g.ld) : 0;
+        non += on[i];
+    }
+    if (non == 0 || z0 >= g.Nz) return;                // uniform over the CTA
+    if (prof && tz == 0 && threadIdx.x == 0) atomicAdd(prof, (unsigned long long)non);
+    const int x0 = xt * T4X, y0 = yt * TY;
+    // bytes of one plane's copies (the lanes that are on, D, their diagonals)
+    const uint32_t tx_bytes = (uint32_t)(non * (T4W * (TY + 2) * 4 + T4X * TY * 4) + T4W * (TY + 2) * 4);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < US4; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s4_u32(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_ok = 1;
+    }
+    __syncthreads();
+    // plane j of the ring = grid plane z0 - 1 + j, in stage j mod US4; planes
+    // z0 - 1 .. z1 are needed
+    const int nplanes = z1 - z0 + 2;
+    auto issue = [&](int j) {                           // thread 0 only
+        const int z = z0 - 1 + j;
+        char *st = sm + (j % US4) * SB;
+        const uint32_t mb = s4_u32(&mbar[j % US4]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx_bytes) : "memory");
+#pragma unroll
+        for (int i = 0; i < ZL; ++i)
+            if (on[i]) {
+                tma4(s4_u32(st + i * PB), &tm_p, x0 - 4, y0 - 1, z, c[i], mb);
+                tma4(s4_u32(st + (ZL + 1) * PB + i * GB), &tm_g, x0, y0, z, slot[i], mb);
+            }
+        tma3(s4_u32(st + ZL * PB), &tm_d, x0 - 4, y0 - 1, z, mb);
+    };
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int j = 0; j < US4 && j < nplanes; ++j) issue(j);
+    }
+    int issued = min(US4, nplanes);                      // planes thread 0 issued (the same count in every thread)
+    int waited = 0;                                      // planes waited for
+    auto wait_plane = [&](int j) -> bool {
+        const uint32_t mb = s4_u32(&mbar[j % US4]);
+        const uint32_t par = (uint32_t)((j / US4) & 1);
+        for (long long it = 0; it < S4T_SPIN; ++it)
+            if (s4_try_wait(mb, par)) return true;
+        return false;
+    };
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int y = y0 + ty, x4 = (x0 >> 2) + tx;
+    const bool yok = y < g.Ny;
+    const long long row4 = (long long)(g.Nx >> 2) * g.Ny;
+    const int cc = (ty + 1) * T4W + 4 + 4 * tx;          // this thread's first float in a p or D box
+    const int gc4 = ty * T4X + 4 * tx;                   // ... in a diagonal box
+    float acc[ZL];
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) acc[i] = 0.f;
+    bool ok = true;
+    // planes z0 - 1 and z0 before the first step; every thread leaves with
+    // the same verdict (the steps below hold barriers)
+    for (; waited < 2 && waited < nplanes; ++waited)
+        if (!wait_plane(waited)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) ok = false;
+    for (int z = z0; z < z1 && ok; ++z) {
+        const int jz = z - z0 + 1;                      // ring index of plane z
+        if (!wait_plane(jz + 1)) { ok = false; s_ok = 0; }
+        waited = jz + 2;
+        __syncthreads();
+        if (!s_ok) { ok = false; break; }
+        if (yok) {
+            const char *sm_m = sm + ((jz - 1) % US4) * SB, *sm_c = sm + (jz % US4) * SB,
+                       *sm_p = sm + ((jz + 1) % US4) * SB;
+            const float *Dc_ = (const float *)(sm_c + ZL * PB);
+            const float4 Dc = *(const float4 *)(Dc_ + cc);
+            const float Dl = Dc_[cc - 1], Dr = Dc_[cc + 4];
+            const float4 Dym = *(const float4 *)(Dc_ + cc - T4W), Dyp = *(const float4 *)(Dc_ + cc + T4W);
+            const float4 Dzm = *(const float4 *)((const float *)(sm_m + ZL * PB) + cc);
+            const float4 Dzp = *(const float4 *)((const float *)(sm_p + ZL * PB) + cc);
+            const float wl = 0.5f * (Dc.x + Dl), wr = 0.5f * (Dc.w + Dr);
+            const float w01 = 0.5f * (Dc.x + Dc.y), w12 = 0.5f * (Dc.y + Dc.z), w23 = 0.5f * (Dc.z + Dc.w);
+            auto fw = [&](const float4 Dn) {
+                return make_float4(0.5f * (Dc.x + Dn.x), 0.5f * (Dc.y + Dn.y), 0.5f * (Dc.z + Dn.z),
+                                   0.5f * (Dc.w + Dn.w));
+            };
+            const float4 wym = fw(Dym), wyp = fw(Dyp), wzm = fw(Dzm), wzp = fw(Dzp);
+            const long long v = (long long)z * row4 + (long long)y * (g.Nx >> 2) + x4;
+#pragma unroll
+            for (int i = 0; i < ZL; ++i) {
+                if (!on[i]) continue;
+                const float *P = (const float *)(sm_c + i * PB);
+                const float4 xc = *(const float4 *)(P + cc);
+                const float xlv = P[cc - 1], xrv = P[cc + 4];
+                const float4 xym = *(const float4 *)(P + cc - T4W), xyp = *(const float4 *)(P + cc + T4W);
+                const float4 xzm = *(const float4 *)((const float *)(sm_m + i * PB) + cc);
+                const float4 xzp = *(const float4 *)((const float *)(sm_p + i * PB) + cc);
+                const float4 dg = *(const float4 *)((const float *)(sm_c + (ZL + 1) * PB + i * GB) + gc4);
+                float4 o;
+                o.x = dg.x * xc.x - (wl * xlv + w01 * xc.y) - (wym.x * xym.x + wyp.x * xyp.x) - (wzm.x * xzm.x + wzp.x * xzp.x);
+                o.y = dg.y * xc.y - (w01 * xc.x + w12 * xc.z) - (wym.y * xym.y + wyp.y * xyp.y) - (wzm.y * xzm.y + wzp.y * xzp.y);
+                o.z = dg.z * xc.z - (w12 * xc.y + w23 * xc.w) - (wym.z * xym.z + wyp.z * xyp.z) - (wzm.z * xzm.z + wzp.z * xzp.z);
+                o.w = dg.w * xc.w - (w23 * xc.z + wr * xrv) - (wym.w * xym.w + wyp.w * xyp.w) - (wzm.w * xzm.w + wzp.w * xzp.w);
+                ((float4 *)dst[c[i]])[v] = o;
+                acc[i] += dot4(xc, o);
+            }
+        }
+        __syncthreads();                                 // plane z - 1's stage is free
+        if (threadIdx.x == 0 && jz - 1 + US4 < nplanes) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(jz - 1 + US4);
+        }
+        if (jz - 1 + US4 < nplanes) issued = jz + US4;
+    }
+    // no copy may land in the CTA's shared memory after it exits: wait for
+    // every issued plane not yet waited for (the normal path has none left)
+    for (int j = waited; j < issued; ++j) wait_plane(j);
+    if (!ok && threadIdx.x == 0) atomicExch(&g_s4t_err, RCG_ERR_TIMEOUT);
+    __shared__ double red[NT / 32][ZL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) {
+        double sacc = (double)acc[i];
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o2);
+        if (lane == 0) red[warp][i] = sacc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ZL; ++i)
+        if (threadIdx.x == i && on[i] && ok) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += red[w][i];
+            atomicAdd(dots + c[i], t);
+        }
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link
+// against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// A float32 tensor map of rank r (dims[0] fastest, strides in bytes of
+// dims 1..r-1) with the given box; zero fill outside.
+void make_map(CUtensorMap *m, const float *base, int r, const cuuint64_t *dims, const cuuint64_t *strides,
+              const cuuint32_t *box) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) throw Error{RCG_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult rc = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)r, (void *)base, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) throw Error{RCG_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)rc) + ")"};
+}
+
+bool s4t_supported(const Grid &g) {
+    return cg4_supported(g) && g.Ny > 1 && g.Nx % T4X == 0 && g.Nx <= 4096 && g.n < (1LL << 31);
+}
+
+bool s4t_usable(const Grid &g, const LaneList &ll) {
+    return s4t_supported(g) && ll.pbase && ll.gbase && ll.pcols > 0 && ll.gslots > 0 && ((uintptr_t)ll.pbase & 15) == 0 &&
+           ((uintptr_t)ll.gbase & 15) == 0 && ll.pld % 4 == 0 && g.ld % 4 == 0;
+}
+
+template <int ZL, int TY>
+void launch_s4t(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, float *const *q,
+                const LaneList &ll, const int *active, double *dots, unsigned long long *prof) {
+    if (!s4t_usable(g, ll)) throw Error{RCG_ERR_INVALID, "k_stencil4t: lane layout unknown"};
+    CUtensorMap tp, td, tg;
+    const cuuint64_t sx = (cuuint64_t)g.Nx * 4, sxy = sx * (cuuint64_t)g.Ny, sxyz = sxy * (cuuint64_t)g.Nz;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz, (cuuint64_t)ll.pcols};
+        const cuuint64_t strides[3] = {sx, sxy, (cuuint64_t)ll.pld * 4};
+        const cuuint32_t box[4] = {T4W, TY + 2, 1, 1};
+        make_map(&tp, ll.pbase, 4, dims, strides, box);
+    }
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz};
+        const cuuint64_t strides[2] = {sx, sxy};
+        const cuuint32_t box[3] = {T4W, TY + 2, 1};
+        make_map(&td, D, 3, dims, strides, box);
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz, (cuuint64_t)ll.gslots};
+        const cuuint64_t strides[3] = {sx, sxy, (cuuint64_t)g.ld * 4};
+        const cuuint32_t box[4] = {T4X, TY, 1, 1};
+        make_map(&tg, ll.gbase, 4, dims, strides, box);
+    }
+    (void)sxyz;
+    const size_t smem = s4t_smem<ZL, TY>();
+    static int occ[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !occ[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_stencil4t<ZL, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int o = 0;
+        RCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_stencil4t<ZL, TY>, 16 * TY, smem));
+        if (dev >= 0 && dev < 64) occ[dev] = std::max(o, 1);
+    }
+    const int o = (dev >= 0 && dev < 64) ? occ[dev] : 1;
+    const long long T = (long long)(g.Nx / T4X) * ((g.Ny + TY - 1) / TY), G = (ll.na + ZL - 1) / ZL;
+    const long long resident = (long long)o * device_sms(dev);
+    long long nzc = (4 * resident + T * G - 1) / (T * G);
+    nzc = std::max<long long>(1, std::min<long long>(nzc, std::max(1, g.Nz / 8)));
+    const int zc = (int)((g.Nz + nzc - 1) / nzc);
+    nzc = (g.Nz + zc - 1) / zc;
+    if (G > 65535) throw Error{RCG_ERR_INVALID, "k_stencil4t: grid extent"};
+    k_stencil4t<ZL, TY><<<dim3((unsigned)(T * nzc), (unsigned)G), 16 * TY, smem, st>>>(
+        tp, td, tg, g, ll.gbase, diag, q, ll.alist, ll.na, active, dots, prof, zc);
+}
+
+
+
 // Stencil variants: 0 the row kernel k_stencil4 (any Nx % 4 == 0), 1 the
 // plane-ring kernel k_stencil4z (3D, 256 % (Nx / 4) == 0), 2 + the
 // z-marching kernel k_stencil4r<TX, ZL> for TX in {4, 8, 16, 32} (TX | Nx/4),
@@ -1486,18 +1789,22 @@ void launch_s4z(cudaStream_t st, const Grid &g, const float *D, const float *con
 // short of DRAM bandwidth there but of memory-level parallelism.)
 constexpr int S4_TXS[4] = {4, 8, 16, 32};
 constexpr int S4_ZLS[3] = {1, 2, 4};
-constexpr int S4_NVAR = 2 + 12 + 2;
+constexpr int S4_NVAR = 2 + 12 + 2 + 3;   // + the TMA plane-ring kernel k_stencil4t <2,16>, <2,8>, <4,8>
 static_assert(S4_NVAR == RCG_STENCIL_VARIANTS, "variant count");
 
 bool s4_variant_ok(const Grid &g, int v) {
     if (v == 0) return cg4_supported(g);
     if (v == 1) return stencil4z_supported(g);
+    if (v >= 16 && v < S4_NVAR) return s4t_supported(g);
     if (v < 2 || v >= S4_NVAR) return false;
     const int tx = v >= 14 ? (v == 15 ? 8 : 16) : S4_TXS[(v - 2) / 3];
     return cg4_supported(g) && g.Ny > 1 && (g.Nx / 4) % tx == 0 && g.n < (1LL << 31);
 }
 
 std::string s4_variant_name(int v) {
+    if (v == 16) return "k_stencil4t<2,16> (TMA plane ring)";
+    if (v == 17) return "k_stencil4t<2,8> (TMA plane ring)";
+    if (v == 18) return "k_stencil4t<4,8> (TMA plane ring)";
     if (v == 0) return "k_stencil4 (rows)";
     if (v == 1) return "k_stencil4z (plane ring)";
     if (v >= 14) return std::string(v == 15 ? "k_stencil4r<8,2>" : "k_stencil4r<16,2>") + ", 3 CTAs per SM";
@@ -1521,6 +1828,9 @@ void s4_launch(int v, cudaStream_t st, const Grid &g, const float *D, const floa
 #undef RCG_S4R
         case 14: launch_s4r<16, 2, 3>(st, g, D, diag, p, q, ll, active, dots, prof); break;
         case 15: launch_s4r<8, 2, 3>(st, g, D, diag, p, q, ll, active, dots, prof); break;
+        case 16: launch_s4t<2, 16>(st, g, D, diag, q, ll, active, dots, prof); break;
+        case 17: launch_s4t<2, 8>(st, g, D, diag, q, ll, active, dots, prof); break;
+        case 18: launch_s4t<4, 8>(st, g, D, diag, q, ll, active, dots, prof); break;
         default: throw Error{RCG_ERR_INVALID, "unknown stencil variant"};
     }
     count_launch();
@@ -1568,7 +1878,7 @@ int s4_tuned(cudaStream_t st, const Grid &g, const float *D, const float *const 
                       ", lanes <= " + std::to_string(1 << key.cls) + ":";
     try {
         for (int v = 0; v < S4_NVAR; ++v) {
-            if (!s4_variant_ok(g, v)) continue;
+            if (!s4_variant_ok(g, v) || (v >= 16 && !s4t_usable(g, ll))) continue;
             s4_launch(v, st, g, D, diag, p, q, ll, active, scr, nullptr);
             RCG_CUDA_TRY(cudaEventRecord(e0, st));
             for (int rep = 0; rep < 3; ++rep) s4_launch(v, st, g, D, diag, p, q, ll, active, scr, nullptr);
@@ -1598,6 +1908,15 @@ int s4_tuned(cudaStream_t st, const Grid &g, const float *D, const float *const 
 
 }  // namespace
 
+int stencil_take_error(cudaStream_t st) {
+    int h = 0, z = 0;
+    RCG_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_s4t_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    RCG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) RCG_CUDA_TRY(cudaMemcpyToSymbolAsync(g_s4t_err, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    if (h) RCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return h;
+}
+
 std::string stencil_tuning_report() {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     std::string s;
@@ -1619,8 +1938,11 @@ int stencil_variant_ok(const Grid &g, int v) { return s4_variant_ok(g, v) ? 1 : 
 // choice), p^T q added into dots[c] (device, ncols doubles): a parity and
 // timing entry for the kernels of the inner iteration.
 void stencil4_apply(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
-                    float *const *q, int ncols, const int *lanes, const int *active, double *dots, int v) {
+                    float *const *q, int ncols, const int *lanes, const int *active, double *dots, int v,
+                    const float *pbase, long long pld, const float *gbase, int gslots) {
     LaneList ll{lanes, ncols, nullptr, nullptr, nullptr, 0};
+    ll.pbase = pbase; ll.pld = pld; ll.pcols = ncols; ll.gbase = gbase; ll.gslots = gslots;
+    if (v >= 16 && !s4t_usable(g, ll)) throw Error{RCG_ERR_INVALID, "the TMA stencil needs the columns' layout"};
     if (ncols <= 0) return;
     if (v < 0) v = s4_tuned(st, g, D, diag, p, q, ll, active, ncols);
     if (!s4_variant_ok(g, v)) throw Error{RCG_ERR_INVALID, "stencil variant does not support this grid"};

@@ -196,6 +196,14 @@ struct LaneList {
     int na;
     const int *tile_lane, *tile_si, *tile_cnt;
     int ntiles;
+    // the lanes' p columns as one array (lane l at pbase + l pld, pcols
+    // columns) and the sample diagonals (slot s at gbase + s Grid::ld,
+    // gslots slots): the TMA stencil's tensor maps; null: not known
+    const float *pbase = nullptr;
+    long long pld = 0;
+    int pcols = 0;
+    const float *gbase = nullptr;
+    int gslots = 0;
 };
 
 // ------------------------------------------------------------ learned augmentation (cnn.cu)
@@ -462,7 +470,10 @@ void lane_zero(cudaStream_t st, LaneState ls, const int *mask);
 // variant v (-1: the autotuned choice; see cg4.cu), p^T q added into
 // dots[lanes[c]]; `active[lanes[c]]` != 0 for the columns to apply.
 void stencil4_apply(cudaStream_t st, const Grid &g, const float *D, const float *const *diag, const float *const *p,
-                    float *const *q, int ncols, const int *lanes, const int *active, double *dots, int v);
+                    float *const *q, int ncols, const int *lanes, const int *active, double *dots, int v,
+                    const float *pbase = nullptr, long long pld = 0, const float *gbase = nullptr, int gslots = 0);
+// RCG_ERR_TIMEOUT if a TMA stencil's wait ran out since the last call (synchronises the stream), else 0
+int stencil_take_error(cudaStream_t st);
 std::string stencil_tuning_report();
 const char *stencil_variant_name(int v);
 int stencil_variant_ok(const Grid &g, int v);

@@ -47,7 +47,7 @@ EXPORTED = [
 ]
 RCG_NOALLOC_MAX_COLS = 1024
 RCG_MAX_PRIVATE = 8
-RCG_STENCIL_VARIANTS = 16
+RCG_STENCIL_VARIANTS = 19
 RCG_COMPRESS_MAX_COLS = 4096
 
 

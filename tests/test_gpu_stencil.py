@@ -1,7 +1,8 @@
 """Every float32 stencil kernel of the inner CG iteration (rcg_apply_f32,
 variants 0..RCG_STENCIL_VARIANTS-1: the row kernel, the plane ring and the
 z-marching tiles with 1, 2 or 4 lanes per CTA, in both grid orders, and two
-with registers for three CTAs per SM) against the oracle's operator
+with registers for three CTAs per SM, and the TMA plane-ring kernels on the
+grids whose Nx is a multiple of 64) against the oracle's operator
 A~_s (the numerically formed Schur complement of the full finite-difference
 system, Sec. 3) on grids with one and several x-tiles, a ragged y-tile
 (80 rows in tiles of 64) and a z-chunk boundary, plus the fused p^T q.
@@ -30,7 +31,7 @@ def rcg():
     return r
 
 
-@pytest.mark.parametrize("N", [16, 32, 48, 64, 80])
+@pytest.mark.parametrize("N", [16, 32, 48, 64, 80, 128])
 def test_every_stencil_variant_matches_the_oracle_operator(rcg, N):
     import torch
     wl = replace(WORKLOADS["t3d_16"], name=f"t3d_{N}", N=N)
@@ -61,9 +62,11 @@ def test_every_stencil_variant_matches_the_oracle_operator(rcg, N):
             dd = dots.cpu().numpy()
             assert np.allclose(dd, d_ref, rtol=1e-5, atol=0), (v, dd, d_ref)
             ran.append(v)
-    # the z-marching tiles run wherever Nx / 4 is a multiple of 4
+    # the z-marching tiles run wherever Nx / 4 is a multiple of 4, the TMA tiles where Nx % 64 == 0
     if (N // 4) % 4 == 0:
         assert any(v >= 2 for v in ran)
+    if N % 64 == 0:
+        assert {16, 17, 18} <= set(ran)
     assert "stencil" in rcg.tuning_report()
 
 
