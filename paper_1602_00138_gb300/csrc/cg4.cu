@@ -732,6 +732,7 @@ k_u0dots(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_la
 // with blockIdx.x == 0 records each lane's step (xa, xt) and clears the next
 // p^T q slot, as the owner CTA of k_update4 does.
 constexpr int kUU = 512;                // threads of k_update_u0
+int device_sms(int dev);                 // SMs of a device (cached)
 template <int KUT, int KPM>
 __global__ void __launch_bounds__(kUU, 1)
 k_update_u0(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane, const int *__restrict__ tile_si,
@@ -1217,6 +1218,179 @@ k_direction4(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// k_direction4s: k_direction4 with every stream staged through shared
+// memory, as k_update_u0s does for the update: 512 threads, each thread
+// serves two lanes of the tile (lanes w and w + 16 of warp w) and copies its
+// own float4 of p, x (lanes that take the step), r and the private W
+// columns of both lanes by cp.async into a ring of NST stages, NST - 1
+// stages ahead of their use, next to the tile's U_0 rows.  The register
+// version keeps one batch of loads per warp in flight and drains it at
+// every stage barrier (16 warps per SM at 128 registers: ~73% of the DRAM
+// bandwidth on the 64^3 bench step).  Same arithmetic.
+template <int KPM>
+__host__ __device__ constexpr int dirs_nst() { return KPM <= 1 ? 3 : 2; }
+template <int KUT, int KPM>
+constexpr size_t dirs_smem() {
+    return sizeof(float4) * (size_t)dirs_nst<KPM>() * (KUT * SN4 + 2 * (3 + KPM) * kUU);
+}
+
+template <int KUT, int KPM>
+__global__ void __launch_bounds__(kUU, 1)
+k_direction4s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ tile_lane,
+              const int *__restrict__ tile_cnt, const float *__restrict__ mu, const float *__restrict__ beta,
+              long long chunk, int it) {
+    constexpr int NST = dirs_nst<KPM>();
+    constexpr int NW = kUU / 32;              // warps
+    constexpr int NL = TILE / NW;             // lanes per thread (2)
+    constexpr int NB = 3 + KPM;               // p, x, r, private columns
+    extern __shared__ float4 dsm[];
+    float4 *Us = dsm;                         // [NST][KUT][SN4]
+    float4 *Ls = dsm + NST * KUT * SN4;       // [NST][NL][NB][kUU]
+    __shared__ float smu[TILE][KU_MAX + KP_MAX];
+    __shared__ float sbeta[TILE], salpha[TILE];
+    __shared__ int slane[TILE], skp[TILE], sdir[TILE];
+    __shared__ const float *spw[TILE][KPM];
+    const int t = blockIdx.y, cnt = tile_cnt[t], ku = gm.k_u;
+    if (threadIdx.x < TILE) {
+        int l = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
+        const bool step = l >= 0 && ls.xt[l] == it;
+        const bool dir = l >= 0 && ls.active[l] != 0;
+        if (!step && !dir) l = -1;
+        slane[threadIdx.x] = l;
+        sdir[threadIdx.x] = dir ? 1 : 0;
+        salpha[threadIdx.x] = step ? ls.xa[l] : 0.f;
+        skp[threadIdx.x] = dir ? gm.kp[l] : 0;
+        sbeta[threadIdx.x] = dir ? beta[l] : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TILE * (KU_MAX + KP_MAX); e += blockDim.x) {
+        const int jj = e / (KU_MAX + KP_MAX), c = e % (KU_MAX + KP_MAX);
+        const int l = slane[jj];
+        smu[jj][c] = (l >= 0 && sdir[jj] && c < ku + skp[jj]) ? mu[(long long)l * KMAX + c] : 0.f;
+    }
+    for (int e = threadIdx.x; e < TILE * KPM; e += blockDim.x) {
+        const int jj = e / KPM, c = e % KPM;
+        const int l = slane[jj];
+        spw[jj][c] = (l >= 0 && sdir[jj] && c < skp[jj]) ? (const float *)gm.wpp[(long long)l * KPT + c] : nullptr;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, tl = threadIdx.x & 31;
+    int myl[NL], myj[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        myj[q] = warp + NW * q;
+        myl[q] = slane[myj[q]];
+    }
+    const float *__restrict__ WU = (const float *)gm.wu;
+    const float *Pb = (const float *)gm.p, *Xb = (const float *)gm.x, *Rb = (const float *)gm.r;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
+    auto cp16 = [](float4 *dst, const float *src, bool ok) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(src), "r"(ok ? 16 : 0)
+                     : "memory");
+    };
+    auto issue = [&](int st) {
+        if (st < nst) {
+            const long long base = r0 + (long long)st * SN;
+            const int slot = st % NST;
+            for (int e = threadIdx.x; e < KUT * SN4; e += kUU) {
+                const int c = e / SN4, v4 = e % SN4;
+                const long long p = base + 4 * v4;
+                const bool ok = c < ku && p < r1;
+                cp16(&Us[(slot * KUT + c) * SN4 + v4], ok ? WU + (long long)c * gm.ld + p : WU, ok);
+            }
+            const long long p = base + 4 * tl;
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int l = myl[q], jj = myj[q];
+                const bool okp = l >= 0 && p < r1;
+                const bool dir = okp && sdir[jj] != 0;
+                const long long o = (long long)(l < 0 ? 0 : l) * gm.ld + p;
+                float4 *dst = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
+                cp16(dst, okp ? Pb + o : Pb, okp);
+                cp16(dst + kUU, (okp && salpha[jj] != 0.f) ? Xb + o : Xb, okp && salpha[jj] != 0.f);
+                cp16(dst + 2 * kUU, dir ? Rb + o : Rb, dir);
+#pragma unroll
+                for (int c = 0; c < KPM; ++c) {
+                    const bool ok = dir && c < skp[jj];
+                    cp16(dst + (3 + c) * kUU, ok ? spw[jj][c] + p : Rb, ok);
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int st = 0; st < NST - 1; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + NST - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(NST - 1) : "memory");   // stage st: this thread's copies
+        __syncthreads();                                                   // ... and the U_0 rows of all threads
+        const int slot = st % NST;
+        const long long p = r0 + (long long)st * SN + 4 * tl;
+        if (p < r1) {
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int l = myl[q], jj = myj[q];
+                if (l < 0) continue;
+                const float4 *src = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
+                const float4 pv = src[0];
+                const long long o = (long long)l * gm.ld + p;
+                const float a = salpha[jj];
+                if (a != 0.f) {
+                    const float4 xv = src[kUU];
+                    *(float4 *)((float *)gm.x + o) =
+                        make_float4(xv.x + a * pv.x, xv.y + a * pv.y, xv.z + a * pv.z, xv.w + a * pv.w);
+                }
+                if (!sdir[jj]) continue;
+                const float4 rv = src[2 * kUU];
+                const float b = sbeta[jj];
+                float4 sres = make_float4(rv.x + b * pv.x, rv.y + b * pv.y, rv.z + b * pv.z, rv.w + b * pv.w);
+#pragma unroll
+                for (int c = 0; c < KUT; ++c) {
+                    const float m = c < ku ? smu[jj][c] : 0.f;
+                    const float4 u = Us[(slot * KUT + c) * SN4 + tl];
+                    sres.x -= m * u.x; sres.y -= m * u.y; sres.z -= m * u.z; sres.w -= m * u.w;
+                }
+                const int kp = skp[jj];
+#pragma unroll
+                for (int c = 0; c < KPM; ++c) {
+                    if (c >= kp) break;
+                    const float m = smu[jj][ku + c];
+                    const float4 w = src[(3 + c) * kUU];
+                    sres.x -= m * w.x; sres.y -= m * w.y; sres.z -= m * w.z; sres.w -= m * w.w;
+                }
+                *(float4 *)((float *)gm.p + o) = sres;
+            }
+        }
+        __syncthreads();                                          // stage st's slot is refilled next
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int KUT, int KPM>
+void dir_launch_s(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const LaneList &ll,
+                  const float *mu, const float *beta, int it) {
+    static bool attr[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        RCG_CUDA_TRY(cudaFuncSetAttribute(k_direction4s<KUT, KPM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)dirs_smem<KUT, KPM>()));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    // node ranges (multiples of SN) for ~4 waves of one CTA per SM over the tiles
+    long long z = std::max<long long>(1, 4LL * device_sms(dev) / std::max(ll.ntiles, 1));
+    const long long maxz = (n + 4 * SN - 1) / (4 * SN);
+    if (z > maxz) z = maxz;
+    long long chunk = (n + z - 1) / z;
+    chunk = (chunk + SN - 1) / SN * SN;
+    z = (n + chunk - 1) / chunk;
+    k_direction4s<KUT, KPM><<<dim3((unsigned)z, ll.ntiles), kUU, dirs_smem<KUT, KPM>(), st>>>(
+        n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, it);
+}
+
 // k_direction4<KUT, KPM> over the tiles of ll in one wave of resident CTAs
 // (occupancy cached per device ordinal): a partial second wave would hold
 // the whole launch.  Node ranges are multiples of SN.
@@ -1249,8 +1423,9 @@ void dir_launch(cudaStream_t st, long long n, const LaneGeom &gm, const LaneStat
 template <int KUT>
 void dir_launch_kp(cudaStream_t st, long long n, const LaneGeom &gm, const LaneState &ls, const LaneList &ll,
                    const float *mu, const float *beta, int it) {
-    if (gm.kp_sel <= 1) dir_launch<KUT, 1>(st, n, gm, ls, ll, mu, beta, it);
-    else if (gm.kp_sel <= 2) dir_launch<KUT, 2>(st, n, gm, ls, ll, mu, beta, it);
+    // up to two private columns: the staged kernel; more: the register version
+    if (gm.kp_sel <= 1) dir_launch_s<KUT, 1>(st, n, gm, ls, ll, mu, beta, it);
+    else if (gm.kp_sel <= 2) dir_launch_s<KUT, 2>(st, n, gm, ls, ll, mu, beta, it);
     else if (gm.kp_sel <= 4) dir_launch<KUT, 4>(st, n, gm, ls, ll, mu, beta, it);
     else dir_launch<KUT, KP_MAX>(st, n, gm, ls, ll, mu, beta, it);
 }
