@@ -896,18 +896,18 @@ k_update_u0s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
     float4 *Ls = usm + NST * KUT * SN4;       // [NST][NL][NB][kUU]
     __shared__ int slane[TILE], skp[TILE];
     __shared__ float salpha[TILE];
-    const int tt = blockIdx.y, cnt = tile_cnt[tt], ku = gm.k_u;
+    const int tt = blockIdx.x, cnt = tile_cnt[tt], ku = gm.k_u;   // tiles fastest: resident CTAs share A~U_0 rows in L2
     if (threadIdx.x < TILE) {
         int l = threadIdx.x < cnt ? tile_lane[tt * TILE + threadIdx.x] : -1;
         float a = 0.f;
         if (l >= 0 && ls.active[l] != 0) {
             const double pq = ls.pq[spq * ls.m + l], rrp = ls.rr[sprev * ls.m + l];
             if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rrp)) {
-                if (blockIdx.x == 0) ls.flag[l] = 2;          // breakdown: every CTA skips the lane
+                if (blockIdx.y == 0) ls.flag[l] = 2;          // breakdown: every CTA skips the lane
                 l = -1;
             } else {
                 a = (float)(rrp / pq);
-                if (blockIdx.x == 0) {
+                if (blockIdx.y == 0) {
                     ls.xa[l] = a;
                     ls.xt[l] = t;
                     ls.pq[(1 - spq) * ls.m + l] = 0.0;
@@ -925,7 +925,7 @@ k_update_u0s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
         skp[threadIdx.x] = l >= 0 ? gm.kp[l] : 0;
     }
     const float *__restrict__ AU = (const float *)gm.awu + (long long)tile_si[tt] * ku * gm.ld;
-    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r0 = (long long)blockIdx.y * chunk;
     const long long r1 = r0 + chunk < n ? r0 + chunk : n;
     const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
     __syncthreads();
@@ -985,21 +985,28 @@ k_update_u0s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ til
         const int slot = st % NST;
         const long long p = r0 + (long long)st * SN + 4 * tl;
         if (p < r1) {
+            float4 rn[NL];
 #pragma unroll
             for (int q = 0; q < NL; ++q) {
                 const int l = myl[q];
+                rn[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (l < 0) continue;
                 const float4 *src = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
                 const float4 rv = src[0], qv = src[kUU];
                 const float a = salpha[warp + NW * q];
-                const float4 rn = make_float4(rv.x - a * qv.x, rv.y - a * qv.y, rv.z - a * qv.z, rv.w - a * qv.w);
-                *(float4 *)((float *)gm.r + (long long)l * gm.ld + p) = rn;
+                rn[q] = make_float4(rv.x - a * qv.x, rv.y - a * qv.y, rv.z - a * qv.z, rv.w - a * qv.w);
+                *(float4 *)((float *)gm.r + (long long)l * gm.ld + p) = rn[q];
                 float *ac = acc[q];
-                ac[0] += dot4(rn, rn);
+                ac[0] += dot4(rn[q], rn[q]);
 #pragma unroll
-                for (int c = 0; c < KUT; ++c) ac[1 + c] += dot4(Us[(slot * KUT + c) * SN4 + tl], rn);
+                for (int c = 0; c < KPM; ++c) ac[1 + KUT + c] += dot4(src[(2 + c) * kUU], rn[q]);
+            }
+            // each U_0 row once for both lanes (an absent lane's rn is zero)
 #pragma unroll
-                for (int c = 0; c < KPM; ++c) ac[1 + KUT + c] += dot4(src[(2 + c) * kUU], rn);
+            for (int c = 0; c < KUT; ++c) {
+                const float4 u = Us[(slot * KUT + c) * SN4 + tl];
+#pragma unroll
+                for (int q = 0; q < NL; ++q) acc[q][1 + c] += dot4(u, rn[q]);
             }
         }
         __syncthreads();                                          // the U_0 slot of stage st is refilled next
@@ -1038,8 +1045,8 @@ void launch_update_u0s(cudaStream_t st, dim3 grid, long long n, LaneGeom gm, Lan
                                           (int)uus_smem<KUT, KPM>()));
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
-    k_update_u0s<KUT, KPM><<<grid, kUU, uus_smem<KUT, KPM>(), st>>>(n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, t,
-                                                                    sprev, scur, spq, sw, chunk);
+    k_update_u0s<KUT, KPM><<<dim3(grid.y, grid.x), kUU, uus_smem<KUT, KPM>(), st>>>(
+        n, gm, ls, ll.tile_lane, ll.tile_si, ll.tile_cnt, t, sprev, scur, spq, sw, chunk);
 }
 
 template <int KUT>
@@ -1250,7 +1257,7 @@ k_direction4s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ ti
     __shared__ float sbeta[TILE], salpha[TILE];
     __shared__ int slane[TILE], skp[TILE], sdir[TILE];
     __shared__ const float *spw[TILE][KPM];
-    const int t = blockIdx.y, cnt = tile_cnt[t], ku = gm.k_u;
+    const int t = blockIdx.x, cnt = tile_cnt[t], ku = gm.k_u;     // tiles fastest: resident CTAs share U_0 rows in L2
     if (threadIdx.x < TILE) {
         int l = threadIdx.x < cnt ? tile_lane[t * TILE + threadIdx.x] : -1;
         const bool step = l >= 0 && ls.xt[l] == it;
@@ -1283,7 +1290,7 @@ k_direction4s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ ti
     }
     const float *__restrict__ WU = (const float *)gm.wu;
     const float *Pb = (const float *)gm.p, *Xb = (const float *)gm.x, *Rb = (const float *)gm.r;
-    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r0 = (long long)blockIdx.y * chunk;
     const long long r1 = r0 + chunk < n ? r0 + chunk : n;
     const int nst = r1 > r0 ? (int)((r1 - r0 + SN - 1) / SN) : 0;
     auto cp16 = [](float4 *dst, const float *src, bool ok) {
@@ -1330,38 +1337,50 @@ k_direction4s(long long n, LaneGeom gm, LaneState ls, const int *__restrict__ ti
         const int slot = st % NST;
         const long long p = r0 + (long long)st * SN + 4 * tl;
         if (p < r1) {
+            float4 sres[NL];
+            bool dq[NL];
 #pragma unroll
             for (int q = 0; q < NL; ++q) {
                 const int l = myl[q], jj = myj[q];
+                sres[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                dq[q] = l >= 0 && sdir[jj] != 0;
                 if (l < 0) continue;
                 const float4 *src = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
                 const float4 pv = src[0];
-                const long long o = (long long)l * gm.ld + p;
                 const float a = salpha[jj];
                 if (a != 0.f) {
                     const float4 xv = src[kUU];
-                    *(float4 *)((float *)gm.x + o) =
+                    *(float4 *)((float *)gm.x + (long long)l * gm.ld + p) =
                         make_float4(xv.x + a * pv.x, xv.y + a * pv.y, xv.z + a * pv.z, xv.w + a * pv.w);
                 }
-                if (!sdir[jj]) continue;
+                if (!dq[q]) continue;
                 const float4 rv = src[2 * kUU];
                 const float b = sbeta[jj];
-                float4 sres = make_float4(rv.x + b * pv.x, rv.y + b * pv.y, rv.z + b * pv.z, rv.w + b * pv.w);
+                sres[q] = make_float4(rv.x + b * pv.x, rv.y + b * pv.y, rv.z + b * pv.z, rv.w + b * pv.w);
+            }
+            // each U_0 row once for both lanes
 #pragma unroll
-                for (int c = 0; c < KUT; ++c) {
-                    const float m = c < ku ? smu[jj][c] : 0.f;
-                    const float4 u = Us[(slot * KUT + c) * SN4 + tl];
-                    sres.x -= m * u.x; sres.y -= m * u.y; sres.z -= m * u.z; sres.w -= m * u.w;
+            for (int c = 0; c < KUT; ++c) {
+                const float4 u = Us[(slot * KUT + c) * SN4 + tl];
+#pragma unroll
+                for (int q = 0; q < NL; ++q) {
+                    const float m = (c < ku && dq[q]) ? smu[myj[q]][c] : 0.f;
+                    sres[q].x -= m * u.x; sres[q].y -= m * u.y; sres[q].z -= m * u.z; sres[q].w -= m * u.w;
                 }
-                const int kp = skp[jj];
+            }
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                if (!dq[q]) continue;
+                const int jj = myj[q], kp = skp[jj];
+                const float4 *src = Ls + ((slot * NL + q) * NB) * kUU + threadIdx.x;
 #pragma unroll
                 for (int c = 0; c < KPM; ++c) {
                     if (c >= kp) break;
                     const float m = smu[jj][ku + c];
                     const float4 w = src[(3 + c) * kUU];
-                    sres.x -= m * w.x; sres.y -= m * w.y; sres.z -= m * w.z; sres.w -= m * w.w;
+                    sres[q].x -= m * w.x; sres[q].y -= m * w.y; sres[q].z -= m * w.z; sres[q].w -= m * w.w;
                 }
-                *(float4 *)((float *)gm.p + o) = sres;
+                *(float4 *)((float *)gm.p + (long long)myl[q] * gm.ld + p) = sres[q];
             }
         }
         __syncthreads();                                          // stage st's slot is refilled next
@@ -1387,7 +1406,7 @@ void dir_launch_s(cudaStream_t st, long long n, const LaneGeom &gm, const LaneSt
     long long chunk = (n + z - 1) / z;
     chunk = (chunk + SN - 1) / SN * SN;
     z = (n + chunk - 1) / chunk;
-    k_direction4s<KUT, KPM><<<dim3((unsigned)z, ll.ntiles), kUU, dirs_smem<KUT, KPM>(), st>>>(
+    k_direction4s<KUT, KPM><<<dim3(ll.ntiles, (unsigned)z), kUU, dirs_smem<KUT, KPM>(), st>>>(
         n, gm, ls, ll.tile_lane, ll.tile_cnt, mu, beta, chunk, it);
 }
 
