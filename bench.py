@@ -382,7 +382,8 @@ def roofline(W, prof, peak, peak_source):
     wl, n, s_bytes = W.wl, W.wl.n, 4
     lanes_per_rhs = wl.K if W.st["wave"] <= 0 else min(W.st["wave"], wl.K)
     names = ["stencil (q = A p)", "update (r, with the shared deflation dots when k_u > 0)",
-             "k_u0dots (shared deflation dots, restarts only)", "k_mu (lane scalars)", "k_direction4 (x, p)"]
+             "k_u0dots (shared deflation dots, restarts only)", "k_mu (lane scalars)",
+             "direction (x, p): k_direction4s, or k_direction4 beyond two private columns"]
 
     def alg_bytes(k):
         P = prof[k]
