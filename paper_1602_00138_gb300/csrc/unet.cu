@@ -733,12 +733,14 @@ void UNet::conv(cudaStream_t st, int l, const bf16 *s0, const bf16 *s1, const fl
     a.mask = mask;
     a.err = d_err;
     const int smem = USTAGE * (UA_BYTES + a.NP * 128) + 1024;
-    static int attr_done = 0;
-    if (!attr_done) {
+    static bool attr_done[64] = {};
+    int dev = 0;
+    RCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {   // function attributes hold per device
         RCG_CUDA_TRY(cudaFuncSetAttribute(k_unet_conv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           USTAGE * (UA_BYTES + 128 * 128) + 1024));
         RCG_CUDA_TRY(cudaFuncSetAttribute(k_unet_conv, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        attr_done = 1;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
     // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per
     // CTA) and tensor memory (512 columns per SM)
@@ -809,10 +811,12 @@ void UNet::backward(cudaStream_t st, const float *dout, int B, float *grad) {
         // node chunks of at least 16 blocks: ~5-8 CTAs per SM over the 27 taps
         const long long per = std::max<long long>(DW_NODES * 16, (tot + 47) / 48 / DW_NODES * DW_NODES);
         dim3 gr((unsigned)((tot + per - 1) / per), 27);
-        static int attr = 0;
-        if (!attr) {
+        static bool attr[64] = {};
+        int dev = 0;
+        RCG_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64 || !attr[dev]) {
             RCG_CUDA_TRY(cudaFuncSetAttribute(k_unet_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM));
-            attr = 1;
+            if (dev >= 0 && dev < 64) attr[dev] = true;
         }
         k_unet_dw<<<gr, 256, DW_SMEM, st>>>(g, L.Cg, L.Cout, x, L.sC[i], L.sreal[i], L.sci0[i], L.Cin, G[li][0],
                                              G[li][1], G[li][2], L.sup[i], G[lo][0], G[lo][1], G[lo][2], B, per,
