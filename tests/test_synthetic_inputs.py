@@ -55,3 +55,30 @@ def test_grid_support_route_gives_the_same_fields():
         p = p.ravel()
         assert np.array_equal(pals_mu(p, X, 0.01), pals_mu(p, X, 0.01, node_grid(wl)))
         assert np.array_equal(pals_dmu(p, X, 0.01), pals_dmu(p, X, 0.01, node_grid(wl)))
+
+
+def test_training_phantoms_draw_two_to_six_anomalies_from_the_seed_law():
+    """The learned network's training phantoms (C4: random 2-6-anomaly
+    phantoms): each vector holds n_a (d + 2) parameters with n_a in 2..6,
+    centres in [0.15, 0.85], widths in [0.05, 0.15], absorptions in
+    [0.02, 0.05]; seeded (the same call gives the same phantoms) and not
+    jitters of the workload's phantom."""
+    import numpy as np
+    from synthetic.phantom import WORKLOADS, training_params, seed_params
+    wl = WORKLOADS["c4_3d128"]
+    ps = training_params(wl, 40)
+    d = wl.dim
+    counts = set()
+    for p in ps:
+        q = np.asarray(p).reshape(-1, d + 2)
+        counts.add(q.shape[0])
+        assert 2 <= q.shape[0] <= 6
+        assert np.all((q[:, :d] >= 0.15) & (q[:, :d] <= 0.85))
+        assert np.all((q[:, d] >= 0.05) & (q[:, d] <= 0.15))
+        assert np.all((q[:, d + 1] >= 0.02) & (q[:, d + 1] <= 0.05))
+    assert counts == {2, 3, 4, 5, 6}
+    again = training_params(wl, 40)
+    assert all(np.array_equal(a, b) for a, b in zip(ps, again))
+    p0 = seed_params(wl, np.random.default_rng(wl.seed)).reshape(-1, d + 2)
+    assert not any(np.asarray(p).size == p0.size and np.allclose(np.asarray(p).reshape(-1, d + 2)[:, :d], p0[:, :d],
+                                                                 atol=0.1) for p in ps)
