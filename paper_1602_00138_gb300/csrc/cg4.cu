@@ -17,6 +17,12 @@
 //                p = r + beta p - U_0 mu_u - W_p mu_p for a tile of lanes;
 //                the U_0 rows of a stage arrive in a shared-memory ring by
 //                cp.async two stages ahead and serve all the tile's lanes
+//   k_update_u0s, k_direction4s  the update (with the shared deflation
+//                dots) and the direction with every stream staged through
+//                shared memory by cp.async (up to four / two private columns)
+//   k_stencil4r, k_stencil4t  z-marching stencil tiles: planes in registers
+//                with cp.async halos, or whole planes by TMA tensor copies
+//                into a shared-memory ring; the autotuner picks one
 //
 // Lanes are addressed through the active list `alist` (rebuilt by the host
 // at every synchronisation) so converged lanes cost no work; tiles group up

@@ -26,7 +26,9 @@
 // the tap's neighbour, zero-filled outside the grid) by cp.async straight
 // into the 128-byte-swizzled K-major layout, beside the chunk's packed
 // weights; one thread issues the four K = 16 MMAs and commits them to the
-// stage's mbarrier; four stages in flight.  The epilogue reads the
+// stage's mbarrier; a ring of four stages, the copies two chunks ahead of the
+// MMAs (so a stage is refilled two chunks after its MMAs were issued), three
+// CTAs per SM at 16 output channels.  The epilogue reads the
 // accumulator (tcgen05.ld), adds the bias, applies the ReLU or a ReLU mask
 // (the backward pass) and stores bfloat16 or float32 channels-last rows.
 //
