@@ -2155,7 +2155,6 @@ void cg_iteration4(cudaStream_t st, const Grid &g, const float *D, const float *
                    float *mu, float *beta, KTimer *kt) {
     if (ll.na <= 0) return;
     const int sprev = (t - 1) % 3, scur = t % 3, snext = (t + 1) % 3, spq = t % 2, sw = t % 2;
-    const long long nv = g.n >> 2;
     const bool tm = kt && kt->on;
     // the tuner's launches (first iteration of a grid and lane class only) run
     // before the timed launch

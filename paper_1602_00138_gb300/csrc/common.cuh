@@ -266,7 +266,6 @@ class UNet {
     long long V[3];
     Layer lay[UNET_LAYERS];
     long long aoff[A_N];
-    int cur_B = 0;
     void *wpf = nullptr, *wpb = nullptr, *abuf = nullptr, *gbuf = nullptr, *fbuf = nullptr;
     long long abuf_cap = 0, gbuf_cap = 0, fbuf_cap = 0;
     int *d_err = nullptr;

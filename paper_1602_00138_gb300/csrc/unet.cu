@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(UT, 1) k_unet_conv(UConv a) {
     char *smem = (char *)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
     const int stage_bytes = UA_BYTES + a.NP * 128;
     const uint32_t ncols = a.NP <= 32 ? 32u : a.NP <= 64 ? 64u : 128u;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
                      "r"(ncols));
@@ -696,7 +696,6 @@ void UNet::layout(int B) {
     put(A_A5, 0, 16);
     put(A_A6, 0, 16);
     grow(abuf, abuf_cap, o * (long long)sizeof(bf16));
-    cur_B = B;
 }
 
 void UNet::conv(cudaStream_t st, int l, const bf16 *s0, const bf16 *s1, const float *bias, bool relu, bf16 *y,
